@@ -1,0 +1,198 @@
+/*
+ * ftgemm.h -- C ABI of libftgemm: GEMM with online algorithm-based fault
+ * tolerance (ABFT) fused into the kernel, for NVIDIA GB300 (sm_103a).
+ *
+ * Method: Wu, Zhai et al., "Anatomy of High-Performance GEMM with Online Fault
+ * Tolerance on GPUs" (ICS'23).  A is encoded with column checksums e^T A
+ * (Eq. 1), B with row checksums B e (Eq. 2); their product carries the
+ * checksums of C (Eq. 3).  In the outer-product form (Eq. 4) the checksums
+ * are updated with every k-step, so each output tile can be verified during
+ * the K loop: a residual above the threshold flags a row and a column, whose
+ * crossing is the corrupted element, and the residual itself is the amount to
+ * subtract (Section 4.2.1).  One fault per verification unit and period is
+ * correctable (single-event upset, Section 4.1).
+ *
+ * Conventions used by every entry point
+ *   - All matrices are row-major.  A is M x K (leading dimension lda >= K),
+ *     B is K x N (ldb >= N), C is M x N (ldc >= N), in elements.
+ *   - Matrix pointers are DEVICE pointers owned by the caller.  Host pointers
+ *     (schedules, injection arrays, reports) are read or written during the
+ *     call only.
+ *   - Work is enqueued on the handle's stream.  Only calls that return a
+ *     report (or fetch one) synchronise that stream.
+ *   - Return value: FTGEMM_OK (0) or a negative FTGEMM_ERR_* code; the text of
+ *     the last error of the calling thread is given by ftgemm_last_error().
+ *   - The handle owns its device workspaces (checksum vectors, norms, split-K
+ *     partials, injection table, report ring); they grow on demand and are
+ *     released by ftgemm_destroy().
+ */
+#ifndef FTGEMM_H
+#define FTGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FTGEMM_OK 0
+#define FTGEMM_ERR_ARG (-1)         /* null pointer, bad size or leading dim */
+#define FTGEMM_ERR_UNSUPPORTED (-2) /* dtype / level / schedule combination  */
+#define FTGEMM_ERR_ALIGN (-3)       /* pointer or stride alignment for TMA   */
+#define FTGEMM_ERR_CUDA (-4)        /* a CUDA runtime call failed            */
+#define FTGEMM_ERR_TIMEOUT (-5)     /* a bounded device wait gave up         */
+
+typedef struct ftgemm_ctx* ftgemm_handle_t;
+
+/* element type of A and B.  C is always fp32, accumulation is always fp32. */
+typedef enum {
+  FTGEMM_F32 = 0,  /* fp32 operands, CUDA-core (SIMT) kernels              */
+  FTGEMM_BF16 = 1, /* bf16 operands, tcgen05 tensor-core kernel            */
+  FTGEMM_E4M3 = 2  /* fp8 E4M3 operands with per-tensor scales, tcgen05    */
+} ftgemm_dtype;
+
+/* granularity of the checksum unit (Section 4.2) */
+typedef enum {
+  FTGEMM_FT_OFF = 0,    /* plain GEMM, no checksums                           */
+  FTGEMM_FT_THREAD = 1, /* unit = one thread's m_t x n_t fragment (4.2.1)     */
+  FTGEMM_FT_WARP = 2,   /* unit = one warp's m_w x n_w tile (4.2.2)           */
+  FTGEMM_FT_BLOCK = 3,  /* unit = the threadblock's m_tb x n_tb tile (4.2.3)  */
+  FTGEMM_FT_TILE = 4    /* unit = the tensor-core CTA tile, verified in the
+                           epilogue (bf16 / e4m3 only)                        */
+} ftgemm_ft_level;
+
+/* Kernel schedule: the 7-parameter tile tuple of Table 1 plus the checksum
+ * cadence and split-K.  m_tb x n_tb is the CTA tile, k_tb the k-step width,
+ * m_w x n_w the warp tile, m_t x n_t the thread tile.  cadence is the number
+ * of k-steps per verification period (0 = verify once, after the last
+ * k-step).  split_k >= 1 splits the k-steps into that many independent
+ * partial products; each verifies its own partial, their sum is unprotected. */
+typedef struct {
+  int32_t m_tb, n_tb, k_tb;
+  int32_t m_w, n_w, m_t, n_t;
+  int32_t cadence;
+  int32_t split_k;
+} ftgemm_schedule;
+
+/* Seeded fault injection (Section 5.3: an additive offset on an accumulator
+ * register emulates a bit flip in the computing units).  n entries, each a
+ * position in the schedule's tiling: output tile (tile_m, tile_n), the k-step
+ * after whose update the offset is added (in units of the kernel's k-step;
+ * -1 = the last k-step), and the tile-local row/col.  target (may be NULL,
+ * meaning 0 for all) selects what is hit: 0 the accumulator of (row, col),
+ * 1 the row checksum of `row` in the unit that holds `col`, 2 the column
+ * checksum of `col` in the unit that holds `row`.  All arrays are HOST
+ * memory; they are copied during the call.  A position outside the matrix
+ * or outside the k range is rejected with FTGEMM_ERR_ARG. */
+typedef struct {
+  int32_t n;
+  const int32_t* tile_m;
+  const int32_t* tile_n;
+  const int32_t* kstep;
+  const int32_t* row;
+  const int32_t* col;
+  const int32_t* target;
+  const float* delta;
+} ftgemm_inject_spec;
+
+/* One verification event with a flagged residual.  row/col are GLOBAL
+ * indices of the located element (-1 when none was flagged on that side).
+ * kind: 0 corrected (one row and one column flagged, residuals consistent),
+ *       1 uncorrectable (more than one row or column flagged, or the two
+ *         residuals disagree: the single-event-upset model was violated),
+ *       2 checksum hit (one row xor one column flagged: the checksum itself
+ *         was corrupted; it is reset from the data and C is left alone).
+ * delta: the amount subtracted (kind 0) or the checksum's offset (kind 2).
+ * residual_r / residual_c: the residuals of the flagged row / column.
+ * tau: the sum of the thresholds of the flagged row and column.            */
+typedef struct {
+  int32_t tile_m, tile_n, kstep, row, col, kind;
+  double delta, residual_r, residual_c, tau;
+} ftgemm_fault_record;
+
+/* Caller-owned report.  records points to `capacity` caller-owned slots.
+ * On return n_records is the number of events (may exceed capacity, then
+ * overflow = 1 and only the first `capacity` in sorted order are written).
+ * Records are sorted by (tile_m, tile_n, kstep, row, col, kind).            */
+typedef struct {
+  int64_t detected;      /* unit-periods with at least one flagged residual */
+  int64_t corrected;     /* kind 0 */
+  int64_t uncorrectable; /* kind 1 */
+  int64_t checksum_only; /* kind 2 */
+  int32_t capacity;
+  int32_t n_records;
+  int32_t overflow;
+  int32_t reserved;
+  ftgemm_fault_record* records;
+} ftgemm_report;
+
+/* ---- handle ------------------------------------------------------------- */
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Makes `device`
+ * current on the calling thread. */
+int ftgemm_create(ftgemm_handle_t* handle, int device, void* cuda_stream);
+/* Release the handle and its workspaces (synchronises its stream). */
+int ftgemm_destroy(ftgemm_handle_t handle);
+/* Change the stream later calls enqueue on. */
+int ftgemm_set_stream(ftgemm_handle_t handle, void* cuda_stream);
+
+/* Fix the schedule of later fp32 calls (NULL = choose per shape, see
+ * ftgemm_get_schedule).  FTGEMM_ERR_UNSUPPORTED if the tile tuple is not one
+ * of the compiled kernels (Table 1's five tuples); cadence must be >= 0 and
+ * split_k >= 1. */
+int ftgemm_set_schedule(ftgemm_handle_t handle, const ftgemm_schedule* schedule);
+/* The schedule ftgemm_gemm would use for this problem. */
+int ftgemm_get_schedule(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
+                        ftgemm_dtype dtype, ftgemm_ft_level ft_level,
+                        ftgemm_schedule* out);
+
+/* Detection threshold (Section 2.2 leaves its value open).
+ * mode 0, analytic:  tau_row(i) = lambda * u * ||A(i,:)||_2 * ||B(:,J)||_F and
+ *                    tau_col(j) = lambda * u * ||A(I,:)||_F * ||B(:,j)||_2,
+ *   J (I) the columns (rows) of the verification unit, u = 2^-24.  lambda <= 0
+ *   keeps the current value (default 32).
+ * Other modes are rejected with FTGEMM_ERR_UNSUPPORTED. */
+int ftgemm_set_threshold(ftgemm_handle_t handle, int mode, double lambda,
+                         const float* mlp_weights, size_t n_weights);
+
+/* ---- compute ------------------------------------------------------------ */
+
+/* C = alpha * A * B + beta * C with online ABFT at `ft_level`.
+ * A, B: device pointers of `dtype` elements; C: device fp32.  With beta == 0
+ * C is not read.  inject: NULL for none.  report: NULL = do not wait (events
+ * accumulate in the handle until ftgemm_report_fetch); non-NULL = the
+ * handle's events are cleared first, the stream is synchronised at the end
+ * and the events of this call are returned.
+ * Supported: F32 with OFF/THREAD/WARP/BLOCK. */
+int ftgemm_gemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
+                double alpha, const void* A, int64_t lda, const void* B,
+                int64_t ldb, double beta, float* C, int64_t ldc,
+                ftgemm_dtype dtype, ftgemm_ft_level ft_level,
+                const ftgemm_inject_spec* inject, ftgemm_report* report);
+
+/* Synchronise the handle's stream, copy out the events accumulated since the
+ * last fetch (or the last call that returned a report) and clear them. */
+int ftgemm_report_fetch(ftgemm_handle_t handle, ftgemm_report* report);
+
+/* Checksum encoding on its own (Eq. 1-2), fp32:
+ *   V[b*k + kk] = sum_{i in [b*m_u, (b+1)*m_u)} A[i][kk]   (ceil(m/m_u) x k)
+ *   W[b*k + kk] = sum_{j in [b*n_u, (b+1)*n_u)} B[kk][j]   (ceil(n/n_u) x k)
+ *   nA[i] = ||A(i,:)||_2 (m values), nB[j] = ||B(:,j)||_2 (n values).
+ * All pointers are device pointers; any output may be NULL to skip it. */
+int ftgemm_encode(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
+                  const float* A, int64_t lda, const float* B, int64_t ldb,
+                  int32_t m_u, int32_t n_u, float* V, float* W, float* nA,
+                  float* nB);
+
+/* Text of a status code. */
+const char* ftgemm_status_string(int status);
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* ftgemm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTGEMM_H */

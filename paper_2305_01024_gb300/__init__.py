@@ -1,0 +1,232 @@
+"""Python binding of libftgemm (GEMM with fused online ABFT on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``csrc/`` behind the C ABI declared in ``include/ftgemm.h``.  The
+names mirror the C entry points.  There is no CPU fallback: if the shared
+library has not been built, importing the library raises.
+
+Torch is used for device memory and streams only; matrices are passed as
+device pointers taken from contiguous CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libftgemm.so")
+
+F32, BF16, E4M3 = 0, 1, 2
+FT_OFF, FT_THREAD, FT_WARP, FT_BLOCK, FT_TILE = 0, 1, 2, 3, 4
+LEVELS = {"off": FT_OFF, "thread": FT_THREAD, "warp": FT_WARP, "block": FT_BLOCK, "tile": FT_TILE}
+CORRECTED, UNCORRECTABLE, CHECKSUM_ONLY = 0, 1, 2
+OK, ERR_ARG, ERR_UNSUPPORTED, ERR_ALIGN, ERR_CUDA, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+
+
+class FtgemmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class Schedule(C.Structure):
+    """ftgemm_schedule: Table 1 tile tuple + cadence + split_k."""
+    _fields_ = [("m_tb", C.c_int32), ("n_tb", C.c_int32), ("k_tb", C.c_int32),
+                ("m_w", C.c_int32), ("n_w", C.c_int32), ("m_t", C.c_int32), ("n_t", C.c_int32),
+                ("cadence", C.c_int32), ("split_k", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class InjectSpec(C.Structure):
+    _fields_ = [("n", C.c_int32), ("tile_m", C.POINTER(C.c_int32)), ("tile_n", C.POINTER(C.c_int32)),
+                ("kstep", C.POINTER(C.c_int32)), ("row", C.POINTER(C.c_int32)),
+                ("col", C.POINTER(C.c_int32)), ("target", C.POINTER(C.c_int32)),
+                ("delta", C.POINTER(C.c_float))]
+
+
+class FaultRecord(C.Structure):
+    _fields_ = [("tile_m", C.c_int32), ("tile_n", C.c_int32), ("kstep", C.c_int32),
+                ("row", C.c_int32), ("col", C.c_int32), ("kind", C.c_int32),
+                ("delta", C.c_double), ("residual_r", C.c_double),
+                ("residual_c", C.c_double), ("tau", C.c_double)]
+
+
+class Report(C.Structure):
+    _fields_ = [("detected", C.c_int64), ("corrected", C.c_int64), ("uncorrectable", C.c_int64),
+                ("checksum_only", C.c_int64), ("capacity", C.c_int32), ("n_records", C.c_int32),
+                ("overflow", C.c_int32), ("reserved", C.c_int32),
+                ("records", C.POINTER(FaultRecord))]
+
+
+@dataclass
+class PyReport:
+    detected: int = 0
+    corrected: int = 0
+    uncorrectable: int = 0
+    checksum_only: int = 0
+    n_records: int = 0
+    overflow: bool = False
+    records: list = field(default_factory=list)
+
+
+_lib = None
+
+
+def lib():
+    """Load libftgemm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libftgemm.so is not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.ftgemm_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+    L.ftgemm_destroy.argtypes = [vp]
+    L.ftgemm_set_stream.argtypes = [vp, vp]
+    L.ftgemm_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    L.ftgemm_get_schedule.argtypes = [vp, i64, i64, i64, C.c_int, C.c_int, C.POINTER(Schedule)]
+    L.ftgemm_set_threshold.argtypes = [vp, C.c_int, dbl, C.POINTER(C.c_float), C.c_size_t]
+    L.ftgemm_gemm.argtypes = [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, C.c_int,
+                              C.c_int, C.POINTER(InjectSpec), C.POINTER(Report)]
+    L.ftgemm_report_fetch.argtypes = [vp, C.POINTER(Report)]
+    L.ftgemm_encode.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, i32, i32, vp, vp, vp, vp]
+    L.ftgemm_status_string.argtypes = [C.c_int]
+    L.ftgemm_status_string.restype = C.c_char_p
+    L.ftgemm_last_error.restype = C.c_char_p
+    for fn in ("ftgemm_create", "ftgemm_destroy", "ftgemm_set_stream", "ftgemm_set_schedule",
+               "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
+               "ftgemm_report_fetch", "ftgemm_encode"):
+        getattr(L, fn).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != OK:
+        msg = lib().ftgemm_last_error().decode()
+        raise FtgemmError(status, msg or lib().ftgemm_status_string(status).decode())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _records(rep: Report, cap: int) -> list:
+    out = []
+    for q in range(min(rep.n_records, cap)):
+        r = rep.records[q]
+        out.append(dict(tile_m=r.tile_m, tile_n=r.tile_n, kstep=r.kstep, row=r.row, col=r.col,
+                        kind=r.kind, delta=r.delta, residual_r=r.residual_r,
+                        residual_c=r.residual_c, tau=r.tau))
+    return out
+
+
+def make_inject(faults):
+    """Build an InjectSpec from tuples (tile_m, tile_n, kstep, row, col, delta[, target]).
+    The returned object keeps its arrays alive."""
+    n = len(faults)
+    arr = {k: (C.c_int32 * max(1, n))() for k in ("tile_m", "tile_n", "kstep", "row", "col", "target")}
+    dl = (C.c_float * max(1, n))()
+    for q, f in enumerate(faults):
+        for k, v in zip(("tile_m", "tile_n", "kstep", "row", "col"), f[:5]):
+            arr[k][q] = int(v)
+        dl[q] = float(f[5])
+        arr["target"][q] = int(f[6]) if len(f) > 6 else 0
+    spec = InjectSpec(n, arr["tile_m"], arr["tile_n"], arr["kstep"], arr["row"], arr["col"],
+                      arr["target"], dl)
+    spec._keep = (arr, dl)
+    return spec
+
+
+class Handle:
+    """Owns an ftgemm handle bound to a device and a stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = device
+        with torch.cuda.device(device):
+            s = _stream_ptr(stream)
+        self._h = C.c_void_p()
+        _check(lib().ftgemm_create(C.byref(self._h), device, s))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ftgemm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lib().ftgemm_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_schedule(self, sched: Schedule | dict | None):
+        if isinstance(sched, dict):
+            sched = Schedule(**sched)
+        _check(lib().ftgemm_set_schedule(self._h, C.byref(sched) if sched is not None else None))
+
+    def get_schedule(self, m, n, k, dtype=F32, level=FT_BLOCK) -> Schedule:
+        s = Schedule()
+        _check(lib().ftgemm_get_schedule(self._h, m, n, k, dtype, level, C.byref(s)))
+        return s
+
+    def set_threshold(self, mode: int = 0, lam: float = 0.0, weights=None):
+        w, nw = None, 0
+        if weights is not None:
+            import numpy as np
+            wa = np.ascontiguousarray(weights, dtype=np.float32)
+            w, nw = wa.ctypes.data_as(C.POINTER(C.c_float)), wa.size
+        _check(lib().ftgemm_set_threshold(self._h, mode, float(lam), w, nw))
+
+    def gemm(self, A, B, C_out, alpha=1.0, beta=0.0, level=FT_BLOCK, dtype=F32,
+             inject=None, report=True, capacity: int = 4096):
+        """C_out = alpha*A@B + beta*C_out through ftgemm_gemm.  A, B, C_out are
+        contiguous (or row-strided) CUDA tensors; returns a PyReport if
+        `report`, else None (events then accumulate in the handle)."""
+        if isinstance(level, str):
+            level = LEVELS[level]
+        M, K = A.shape
+        K2, N = B.shape
+        assert K == K2 and tuple(C_out.shape) == (M, N)
+        spec = make_inject(inject) if inject else None
+        rep, recs = None, None
+        if report:
+            recs = (FaultRecord * capacity)()
+            rep = Report(capacity=capacity, records=recs)
+        st = lib().ftgemm_gemm(self._h, M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B),
+                               B.stride(0), float(beta), _ptr(C_out), C_out.stride(0), dtype,
+                               level, C.byref(spec) if spec else None,
+                               C.byref(rep) if rep else None)
+        _check(st)
+        if not report:
+            return None
+        return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
+                        rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def report_fetch(self, capacity: int = 4096) -> PyReport:
+        recs = (FaultRecord * capacity)()
+        rep = Report(capacity=capacity, records=recs)
+        _check(lib().ftgemm_report_fetch(self._h, C.byref(rep)))
+        return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
+                        rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def encode(self, A, B, m_u, n_u, V=None, W=None, nA=None, nB=None):
+        M, K = A.shape
+        _, N = B.shape
+        _check(lib().ftgemm_encode(self._h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                   m_u, n_u, _ptr(V), _ptr(W), _ptr(nA), _ptr(nB)))

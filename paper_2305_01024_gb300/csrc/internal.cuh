@@ -1,0 +1,89 @@
+// internal.cuh -- device-side types shared by the libftgemm translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ftgemm.h"
+
+namespace ftg {
+
+enum Level { L_OFF = 0, L_THREAD = 1, L_WARP = 2, L_BLOCK = 3, L_TILE = 4 };
+enum Kind { K_CORRECTED = 0, K_UNCORRECTABLE = 1, K_CHECKSUM = 2 };
+enum Target { T_ACC = 0, T_ROWSUM = 1, T_COLSUM = 2 };
+
+// One scheduled fault, sorted on the device table by (tile, kstep).
+struct Fault {
+  int32_t tile;   // tile_m * tiles_n + tile_n
+  int32_t kstep;  // global k-step after which it is added
+  int32_t row, col, target;
+  float delta;
+};
+
+// Device report header; records live in a separate array of `capacity`.
+struct DevReport {
+  unsigned long long detected, corrected, uncorrectable, checksum_only;
+  int n_records;
+  int capacity;
+  int timeouts;  // bounded device waits that gave up
+  int pad;
+};
+
+static_assert(sizeof(ftgemm_fault_record) == 56, "record layout");
+
+__device__ __forceinline__ void report_event(DevReport* rep, ftgemm_fault_record* recs,
+                                             const ftgemm_fault_record& r) {
+  atomicAdd(&rep->detected, 1ull);
+  if (r.kind == K_CORRECTED) atomicAdd(&rep->corrected, 1ull);
+  else if (r.kind == K_UNCORRECTABLE) atomicAdd(&rep->uncorrectable, 1ull);
+  else atomicAdd(&rep->checksum_only, 1ull);
+  int slot = atomicAdd(&rep->n_records, 1);
+  if (slot < rep->capacity) recs[slot] = r;
+}
+
+// Ordering key of a flagged residual: larger |d|/tau first, ties to the
+// smaller index.  score >= 0, so its float bits order like the value.
+__device__ __forceinline__ unsigned long long flag_key(float score, int idx) {
+  return ((unsigned long long)__float_as_uint(score) << 32) |
+         (unsigned long long)(0xFFFFFFFFu - (unsigned)idx);
+}
+__device__ __forceinline__ int key_index(unsigned long long key) {
+  return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+}
+__device__ __forceinline__ float flag_score(float d, float tau) {
+  float a = fabsf(d);
+  if (tau > 0.f) return a / tau;
+  return a > 0.f ? __int_as_float(0x7f800000) : 0.f;
+}
+
+// Binary search of the first fault of `tile` in a table sorted by tile.
+__device__ __forceinline__ int first_fault(const Fault* f, int n, int tile) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (f[mid].tile < tile) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Parameters of the SIMT fused-ABFT SGEMM.
+struct SimtParams {
+  int M, N, K;
+  const float* A; long long lda;
+  const float* B; long long ldb;
+  float* C; long long ldc;
+  float alpha, beta;
+  const float* V;   // [ceil(M/m_u)][K] row-block sums of A (WARP/BLOCK)
+  const float* Wt;  // [ceil(N/n_u)][K] column-block sums of B (WARP/BLOCK)
+  const float* nA;  // [M] row 2-norms of A
+  const float* nB;  // [N] column 2-norms of B
+  float lam_u;      // lambda * u
+  int cadence;      // k-steps per period (>= 1)
+  int ksteps;       // ceil(K / k_tb)
+  int ks_per_split; // k-steps per split
+  float* partial;   // [split][M][N] when split_k > 1, else nullptr
+  const Fault* faults; int nfaults;
+  DevReport* rep; ftgemm_fault_record* recs;
+  int tiles_n;
+};
+
+}  // namespace ftg
