@@ -1,0 +1,458 @@
+#!/usr/bin/env python
+"""Throughput of GEMM with fused online ABFT on GB300.
+
+Workload (one step): C = A*B + 0.5*C with M = N = K = 16384 fp32, A, B, C
+uniform on [-1, 1), threadblock-level checksums (the paper's best scheme,
+Section 4.2.3) on the 128x128x8 tile tuple, verification every 256 of K, and
+faults injected at a seeded Poisson rate of 200 per minute of kernel time with
+magnitudes log-uniform in [1e-2, 1e3] x the expected tile maximum.  Inputs
+(3.2 GB) are larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line: TFLOP/s of the ABFT GEMM (2*M*N*K per step), overhead
+against the same kernel with ABFT off, detection / false-alarm counts, the
+roofline of the dominant kernel against the fp32 CUDA-core peak, the same
+metric end to end from host buffers, the CPU oracle as a bounded-sample
+baseline, clocks sampled during the timed region and the kernel launch count.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own problem (weak scaling; no collective on
+the data path).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ABFT GEMM TFLOP/s, % overhead vs no-FT; fault detect rate at 0 false alarms"
+SCHED = dict(m_tb=128, n_tb=128, k_tb=16, m_w=32, n_w=64, m_t=8, n_t=8, cadence=16, split_k=1)
+FAULTS_PER_MIN = 200.0
+KERNEL_SOURCES = ["simt_ftgemm.cuh", "simt_huge16.cu", "internal.cuh", "ptx.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=16384)
+    ap.add_argument("--level", default="block", choices=["block", "warp", "thread"])
+    ap.add_argument("--no-extras", action="store_true", help="skip levels/sweep side measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
+    return ap.parse_args()
+
+
+def workload_config(n, level):
+    return {
+        "workload": f"fp32 ABFT SGEMM M=N=K={n} (square sweep, largest size), {level}-level checksums,"
+                    " A,B,C~U(-1,1), alpha=1, beta=0.5, Poisson 200 faults/min of kernel time,"
+                    " |delta| log-uniform in [1e-2,1e3] x expected tile max",
+        "M": n, "N": n, "K": n, "level": level,
+        "schedule": dict(SCHED),
+        "l2": f"inputs {3 * n * n * 4 / 1e9:.1f} GB > 129 MB L2 (no flush needed)",
+        "parallelism": "replicas (weak)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2305_01024_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = data.get(kernel_key)
+    if not ent or ent.get("source_sha256") != kernel_source_sha():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def fp32_peak_tflops(sms, mhz):
+    # CUDA-core fp32: SMs x 128 lanes x 2 flop (FMA) x clock
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def make_faults(step_seed, t_kernel_s, n, ksteps):
+    import synth
+    lam = FAULTS_PER_MIN / 60.0 * t_kernel_s
+    nf = synth.poisson(step_seed, lam)
+    if nf == 0:
+        return []
+    tiles = -(-n // SCHED["m_tb"])
+    pos = synth.fault_positions(step_seed + 1, nf, tiles, tiles, ksteps, SCHED["m_tb"], SCHED["n_tb"],
+                                n, n, SCHED["cadence"])
+    # expected max |(AB)_ij| over a 128x128 tile: acc ~ N(0, K/9) for U(-1,1)
+    # inputs, and the max of 16384 such values is about 4 standard deviations
+    tile_max = 4.0 * math.sqrt(n / 9.0)
+    mags = synth.log_uniform(step_seed + 2, nf, 1e-2, 1e3) * tile_max
+    signs = synth.unit(step_seed + 3, nf) < 0.5
+    return [p + (float(-m if s else m),) for p, m, s in zip(pos, mags, signs)]
+
+
+def cpu_oracle_sample(n, target_s, seed_base=2):
+    """Time the oracle on a bounded block of the same workload: rows x cols of C
+    with the full K, BLOCK level, the same schedule.  Returns a cpu_baseline dict."""
+    import numpy as np
+    import oracle
+    import synth
+    K = n
+    sched = oracle.Schedule(**{k: SCHED[k] for k in ("m_tb", "n_tb", "k_tb", "m_w", "n_w", "m_t", "n_t",
+                                                     "cadence", "split_k")}, level=oracle.BLOCK)
+
+    def run(rows, cols):
+        A = synth.block("uniform", synth.config_seed(2, 0), (n, K), (0, rows), (0, K))
+        B = synth.block("uniform", synth.config_seed(2, 1), (K, n), (0, K), (0, cols))
+        Cin = synth.block("uniform", synth.config_seed(2, 2), (n, n), (0, rows), (0, cols))
+        t0 = time.perf_counter()
+        oracle.gemm_ft(A, B, sched, alpha=1.0, beta=0.5, Cin=Cin)
+        return time.perf_counter() - t0
+
+    threads = oracle.num_threads()
+    side = SCHED["m_tb"]
+    max_tiles = (n // side)
+    # calibrate on one tile per thread (one parallel round), then scale the
+    # number of rounds to the target time
+    t = run(side, side * min(threads, max_tiles))
+    rounds = max(1, int(target_s / max(t, 1e-3)))
+    want = min(max_tiles * max_tiles, rounds * threads)
+    c_tiles = min(max_tiles, want)
+    r_tiles = max(1, min(max_tiles, want // c_tiles))
+    rows, cols = side * r_tiles, side * c_tiles
+    t = run(rows, cols)
+    flops = 2.0 * rows * cols * K
+    used = min(threads, r_tiles * c_tiles)
+    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": used, "kind": "oracle",
+            "sample": f"C[0:{rows},0:{cols}] of the {n}^3 problem with the full K={K} "
+                      f"(block-level ABFT in fp64, {r_tiles * c_tiles} tiles of 128x128)",
+            "seconds": t, "flops": flops, "rows": rows, "cols": cols}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle timed as the comparison program
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.size
+    cal = cpu_oracle_sample(n, target_s=3.0)
+    # each step re-runs the same bounded sample
+    import oracle
+    import synth
+    rows, cols = cal["rows"], cal["cols"]
+    A = synth.block("uniform", synth.config_seed(2, 0), (n, n), (0, rows), (0, n))
+    B = synth.block("uniform", synth.config_seed(2, 1), (n, n), (0, n), (0, cols))
+    Cin = synth.block("uniform", synth.config_seed(2, 2), (n, n), (0, rows), (0, cols))
+    sched = oracle.Schedule(**{k: SCHED[k] for k in ("m_tb", "n_tb", "k_tb", "m_w", "n_w", "m_t", "n_t",
+                                                     "cadence", "split_k")}, level=oracle.BLOCK)
+    for _ in range(args.warmup):
+        oracle.gemm_ft(A, B, sched, alpha=1.0, beta=0.5, Cin=Cin)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gemm_ft(A, B, sched, alpha=1.0, beta=0.5, Cin=Cin)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    flops = 2.0 * rows * cols * n
+    v = flops / dt / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(n, "block"),
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cal["cores"], "kind": "oracle",
+                         "sample": cal["sample"] + ", one per step"},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2305_01024_gb300 as ft
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.size
+    level = ft.LEVELS[args.level]
+    flops = 2.0 * n * n * n
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    # inputs: each rank its own problem (a different batch element)
+    A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 0) + 1000 * rank, dev)
+    B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 1) + 1000 * rank, dev)
+    C0 = synth.torch_make("uniform", (n, n), synth.config_seed(2, 2) + 1000 * rank, dev)
+    C = C0.clone()
+    torch.cuda.synchronize()
+
+    h = ft.Handle(local)
+    h.set_schedule(SCHED)
+    ksteps = -(-n // SCHED["k_tb"])
+    stream = torch.cuda.current_stream()
+
+    def step(lv, faults=None):
+        h.gemm(A, B, C, alpha=1.0, beta=0.5, level=lv, inject=faults, report=False)
+
+    def timed_loop(fn, steps, warm=0):
+        for i in range(warm):
+            fn(i)
+        barrier()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for i in range(steps):
+            fn(i)
+        e.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return s.elapsed_time(e) / steps
+
+    # warm-up (also estimates the kernel time for the Poisson fault rate)
+    for _ in range(args.warmup):
+        step(level)
+    torch.cuda.synchronize()
+    t_est = timed_loop(lambda i: step(level), 1) / 1e3
+    h.report_fetch()
+
+    faults = [make_faults(synth.config_seed(2, 10) + 7919 * (s + 1) + 1000 * rank, t_est, n, ksteps)
+              for s in range(args.steps)]
+    injected = sum(len(f) for f in faults)
+
+    # ---- timed region: the ABFT GEMM with faults --------------------------
+    h.enable_timing(True)
+    h.stats(reset=True)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    clocks.start()
+    ms = timed_loop(lambda i: step(level, faults[i]), args.steps)
+    clk = clocks.stop()
+    st = h.stats(reset=True)
+    h.enable_timing(False)
+    rep = h.report_fetch(capacity=1 << 14)
+    ms = max_over_ranks(ms)
+    value = flops * world / (ms / 1e3) / 1e12
+
+    # detection bookkeeping: each injected fault must show up as one
+    # corrected record at its position; anything else is a false alarm
+    want = {}
+    for s_, fl in enumerate(faults):
+        for (tm, tn, ks, r, c, d) in fl:
+            key = (tm, tn, tm * SCHED["m_tb"] + r, tn * SCHED["n_tb"] + c)
+            want[key] = want.get(key, 0) + 1
+    found = 0
+    false_alarms = 0
+    for r in rep.records:
+        key = (r["tile_m"], r["tile_n"], r["row"], r["col"])
+        if r["kind"] == ft.CORRECTED and want.get(key, 0) > 0:
+            want[key] -= 1
+            found += 1
+        else:
+            false_alarms += 1
+
+    kern_ms = st["kernel_ms"] / max(1, st["timed_launches"])
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    peak_spec = fp32_peak_tflops(sms, 2070.0)
+    peak_meas = fp32_peak_tflops(sms, clk["sm_mhz"]) if clk.get("sm_mhz") else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_spec, "unit": "TFLOP/s",
+                "frac": achieved / peak_spec, "traffic": committed_traffic("simt_ftgemm_block_huge16_16384"),
+                "kernel": "simt_ftgemm_kernel<128x128x16, BLOCK>",
+                "peak_basis": f"fp32 CUDA cores: {sms} SMs x 128 x 2 flop x 2070 MHz (max SM clock)",
+                "peak_at_measured_clock": peak_meas,
+                "frac_at_measured_clock": achieved / peak_meas if peak_meas else None,
+                "kernel_ms": kern_ms}
+
+    # ---- the same kernel with ABFT off, and torch.matmul ------------------
+    ms_off = max_over_ranks(timed_loop(lambda i: step(ft.FT_OFF), args.steps, warm=args.warmup))
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Ct = torch.empty_like(C)
+    ms_torch = max_over_ranks(timed_loop(lambda i: torch.matmul(A, B, out=Ct), args.steps, warm=args.warmup))
+    extras = {}
+    if not args.no_extras:
+        lv_steps = max(2, args.steps // 4)
+        for name in ("thread", "warp", "block"):
+            if name == args.level:
+                continue
+            m_ = max_over_ranks(timed_loop(lambda i: step(ft.LEVELS[name]), lv_steps, warm=1))
+            extras[name] = flops / (m_ / 1e3) / 1e12
+        h.report_fetch()
+        sweep = {}
+        for sz in (1024, 2048, 4096, 8192):
+            a, b = A[:sz, :sz].contiguous(), B[:sz, :sz].contiguous()
+            c = C[:sz, :sz].contiguous()
+            fl = 2.0 * sz ** 3
+            it = 5
+            row = {}
+            for name, lv in (("block", ft.FT_BLOCK), ("off", ft.FT_OFF)):
+                h.set_schedule(None)
+                row[name] = fl / (timed_loop(lambda i: h.gemm(a, b, c, 1.0, 0.5, level=lv, report=False), it, warm=2) / 1e3) / 1e12
+            ct = torch.empty_like(c)
+            row["torch_fp32"] = fl / (timed_loop(lambda i: torch.matmul(a, b, out=ct), it, warm=2) / 1e3) / 1e12
+            row["overhead_pct"] = 100.0 * (row["off"] / row["block"] - 1.0)
+            sweep[str(sz)] = {k: round(v, 3) for k, v in row.items()}
+        h.report_fetch()
+        h.set_schedule(SCHED)
+        del a, b, c, ct
+
+    # ---- end to end through the C ABI from pinned host buffers -------------
+    hA = A.cpu().pin_memory()
+    hB = B.cpu().pin_memory()
+    hC = C0.cpu().pin_memory()
+    hOut = torch.empty_like(hC).pin_memory()
+    e2e_steps = args.steps
+
+    def e2e_step(i):
+        A.copy_(hA, non_blocking=True)
+        B.copy_(hB, non_blocking=True)
+        C.copy_(hC, non_blocking=True)
+        h.gemm(A, B, C, alpha=1.0, beta=0.5, level=level, report=False)
+        hOut.copy_(C, non_blocking=True)
+
+    ms_e2e = max_over_ranks(timed_loop(e2e_step, e2e_steps, warm=1))
+    h.report_fetch()
+    e2e = {"value": flops * world / (ms_e2e / 1e3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
+           "ms_per_step": ms_e2e}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(n, args.level),
+        "overhead_pct_vs_ft_off": 100.0 * (ms / ms_off - 1.0),
+        "ft_off_tflops": flops * world / (ms_off / 1e3) / 1e12,
+        "torch_matmul_fp32_tflops": flops * world / (ms_torch / 1e3) / 1e12,
+        "vs_torch_matmul": ms_torch / ms,
+        "faults": {"injected": injected, "corrected_at_injected_position": found,
+                   "false_alarms": false_alarms, "detect_rate": (found / injected) if injected else None,
+                   "uncorrectable": rep.uncorrectable, "checksum_only": rep.checksum_only,
+                   "poisson_per_min": FAULTS_PER_MIN, "t_kernel_s": t_est},
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": st["launches"],
+    }
+    if extras:
+        line["other_levels_tflops"] = extras
+        line["sweep"] = sweep
+    h.close()
+    del A, B, C, C0, Ct
+    if rank == 0:
+        cb = cpu_oracle_sample(n, args.cpu_seconds)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -187,6 +187,24 @@ int ftgemm_encode(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                   int32_t m_u, int32_t n_u, float* V, float* W, float* nA,
                   float* nB);
 
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Counters of the handle.  launches: kernels enqueued by this handle (all
+ * kinds).  With timing enabled, CUDA events recorded on the handle's stream
+ * bracket every main GEMM kernel launch; kernel_ms is the sum of their
+ * durations and timed_launches their number. */
+typedef struct {
+  int64_t launches;
+  int64_t timed_launches;
+  double kernel_ms;
+} ftgemm_stats;
+
+/* Enable (1) or disable (0) the events around the main GEMM kernel. */
+int ftgemm_enable_timing(ftgemm_handle_t handle, int enable);
+/* Synchronise the handle's stream and read the counters; reset != 0 zeroes
+ * them afterwards. */
+int ftgemm_get_stats(ftgemm_handle_t handle, ftgemm_stats* out, int reset);
+
 /* Text of a status code. */
 const char* ftgemm_status_string(int status);
 /* Text of the last error raised on the calling thread ("" if none). */

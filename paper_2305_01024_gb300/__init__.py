@@ -54,6 +54,10 @@ class FaultRecord(C.Structure):
                 ("residual_c", C.c_double), ("tau", C.c_double)]
 
 
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("timed_launches", C.c_int64), ("kernel_ms", C.c_double)]
+
+
 class Report(C.Structure):
     _fields_ = [("detected", C.c_int64), ("corrected", C.c_int64), ("uncorrectable", C.c_int64),
                 ("checksum_only", C.c_int64), ("capacity", C.c_int32), ("n_records", C.c_int32),
@@ -95,12 +99,15 @@ def lib():
                               C.c_int, C.POINTER(InjectSpec), C.POINTER(Report)]
     L.ftgemm_report_fetch.argtypes = [vp, C.POINTER(Report)]
     L.ftgemm_encode.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, i32, i32, vp, vp, vp, vp]
+    L.ftgemm_enable_timing.argtypes = [vp, C.c_int]
+    L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
     for fn in ("ftgemm_create", "ftgemm_destroy", "ftgemm_set_stream", "ftgemm_set_schedule",
                "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
-               "ftgemm_report_fetch", "ftgemm_encode"):
+               "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
+               "ftgemm_get_stats"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -224,6 +231,14 @@ class Handle:
         _check(lib().ftgemm_report_fetch(self._h, C.byref(rep)))
         return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
                         rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def enable_timing(self, enable: bool = True):
+        _check(lib().ftgemm_enable_timing(self._h, 1 if enable else 0))
+
+    def stats(self, reset: bool = False) -> dict:
+        st = Stats()
+        _check(lib().ftgemm_get_stats(self._h, C.byref(st), 1 if reset else 0))
+        return dict(launches=st.launches, timed_launches=st.timed_launches, kernel_ms=st.kernel_ms)
 
     def encode(self, A, B, m_u, n_u, V=None, W=None, nA=None, nB=None):
         M, K = A.shape

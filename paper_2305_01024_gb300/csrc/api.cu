@@ -12,26 +12,30 @@
 #include "internal.cuh"
 
 namespace ftg {
-cudaError_t simt_launch_small(int, bool, const SimtParams&, int, cudaStream_t);
-cudaError_t simt_launch_medium(int, bool, const SimtParams&, int, cudaStream_t);
-cudaError_t simt_launch_large(int, bool, const SimtParams&, int, cudaStream_t);
-cudaError_t simt_launch_tall(int, bool, const SimtParams&, int, cudaStream_t);
-cudaError_t simt_launch_huge(int, bool, const SimtParams&, int, cudaStream_t);
-cudaError_t launch_encode(const float*, long long, const float*, long long, int, int, int, int, int,
-                          float*, float*, float*, float*, float*, cudaStream_t);
-long long colnorm_scratch_floats(int K, int N);
+using SimtLaunch = cudaError_t (*)(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_small(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_medium(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_large(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_tall(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_huge(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_huge16(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t launch_transpose(const float*, long long, int, int, float*, long long, cudaStream_t);
+cudaError_t launch_copy_pad(const float*, long long, int, int, float*, long long, cudaStream_t);
+long long kmajor_scratch_floats(int K, int L);
+cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*, long long, float*,
+                                 float*, int*, cudaStream_t);
 cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, float*, long long,
                                  cudaStream_t);
 
-using SimtLaunch = cudaError_t (*)(int, bool, const SimtParams&, int, cudaStream_t);
-
-// The compiled SIMT tile tuples: the five kernel setups of Table 1.
+// The compiled SIMT tile tuples: the five kernel setups of Table 1, plus the
+// large tile with a 16-wide k-step (the GB300 default for big problems).
 struct SimtConfig {
   const char* name;
   int m_tb, n_tb, k_tb, m_w, n_w, m_t, n_t;
   SimtLaunch launch;
 };
 static const SimtConfig kSimtConfigs[] = {
+    {"huge16", 128, 128, 16, 32, 64, 8, 8, simt_launch_huge16},
     {"huge", 128, 128, 8, 32, 64, 8, 8, simt_launch_huge},
     {"large", 64, 64, 8, 32, 64, 8, 8, simt_launch_large},
     {"tall", 32, 128, 8, 16, 64, 4, 8, simt_launch_tall},
@@ -73,6 +77,12 @@ struct ftgemm_ctx {
   bool has_sched = false;
   ftgemm_schedule sched{};
   double lambda = 32.0;
+  // instrumentation
+  int64_t launches = 0;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pool;
+  int64_t timed = 0;
+  double kernel_ms = 0.0;
 };
 
 #define FAIL(code, ...)                                                         \
@@ -125,6 +135,7 @@ static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
   const int sms = h->num_sms > 0 ? h->num_sms : 152;
   const SimtConfig* pick = nullptr;
   for (const auto& c : kSimtConfigs) {
+    if (c.launch == simt_launch_huge) continue;  // the k_tb=8 variant only on request
     int64_t tiles = ((m + c.m_tb - 1) / c.m_tb) * ((n + c.n_tb - 1) / c.n_tb);
     if (tiles >= sms) { pick = &c; break; }
   }
@@ -150,7 +161,92 @@ static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
   return FTGEMM_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2-D fp32 tensor map: dims {inner, outer}, row stride in elements, box {bi, bo}.
+// Out-of-range box elements read as zero.
+static int make_map_2d(CUtensorMap* m, const float* base, uint64_t inner, uint64_t outer,
+                       uint64_t ld, uint32_t bi, uint32_t bo) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) FAIL(FTGEMM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld * sizeof(float)};
+  cuuint32_t box[2] = {bi, bo};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    FAIL(FTGEMM_ERR_ALIGN, "cuTensorMapEncodeTiled failed (%d) for dims {%llu,%llu} ld %llu box {%u,%u}",
+         (int)r, (unsigned long long)inner, (unsigned long long)outer, (unsigned long long)ld, bi, bo);
+  return FTGEMM_OK;
+}
+
+static int take_events(ftgemm_ctx* h, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
+  if (!h->pool.empty()) {
+    *ev = h->pool.back();
+    h->pool.pop_back();
+    return FTGEMM_OK;
+  }
+  CK(cudaEventCreate(&ev->first));
+  CK(cudaEventCreate(&ev->second));
+  return FTGEMM_OK;
+}
+
+static int drain_events(ftgemm_ctx* h) {
+  if (h->pending.empty()) return FTGEMM_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& e : h->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e.first, e.second));
+    h->kernel_ms += ms;
+    h->timed += 1;
+    h->pool.push_back(e);
+  }
+  h->pending.clear();
+  return FTGEMM_OK;
+}
+
 extern "C" {
+
+int ftgemm_enable_timing(ftgemm_handle_t h, int enable) {
+  if (!h) FAIL(FTGEMM_ERR_ARG, "ftgemm_enable_timing: NULL handle");
+  h->timing = enable != 0;
+  return FTGEMM_OK;
+}
+
+int ftgemm_get_stats(ftgemm_handle_t h, ftgemm_stats* out, int reset) {
+  if (!h || !out) FAIL(FTGEMM_ERR_ARG, "ftgemm_get_stats: NULL argument");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  int rc = drain_events(h);
+  if (rc) return rc;
+  out->launches = h->launches;
+  out->timed_launches = h->timed;
+  out->kernel_ms = h->kernel_ms;
+  if (reset) {
+    h->launches = 0;
+    h->timed = 0;
+    h->kernel_ms = 0.0;
+  }
+  return FTGEMM_OK;
+}
 
 const char* ftgemm_status_string(int status) {
   switch (status) {
@@ -202,6 +298,8 @@ int ftgemm_destroy(ftgemm_handle_t h) {
   if (h->d_faults) cudaFree(h->d_faults);
   if (h->h_faults) cudaFreeHost(h->h_faults);
   if (h->faults_free) cudaEventDestroy(h->faults_free);
+  for (auto& e : h->pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (auto& e : h->pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   delete h;
   return FTGEMM_OK;
 }
@@ -286,18 +384,26 @@ int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out) {
 int ftgemm_encode(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
                   const float* B, int64_t ldb, int32_t m_u, int32_t n_u, float* V, float* W,
                   float* nA, float* nB) {
-  if (!h || !A || !B || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n || m_u <= 0 || n_u <= 0 ||
-      m > INT32_MAX || n > INT32_MAX || k > INT32_MAX)
-    FAIL(FTGEMM_ERR_ARG, "ftgemm_encode: bad argument");
+  if (!h || !A || !B || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n || m_u < 2 || n_u < 2 ||
+      m_u > 1024 || n_u > 1024 || (m_u & (m_u - 1)) || (n_u & (n_u - 1)) || m > INT32_MAX ||
+      n > INT32_MAX || k > INT32_MAX)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_encode: bad argument (block sizes must be powers of two in [2,1024])");
   CK(cudaSetDevice(h->device));
-  float* scratch = nullptr;
-  if (nB) {
-    int rc = ensure_ws(h, (size_t)colnorm_scratch_floats((int)k, (int)n));
-    if (rc) return rc;
-    scratch = h->ws;
+  const int M = (int)m, N = (int)n, K = (int)k;
+  const long long ldt = (M + 3) / 4 * 4;
+  const size_t oAt = 0, oScr = align64(oAt + (size_t)K * ldt);
+  const size_t nScr = (size_t)std::max(kmajor_scratch_floats(K, M), kmajor_scratch_floats(K, N));
+  int rc = ensure_ws(h, align64(oScr + nScr));
+  if (rc) return rc;
+  int launches = 0;
+  if (V || nA) {
+    CK(launch_transpose(A, lda, M, K, h->ws + oAt, ldt, h->stream));
+    ++launches;
+    CK(launch_encode_kmajor(h->ws + oAt, ldt, K, M, m_u, V, K, nA, h->ws + oScr, &launches, h->stream));
   }
-  CK(launch_encode(A, lda, B, ldb, (int)m, (int)n, (int)k, m_u, n_u, V, W, nA, nB, scratch,
-                   h->stream));
+  if (W || nB)
+    CK(launch_encode_kmajor(B, ldb, K, N, n_u, W, K, nB, h->ws + oScr, &launches, h->stream));
+  h->launches += launches;
   return FTGEMM_OK;
 }
 
@@ -333,8 +439,6 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   const float* Af = (const float*)A;
   const float* Bf = (const float*)B;
   auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-  const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) && (K % 4 == 0) &&
-                   (N % 4 == 0) && al16(A) && al16(B) && al16(C);
 
   // ---- faults: validate, resolve, sort, upload -----------------------------
   int nf = inject ? inject->n : 0;
@@ -376,36 +480,65 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
     if (rc) return rc;
   }
 
-  // ---- workspace ----------------------------------------------------------
+  // ---- workspace: k-major operands, encoded vectors, norms, partials -----
   const bool abft = level != FTGEMM_FT_OFF;
   int m_u = 1, n_u = 1;
   bool need_vw = false;
   if (level == FTGEMM_FT_WARP) { m_u = s.m_w; n_u = s.n_w; need_vw = true; }
   if (level == FTGEMM_FT_BLOCK) { m_u = s.m_tb; n_u = s.n_tb; need_vw = true; }
-  const size_t nV = need_vw ? (size_t)((M + m_u - 1) / m_u) * K : 0;
-  const size_t nW = need_vw ? (size_t)((N + n_u - 1) / n_u) * K : 0;
+  const int NV = level == FTGEMM_FT_WARP ? s.m_tb / s.m_w : 1;
+  const int NW = level == FTGEMM_FT_WARP ? s.n_tb / s.n_w : 1;
+  const long long ldt = (M + 3) / 4 * 4;  // A^T row stride (16-byte multiple)
+  const long long ldv = (K + 3) / 4 * 4;  // encoded-vector row stride
+  const bool b_ok = (ldb % 4 == 0) && al16(B);
+  const long long ldbp = b_ok ? ldb : (N + 3) / 4 * 4;
+  const int nvb = (M + m_u - 1) / m_u, nwb = (N + n_u - 1) / n_u;
+  const size_t nAt = (size_t)K * ldt;
+  const size_t nBp = b_ok ? 0 : (size_t)K * ldbp;
+  const size_t nV = need_vw ? (size_t)nvb * ldv : 0;
+  const size_t nW = need_vw ? (size_t)nwb * ldv : 0;
   const size_t nNa = abft ? (size_t)M : 0, nNb = abft ? (size_t)N : 0;
-  const size_t nScr = abft ? (size_t)colnorm_scratch_floats(K, N) : 0;
+  const size_t nScr = abft ? (size_t)std::max(kmajor_scratch_floats(K, M), kmajor_scratch_floats(K, N)) : 0;
   const size_t nPart = split > 1 ? (size_t)split * M * N : 0;
-  const size_t oV = 0, oW = align64(oV + nV), oNa = align64(oW + nW), oNb = align64(oNa + nNa),
-               oScr = align64(oNb + nNb), oPart = align64(oScr + nScr), total = align64(oPart + nPart);
-  if (total > 0) {
+  const size_t oAt = 0, oBp = align64(oAt + nAt), oV = align64(oBp + nBp), oW = align64(oV + nV),
+               oNa = align64(oW + nW), oNb = align64(oNa + nNa), oScr = align64(oNb + nNb),
+               oPart = align64(oScr + nScr), total = align64(oPart + nPart);
+  {
     int rc = ensure_ws(h, total);
     if (rc) return rc;
   }
   float* ws = h->ws;
-
+  int launches = 0;
+  CK(launch_transpose(Af, lda, M, K, ws + oAt, ldt, h->stream));
+  ++launches;
+  const float* Bk = Bf;
+  if (!b_ok) {
+    CK(launch_copy_pad(Bf, ldb, K, N, ws + oBp, ldbp, h->stream));
+    ++launches;
+    Bk = ws + oBp;
+  }
   if (abft) {
-    CK(launch_encode(Af, lda, Bf, ldb, M, N, K, m_u, n_u, need_vw ? ws + oV : nullptr,
-                     need_vw ? ws + oW : nullptr, ws + oNa, ws + oNb, ws + oScr, h->stream));
+    CK(launch_encode_kmajor(ws + oAt, ldt, K, M, need_vw ? m_u : 2, need_vw ? ws + oV : nullptr, ldv,
+                            ws + oNa, ws + oScr, &launches, h->stream));
+    CK(launch_encode_kmajor(Bk, ldbp, K, N, need_vw ? n_u : 2, need_vw ? ws + oW : nullptr, ldv,
+                            ws + oNb, ws + oScr, &launches, h->stream));
+  }
+
+  SimtMaps maps;
+  {
+    int rc = make_map_2d(&maps.A, ws + oAt, M, K, ldt, s.m_tb, s.k_tb);
+    if (!rc) rc = make_map_2d(&maps.B, Bk, N, K, ldbp, s.n_tb, s.k_tb);
+    if (!rc && need_vw) rc = make_map_2d(&maps.V, ws + oV, K, nvb, ldv, s.k_tb, NV);
+    if (!rc && need_vw) rc = make_map_2d(&maps.W, ws + oW, K, nwb, ldv, s.k_tb, NW);
+    if (rc) return rc;
+    if (!need_vw) { maps.V = maps.A; maps.W = maps.A; }
   }
 
   SimtParams p;
   p.M = M; p.N = N; p.K = K;
-  p.A = Af; p.lda = lda; p.B = Bf; p.ldb = ldb; p.C = C; p.ldc = ldc;
+  p.C = C; p.ldc = ldc;
+  p.c_vec = (ldc % 4 == 0) && al16(C);
   p.alpha = (float)alpha; p.beta = (float)beta;
-  p.V = need_vw ? ws + oV : nullptr;
-  p.Wt = need_vw ? ws + oW : nullptr;
   p.nA = abft ? ws + oNa : nullptr;
   p.nB = abft ? ws + oNb : nullptr;
   p.lam_u = (float)(h->lambda * std::ldexp(1.0, -24));
@@ -418,9 +551,23 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   p.rep = h->rep;
   p.recs = h->recs;
   p.tiles_n = tiles_n;
-  CK(cfg->launch((int)level, vec, p, split, h->stream));
-  if (split > 1)
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (h->timing) {
+    int rc = take_events(h, &ev);
+    if (rc) return rc;
+    CK(cudaEventRecord(ev.first, h->stream));
+  }
+  CK(cfg->launch((int)level, maps, p, split, h->stream));
+  ++launches;
+  if (h->timing) {
+    CK(cudaEventRecord(ev.second, h->stream));
+    h->pending.push_back(ev);
+  }
+  if (split > 1) {
     CK(launch_splitk_reduce(ws + oPart, split, M, N, (float)alpha, (float)beta, C, ldc, h->stream));
+    ++launches;
+  }
+  h->launches += launches;
 
   if (report) return ftgemm_report_fetch(h, report);
   return FTGEMM_OK;

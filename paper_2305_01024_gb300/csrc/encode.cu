@@ -1,102 +1,118 @@
-// encode.cu -- checksum encoding (Eq. 1-2 of Wu, Zhai et al., ICS'23) and
-// the norms that scale the detection threshold; split-K reduction.
+// encode.cu -- checksum encoding (Eq. 1-2 of Wu, Zhai et al., ICS'23), the
+// norms that scale the detection threshold, the k-major operand layout the
+// SIMT kernel streams with TMA, and the split-K reduction.
 //
-//   V[b][k]  = sum_{i in rows b*m_u .. } A[i][k]     (e^T A per row block)
-//   Wt[b][k] = sum_{j in cols b*n_u .. } B[k][j]     (B e per column block)
-//   nA[i] = ||A(i,:)||_2,  nB[j] = ||B(:,j)||_2
-//
-// All four are HBM-bound passes over A or B; the GEMM kernels read the
-// small vectors V/Wt with each k-slice.
+// Both GEMM operands are consumed k-major: B (K x N) as given, A as its
+// transpose A^T (K x M).  On a k-major matrix X (K x L) one pass gives
+//   S[b][k] = sum_{l in block b of n_u columns} X[k][l]   (block checksums)
+//   n[l]    = ||X(:, l)||_2                               (column norms)
+// so with X = A^T it yields e^T A per row block of A and ||A(i,:)||, and
+// with X = B it yields B e per column block and ||B(:,j)||.
 #include "internal.cuh"
 
 namespace ftg {
 
-// V: one thread per (row block, k); consecutive threads take consecutive k,
-// so every warp-wide load is one contiguous 128-byte row segment.
-__global__ void encode_colsum_kernel(const float* __restrict__ A, long long lda, int M, int K,
-                                     int m_u, float* __restrict__ V) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (k >= K) return;
-  const int r1 = min(M, (b + 1) * m_u);
-  float s = 0.f;
-  for (int r = b * m_u; r < r1; ++r) s += __ldg(A + (long long)r * lda + k);
-  V[(long long)b * K + k] = s;
-}
-
-// Wt: one warp per row k of B; each lane sums a run of columns of one block
-// and the runs of a block are combined with shuffles (blocks are aligned to
-// the warp's 32-column window when n_u is a power of two <= 32, else a lane
-// accumulates across windows of the same block).
-__global__ void encode_rowsum_kernel(const float* __restrict__ B, long long ldb, int K, int N,
-                                     int n_u, float* __restrict__ Wt) {
-  const int warps = blockDim.x >> 5;
-  const int k = blockIdx.x * warps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (k >= K) return;
-  const float* row = B + (long long)k * ldb;
-  const int nb = (N + n_u - 1) / n_u;
-  if (n_u <= 32 && (n_u & (n_u - 1)) == 0) {
-    for (int c0 = 0; c0 < N; c0 += 32) {
-      const int c = c0 + lane;
-      float v = c < N ? __ldg(row + c) : 0.f;
-      for (int o = 1; o < n_u; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      const int b = c / n_u;
-      if ((lane % n_u) == 0 && b < nb) Wt[(long long)b * K + k] = v;
-    }
-  } else {
-    for (int b = 0; b < nb; ++b) {
-      const int c1 = min(N, (b + 1) * n_u);
-      float v = 0.f;
-      for (int c = b * n_u + lane; c < c1; c += 32) v += __ldg(row + c);
+// A (M x K, lda) -> At (K x ldt): 32 x 32 tiles through shared memory, both
+// the read and the write coalesced.
+__global__ void transpose_kernel(const float* __restrict__ A, long long lda, int M, int K,
+                                 float* __restrict__ At, long long ldt) {
+  __shared__ float tile[32][33];
+  const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) Wt[(long long)b * K + k] = v;
+  for (int r = ty; r < 32; r += 8) {
+    const int m = m0 + r, k = k0 + tx;
+    tile[r][tx] = (m < M && k < K) ? __ldg(A + (long long)m * lda + k) : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, m = m0 + tx;
+    if (k < K && m < M) At[(long long)k * ldt + m] = tile[tx][r];
+  }
+}
+
+// Row-padded copy X (R x C, ldx) -> Y (R x ldy), for operands whose stride
+// or base address does not meet the 16-byte rule of TMA.
+__global__ void copy_pad_kernel(const float* __restrict__ X, long long ldx, int R, int Cn,
+                                float* __restrict__ Y, long long ldy) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)R * Cn) return;
+  const int r = (int)(idx / Cn), c = (int)(idx % Cn);
+  Y[(long long)r * ldy + c] = __ldg(X + (long long)r * ldx + c);
+}
+
+constexpr int kEncRows = 64;     // k-rows per CTA
+constexpr int kEncCols = 1024;   // columns per CTA (256 threads x 4)
+
+// One CTA: kEncRows rows x kEncCols columns of a k-major X.  Block sums over
+// groups of n_u columns (n_u a power of two, 2..1024) for every row, and
+// partial column sums of squares over the CTA's rows.
+__global__ void __launch_bounds__(256) encode_kmajor_kernel(const float* __restrict__ X, long long ldx,
+                                                            int K, int L, int n_u,
+                                                            float* __restrict__ S, long long lds,
+                                                            float* __restrict__ part) {
+  __shared__ float wpart[kEncRows][8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.x * kEncCols + tid * 4;
+  const int k0 = blockIdx.y * kEncRows;
+  const int k1 = min(K, k0 + kEncRows);
+  const int g = n_u / 4;  // lanes per block when n_u <= 128
+  float sq[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = k0; k < k1; ++k) {
+    const float* row = X + (long long)k * ldx;
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (c0 + q < L) ? __ldg(row + c0 + q) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sq[q] = fmaf(v[q], v[q], sq[q]);
+    if (S) {
+      float s = (v[0] + v[1]) + (v[2] + v[3]);
+      if (n_u <= 128) {
+        for (int o = 1; o < g; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (n_u >= 4) {
+          if ((lane % g) == 0 && c0 < L) S[(long long)(c0 / n_u) * lds + k] = s;
+        } else {
+          // n_u == 2: each lane holds two blocks
+          const float s0 = v[0] + v[1], s1 = v[2] + v[3];
+          if (c0 < L) S[(long long)(c0 / 2) * lds + k] = s0;
+          if (c0 + 2 < L) S[(long long)(c0 / 2 + 1) * lds + k] = s1;
+        }
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) wpart[k - k0][warp] = s;
+      }
     }
   }
-}
-
-// nA: one warp per row.
-__global__ void encode_rownorm_kernel(const float* __restrict__ A, long long lda, int M, int K,
-                                      float* __restrict__ nA) {
-  const int warps = blockDim.x >> 5;
-  const int r = blockIdx.x * warps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= M) return;
-  const float* row = A + (long long)r * lda;
-  float s = 0.f;
-  for (int k = lane; k < K; k += 32) {
-    const float v = __ldg(row + k);
-    s = fmaf(v, v, s);
+  if (S && n_u > 128) {
+    __syncthreads();
+    // blocks of n_u columns = n_u/128 consecutive warps of this CTA
+    const int wpb = n_u / 128;
+    const int nblk = 8 / wpb;
+    for (int t = tid; t < (k1 - k0) * nblk; t += 256) {
+      const int kk = t / nblk, bl = t % nblk;
+      const int cfirst = blockIdx.x * kEncCols + bl * n_u;
+      if (cfirst >= L) continue;
+      float s = 0.f;
+      for (int w = 0; w < wpb; ++w) s += wpart[kk][bl * wpb + w];
+      S[(long long)(cfirst / n_u) * lds + k0 + kk] = s;
+    }
   }
+  if (part) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) nA[r] = sqrtf(s);
+    for (int q = 0; q < 4; ++q)
+      if (c0 + q < L) part[(long long)blockIdx.y * L + c0 + q] = sq[q];
+  }
 }
 
-// nB in two deterministic passes: partial sums of squares over chunks of
-// 256 rows (one thread per column and chunk), then a sum over the chunks.
-constexpr int kColnormChunk = 256;
-__global__ void encode_colnorm_partial_kernel(const float* __restrict__ B, long long ldb, int K,
-                                              int N, float* __restrict__ part) {
+__global__ void colnorm_finish_kernel(const float* __restrict__ part, int chunks, int L,
+                                      float* __restrict__ nrm) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
-  if (j >= N) return;
-  const int k1 = min(K, (c + 1) * kColnormChunk);
+  if (j >= L) return;
   float s = 0.f;
-  for (int k = c * kColnormChunk; k < k1; ++k) {
-    const float v = __ldg(B + (long long)k * ldb + j);
-    s = fmaf(v, v, s);
-  }
-  part[(long long)c * N + j] = s;
-}
-__global__ void encode_colnorm_finish_kernel(const float* __restrict__ part, int chunks, int N,
-                                             float* __restrict__ nB) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  float s = 0.f;
-  for (int c = 0; c < chunks; ++c) s += part[(long long)c * N + j];
-  nB[j] = sqrtf(s);
+  for (int c = 0; c < chunks; ++c) s += part[(long long)c * L + j];
+  nrm[j] = sqrtf(s);
 }
 
 // C = alpha * sum_s partial[s] + beta * C   (split-K; the sum is unprotected)
@@ -113,26 +129,41 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits,
   *cp = beta != 0.f ? fmaf(beta, *cp, v) : v;
 }
 
-cudaError_t launch_encode(const float* A, long long lda, const float* B, long long ldb, int M,
-                          int N, int K, int m_u, int n_u, float* V, float* Wt, float* nA,
-                          float* nB, float* scratch, cudaStream_t st) {
-  if (V) {
-    dim3 g((K + 255) / 256, (M + m_u - 1) / m_u);
-    encode_colsum_kernel<<<g, 256, 0, st>>>(A, lda, M, K, m_u, V);
-  }
-  if (Wt) encode_rowsum_kernel<<<(K + 7) / 8, 256, 0, st>>>(B, ldb, K, N, n_u, Wt);
-  if (nA) encode_rownorm_kernel<<<(M + 7) / 8, 256, 0, st>>>(A, lda, M, K, nA);
-  if (nB) {
-    // scratch holds colnorm_scratch_floats(K, N) floats
-    const int chunks = (K + kColnormChunk - 1) / kColnormChunk;
-    encode_colnorm_partial_kernel<<<dim3((N + 255) / 256, chunks), 256, 0, st>>>(B, ldb, K, N, scratch);
-    encode_colnorm_finish_kernel<<<(N + 255) / 256, 256, 0, st>>>(scratch, chunks, N, nB);
-  }
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_transpose(const float* A, long long lda, int M, int K, float* At, long long ldt,
+                             cudaStream_t st) {
+  dim3 g((K + 31) / 32, (M + 31) / 32);
+  transpose_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, M, K, At, ldt);
   return cudaGetLastError();
 }
 
-long long colnorm_scratch_floats(int K, int N) {
-  return (long long)((K + kColnormChunk - 1) / kColnormChunk) * N;
+cudaError_t launch_copy_pad(const float* X, long long ldx, int R, int Cn, float* Y, long long ldy,
+                            cudaStream_t st) {
+  const long long total = (long long)R * Cn;
+  copy_pad_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, ldx, R, Cn, Y, ldy);
+  return cudaGetLastError();
+}
+
+long long kmajor_scratch_floats(int K, int L) {
+  return (long long)((K + kEncRows - 1) / kEncRows) * L;
+}
+
+// S (may be null): [ceil(L/n_u)][lds] block sums; nrm (may be null): [L].
+// scratch: kmajor_scratch_floats(K, L) floats when nrm is requested.
+cudaError_t launch_encode_kmajor(const float* X, long long ldx, int K, int L, int n_u, float* S,
+                                 long long lds, float* nrm, float* scratch, int* launches,
+                                 cudaStream_t st) {
+  if (n_u < 2 || n_u > kEncCols || (n_u & (n_u - 1))) return cudaErrorInvalidValue;
+  const int chunks = (K + kEncRows - 1) / kEncRows;
+  dim3 g((L + kEncCols - 1) / kEncCols, chunks);
+  encode_kmajor_kernel<<<g, 256, 0, st>>>(X, ldx, K, L, n_u, S, lds, nrm ? scratch : nullptr);
+  *launches += 1;
+  if (nrm) {
+    colnorm_finish_kernel<<<(L + 255) / 256, 256, 0, st>>>(scratch, chunks, L, nrm);
+    *launches += 1;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_splitk_reduce(const float* part, int splits, int M, int N, float alpha,

@@ -1,5 +1,6 @@
 // internal.cuh -- device-side types shared by the libftgemm translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,15 +66,13 @@ __device__ __forceinline__ int first_fault(const Fault* f, int n, int tile) {
   return lo;
 }
 
-// Parameters of the SIMT fused-ABFT SGEMM.
+// Parameters of the SIMT fused-ABFT SGEMM (operands arrive through the TMA
+// descriptors of SimtMaps: A^T and B k-major, e^T A and B e per k).
 struct SimtParams {
   int M, N, K;
-  const float* A; long long lda;
-  const float* B; long long ldb;
   float* C; long long ldc;
+  int c_vec;        // C rows are 16-byte aligned (float4 epilogue)
   float alpha, beta;
-  const float* V;   // [ceil(M/m_u)][K] row-block sums of A (WARP/BLOCK)
-  const float* Wt;  // [ceil(N/n_u)][K] column-block sums of B (WARP/BLOCK)
   const float* nA;  // [M] row 2-norms of A
   const float* nB;  // [N] column 2-norms of B
   float lam_u;      // lambda * u
@@ -84,6 +83,13 @@ struct SimtParams {
   const Fault* faults; int nfaults;
   DevReport* rep; ftgemm_fault_record* recs;
   int tiles_n;
+};
+
+struct SimtMaps {
+  CUtensorMap A;  // A^T: dims {M, K}, box {m_tb, k_tb}
+  CUtensorMap B;  // B:   dims {N, K}, box {n_tb, k_tb}
+  CUtensorMap V;  // e^T A per row block: dims {K, blocks}, box {k_tb, NV}
+  CUtensorMap W;  // B e per column block: dims {K, blocks}, box {k_tb, NW}
 };
 
 }  // namespace ftg

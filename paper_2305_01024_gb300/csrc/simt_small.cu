@@ -1,10 +1,11 @@
-// simt_small.cu -- instantiates the fused-ABFT SGEMM for the "small" tile tuple of
-// Table 1 (m_tb=16, n_tb=16, k_tb=16, m_w=8, n_w=16, m_t=2, n_t=2), all levels.
+// simt_small.cu -- instantiates the fused-ABFT SGEMM for the tile tuple
+// m_tb=16, n_tb=16, k_tb=16, m_w=8, n_w=16, m_t=2, n_t=2 at every checksum level.
 #include "simt_ftgemm.cuh"
 
 namespace ftg {
-cudaError_t simt_launch_small(int level, bool vec, const SimtParams& p, int split, cudaStream_t st) {
+cudaError_t simt_launch_small(int level, const SimtMaps& maps, const SimtParams& p, int split,
+                           cudaStream_t st) {
   using T = SimtTile<16, 16, 16, 8, 16, 2, 2>;
-  return launch_simt_level<T>(level, vec, p, split, st);
+  return launch_simt_level<T>(level, maps, p, split, st);
 }
 }  // namespace ftg

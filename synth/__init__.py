@@ -1,9 +1,10 @@
 """Seeded synthetic inputs shared by the oracle harness, the GPU tests and bench.py.
 
 This module holds no ABFT arithmetic: it only turns (seed, index) into numbers.
-The generator is counter based: element ``i`` of stream ``seed`` is
-``splitmix64(seed * 0x9E3779B97F4A7C15 + i + 1)`` (Steele, Lea and Flood,
-"Fast splittable pseudorandom number generators", OOPSLA 2014), so any
+The generator is counter based: element ``i`` of stream ``seed`` is the
+splitmix64 output function (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) applied to the state
+``seed*phi + i + phi`` (mod 2^64, phi = 0x9E3779B97F4A7C15), so any
 element can be produced independently, in numpy on the host or in torch on a
 device, with identical bits for the uniform and integer families.
 
@@ -188,3 +189,27 @@ def poisson(seed: int, lam: float, index: int = 0) -> int:
         p *= lam / k
         cdf += p
     return k
+
+
+def block(kind: str, seed: int, full_shape, rows, cols, dtype=np.float32) -> np.ndarray:
+    """The sub-block [rows[0]:rows[1], cols[0]:cols[1]] of the row-major matrix
+    that ``make(kind, full_shape, seed)`` would build, without building it."""
+    R, Cn = full_shape
+    r0, r1 = rows
+    c0, c1 = cols
+    out = np.empty((r1 - r0, c1 - c0), dtype=dtype)
+    for r in range(r0, r1):
+        off = r * Cn + c0
+        n = c1 - c0
+        if kind == "int":
+            u = unit(seed, n, off)
+            out[r - r0] = (np.floor(u * 9).astype(np.int64) - 4).astype(dtype)
+        elif kind == "uniform":
+            out[r - r0] = (-1.0 + 2.0 * unit(seed, n, off)).astype(dtype)
+        elif kind == "normal":
+            u1 = unit(seed, n, off)
+            u2 = unit(seed ^ 0x5BD1E995, n, off)
+            out[r - r0] = (np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)).astype(dtype)
+        else:
+            raise ValueError(kind)
+    return out

@@ -13,6 +13,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TUPLES = {
+    "huge16": (128, 128, 16, 32, 64, 8, 8),
     "huge": (128, 128, 8, 32, 64, 8, 8),
     "large": (64, 64, 8, 32, 64, 8, 8),
     "tall": (32, 128, 8, 16, 64, 4, 8),
