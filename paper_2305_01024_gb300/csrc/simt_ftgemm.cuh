@@ -76,7 +76,7 @@ template <class T, int LEVEL>
 struct SimtAux {
   using L = SimtLayout<T, LEVEL>;
   uint64_t full[T::STAGES];
-  int released[T::STAGES];  // warps done with the slot's current k-step
+  uint64_t empty[T::STAGES];
   double sum64[L::E];
   double dres[L::E];
   double fix_delta;
@@ -87,6 +87,7 @@ struct SimtAux {
   float froBw[T::WGN];
   float rowpart[LEVEL == L_BLOCK ? T::WGN : 1][T::MT];
   float colpart[LEVEL == L_BLOCK ? T::WGM : 1][T::NT];
+  float csum[LEVEL == L_BLOCK ? 4 : 1][L::E];  // running block checksums, per k-quarter
   float cval[L::E];
   float tres[L::E];
   int eflag[L::E];
@@ -112,6 +113,29 @@ __device__ __forceinline__ void lds_vec(float* d, const float* s) {
   } else {
     d[0] = s[0];
   }
+}
+
+// d0 += a * b0, d1 += a * b1 in one packed fp32 instruction (sm_100+).
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+  asm("{\n.reg .b64 ra, rb, rd;\n"
+      "mov.b64 ra, {%2, %3};\n"
+      "mov.b64 rb, {%4, %5};\n"
+      "mov.b64 rd, {%0, %1};\n"
+      "fma.rn.f32x2 rd, ra, rb, rd;\n"
+      "mov.b64 {%0, %1}, rd;\n}"
+      : "+f"(d0), "+f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// (d0, d1) = (a0 + b0, a1 + b1) in one packed fp32 instruction (sm_100+).
+__device__ __forceinline__ void add2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+  asm("{\n.reg .b64 ra, rb, rd;\n"
+      "mov.b64 ra, {%2, %3};\n"
+      "mov.b64 rb, {%4, %5};\n"
+      "add.rn.f32x2 rd, ra, rb;\n"
+      "mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
@@ -182,7 +206,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #pragma unroll
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&X.full[s], 1);
-      X.released[s] = 0;
+      mbar_init(&X.empty[s], T::NWARP);
     }
     fence_mbar_init();
   }
@@ -216,6 +240,10 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   constexpr int RPL = (TM + LN - 1) / LN;           // WARP: row entries per lane
   constexpr int CPL = (TN + LM - 1) / LM;           // WARP: column entries per lane
   constexpr int ENT = (MT + NT + NTHR - 1) / NTHR;  // BLOCK: entries per thread
+  // BLOCK on the 128 x 128 tile: checksums kept in shared memory (see below)
+  constexpr bool kSCS = LEVEL == L_BLOCK && MT == 128 && NT == 128 && NTHR == 256 &&
+                        (KT == 4 || KT == 8 || KT == 16);
+  constexpr int KQ = KT / 4;
   float cr[LEVEL == L_THREAD ? TM : 1], cc[LEVEL == L_THREAD ? TN : 1];
   float wr[LEVEL == L_WARP ? RPL : 1], wc[LEVEL == L_WARP ? CPL : 1];
   float bc[LEVEL == L_BLOCK ? ENT : 1];
@@ -231,6 +259,9 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   for (int q = 0; q < (LEVEL == L_BLOCK ? ENT : 1); ++q) bc[q] = 0.f;
 
   float froAt = 0.f, froBt = 0.f;  // THREAD: Frobenius norms over the fragment's rows / columns
+  if constexpr (kSCS) {
+    for (int e = tid; e < 4 * (MT + NT); e += NTHR) (&X.csum[0][0])[e] = 0.f;
+  }
   if constexpr (LEVEL != L_OFF) {
     for (int r = tid; r < MT; r += NTHR) X.nA[r] = (row0 + r < M) ? p.nA[row0 + r] : 0.f;
     for (int c = tid; c < NT; c += NTHR) X.nB[c] = (col0 + c < N) ? p.nB[col0 + c] : 0.f;
@@ -290,19 +321,6 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
     for (int c = 0; c < T::CM; ++c) lds_vec<VM>(&a[0][c * VM], As + arow + c * LM * VM);
 #pragma unroll
     for (int c = 0; c < T::CN; ++c) lds_vec<VN>(&b[0][c * VN], Bs + bcol + c * LN * VN);
-    // BLOCK: this thread's checksum entry e reads column e of the B slice
-    // (column checksum) or row e - NT of the A slice (row checksum), scaled
-    // by the staged e^T A / B e; one FMA per k, interleaved with the outer
-    // products so its loads hide behind them (Eq. 4).  Both slices have
-    // rows of MT == NT floats, so the per-k stride is a constant.
-    constexpr bool kInter = LEVEL == L_BLOCK && ENT == 1 && MT == NT;
-    const float* csrc = As;
-    const float* cvec = ws;
-    if constexpr (kInter) {
-      if (tid < NT) { csrc = Bs + tid; cvec = vs; }
-      else { csrc = As + (tid - NT); cvec = ws; }
-    }
-    float cv[4];
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       const int cu = k & 1;
@@ -312,10 +330,6 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
         for (int c = 0; c < T::CM; ++c) lds_vec<VM>(&a[nx][c * VM], As + (k + 1) * MT + arow + c * LM * VM);
 #pragma unroll
         for (int c = 0; c < T::CN; ++c) lds_vec<VN>(&b[nx][c * VN], Bs + (k + 1) * NT + bcol + c * LN * VN);
-      }
-      if constexpr (kInter) {
-        if ((k & 3) == 0) lds_vec<4>(cv, cvec + k);
-        bc[0] = fmaf(cv[k & 3], csrc[k * MT], bc[0]);
       }
       if constexpr (LEVEL == L_THREAD) {
         float as = 0.f, bs = 0.f;
@@ -331,7 +345,8 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[cu][i], b[cu][j], acc[i][j]);
+        for (int j = 0; j < TN; j += 2)
+          fma2(acc[i][j], acc[i][j + 1], a[cu][i], a[cu][i], b[cu][j], b[cu][j + 1]);
     }
 
     // ---- warp / block checksum update from the staged slice (Eq. 4) -----
@@ -358,7 +373,31 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
           wc[y] = s;
         }
       }
-    } else if constexpr (LEVEL == L_BLOCK && !(ENT == 1 && MT == NT)) {
+    } else if constexpr (kSCS) {
+      // 128 x 128 tile: warps 0-3 update the column checksums, warps 4-7 the
+      // row checksums; warp r covers k-quarter r of the slice and lane g the
+      // four entries 4g..4g+3, so every load is a 128-bit row segment and the
+      // multiply-adds are packed.  The running sums live in shared memory.
+      const int side = warp >> 2, r = warp & 3, g = lane;
+      const float* src = side ? As : Bs;
+      const float* cvs = (side ? ws : vs) + r * KQ;
+      float vq[KQ];
+      lds_vec<KQ>(vq, cvs);
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kk = 0; kk < KQ; ++kk) {
+        float x[4];
+        lds_vec<4>(x, src + (r * KQ + kk) * MT + 4 * g);
+        fma2(s4[0], s4[1], vq[kk], vq[kk], x[0], x[1]);
+        fma2(s4[2], s4[3], vq[kk], vq[kk], x[2], x[3]);
+      }
+      float* cs = &X.csum[r][side * NT + 4 * g];
+      float o[4];
+      lds_vec<4>(o, cs);
+      add2(o[0], o[1], o[0], o[1], s4[0], s4[1]);
+      add2(o[2], o[3], o[2], o[3], s4[2], s4[3]);
+      *reinterpret_cast<float4*>(cs) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (LEVEL == L_BLOCK) {
 #pragma unroll
       for (int q = 0; q < ENT; ++q) {
         const int e = tid + q * NTHR;
@@ -382,13 +421,18 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
     // have counted themselves out the slot may be overwritten.  No warp
     // waits here; the refill goes to whichever warp finishes last.
     __syncwarp();
-    if (lane == 0) {
-      if (atomicAdd(&X.released[slot], 1) % T::NWARP == T::NWARP - 1) {
-        if (t + STAGES < nk && !dead) {
-          fence_proxy_async_smem();
-          issue(t + STAGES);
-          issued = t + STAGES + 1;
-        }
+    if (lane == 0) mbar_arrive(&X.empty[slot]);
+    // lane 0 of warp (t mod NWARP) refills the slot of the previous k-step,
+    // which every warp has almost always released by now, with the k-step
+    // STAGES - 1 ahead; rotating the role spreads its small lag over warps
+    if (lane == 0 && warp == t % T::NWARP && t >= 1 && t - 1 + STAGES < nk && !dead) {
+      const int ps = (t - 1) % STAGES;
+      if (mbar_wait(&X.empty[ps], (uint32_t)((t - 1) / STAGES) & 1u)) {
+        issue(t - 1 + STAGES);
+        issued = t - 1 + STAGES + 1;
+      } else {
+        ++timeouts;
+        dead = true;
       }
     }
 
@@ -430,9 +474,14 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
           }
         } else if constexpr (LEVEL == L_BLOCK) {
           const int e = f.target == T_ROWSUM ? NT + f.row : f.col;
+          if constexpr (kSCS) {
+            // the owner of quarter 0 of entry e adds the offset
+            if (tid == (e < NT ? e / 4 : 128 + (e - NT) / 4)) X.csum[0][e] += f.delta;
+          } else {
 #pragma unroll
-          for (int q = 0; q < ENT; ++q)
-            if (tid + q * NTHR == e) bc[q] += f.delta;
+            for (int q = 0; q < ENT; ++q)
+              if (tid + q * NTHR == e) bc[q] += f.delta;
+          }
         }
       }
       next_ks = (fidx < p.nfaults && p.faults[fidx].tile == my_tile) ? p.faults[fidx].kstep : INT_MAX;
@@ -524,30 +573,90 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
             }
           }
         } else {
-          // fragment partial sums, then all-reduce inside the warp
+          // fragment partial sums, then a reduction inside the warp.  For the
+          // block level on 8x8 fragments (4 x 8 lanes) the sums use packed
+          // adds and the reduction is a reduce-scatter: each lane ends with
+          // one row and two column sums of the warp tile.
+          constexpr bool kRS = LEVEL == L_BLOCK && TM == 8 && TN == 8 && LN == 8 && LM == 4;
           float pr[TM], pc[TN];
+          float rs_row = 0.f, rs_c0 = 0.f, rs_c1 = 0.f;
+          if constexpr (kRS) {
 #pragma unroll
-          for (int i = 0; i < TM; ++i) {
-            float s = 0.f;
+            for (int i = 0; i < TM; ++i) {
+              float x0, x1, y0, y1;
+              add2(x0, x1, acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+              add2(y0, y1, acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+              add2(x0, x1, x0, x1, y0, y1);
+              pr[i] = x0 + x1;
+            }
 #pragma unroll
-            for (int j = 0; j < TN; ++j) s += acc[i][j];
-            pr[i] = s;
+            for (int j = 0; j < TN; j += 2) {
+              float s0 = acc[0][j], s1 = acc[0][j + 1];
+#pragma unroll
+              for (int i = 1; i < TM; ++i) add2(s0, s1, s0, s1, acc[i][j], acc[i][j + 1]);
+              pc[j] = s0;
+              pc[j + 1] = s1;
+            }
+            // rows over the 8 lanes tn (lane bits 0..2)
+            const bool b2 = (tn >> 2) & 1, b1 = (tn >> 1) & 1, b0 = tn & 1;
+            float r1[4], r2[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float snd = b2 ? pr[q] : pr[q + 4];
+              const float kp = b2 ? pr[q + 4] : pr[q];
+              r1[q] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const float snd = b1 ? r1[q] : r1[q + 2];
+              const float kp = b1 ? r1[q + 2] : r1[q];
+              r2[q] = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
+            }
+            {
+              const float snd = b0 ? r2[0] : r2[1];
+              const float kp = b0 ? r2[1] : r2[0];
+              rs_row = kp + __shfl_xor_sync(0xffffffffu, snd, 1);
+            }
+            // columns over the 4 lanes tm (lane bits 3..4)
+            const bool t1 = (tm >> 1) & 1, t0 = tm & 1;
+            float c1[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float snd = t1 ? pc[q] : pc[q + 4];
+              const float kp = t1 ? pc[q + 4] : pc[q];
+              c1[q] = kp + __shfl_xor_sync(0xffffffffu, snd, 16);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const float snd = t0 ? c1[q] : c1[q + 2];
+              const float kp = t0 ? c1[q + 2] : c1[q];
+              const float v = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
+              if (q == 0) rs_c0 = v; else rs_c1 = v;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+              float s = 0.f;
+#pragma unroll
+              for (int j = 0; j < TN; ++j) s += acc[i][j];
+              pr[i] = s;
+            }
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+              float s = 0.f;
+#pragma unroll
+              for (int i = 0; i < TM; ++i) s += acc[i][j];
+              pc[j] = s;
+            }
+#pragma unroll
+            for (int o = 1; o < LN; o <<= 1)
+#pragma unroll
+              for (int i = 0; i < TM; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], o);
+#pragma unroll
+            for (int o = LN; o < 32; o <<= 1)
+#pragma unroll
+              for (int j = 0; j < TN; ++j) pc[j] += __shfl_xor_sync(0xffffffffu, pc[j], o);
           }
-#pragma unroll
-          for (int j = 0; j < TN; ++j) {
-            float s = 0.f;
-#pragma unroll
-            for (int i = 0; i < TM; ++i) s += acc[i][j];
-            pc[j] = s;
-          }
-#pragma unroll
-          for (int o = 1; o < LN; o <<= 1)
-#pragma unroll
-            for (int i = 0; i < TM; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], o);
-#pragma unroll
-          for (int o = LN; o < 32; o <<= 1)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) pc[j] += __shfl_xor_sync(0xffffffffu, pc[j], o);
 
           if constexpr (LEVEL == L_WARP) {
             // lane (tm, tn) owns row values i = tn + x*LN and column values j = tm + y*LM
@@ -703,19 +812,31 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               }
             }
           } else {  // L_BLOCK
+            if constexpr (kRS) {
+              // lane keeps row value tn and column values 2tm, 2tm+1
+              X.rowpart[wn][FROW(tn)] = rs_row;
+              X.colpart[wm][FCOL(2 * tm)] = rs_c0;
+              X.colpart[wm][FCOL(2 * tm + 1)] = rs_c1;
+            } else {
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
-              if ((i % LN) == tn) X.rowpart[wn][FROW(i)] = pr[i];
+              for (int i = 0; i < TM; ++i)
+                if ((i % LN) == tn) X.rowpart[wn][FROW(i)] = pr[i];
 #pragma unroll
-            for (int j = 0; j < TN; ++j)
-              if ((j % LM) == tm) X.colpart[wm][FCOL(j)] = pc[j];
+              for (int j = 0; j < TN; ++j)
+                if ((j % LM) == tm) X.colpart[wm][FCOL(j)] = pc[j];
+            }
             __syncthreads();
             int myflag = 0;
-            float tq[ENT];
+            float tq[ENT], cq[ENT];
             unsigned fq = 0u;
 #pragma unroll
             for (int q = 0; q < ENT; ++q) {
               const int e = tid + q * NTHR;
+              if constexpr (kSCS) {
+                cq[q] = (X.csum[0][e] + X.csum[1][e]) + (X.csum[2][e] + X.csum[3][e]);
+              } else {
+                cq[q] = bc[q];
+              }
               float s = 0.f, tau = 0.f;
               if (e < NT) {
 #pragma unroll
@@ -727,7 +848,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                 tau = p.lam_u * X.nA[e - NT] * X.froBw[0];
               }
               tq[q] = tau;
-              if (e < NT + MT && fabsf(s - bc[q]) > tau) { myflag = 1; fq |= 1u << q; }
+              if (e < NT + MT && fabsf(s - cq[q]) > tau) { myflag = 1; fq |= 1u << q; }
             }
             if (__syncthreads_or(myflag)) {
               // fp64 confirmation: exact sums of every screened row / column
@@ -737,7 +858,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                 if (e < NT + MT) {
                   X.eflag[e] = (fq >> q) & 1u;
                   X.sum64[e] = 0.0;
-                  X.cval[e] = bc[q];
+                  X.cval[e] = cq[q];
                   X.tres[e] = tq[q];
                 }
               }
@@ -771,7 +892,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               for (int q = 0; q < ENT; ++q) {
                 const int e = tid + q * NTHR;
                 if (e < NT + MT && ((fq >> q) & 1u)) {
-                  const double d = X.sum64[e] - (double)bc[q];
+                  const double d = X.sum64[e] - (double)cq[q];
                   X.dres[e] = d;
                   if (fabs(d) > (double)tq[q]) {
                     const float sc = flag_score((float)d, tq[q]);
@@ -824,9 +945,15 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               }
               if (re >= 0) {
                 const float rv2 = X.reset_value;
+                if constexpr (kSCS) {
+                  // each quarter's owner resets its own part (it alone writes it)
+                  const int side = re >= NT, g = (re - side * NT) / 4;
+                  if (lane == g && (warp >> 2) == side) X.csum[warp & 3][re] = (warp & 3) == 0 ? rv2 : 0.f;
+                } else {
 #pragma unroll
-                for (int q = 0; q < ENT; ++q)
-                  if (tid + q * NTHR == re) bc[q] = rv2;
+                  for (int q = 0; q < ENT; ++q)
+                    if (tid + q * NTHR == re) bc[q] = rv2;
+                }
               }
             }
           }
