@@ -205,6 +205,38 @@ int ftgemm_enable_timing(ftgemm_handle_t handle, int enable);
  * them afterwards. */
 int ftgemm_get_stats(ftgemm_handle_t handle, ftgemm_stats* out, int reset);
 
+/* ---- allocation-free entry point --------------------------------------- */
+/* The paper has no counterpart of this entry point.
+ *
+ * Size of the fixed device array ftgemm_gemm_noalloc works in (16 MiB).  It
+ * is compiled into the library, so every GPU that loads the library holds it
+ * until the process exits. */
+#define FTGEMM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* C = alpha * A * B + beta * C (fp32, the 128 x 128 x 16 tile, verification
+ * every 256 of K, no split-K, no fault injection) without allocating any
+ * device memory and without a handle.  It is for callers that may not call
+ * cudaMalloc when they need the GEMM: a framework whose memory pool owns the
+ * device, code that must not cause the device-wide synchronisation that
+ * cudaMalloc / cudaFree can, or recovery code after an out-of-memory error.
+ * All temporaries (transposed A, encoded vectors, norms, event report) live
+ * in the library's fixed array of FTGEMM_NOALLOC_SCRATCH_BYTES; a problem
+ * that needs more is rejected with FTGEMM_ERR_ARG and a message naming the
+ * bytes it would need (roughly 4*K*M bytes plus small vectors).
+ * The array is shared by every call and keeps the last call's contents; each
+ * call clears the report counters it relies on.  Calls that overlap on the
+ * GPU (different streams, concurrent host threads) race on the array:
+ * serialise them.  The first call on a device looks up the array's address
+ * with that device current; make that first call before any stream capture.
+ * A, B, C: device pointers on the current device; cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream); level: FTGEMM_FT_OFF..BLOCK;
+ * report: NULL, or as for ftgemm_gemm (at most 256 records per call; the
+ * call then synchronises the stream). */
+int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha, const float* A,
+                        int64_t lda, const float* B, int64_t ldb, double beta, float* C,
+                        int64_t ldc, ftgemm_ft_level ft_level, void* cuda_stream,
+                        ftgemm_report* report);
+
 /* Text of a status code. */
 const char* ftgemm_status_string(int status);
 /* Text of the last error raised on the calling thread ("" if none). */

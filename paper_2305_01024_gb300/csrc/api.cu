@@ -53,6 +53,9 @@ static const SimtConfig* find_simt(const ftgemm_schedule& s) {
 
 static thread_local std::string g_last_error;
 
+// Lets other translation units report through ftgemm_last_error().
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 }  // namespace ftg
 
 using namespace ftg;
