@@ -19,6 +19,7 @@ cudaError_t simt_launch_large(int, const SimtMaps&, const SimtParams&, int, cuda
 cudaError_t simt_launch_tall(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_huge(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_huge16(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_wide(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t launch_transpose(const float*, long long, int, int, float*, long long, cudaStream_t);
 cudaError_t launch_copy_pad(const float*, long long, int, int, float*, long long, cudaStream_t);
 long long kmajor_scratch_floats(int K, int L);
@@ -28,13 +29,16 @@ cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, floa
                                  cudaStream_t);
 
 // The compiled SIMT tile tuples: the five kernel setups of Table 1, plus the
-// large tile with a 16-wide k-step (the GB300 default for big problems).
+// large tile with a 16-wide k-step in two thread layouts (8 x 8 fragments on
+// 256 threads, and 16 x 8 fragments on 128 threads, the GB300 default for
+// big problems: fewer shared-memory wavefronts per FMA).
 struct SimtConfig {
   const char* name;
   int m_tb, n_tb, k_tb, m_w, n_w, m_t, n_t;
   SimtLaunch launch;
 };
 static const SimtConfig kSimtConfigs[] = {
+    {"wide", 128, 128, 16, 64, 64, 16, 8, simt_launch_wide},
     {"huge16", 128, 128, 16, 32, 64, 8, 8, simt_launch_huge16},
     {"huge", 128, 128, 8, 32, 64, 8, 8, simt_launch_huge},
     {"large", 64, 64, 8, 32, 64, 8, 8, simt_launch_large},
@@ -133,12 +137,17 @@ static int ensure_faults(ftgemm_ctx* h, int n) {
 
 static size_t align64(size_t x) { return (x + 63) & ~size_t(63); }
 
-static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k,
+static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, int level,
                             ftgemm_schedule* s) {
   const int sms = h->num_sms > 0 ? h->num_sms : 152;
   const SimtConfig* pick = nullptr;
   for (const auto& c : kSimtConfigs) {
     if (c.launch == simt_launch_huge) continue;  // the k_tb=8 variant only on request
+    // on the 128 x 128 tile, 16 x 8 fragments win with checksums (fewer
+    // shared-memory wavefronts per FMA leave room for the checksum loads),
+    // 8 x 8 fragments without
+    if (c.launch == simt_launch_wide && level == FTGEMM_FT_OFF) continue;
+    if (c.launch == simt_launch_huge16 && level != FTGEMM_FT_OFF) continue;
     int64_t tiles = ((m + c.m_tb - 1) / c.m_tb) * ((n + c.n_tb - 1) / c.n_tb);
     if (tiles >= sms) { pick = &c; break; }
   }
@@ -331,7 +340,7 @@ int ftgemm_get_schedule(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, ftge
   if (dtype != FTGEMM_F32) FAIL(FTGEMM_ERR_UNSUPPORTED, "only FTGEMM_F32 has a SIMT schedule");
   (void)level;
   if (h->has_sched) { *out = h->sched; return FTGEMM_OK; }
-  return default_schedule(h, m, n, k, out);
+  return default_schedule(h, m, n, k, (int)level, out);
 }
 
 int ftgemm_set_threshold(ftgemm_handle_t h, int mode, double lambda, const float* w, size_t nw) {
@@ -427,7 +436,7 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
 
   ftgemm_schedule s;
   if (h->has_sched) s = h->sched;
-  else default_schedule(h, m, n, k, &s);
+  else default_schedule(h, m, n, k, (int)level, &s);
   const SimtConfig* cfg = find_simt(s);
   if (!cfg) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: schedule is not a compiled kernel");
 
@@ -553,7 +562,9 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   p.nfaults = nf;
   p.rep = h->rep;
   p.recs = h->recs;
+  p.tiles_m = tiles_m;
   p.tiles_n = tiles_n;
+  p.group_m = std::min(tiles_m, 16);
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (h->timing) {
     int rc = take_events(h, &ev);

@@ -82,7 +82,8 @@ struct SimtParams {
   float* partial;   // [split][M][N] when split_k > 1, else nullptr
   const Fault* faults; int nfaults;
   DevReport* rep; ftgemm_fault_record* recs;
-  int tiles_n;
+  int tiles_m, tiles_n;
+  int group_m;      // tile rows per raster group
 };
 
 struct SimtMaps {

@@ -210,7 +210,9 @@ extern "C" int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha
   p.nfaults = 0;
   p.rep = rep;
   p.recs = recs;
+  p.tiles_m = (M + MT - 1) / MT;
   p.tiles_n = (N + NT - 1) / NT;
+  p.group_m = std::min(p.tiles_m, 16);
   NA_CK(simt_launch_huge16((int)level, maps, p, 1, st));
 
   if (report) {

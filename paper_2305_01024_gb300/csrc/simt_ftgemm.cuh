@@ -35,6 +35,7 @@
 // registers (Section 5.3).
 #pragma once
 #include <climits>
+#include <cstddef>
 
 #include "internal.cuh"
 #include "ptx.cuh"
@@ -51,7 +52,10 @@ struct SimtTile {
   static constexpr int LM = WM / TM, LN = WN / TN;    // lane grid (4 x 8)
   static constexpr int VM = TM < 4 ? TM : 4, VN = TN < 4 ? TN : 4;
   static constexpr int CM = TM / VM, CN = TN / VN;    // float-vector chunks
-  static constexpr int MINB = NTHR >= 256 ? 2 : (NTHR >= 128 ? 4 : 8);
+  // CTAs per SM the register budget aims at: 128 registers per thread for
+  // fragments up to 8 x 8, up to 255 for larger ones
+  static constexpr int MINB = 65536 / (NTHR * (TM * TN > 64 ? 256 : 128)) > 0
+                                  ? 65536 / (NTHR * (TM * TN > 64 ? 256 : 128)) : 1;
   static_assert(LM * LN == 32, "a warp is 32 lanes");
   static_assert(WGM * WGN == NWARP, "warp grid covers the tile");
   static_assert((MT * 4) % 16 == 0 && (NT * 4) % 16 == 0 && (KT * 4) % 16 == 0, "TMA boxes");
@@ -87,7 +91,8 @@ struct SimtAux {
   float froBw[T::WGN];
   float rowpart[LEVEL == L_BLOCK ? T::WGN : 1][T::MT];
   float colpart[LEVEL == L_BLOCK ? T::WGM : 1][T::NT];
-  float csum[LEVEL == L_BLOCK ? 4 : 1][L::E];  // running block checksums, per k-quarter
+  // running block checksums, per k-part; read and written as float4
+  alignas(16) float csum[LEVEL == L_BLOCK ? T::NWARP / 2 : 1][L::E];
   float cval[L::E];
   float tres[L::E];
   int eflag[L::E];
@@ -99,6 +104,9 @@ struct SimtAux {
 
 template <class T, int LEVEL>
 constexpr size_t simt_smem_bytes() {
+  using Aux = SimtAux<T, LEVEL>;
+  static_assert(offsetof(Aux, csum) % 16 == 0, "float4 access to csum");
+  static_assert((T::STAGES * SimtLayout<T, LEVEL>::STAGE_FL * 4) % 128 == 0, "aux alignment");
   return 1024 + (size_t)T::STAGES * SimtLayout<T, LEVEL>::STAGE_FL * 4 + sizeof(SimtAux<T, LEVEL>);
 }
 
@@ -185,7 +193,18 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp / T::WGN, wn = warp % T::WGN;
   const int tm = lane / LN, tn = lane % LN;
-  const int tile_m = blockIdx.y, tile_n = blockIdx.x;
+  // grouped raster: consecutive CTAs sweep the columns of a group of
+  // p.group_m tile rows, so CTAs running together share A and B panels in L2
+  int tile_m, tile_n;
+  {
+    const int lin = blockIdx.y * gridDim.x + blockIdx.x;
+    const int per_group = p.group_m * p.tiles_n;
+    const int grp = lin / per_group, first_m = grp * p.group_m;
+    const int gsz = min(p.group_m, p.tiles_m - first_m);
+    const int in = lin - grp * per_group;
+    tile_m = first_m + in % gsz;
+    tile_n = in / gsz;
+  }
   const int row0 = tile_m * MT, col0 = tile_n * NT;
   const int M = p.M, N = p.N;
   const int ks0 = blockIdx.z * p.ks_per_split;
@@ -241,9 +260,10 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   constexpr int CPL = (TN + LM - 1) / LM;           // WARP: column entries per lane
   constexpr int ENT = (MT + NT + NTHR - 1) / NTHR;  // BLOCK: entries per thread
   // BLOCK on the 128 x 128 tile: checksums kept in shared memory (see below)
-  constexpr bool kSCS = LEVEL == L_BLOCK && MT == 128 && NT == 128 && NTHR == 256 &&
-                        (KT == 4 || KT == 8 || KT == 16);
-  constexpr int KQ = KT / 4;
+  constexpr int NSIDE = T::NWARP / 2;  // warps per checksum side
+  constexpr bool kSCS = LEVEL == L_BLOCK && MT == 128 && NT == 128 && (NSIDE == 2 || NSIDE == 4) &&
+                        KT % NSIDE == 0 && (KT / NSIDE == 2 || KT / NSIDE == 4 || KT / NSIDE == 8);
+  constexpr int KQ = kSCS ? KT / NSIDE : 1;
   float cr[LEVEL == L_THREAD ? TM : 1], cc[LEVEL == L_THREAD ? TN : 1];
   float wr[LEVEL == L_WARP ? RPL : 1], wc[LEVEL == L_WARP ? CPL : 1];
   float bc[LEVEL == L_BLOCK ? ENT : 1];
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 
   float froAt = 0.f, froBt = 0.f;  // THREAD: Frobenius norms over the fragment's rows / columns
   if constexpr (kSCS) {
-    for (int e = tid; e < 4 * (MT + NT); e += NTHR) (&X.csum[0][0])[e] = 0.f;
+    for (int e = tid; e < NSIDE * (MT + NT); e += NTHR) (&X.csum[0][0])[e] = 0.f;
   }
   if constexpr (LEVEL != L_OFF) {
     for (int r = tid; r < MT; r += NTHR) X.nA[r] = (row0 + r < M) ? p.nA[row0 + r] : 0.f;
@@ -374,15 +394,17 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
         }
       }
     } else if constexpr (kSCS) {
-      // 128 x 128 tile: warps 0-3 update the column checksums, warps 4-7 the
-      // row checksums; warp r covers k-quarter r of the slice and lane g the
-      // four entries 4g..4g+3, so every load is a 128-bit row segment and the
-      // multiply-adds are packed.  The running sums live in shared memory.
-      const int side = warp >> 2, r = warp & 3, g = lane;
+      // 128 x 128 tile: the first half of the warps update the column
+      // checksums, the second half the row checksums; warp r of a side covers
+      // k-part r of the slice and lane g the four entries 4g..4g+3, so every
+      // load is a 128-bit row segment and the multiply-adds are packed.  The
+      // running sums live in shared memory.
+      const int side = warp / NSIDE, r = warp % NSIDE, g = lane;
       const float* src = side ? As : Bs;
       const float* cvs = (side ? ws : vs) + r * KQ;
       float vq[KQ];
-      lds_vec<KQ>(vq, cvs);
+#pragma unroll
+      for (int q = 0; q < KQ; q += 4) lds_vec<(KQ < 4 ? KQ : 4)>(&vq[q], cvs + q);
       float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int kk = 0; kk < KQ; ++kk) {
@@ -476,7 +498,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
           const int e = f.target == T_ROWSUM ? NT + f.row : f.col;
           if constexpr (kSCS) {
             // the owner of quarter 0 of entry e adds the offset
-            if (tid == (e < NT ? e / 4 : 128 + (e - NT) / 4)) X.csum[0][e] += f.delta;
+            if (tid == (e < NT ? e / 4 : NSIDE * 32 + (e - NT) / 4)) X.csum[0][e] += f.delta;
           } else {
 #pragma unroll
             for (int q = 0; q < ENT; ++q)
@@ -833,7 +855,10 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
             for (int q = 0; q < ENT; ++q) {
               const int e = tid + q * NTHR;
               if constexpr (kSCS) {
-                cq[q] = (X.csum[0][e] + X.csum[1][e]) + (X.csum[2][e] + X.csum[3][e]);
+                float c = 0.f;
+#pragma unroll
+                for (int r = 0; r < NSIDE; ++r) c += X.csum[r][e];
+                cq[q] = c;
               } else {
                 cq[q] = bc[q];
               }
@@ -948,7 +973,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                 if constexpr (kSCS) {
                   // each quarter's owner resets its own part (it alone writes it)
                   const int side = re >= NT, g = (re - side * NT) / 4;
-                  if (lane == g && (warp >> 2) == side) X.csum[warp & 3][re] = (warp & 3) == 0 ? rv2 : 0.f;
+                  if (lane == g && warp / NSIDE == side) X.csum[warp % NSIDE][re] = warp % NSIDE == 0 ? rv2 : 0.f;
                 } else {
 #pragma unroll
                   for (int q = 0; q < ENT; ++q)
