@@ -158,7 +158,20 @@ int ftgemm_get_schedule(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
 int ftgemm_set_threshold(ftgemm_handle_t handle, int mode, double lambda,
                          const float* mlp_weights, size_t n_weights);
 
+/* Per-tensor scales of E4M3 operands: the product is scale_a * scale_b *
+ * (A_q B_q) with A_q, B_q the stored codes (see ftgemm_quantize). */
+int ftgemm_set_fp8_scales(ftgemm_handle_t handle, float scale_a, float scale_b);
+
 /* ---- compute ------------------------------------------------------------ */
+
+/* Operand quantization for the tensor-core path (no counterpart in the
+ * paper, whose kernels are fp32).  x: n fp32 values (device); y: n outputs of
+ * `dtype` (device).  FTGEMM_BF16: round to nearest even.  FTGEMM_E4M3: the
+ * per-tensor scale s = amax(|x|) / 448 is computed on the device and
+ * y = sat(RNE(x / s)) (OCP FP8 E4M3, saturating to +-448); if scale_out is
+ * not NULL the stream is synchronised and s is written there (1 for bf16). */
+int ftgemm_quantize(ftgemm_handle_t handle, int64_t n, const float* x, void* y,
+                    ftgemm_dtype dtype, float* scale_out);
 
 /* C = alpha * A * B + beta * C with online ABFT at `ft_level`.
  * A, B: device pointers of `dtype` elements; C: device fp32.  With beta == 0
@@ -166,7 +179,14 @@ int ftgemm_set_threshold(ftgemm_handle_t handle, int mode, double lambda,
  * accumulate in the handle until ftgemm_report_fetch); non-NULL = the
  * handle's events are cleared first, the stream is synchronised at the end
  * and the events of this call are returned.
- * Supported: F32 with OFF/THREAD/WARP/BLOCK. */
+ * Supported: F32 with OFF/THREAD/WARP/BLOCK; BF16 and E4M3 with OFF/TILE.
+ * Tensor-core path (BF16/E4M3): the CTA tile is 128 x 256, the k-step one
+ * 128-byte k-block (64 bf16 or 128 e4m3 elements); A must have a 16-byte
+ * aligned base and row stride (FTGEMM_ERR_ALIGN otherwise); the checksums
+ * of the tile are verified once, after its last k-step, from tensor memory;
+ * injected faults are applied to the tensor-memory accumulator at that
+ * point (the accumulation being additive, the k-step of a fault changes
+ * only rounding); E4M3 results are scaled by ftgemm_set_fp8_scales. */
 int ftgemm_gemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                 double alpha, const void* A, int64_t lda, const void* B,
                 int64_t ldb, double beta, float* C, int64_t ldc,

@@ -99,6 +99,8 @@ def lib():
                               C.c_int, C.POINTER(InjectSpec), C.POINTER(Report)]
     L.ftgemm_report_fetch.argtypes = [vp, C.POINTER(Report)]
     L.ftgemm_encode.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, i32, i32, vp, vp, vp, vp]
+    L.ftgemm_set_fp8_scales.argtypes = [vp, C.c_float, C.c_float]
+    L.ftgemm_quantize.argtypes = [vp, i64, vp, vp, C.c_int, C.POINTER(C.c_float)]
     L.ftgemm_enable_timing.argtypes = [vp, C.c_int]
     L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.ftgemm_status_string.argtypes = [C.c_int]
@@ -107,7 +109,7 @@ def lib():
     for fn in ("ftgemm_create", "ftgemm_destroy", "ftgemm_set_stream", "ftgemm_set_schedule",
                "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
-               "ftgemm_get_stats"):
+               "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -231,6 +233,21 @@ class Handle:
         _check(lib().ftgemm_report_fetch(self._h, C.byref(rep)))
         return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
                         rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def set_fp8_scales(self, scale_a: float, scale_b: float):
+        _check(lib().ftgemm_set_fp8_scales(self._h, float(scale_a), float(scale_b)))
+
+    def quantize(self, x, dtype=BF16):
+        """Quantize a contiguous fp32 CUDA tensor to bf16 (torch.bfloat16) or
+        E4M3 codes (torch.uint8).  Returns (y, scale)."""
+        import torch
+        if dtype == BF16:
+            y = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+        else:
+            y = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+        sc = C.c_float(0.0)
+        _check(lib().ftgemm_quantize(self._h, x.numel(), _ptr(x), _ptr(y), dtype, C.byref(sc)))
+        return y, sc.value
 
     def enable_timing(self, enable: bool = True):
         _check(lib().ftgemm_enable_timing(self._h, 1 if enable else 0))

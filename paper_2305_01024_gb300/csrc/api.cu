@@ -27,6 +27,11 @@ cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*,
                                  float*, int*, cudaStream_t);
 cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, float*, long long,
                                  cudaStream_t);
+cudaError_t launch_tc_prep(int dt, const void* A, long long lda, const void* B, long long ldb, int M, int N,
+                           int K, bool abft, const TcPrepBuffers& w, int* launches, cudaStream_t st);
+cudaError_t launch_tc_gemm(int dt, bool abft, const TcMaps& maps, const TcParams& p, cudaStream_t st);
+cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
+                            int* launches, cudaStream_t st);
 
 // The compiled SIMT tile tuples: the five kernel setups of Table 1, plus the
 // large tile with a 16-wide k-step in two thread layouts (8 x 8 fragments on
@@ -84,6 +89,9 @@ struct ftgemm_ctx {
   bool has_sched = false;
   ftgemm_schedule sched{};
   double lambda = 32.0;
+  double lambda_tc[2] = {32.0, 32.0};  // bf16, e4m3
+  float fp8_sa = 1.f, fp8_sb = 1.f;
+  float* qscratch = nullptr;  // amax bits + scale of ftgemm_quantize
   // instrumentation
   int64_t launches = 0;
   bool timing = false;
@@ -210,6 +218,26 @@ static int make_map_2d(CUtensorMap* m, const float* base, uint64_t inner, uint64
   return FTGEMM_OK;
 }
 
+// 2-D tensor map of 1- or 2-byte elements with the 128-byte swizzle (the
+// K-major operand tiles of the tensor-core kernel).
+static int make_map_sw128(CUtensorMap* m, const void* base, int elem, uint64_t inner, uint64_t outer,
+                          uint64_t ld, uint32_t bi, uint32_t bo) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) FAIL(FTGEMM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld * (uint64_t)elem};
+  cuuint32_t box[2] = {bi, bo};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    FAIL(FTGEMM_ERR_ALIGN, "cuTensorMapEncodeTiled (swizzled) failed (%d): dims {%llu,%llu} ld %llu box {%u,%u}",
+         (int)r, (unsigned long long)inner, (unsigned long long)outer, (unsigned long long)ld, bi, bo);
+  return FTGEMM_OK;
+}
+
 static int take_events(ftgemm_ctx* h, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
   if (!h->pool.empty()) {
     *ev = h->pool.back();
@@ -232,6 +260,100 @@ static int drain_events(ftgemm_ctx* h) {
     h->pool.push_back(e);
   }
   h->pending.clear();
+  return FTGEMM_OK;
+}
+
+static int clear_report(ftgemm_ctx* h) {
+  CK(cudaMemsetAsync(h->rep, 0, offsetof(DevReport, capacity), h->stream));
+  CK(cudaMemsetAsync(&h->rep->timeouts, 0, sizeof(int), h->stream));
+  return FTGEMM_OK;
+}
+extern "C" int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out);
+
+// Tensor-core path of ftgemm_gemm (BF16 / E4M3 operands, levels OFF and TILE).
+static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda,
+                   const void* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_dtype dtype,
+                   ftgemm_ft_level level, const ftgemm_inject_spec* inject, ftgemm_report* report) {
+  if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: bf16/e4m3 take level OFF or TILE, not %d", (int)level);
+  const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
+  const int elem = dt == 0 ? 2 : 1;
+  if (((uintptr_t)A & 15) || (lda * elem) % 16)
+    FAIL(FTGEMM_ERR_ALIGN, "ftgemm_gemm: A needs a 16-byte aligned base and row stride for TMA");
+  if (inject && inject->n > 0)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: fault injection on the tensor-core path is not available yet");
+  CK(cudaSetDevice(h->device));
+  const int M = (int)m, N = (int)n, K = (int)k;
+  const bool abft = level == FTGEMM_FT_TILE;
+  const int tiles_m = (M + 127) / 128, tiles_n = (N + 255) / 256;
+  const long long ldk = (K + 127) / 128 * 128;  // elements; 16-byte multiple for both types
+  const size_t eb = (size_t)elem;
+  // workspace layout (floats)
+  auto fl = [&](size_t bytes) { return (bytes + 3) / 4; };
+  const size_t oBt = 0;
+  const size_t oVf = align64(oBt + fl(eb * (size_t)N * ldk));
+  const size_t oWf = align64(oVf + (abft ? (size_t)tiles_m * K : 0));
+  const size_t oVt = align64(oWf + (abft ? (size_t)tiles_n * K : 0));
+  const size_t oWt = align64(oVt + (abft ? fl(eb * (size_t)tiles_m * 16 * ldk) : 0));
+  const size_t oVs = align64(oWt + (abft ? fl(eb * (size_t)tiles_n * 16 * ldk) : 0));
+  const size_t oWs = align64(oVs + (size_t)tiles_m * 16);
+  const size_t oS0 = align64(oWs + (size_t)tiles_n * 16);
+  const size_t oNa = align64(oS0 + (size_t)tiles_m + tiles_n);
+  const size_t oNb = align64(oNa + (size_t)M);
+  const size_t oFa = align64(oNb + (size_t)N);
+  const size_t oFb = align64(oFa + (size_t)tiles_m);
+  const size_t total = align64(oFb + (size_t)tiles_n);
+  {
+    int rc = ensure_ws(h, total);
+    if (rc) return rc;
+  }
+  float* ws = h->ws;
+  if (report) {
+    int rc = clear_report(h);
+    if (rc) return rc;
+  }
+  TcPrepBuffers w;
+  w.Bt = ws + oBt; w.ldk = ldk;
+  w.Vf = ws + oVf; w.Wf = ws + oWf; w.Vt = ws + oVt; w.Wt = ws + oWt;
+  w.vscale = ws + oVs; w.wscale = ws + oWs; w.s0v = ws + oS0; w.s0w = ws + oS0 + tiles_m;
+  w.nA = ws + oNa; w.nB = ws + oNb; w.froA = ws + oFa; w.froB = ws + oFb;
+  int launches = 0;
+  CK(launch_tc_prep(dt, A, lda, B, ldb, M, N, K, abft, w, &launches, h->stream));
+  const int BK = 128 / elem;
+  TcMaps maps;
+  {
+    int rc = make_map_sw128(&maps.A, A, elem, K, M, lda, BK, 128);
+    if (!rc) rc = make_map_sw128(&maps.B, w.Bt, elem, K, N, ldk, BK, 256);
+    if (!rc && abft) rc = make_map_sw128(&maps.W, w.Wt, elem, K, (uint64_t)tiles_n * 16, ldk, BK, 16);
+    if (!rc && abft) rc = make_map_sw128(&maps.V, w.Vt, elem, K, (uint64_t)tiles_m * 16, ldk, BK, 16);
+    if (rc) return rc;
+    if (!abft) { maps.W = maps.A; maps.V = maps.A; }
+  }
+  TcParams p;
+  memset(&p, 0, sizeof(p));
+  p.M = M; p.N = N; p.K = K;
+  p.C = C; p.ldc = ldc;
+  p.c_vec = (ldc % 4 == 0) && (((uintptr_t)C & 15) == 0);
+  p.alpha = (float)alpha; p.beta = (float)beta;
+  p.acc_scale = dt == 1 ? h->fp8_sa * h->fp8_sb : 1.f;
+  p.nA = w.nA; p.nB = w.nB; p.froA = w.froA; p.froB = w.froB;
+  p.wscale = w.wscale; p.vscale = w.vscale;
+  p.lam_u = (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24));
+  p.rep = h->rep; p.recs = h->recs;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (h->timing) {
+    int rc = take_events(h, &ev);
+    if (rc) return rc;
+    CK(cudaEventRecord(ev.first, h->stream));
+  }
+  CK(launch_tc_gemm(dt, abft, maps, p, h->stream));
+  ++launches;
+  if (h->timing) {
+    CK(cudaEventRecord(ev.second, h->stream));
+    h->pending.push_back(ev);
+  }
+  h->launches += launches;
+  if (report) return ftgemm_report_fetch(h, report);
   return FTGEMM_OK;
 }
 
@@ -310,6 +432,7 @@ int ftgemm_destroy(ftgemm_handle_t h) {
   if (h->d_faults) cudaFree(h->d_faults);
   if (h->h_faults) cudaFreeHost(h->h_faults);
   if (h->faults_free) cudaEventDestroy(h->faults_free);
+  if (h->qscratch) cudaFree(h->qscratch);
   for (auto& e : h->pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   for (auto& e : h->pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   delete h;
@@ -351,9 +474,32 @@ int ftgemm_set_threshold(ftgemm_handle_t h, int mode, double lambda, const float
   return FTGEMM_OK;
 }
 
-static int clear_report(ftgemm_ctx* h) {
-  CK(cudaMemsetAsync(h->rep, 0, offsetof(DevReport, capacity), h->stream));
-  CK(cudaMemsetAsync(&h->rep->timeouts, 0, sizeof(int), h->stream));
+
+int ftgemm_set_fp8_scales(ftgemm_handle_t h, float sa, float sb) {
+  if (!h) FAIL(FTGEMM_ERR_ARG, "ftgemm_set_fp8_scales: NULL handle");
+  if (!(sa > 0.f) || !(sb > 0.f)) FAIL(FTGEMM_ERR_ARG, "fp8 scales must be positive");
+  h->fp8_sa = sa;
+  h->fp8_sb = sb;
+  return FTGEMM_OK;
+}
+
+int ftgemm_quantize(ftgemm_handle_t h, int64_t n, const float* x, void* y, ftgemm_dtype dtype, float* scale_out) {
+  if (!h || !x || !y || n <= 0) FAIL(FTGEMM_ERR_ARG, "ftgemm_quantize: bad argument");
+  if (dtype != FTGEMM_BF16 && dtype != FTGEMM_E4M3) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_quantize: dtype %d", (int)dtype);
+  CK(cudaSetDevice(h->device));
+  if (!h->qscratch) CK(cudaMalloc(&h->qscratch, 2 * sizeof(float)));
+  int launches = 0;
+  CK(launch_quantize(dtype == FTGEMM_BF16 ? 0 : 1, x, n, y, reinterpret_cast<unsigned int*>(h->qscratch),
+                     h->qscratch + 1, &launches, h->stream));
+  h->launches += launches;
+  if (scale_out) {
+    if (dtype == FTGEMM_BF16) {
+      *scale_out = 1.f;
+    } else {
+      CK(cudaMemcpyAsync(scale_out, h->qscratch + 1, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+  }
   return FTGEMM_OK;
 }
 
@@ -428,8 +574,9 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   if (m <= 0 || n <= 0 || k <= 0) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm: m, n, k must be positive");
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm: size too large");
   if (lda < k || ldb < n || ldc < n) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm: leading dimension too small");
-  if (dtype != FTGEMM_F32)
-    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: dtype %d is not available in this build", (int)dtype);
+  if (dtype == FTGEMM_BF16 || dtype == FTGEMM_E4M3)
+    return tc_gemm(h, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, dtype, level, inject, report);
+  if (dtype != FTGEMM_F32) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: dtype %d", (int)dtype);
   if (level < FTGEMM_FT_OFF || level > FTGEMM_FT_BLOCK)
     FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: level %d needs a tensor-core dtype", (int)level);
   CK(cudaSetDevice(h->device));

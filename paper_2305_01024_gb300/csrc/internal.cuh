@@ -93,4 +93,39 @@ struct SimtMaps {
   CUtensorMap W;  // B e per column block: dims {K, blocks}, box {k_tb, NW}
 };
 
+// Parameters of the tensor-core GEMM (operands through TcMaps).
+struct TcParams {
+  int M, N, K;
+  float* C; long long ldc;
+  int c_vec;
+  float alpha, beta;
+  float acc_scale;        // fp8: product of the per-tensor scales; bf16: 1
+  const float* nA;        // [M] row 2-norms of A (operand values as stored)
+  const float* nB;        // [N] column 2-norms of B
+  const float* froA;      // [tiles_m] Frobenius norm of each 128-row block of A
+  const float* froB;      // [tiles_n] Frobenius norm of each 256-column block of B
+  const float* wscale;    // [tiles_n * 16] multiplier of each B e piece
+  const float* vscale;    // [tiles_m * 16] multiplier of each e^T A piece
+  float lam_u;
+  DevReport* rep; ftgemm_fault_record* recs;
+};
+
+// Buffers of the tensor-core encoding pass.
+struct TcPrepBuffers {
+  void* Bt; long long ldk;  // B^T (N x ldk), operand type; ldk also the row stride of Vt/Wt
+  float* Vf; float* Wf;     // fp32 e^T A [tiles_m][K] and B e [tiles_n][K]
+  void* Vt; void* Wt;       // pieces [tiles * 16][ldk], operand type
+  float* vscale; float* wscale;  // [tiles * 16]
+  float* s0v; float* s0w;        // [tiles] fp8 piece base scales
+  float* nA; float* nB;          // [M], [N]
+  float* froA; float* froB;      // [tiles_m], [tiles_n]
+};
+
+struct TcMaps {
+  CUtensorMap A;  // A:   dims {K, M}, box {k-block, 128}, 128-byte swizzle
+  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, 256}
+  CUtensorMap W;  // pieces of B e:   dims {K, 16 * tiles_n}, box {k-block, 16}
+  CUtensorMap V;  // pieces of e^T A: dims {K, 16 * tiles_m}, box {k-block, 16}
+};
+
 }  // namespace ftg

@@ -1,0 +1,119 @@
+"""Parity of the tensor-core (tcgen05 / TMEM) path with the CPU oracle:
+bf16 and fp8 E4M3 operands, fp32 accumulation, the plain GEMM and the
+tile-level ABFT whose checksums ride through the MMA; the operand quantizer
+against the oracle's RNE / OCP E4M3 rounding."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ft():
+    import torch
+    import paper_2305_01024_gb300 as ft
+    assert torch.cuda.is_available()
+    ft.lib()
+    return ft
+
+
+@pytest.fixture()
+def handle(ft):
+    h = ft.Handle(0)
+    yield h
+    h.close()
+
+
+def _tc_sched(orc, K, dt):
+    bk = 64 if dt == "bf16" else 128
+    nks = -(-K // bk)
+    return orc.Schedule(m_tb=128, n_tb=256, k_tb=bk, m_w=128, n_w=256, m_t=128, n_t=256,
+                        cadence=nks, split_k=1, level=orc.TILE, lam=32.0, u=U32)
+
+
+def _bf16_inputs(orc, kind, M, N, K, seed):
+    A = synth.make(kind, (M, K), seed)
+    B = synth.make(kind, (K, N), seed + 1)
+    return orc.round_bf16(A).astype(np.float32), orc.round_bf16(B).astype(np.float32)
+
+
+def _run_bf16(ft, handle, A, B, Cin, alpha, beta, level):
+    import torch
+    dA = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    dB = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    dC = torch.from_numpy(Cin.copy()).cuda()
+    rep = handle.gemm(dA, dB, dC, alpha=alpha, beta=beta, level=level, dtype=ft.BF16)
+    torch.cuda.synchronize()
+    return dC.cpu().numpy().astype(np.float64), rep
+
+
+def _bound(A, B, Cin, alpha, beta, K):
+    absprod = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+    return 2 * K * U32 * (abs(alpha) * absprod + abs(beta) * np.abs(Cin.astype(np.float64)))
+
+
+@pytest.mark.parametrize("level", ["off", "tile"])
+@pytest.mark.parametrize("shape", [(256, 512, 320), (200, 300, 136), (128, 256, 64), (130, 260, 72)])
+def test_tc_bf16_integers_exact(ft, handle, orc, level, shape):
+    M, N, K = shape
+    A, B = _bf16_inputs(orc, "int", M, N, K, 500 + M)
+    Cin = synth.integers((M, N), 600 + N)
+    lv = ft.LEVELS[level]
+    C, rep = _run_bf16(ft, handle, A, B, Cin, 2.0, -1.0, lv)
+    ref = 2 * (A.astype(np.int64) @ B.astype(np.int64)) - Cin.astype(np.int64)
+    assert np.array_equal(C, ref)
+    assert rep.detected == 0
+    if lv == ft.FT_TILE:
+        res = orc.gemm_ft(A, B, _tc_sched(orc, K, "bf16"), alpha=2.0, beta=-1.0, Cin=Cin)
+        assert np.array_equal(res.C, ref) and res.detected == 0
+
+
+@pytest.mark.parametrize("level", ["off", "tile"])
+def test_tc_bf16_normal_within_bound(ft, handle, orc, level):
+    M, N, K = 384, 512, 1024
+    A, B = _bf16_inputs(orc, "normal", M, N, K, synth.config_seed(4, 0))
+    Cin = synth.normal((M, N), synth.config_seed(4, 2))
+    C, rep = _run_bf16(ft, handle, A, B, Cin, 1.0, 0.5, ft.LEVELS[level])
+    ref = orc.gemm_ref(A, B, 1.0, 0.5, Cin)
+    assert np.all(np.abs(C - ref) <= _bound(A, B, Cin, 1.0, 0.5, K))
+    assert rep.detected == 0
+
+
+def test_quantize_matches_oracle(ft, handle, orc):
+    import torch
+    x = synth.normal((4096 + 7,), 77) * 3.0
+    dx = torch.from_numpy(x).cuda()
+    yb, sb = handle.quantize(dx, ft.BF16)
+    assert sb == 1.0
+    assert np.array_equal(yb.float().cpu().numpy().astype(np.float64), orc.round_bf16(x))
+    y8, s8 = handle.quantize(dx, ft.E4M3)
+    deq, q, scale = orc.quant_e4m3(x)
+    assert np.float32(s8) == np.float32(scale)
+    codes = y8.cpu().numpy()
+    got = torch.from_numpy(codes).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(got, q)
+
+
+@pytest.mark.parametrize("level", ["off", "tile"])
+def test_tc_fp8_normal_within_bound(ft, handle, orc, level):
+    import torch
+    M, N, K = 256, 512, 1024
+    A = synth.normal((M, K), synth.config_seed(4, 10))
+    B = synth.normal((K, N), synth.config_seed(4, 11))
+    dA8, sa = handle.quantize(torch.from_numpy(A).cuda(), ft.E4M3)
+    # B is quantized as the K x N matrix it is
+    dB8, sb = handle.quantize(torch.from_numpy(np.ascontiguousarray(B)).cuda(), ft.E4M3)
+    _, Aq, _ = orc.quant_e4m3(A)
+    _, Bq, _ = orc.quant_e4m3(B)
+    handle.set_fp8_scales(sa, sb)
+    dC = torch.zeros(M, N, device="cuda")
+    rep = handle.gemm(dA8, dB8, dC, alpha=1.0, beta=0.0, level=ft.LEVELS[level], dtype=ft.E4M3)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().astype(np.float64)
+    ref = orc.gemm_ref(Aq, Bq) * (np.float64(np.float32(sa)) * np.float64(np.float32(sb)))
+    bound = _bound(Aq, Bq, np.zeros((M, N)), 1.0, 0.0, K) * (sa * sb) + 4 * U32 * np.abs(ref)
+    assert np.all(np.abs(C - ref) <= bound)
+    assert rep.detected == 0
