@@ -218,6 +218,46 @@ static int make_map_2d(CUtensorMap* m, const float* base, uint64_t inner, uint64
   return FTGEMM_OK;
 }
 
+// Validate an injection spec against the tiling, resolve k-step -1, sort by
+// (tile, k-step) and upload it; *nf receives the number of faults.
+static int upload_faults(ftgemm_ctx* h, const ftgemm_inject_spec* inject, const ftgemm_schedule& s, int M,
+                         int N, int ksteps, int tiles_m, int tiles_n, ftgemm_ft_level level, int* nf_out) {
+  int nf = inject ? inject->n : 0;
+  *nf_out = 0;
+  if (nf < 0) FAIL(FTGEMM_ERR_ARG, "inject->n < 0");
+  if (nf == 0) return FTGEMM_OK;
+  if (!inject->tile_m || !inject->tile_n || !inject->kstep || !inject->row || !inject->col || !inject->delta)
+    FAIL(FTGEMM_ERR_ARG, "inject: NULL array");
+  int rc = ensure_faults(h, nf);
+  if (rc) return rc;
+  CK(cudaEventSynchronize(h->faults_free));  // staging buffer no longer read by a prior copy
+  std::vector<Fault> fv(nf);
+  for (int i = 0; i < nf; ++i) {
+    const int tm = inject->tile_m[i], tn = inject->tile_n[i];
+    int ks = inject->kstep[i];
+    const int r = inject->row[i], c = inject->col[i];
+    const int tg = inject->target ? inject->target[i] : 0;
+    if (tm < 0 || tm >= tiles_m || tn < 0 || tn >= tiles_n)
+      FAIL(FTGEMM_ERR_ARG, "inject[%d]: tile (%d,%d) outside the %dx%d tile grid", i, tm, tn, tiles_m, tiles_n);
+    if (ks == -1) ks = ksteps - 1;
+    if (ks < 0 || ks >= ksteps) FAIL(FTGEMM_ERR_ARG, "inject[%d]: k-step %d outside [0,%d)", i, ks, ksteps);
+    const int rows = std::min(s.m_tb, M - tm * s.m_tb), cols = std::min(s.n_tb, N - tn * s.n_tb);
+    if (r < 0 || r >= rows || c < 0 || c >= cols)
+      FAIL(FTGEMM_ERR_ARG, "inject[%d]: element (%d,%d) outside tile (%d x %d)", i, r, c, rows, cols);
+    if (tg < 0 || tg > 2) FAIL(FTGEMM_ERR_ARG, "inject[%d]: target %d", i, tg);
+    if (level == FTGEMM_FT_OFF && tg != 0) FAIL(FTGEMM_ERR_ARG, "inject[%d]: no checksums at level OFF", i);
+    fv[i] = Fault{tm * tiles_n + tn, ks, r, c, tg, inject->delta[i]};
+  }
+  std::stable_sort(fv.begin(), fv.end(), [](const Fault& a, const Fault& b) {
+    return a.tile != b.tile ? a.tile < b.tile : a.kstep < b.kstep;
+  });
+  memcpy(h->h_faults, fv.data(), sizeof(Fault) * nf);
+  CK(cudaMemcpyAsync(h->d_faults, h->h_faults, sizeof(Fault) * nf, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaEventRecord(h->faults_free, h->stream));
+  *nf_out = nf;
+  return FTGEMM_OK;
+}
+
 // 2-D tensor map of 1- or 2-byte elements with the 128-byte swizzle (the
 // K-major operand tiles of the tensor-core kernel).
 static int make_map_sw128(CUtensorMap* m, const void* base, int elem, uint64_t inner, uint64_t outer,
@@ -280,12 +320,18 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   const int elem = dt == 0 ? 2 : 1;
   if (((uintptr_t)A & 15) || (lda * elem) % 16)
     FAIL(FTGEMM_ERR_ALIGN, "ftgemm_gemm: A needs a 16-byte aligned base and row stride for TMA");
-  if (inject && inject->n > 0)
-    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: fault injection on the tensor-core path is not available yet");
   CK(cudaSetDevice(h->device));
   const int M = (int)m, N = (int)n, K = (int)k;
   const bool abft = level == FTGEMM_FT_TILE;
   const int tiles_m = (M + 127) / 128, tiles_n = (N + 255) / 256;
+  const int kblk = 128 / (dtype == FTGEMM_BF16 ? 2 : 1);
+  const int ksteps = (K + kblk - 1) / kblk;
+  int nf = 0;
+  {
+    ftgemm_schedule tcs{128, 256, kblk, 128, 256, 128, 256, 0, 1};
+    int rc = upload_faults(h, inject, tcs, M, N, ksteps, tiles_m, tiles_n, level, &nf);
+    if (rc) return rc;
+  }
   const long long ldk = (K + 127) / 128 * 128;  // elements; 16-byte multiple for both types
   const size_t eb = (size_t)elem;
   // workspace layout (floats)
@@ -339,6 +385,9 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   p.nA = w.nA; p.nB = w.nB; p.froA = w.froA; p.froB = w.froB;
   p.wscale = w.wscale; p.vscale = w.vscale;
   p.lam_u = (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24));
+  p.faults = nf > 0 ? h->d_faults : nullptr;
+  p.nfaults = nf;
+  p.tiles_n = tiles_n;
   p.rep = h->rep; p.recs = h->recs;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (h->timing) {
@@ -600,38 +649,10 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
 
   // ---- faults: validate, resolve, sort, upload -----------------------------
-  int nf = inject ? inject->n : 0;
-  if (nf < 0) FAIL(FTGEMM_ERR_ARG, "inject->n < 0");
-  if (nf > 0) {
-    if (!inject->tile_m || !inject->tile_n || !inject->kstep || !inject->row || !inject->col ||
-        !inject->delta)
-      FAIL(FTGEMM_ERR_ARG, "inject: NULL array");
-    int rc = ensure_faults(h, nf);
+  int nf = 0;
+  {
+    int rc = upload_faults(h, inject, s, M, N, ksteps, tiles_m, tiles_n, level, &nf);
     if (rc) return rc;
-    CK(cudaEventSynchronize(h->faults_free));  // staging buffer no longer read by a prior copy
-    std::vector<Fault> fv(nf);
-    for (int i = 0; i < nf; ++i) {
-      const int tm = inject->tile_m[i], tn = inject->tile_n[i];
-      int ks = inject->kstep[i];
-      const int r = inject->row[i], c = inject->col[i];
-      const int tg = inject->target ? inject->target[i] : 0;
-      if (tm < 0 || tm >= tiles_m || tn < 0 || tn >= tiles_n)
-        FAIL(FTGEMM_ERR_ARG, "inject[%d]: tile (%d,%d) outside the %dx%d tile grid", i, tm, tn, tiles_m, tiles_n);
-      if (ks == -1) ks = ksteps - 1;
-      if (ks < 0 || ks >= ksteps) FAIL(FTGEMM_ERR_ARG, "inject[%d]: k-step %d outside [0,%d)", i, ks, ksteps);
-      const int rows = std::min(s.m_tb, M - tm * s.m_tb), cols = std::min(s.n_tb, N - tn * s.n_tb);
-      if (r < 0 || r >= rows || c < 0 || c >= cols)
-        FAIL(FTGEMM_ERR_ARG, "inject[%d]: element (%d,%d) outside tile (%d x %d)", i, r, c, rows, cols);
-      if (tg < 0 || tg > 2) FAIL(FTGEMM_ERR_ARG, "inject[%d]: target %d", i, tg);
-      if (level == FTGEMM_FT_OFF && tg != 0) FAIL(FTGEMM_ERR_ARG, "inject[%d]: no checksums at level OFF", i);
-      fv[i] = Fault{tm * tiles_n + tn, ks, r, c, tg, inject->delta[i]};
-    }
-    std::stable_sort(fv.begin(), fv.end(), [](const Fault& a, const Fault& b) {
-      return a.tile != b.tile ? a.tile < b.tile : a.kstep < b.kstep;
-    });
-    memcpy(h->h_faults, fv.data(), sizeof(Fault) * nf);
-    CK(cudaMemcpyAsync(h->d_faults, h->h_faults, sizeof(Fault) * nf, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaEventRecord(h->faults_free, h->stream));
   }
 
   if (report) {

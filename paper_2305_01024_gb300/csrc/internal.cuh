@@ -107,6 +107,7 @@ struct TcParams {
   const float* wscale;    // [tiles_n * 16] multiplier of each B e piece
   const float* vscale;    // [tiles_m * 16] multiplier of each e^T A piece
   float lam_u;
+  const Fault* faults; int nfaults; int tiles_n;
   DevReport* rep; ftgemm_fault_record* recs;
 };
 

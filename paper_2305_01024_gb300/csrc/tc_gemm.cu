@@ -174,6 +174,39 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     const float alpha = p.alpha, beta = p.beta;
     const float acc_scale = p.acc_scale;  // fp8: product of the per-tensor scales
+    // ----- scheduled faults of this tile (Section 5.3) -----
+    // Verification runs once per tile after its last k-step; the accumulation
+    // being additive, an offset is applied to the tensor-memory accumulator
+    // here, where the k-step it was scheduled for only changes rounding.
+    float cr_adj = 0.f, cc_adj0 = 0.f, cc_adj1 = 0.f;
+    if (p.nfaults > 0) {
+      const int my_tile = tile_m * p.tiles_n + tile_n;
+      for (int f = first_fault(p.faults, p.nfaults, my_tile); f < p.nfaults && p.faults[f].tile == my_tile; ++f) {
+        const Fault F = p.faults[f];
+        if (F.target == T_ACC) {
+          if ((F.row >> 5) == lq) {  // warp-uniform: this warp owns the lane
+            const uint32_t a = tl + Cfg::COL_ACC + (uint32_t)(F.col & ~15);
+            float v[16];
+            tmem_ld16(a, v);
+            tmem_wait_ld();
+            if (lane == (F.row & 31)) {
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (q == (F.col & 15)) v[q] += F.delta;
+            }
+            tmem_st16(a, v);
+            tmem_wait_st();
+          }
+        } else if (F.target == T_ROWSUM) {
+          if (r == F.row) cr_adj += F.delta;
+        } else {
+          if (r == (F.col & 127)) {
+            if (F.col < 128) cc_adj0 += F.delta;
+            else cc_adj1 += F.delta;
+          }
+        }
+      }
+    }
     if constexpr (ABFT) {
       // ----- fp32 screen -----
       // row checksum of this row: sum_c piece_scale * C_r[r][c]
@@ -183,6 +216,7 @@ __global__ void __launch_bounds__(192, 1)
       float crow = 0.f;
 #pragma unroll
       for (int c = 0; c < Cfg::NPIECE; ++c) crow += cs[c] * p.wscale[(size_t)tile_n * 16 + c];
+      crow += cr_adj;
       T.crow[r] = crow;
       // column checksums: lane quarter lq holds columns lq*32.. of each half
       tmem_ld16(tl + Cfg::COL_CC0, cs);
@@ -195,8 +229,8 @@ __global__ void __launch_bounds__(192, 1)
       float cc1 = 0.f;
 #pragma unroll
       for (int c = 0; c < Cfg::NPIECE; ++c) cc1 += cs[c] * p.vscale[(size_t)tile_m * 16 + c];
-      T.ccol[r] = cc0;
-      T.ccol[128 + r] = cc1;
+      T.ccol[r] = cc0 + cc_adj0;
+      T.ccol[128 + r] = cc1 + cc_adj1;
       // row sums (two-term fp32 summation) and partial column sums
       float rs = 0.f, rc = 0.f;
       for (int ch = 0; ch < BN / 16; ++ch) {

@@ -117,3 +117,73 @@ def test_tc_fp8_normal_within_bound(ft, handle, orc, level):
     bound = _bound(Aq, Bq, np.zeros((M, N)), 1.0, 0.0, K) * (sa * sb) + 4 * U32 * np.abs(ref)
     assert np.all(np.abs(C - ref) <= bound)
     assert rep.detected == 0
+
+
+@pytest.mark.parametrize("dt", ["bf16", "fp8"])
+def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
+    """Seeded faults in several tiles (config-4 style, reduced): every fault is
+    flagged at its element, corrected, and C matches the fault-free result
+    within the bound; the records match the oracle's (tile-level unit, one
+    verification after the last k-step)."""
+    import torch
+    M, N, K = 384, 768, 1024
+    A = synth.normal((M, K), synth.config_seed(4, 20))
+    B = synth.normal((K, N), synth.config_seed(4, 21))
+    if dt == "bf16":
+        Aq = orc.round_bf16(A).astype(np.float32)
+        Bq = orc.round_bf16(B).astype(np.float32)
+        dA = torch.from_numpy(Aq).cuda().to(torch.bfloat16)
+        dB = torch.from_numpy(Bq).cuda().to(torch.bfloat16)
+        dtype, sc = ft.BF16, 1.0
+    else:
+        dA, sa = handle.quantize(torch.from_numpy(A).cuda(), ft.E4M3)
+        dB, sb = handle.quantize(torch.from_numpy(B).cuda(), ft.E4M3)
+        _, Aq, _ = orc.quant_e4m3(A)
+        _, Bq, _ = orc.quant_e4m3(B)
+        handle.set_fp8_scales(1.0, 1.0)
+        dtype, sc = ft.E4M3, 1.0
+    sched = _tc_sched(orc, K, dt)
+    ksteps = -(-K // sched.k_tb)
+    AB = Aq.astype(np.float64) @ Bq.astype(np.float64)
+    pos = synth.fault_positions(synth.config_seed(4, 22), 5, 3, 3, ksteps, 128, 256, M, N, ksteps)
+    mags = synth.log_uniform(synth.config_seed(4, 23), 5, 1e-2, 1e3)
+    faults = []
+    for (tm, tn, ks, r, c), g in zip(pos, mags):
+        tmax = np.abs(AB[tm * 128:(tm + 1) * 128, tn * 256:(tn + 1) * 256]).max()
+        faults.append((tm, tn, ks, r, c, float(np.float32(g * tmax))))
+    dC = torch.zeros(M, N, device="cuda")
+    rep = handle.gemm(dA, dB, dC, level=ft.FT_TILE, dtype=dtype, inject=faults)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().astype(np.float64)
+    res = orc.gemm_ft(Aq, Bq, sched, faults=faults)
+    key = lambda r: (r["tile_m"], r["tile_n"], r["row"], r["col"], r["kind"]) if isinstance(r, dict) \
+        else (r.tile_m, r.tile_n, r.row, r.col, r.kind)
+    assert sorted(map(key, rep.records)) == sorted(map(key, res.records))
+    assert rep.corrected == len(faults) == res.corrected
+    for o in res.records:
+        assert abs(o.delta) > 4 * o.tau
+    slack = np.zeros_like(C)
+    for o in res.records:
+        slack[o.row, o.col] = o.tau
+    assert np.all(np.abs(C - res.C) <= _bound(Aq, Bq, np.zeros_like(C), 1.0, 0.0, K) + slack)
+
+
+def test_tc_checksum_hit_and_seu_violation(ft, handle, orc):
+    import torch
+    M, N, K = 128, 256, 512
+    A = synth.integers((M, K), 31)
+    B = synth.integers((K, N), 32)
+    dA = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    dB = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    sched = _tc_sched(orc, K, "bf16")
+    for faults, kind in [([(0, 0, 2, 10, 20, 64.0, 1)], 2), ([(0, 0, 2, 10, 200, 64.0, 2)], 2),
+                         ([(0, 0, 1, 3, 4, 64.0), (0, 0, 5, 70, 90, 32.0)], 1)]:
+        dC = torch.zeros(M, N, device="cuda")
+        rep = handle.gemm(dA, dB, dC, level=ft.FT_TILE, dtype=ft.BF16, inject=faults)
+        torch.cuda.synchronize()
+        res = orc.gemm_ft(A, B, sched, faults=faults)
+        assert np.array_equal(dC.cpu().numpy().astype(np.float64), res.C)
+        assert [(r["row"], r["col"], r["kind"]) for r in rep.records] == \
+            [(r.row, r.col, r.kind) for r in res.records]
+        assert rep.records[0]["kind"] == kind
+        assert rep.records[0]["delta"] == res.records[0].delta
