@@ -180,7 +180,10 @@ int ftgemm_quantize(ftgemm_handle_t handle, int64_t n, const float* x, void* y,
  * handle's events are cleared first, the stream is synchronised at the end
  * and the events of this call are returned.
  * Supported: F32 with OFF/THREAD/WARP/BLOCK; BF16 and E4M3 with OFF/TILE.
- * Tensor-core path (BF16/E4M3): the CTA tile is 128 x 256, the k-step one
+ * Tensor-core path (BF16/E4M3): the MMA tile is 128 x 256; at level TILE
+ * 8 of its rows and 8 of its columns carry the checksums, so a CTA computes
+ * a 120 x 248 tile of C (128 x 256 at level OFF) and inject tile indices
+ * and in-tile offsets refer to that grid; the k-step is one
  * 128-byte k-block (64 bf16 or 128 e4m3 elements); A must have a 16-byte
  * aligned base and row stride (FTGEMM_ERR_ALIGN otherwise); the checksums
  * of the tile are verified once, after its last k-step, from tensor memory;

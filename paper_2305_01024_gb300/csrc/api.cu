@@ -323,12 +323,15 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   CK(cudaSetDevice(h->device));
   const int M = (int)m, N = (int)n, K = (int)k;
   const bool abft = level == FTGEMM_FT_TILE;
-  const int tiles_m = (M + 127) / 128, tiles_n = (N + 255) / 256;
+  // data tile of C per CTA: 128 x 256, or 120 x 248 when 8 rows and 8
+  // columns of the MMA tile carry the checksums
+  const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
+  const int tiles_m = (M + dm - 1) / dm, tiles_n = (N + dn - 1) / dn;
   const int kblk = 128 / (dtype == FTGEMM_BF16 ? 2 : 1);
   const int ksteps = (K + kblk - 1) / kblk;
   int nf = 0;
   {
-    ftgemm_schedule tcs{128, 256, kblk, 128, 256, 128, 256, 0, 1};
+    ftgemm_schedule tcs{dm, dn, kblk, dm, dn, dm, dn, 0, 1};
     int rc = upload_faults(h, inject, tcs, M, N, ksteps, tiles_m, tiles_n, level, &nf);
     if (rc) return rc;
   }
@@ -339,11 +342,12 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   const size_t oBt = 0;
   const size_t oVf = align64(oBt + fl(eb * (size_t)N * ldk));
   const size_t oWf = align64(oVf + (abft ? (size_t)tiles_m * K : 0));
+  const size_t ns = TC_CS_SLOTS;
   const size_t oVt = align64(oWf + (abft ? (size_t)tiles_n * K : 0));
-  const size_t oWt = align64(oVt + (abft ? fl(eb * (size_t)tiles_m * 16 * ldk) : 0));
-  const size_t oVs = align64(oWt + (abft ? fl(eb * (size_t)tiles_n * 16 * ldk) : 0));
-  const size_t oWs = align64(oVs + (size_t)tiles_m * 16);
-  const size_t oS0 = align64(oWs + (size_t)tiles_n * 16);
+  const size_t oWt = align64(oVt + (abft ? fl(eb * (size_t)tiles_m * ns * ldk) : 0));
+  const size_t oVs = align64(oWt + (abft ? fl(eb * (size_t)tiles_n * ns * ldk) : 0));
+  const size_t oWs = align64(oVs + (size_t)tiles_m * ns);
+  const size_t oS0 = align64(oWs + (size_t)tiles_n * ns);
   const size_t oNa = align64(oS0 + (size_t)tiles_m + tiles_n);
   const size_t oNb = align64(oNa + (size_t)M);
   const size_t oFa = align64(oNb + (size_t)N);
@@ -368,10 +372,10 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   const int BK = 128 / elem;
   TcMaps maps;
   {
-    int rc = make_map_sw128(&maps.A, A, elem, K, M, lda, BK, 128);
-    if (!rc) rc = make_map_sw128(&maps.B, w.Bt, elem, K, N, ldk, BK, 256);
-    if (!rc && abft) rc = make_map_sw128(&maps.W, w.Wt, elem, K, (uint64_t)tiles_n * 16, ldk, BK, 16);
-    if (!rc && abft) rc = make_map_sw128(&maps.V, w.Vt, elem, K, (uint64_t)tiles_m * 16, ldk, BK, 16);
+    int rc = make_map_sw128(&maps.A, A, elem, K, M, lda, BK, dm);
+    if (!rc) rc = make_map_sw128(&maps.B, w.Bt, elem, K, N, ldk, BK, dn);
+    if (!rc && abft) rc = make_map_sw128(&maps.W, w.Wt, elem, K, (uint64_t)tiles_n * ns, ldk, BK, ns);
+    if (!rc && abft) rc = make_map_sw128(&maps.V, w.Vt, elem, K, (uint64_t)tiles_m * ns, ldk, BK, ns);
     if (rc) return rc;
     if (!abft) { maps.W = maps.A; maps.V = maps.A; }
   }

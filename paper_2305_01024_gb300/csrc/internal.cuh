@@ -93,6 +93,12 @@ struct SimtMaps {
   CUtensorMap W;  // B e per column block: dims {K, blocks}, box {k_tb, NW}
 };
 
+// Tensor-core path geometry: the MMA tile is 128 x 256; with checksums on,
+// TC_CS_SLOTS of its rows carry the pieces of e^T A and as many of its
+// columns the pieces of B e, leaving a TC_DM x TC_DN data tile of C.
+constexpr int TC_BM = 128, TC_BN = 256, TC_CS_SLOTS = 8;
+constexpr int TC_DM = TC_BM - TC_CS_SLOTS, TC_DN = TC_BN - TC_CS_SLOTS;  // 120, 248
+
 // Parameters of the tensor-core GEMM (operands through TcMaps).
 struct TcParams {
   int M, N, K;
@@ -102,10 +108,10 @@ struct TcParams {
   float acc_scale;        // fp8: product of the per-tensor scales; bf16: 1
   const float* nA;        // [M] row 2-norms of A (operand values as stored)
   const float* nB;        // [N] column 2-norms of B
-  const float* froA;      // [tiles_m] Frobenius norm of each 128-row block of A
-  const float* froB;      // [tiles_n] Frobenius norm of each 256-column block of B
-  const float* wscale;    // [tiles_n * 16] multiplier of each B e piece
-  const float* vscale;    // [tiles_m * 16] multiplier of each e^T A piece
+  const float* froA;      // [tiles_m] Frobenius norm of each data-row block of A
+  const float* froB;      // [tiles_n] Frobenius norm of each data-column block of B
+  const float* wscale;    // [tiles_n * TC_CS_SLOTS] multiplier of each B e piece
+  const float* vscale;    // [tiles_m * TC_CS_SLOTS] multiplier of each e^T A piece
   float lam_u;
   const Fault* faults; int nfaults; int tiles_n;
   DevReport* rep; ftgemm_fault_record* recs;
@@ -115,18 +121,18 @@ struct TcParams {
 struct TcPrepBuffers {
   void* Bt; long long ldk;  // B^T (N x ldk), operand type; ldk also the row stride of Vt/Wt
   float* Vf; float* Wf;     // fp32 e^T A [tiles_m][K] and B e [tiles_n][K]
-  void* Vt; void* Wt;       // pieces [tiles * 16][ldk], operand type
-  float* vscale; float* wscale;  // [tiles * 16]
+  void* Vt; void* Wt;       // pieces [tiles * TC_CS_SLOTS][ldk], operand type
+  float* vscale; float* wscale;  // [tiles * TC_CS_SLOTS]
   float* s0v; float* s0w;        // [tiles] fp8 piece base scales
   float* nA; float* nB;          // [M], [N]
   float* froA; float* froB;      // [tiles_m], [tiles_n]
 };
 
 struct TcMaps {
-  CUtensorMap A;  // A:   dims {K, M}, box {k-block, 128}, 128-byte swizzle
-  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, 256}
-  CUtensorMap W;  // pieces of B e:   dims {K, 16 * tiles_n}, box {k-block, 16}
-  CUtensorMap V;  // pieces of e^T A: dims {K, 16 * tiles_m}, box {k-block, 16}
+  CUtensorMap A;  // A:   dims {K, M}, box {k-block, data rows}, 128-byte swizzle
+  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, data columns}
+  CUtensorMap W;  // pieces of B e:   dims {K, 8 * tiles_n}, box {k-block, 8}
+  CUtensorMap V;  // pieces of e^T A: dims {K, 8 * tiles_m}, box {k-block, 8}
 };
 
 }  // namespace ftg

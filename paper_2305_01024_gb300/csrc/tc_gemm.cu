@@ -5,21 +5,26 @@
 // The method is that of Wu, Zhai et al. (ICS'23): A encoded with column
 // checksums e^T A (Eq. 1), B with row checksums B e (Eq. 2), their product
 // carrying the checksums of C (Eq. 3), a flagged row and column locating a
-// corrupted element whose residual is subtracted (Section 4.2.1).  On the
-// tensor cores the checksums ride in extra MMAs of the same k-loop (Eq. 4):
-//   row checksums     C_r (128 x 16) += A_tile (128 x k) * W (k x 16)
-//   column checksums  C_c (256 x 16) += B_tile^T (256 x k) * V (k x 16)
-// where the 16 columns of W hold the pieces of w = B_J e and those of V the
-// pieces of v = e^T A_I, each piece representable in the operand type, so
-// that sum_c scale_c * piece_c reproduces the fp32 checksum vector.  The
-// column-checksum MMA swaps roles: the B tile already in shared memory is
-// the A operand.  Verification happens once per tile, in the epilogue, from
-// TMEM: fp32 sums screen every row and column, fp64 sums confirm.
+// corrupted element whose residual is subtracted (Section 4.2.1).
+//
+// On the tensor cores the encoded operands of Eq. 1-3 are formed inside one
+// MMA tile: with checksums on, the 128 x 256 MMA tile holds 120 data rows of
+// A plus 8 rows carrying the pieces of v = e^T A_I, and 248 data columns of
+// B plus 8 columns carrying the pieces of w = B_J e.  Each piece is
+// representable in the operand type and sum_c scale_c * piece_c rebuilds the
+// fp32 checksum vector.  The one MMA of each k-slice then accumulates C_IJ,
+// its row checksums A_I w (TMEM columns 248..255) and its column checksums
+// v B_J (TMEM lanes 120..127) -- Eq. 3, k-step by k-step as in Eq. 4 -- with
+// no extra MMA instruction and no extra shared-memory operand traffic; the
+// cost is the 1 - (120 * 248) / (128 * 256) = 9.2% of the tile that carries
+// checksums instead of data.  Verification runs once per tile, after its
+// last k-step, from TMEM: fp32 sums screen every row and column, fp64 sums
+// confirm the flagged ones.
 //
 // CTA: warp 0 issues TMA loads, warp 1 allocates TMEM and issues MMAs,
 // warps 2..5 read TMEM (each warp the 32 lanes its index allows), verify,
-// correct and store.  Tile 128 x 256, k-block = one 128-byte swizzle row
-// (64 bf16 or 128 fp8), STAGES-deep ring.
+// correct and store.  k-block = one 128-byte swizzle row (64 bf16 or 128
+// fp8 elements), STAGES-deep ring.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -30,21 +35,24 @@
 
 namespace ftg {
 
-template <int DT>
+template <int DT, bool ABFT>
 struct TcCfg {
-  static constexpr int BM = 128, BN = 256;
-  static constexpr int ELEM = DT == 0 ? 2 : 1;      // bytes per operand element
-  static constexpr int BK = 128 / ELEM;             // one 128-byte row per k-block
-  static constexpr int UK = 32 / ELEM;              // K per MMA instruction
+  static constexpr int BM = TC_BM, BN = TC_BN;        // MMA tile
+  static constexpr int CSR = ABFT ? TC_CS_SLOTS : 0;  // checksum rows of A / columns of B
+  static constexpr int DM = BM - CSR, DN = BN - CSR;  // data rows / columns of C per tile
+  static constexpr int ELEM = DT == 0 ? 2 : 1;        // bytes per operand element
+  static constexpr int BK = 128 / ELEM;               // one 128-byte row per k-block
+  static constexpr int UK = 32 / ELEM;                // K per MMA instruction
   static constexpr int STAGES = 4;
-  static constexpr int A_BYTES = BM * 128;          // 16 KB
-  static constexpr int B_BYTES = BN * 128;          // 32 KB
-  static constexpr int CS_BYTES = 16 * 128;         // 2 KB: 16 checksum pieces x k-block
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES + 2 * CS_BYTES;
+  static constexpr int A_BYTES = BM * 128;            // 16 KB
+  static constexpr int B_BYTES = BN * 128;            // 32 KB
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int THREADS = 192;
-  static constexpr uint32_t TMEM_COLS = 512;
-  static constexpr uint32_t COL_ACC = 0, COL_CR = 256, COL_CC0 = 288, COL_CC1 = 320;
-  static constexpr int NPIECE = DT == 0 ? 3 : 5;   // checksum pieces in use
+  static constexpr uint32_t TMEM_COLS = 256;
+  static constexpr int NPIECE = DT == 0 ? 3 : 5;      // checksum pieces in use
+  static_assert(!ABFT || NPIECE <= CSR, "pieces must fit the checksum slots");
+  // the checksum rows start on a 1024-byte (8-row) swizzle boundary
+  static_assert((DM * 128) % 1024 == 0 && (DN * 128) % 1024 == 0, "checksum slots misaligned");
 };
 
 // instruction descriptor: fp32 accumulator, K-major A and B, M x N
@@ -67,35 +75,38 @@ struct TcSmemTail {
   int abort;
   int nr, nc;
   unsigned long long bestr, bestc;
-  int fix_row, fix_col, reset_side, reset_idx;
-  double fix_delta, reset_value;
-  float colpart[4][256];  // per epilogue warp partial column sums
-  float crow[128];        // row checksums (reconstructed, fp32 screen)
-  float ccol[256];        // column checksums
-  float tr[128], tc[256]; // thresholds
+  int fix_row, fix_col;
+  double fix_delta;
+  float colpart[4][256];           // per epilogue warp partial column sums (data rows)
+  float ccp[TC_CS_SLOTS][256];     // column-checksum pieces, TMEM lanes 120..127
+  float crow[128];                 // row checksums
+  float ccol[256];                 // column checksums
+  float cradj[128], ccadj[256];    // injected offsets of the checksums
+  float tr[128], tc[256];          // thresholds
   int flag_r[128], flag_c[256];
-  double sum_r[128], sum_c[256];  // fp64 confirmation sums (flagged only)
+  double sum_r[128], sum_c[256];   // fp64 confirmation sums
 };
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 template <int DT, bool ABFT>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmV,
                    const TcParams p) {
-  using Cfg = TcCfg<DT>;
-  constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, UK = Cfg::UK, S = Cfg::STAGES;
+  using Cfg = TcCfg<DT, ABFT>;
+  constexpr int BM = Cfg::BM, BN = Cfg::BN, DM = Cfg::DM, DN = Cfg::DN, BK = Cfg::BK, UK = Cfg::UK;
+  constexpr int S = Cfg::STAGES, CSR = Cfg::CSR;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~uintptr_t(1023));
   TcSmemTail& T = *reinterpret_cast<TcSmemTail*>(base + S * Cfg::STAGE_BYTES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile_m = blockIdx.y, tile_n = blockIdx.x;
-  const int row0 = tile_m * BM, col0 = tile_n * BN;
+  const int row0 = tile_m * DM, col0 = tile_n * DN;
   const int nkb = (p.K + BK - 1) / BK;
   auto sA = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
   auto sB = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
-  auto sW = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES + Cfg::B_BYTES; };
-  auto sV = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES + Cfg::B_BYTES + Cfg::CS_BYTES; };
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -106,6 +117,7 @@ __global__ void __launch_bounds__(192, 1)
     T.abort = 0;
     T.fix_row = -1;
     T.fix_col = -1;
+    T.fix_delta = 0.0;
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -118,46 +130,36 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = T.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer ---------------------------------------------------
+    // ---- TMA producer: data rows of A and B^T, then the checksum slots -----
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
-    const uint32_t bytes = Cfg::A_BYTES + Cfg::B_BYTES + (ABFT ? 2 * Cfg::CS_BYTES : 0);
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % S;
       if (kb >= S && !mbar_wait(&T.empty[s], (uint32_t)((kb / S) - 1) & 1u)) {
         atomicExch(&T.abort, 1);
         break;
       }
-      mbar_arrive_expect_tx(&T.full[s], bytes);
+      mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
       tma_load_2d(sA(s), &tmA, &T.full[s], kb * BK, row0);
       tma_load_2d(sB(s), &tmB, &T.full[s], kb * BK, col0);
       if constexpr (ABFT) {
-        tma_load_2d(sW(s), &tmW, &T.full[s], kb * BK, tile_n * 16);
-        tma_load_2d(sV(s), &tmV, &T.full[s], kb * BK, tile_m * 16);
+        tma_load_2d(sA(s) + DM * 128, &tmV, &T.full[s], kb * BK, tile_m * CSR);
+        tma_load_2d(sB(s) + DN * 128, &tmW, &T.full[s], kb * BK, tile_n * CSR);
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer -----------------------------------------------------
-    constexpr uint32_t id_main = tc_idesc(DT, BM, BN);
-    constexpr uint32_t id_cs = tc_idesc(DT, 128, 16);
+    // ---- MMA issuer: one 128 x 256 MMA per 32-byte k-slice ----------------
+    constexpr uint32_t idesc = tc_idesc(DT, BM, BN);
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % S;
       if (!mbar_wait(&T.full[s], (uint32_t)(kb / S) & 1u)) { ok = false; break; }
       tc_fence_after();
       const uint64_t da = smem_desc_sw128(sA(s)), db = smem_desc_sw128(sB(s));
-      const uint64_t dw = smem_desc_sw128(sW(s)), dv = smem_desc_sw128(sV(s));
-      const uint64_t db_hi = smem_desc_sw128(sB(s) + 128 * 128);  // B rows 128..255
 #pragma unroll
       for (int kk = 0; kk < BK / UK; ++kk) {
-        const uint32_t acc = (kb | kk) != 0;
         const uint64_t step = (uint64_t)(kk * 32) >> 4;  // 32 bytes per instruction
-        tc_mma<DT>(tmem + Cfg::COL_ACC, da + step, db + step, id_main, acc);
-        if constexpr (ABFT) {
-          tc_mma<DT>(tmem + Cfg::COL_CR, da + step, dw + step, id_cs, acc);
-          tc_mma<DT>(tmem + Cfg::COL_CC0, db + step, dv + step, id_cs, acc);
-          tc_mma<DT>(tmem + Cfg::COL_CC1, db_hi + step, dv + step, id_cs, acc);
-        }
+        tc_mma<DT>(tmem, da + step, db + step, idesc, (kb | kk) != 0);
       }
       tc_commit(&T.empty[s]);  // the stage is free once these MMAs completed
     }
@@ -166,26 +168,32 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp >= 2) {
     // ---- epilogue -------------------------------------------------------
     const int lq = warp & 3;            // TMEM lane quarter this warp may access
-    const int r = lq * 32 + lane;       // tile-local row == TMEM lane
+    const int r = lq * 32 + lane;       // tile row == TMEM lane
     const int gr = row0 + r;
+    const bool data_row = r < DM;
     const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
-    bool done = mbar_wait(&T.acc_full, 0);
-    if (!done) atomicExch(&T.abort, 1);
+    if (!mbar_wait(&T.acc_full, 0)) atomicExch(&T.abort, 1);
     tc_fence_after();
     const float alpha = p.alpha, beta = p.beta;
     const float acc_scale = p.acc_scale;  // fp8: product of the per-tensor scales
+
+    if constexpr (ABFT) {
+      T.cradj[r] = 0.f;
+      T.ccadj[r] = 0.f;
+      T.ccadj[128 + r] = 0.f;
+      epi_bar();
+    }
     // ----- scheduled faults of this tile (Section 5.3) -----
     // Verification runs once per tile after its last k-step; the accumulation
     // being additive, an offset is applied to the tensor-memory accumulator
     // here, where the k-step it was scheduled for only changes rounding.
-    float cr_adj = 0.f, cc_adj0 = 0.f, cc_adj1 = 0.f;
     if (p.nfaults > 0) {
       const int my_tile = tile_m * p.tiles_n + tile_n;
       for (int f = first_fault(p.faults, p.nfaults, my_tile); f < p.nfaults && p.faults[f].tile == my_tile; ++f) {
         const Fault F = p.faults[f];
         if (F.target == T_ACC) {
           if ((F.row >> 5) == lq) {  // warp-uniform: this warp owns the lane
-            const uint32_t a = tl + Cfg::COL_ACC + (uint32_t)(F.col & ~15);
+            const uint32_t a = tl + (uint32_t)(F.col & ~15);
             float v[16];
             tmem_ld16(a, v);
             tmem_wait_ld();
@@ -197,58 +205,47 @@ __global__ void __launch_bounds__(192, 1)
             tmem_st16(a, v);
             tmem_wait_st();
           }
-        } else if (F.target == T_ROWSUM) {
-          if (r == F.row) cr_adj += F.delta;
-        } else {
-          if (r == (F.col & 127)) {
-            if (F.col < 128) cc_adj0 += F.delta;
-            else cc_adj1 += F.delta;
+        } else if constexpr (ABFT) {
+          if (r == 0) {
+            if (F.target == T_ROWSUM) T.cradj[F.row] += F.delta;
+            else T.ccadj[F.col] += F.delta;
           }
         }
       }
     }
+
     if constexpr (ABFT) {
+      epi_bar();
       // ----- fp32 screen -----
-      // row checksum of this row: sum_c piece_scale * C_r[r][c]
-      float cs[16];
-      tmem_ld16(tl + Cfg::COL_CR, cs);
-      tmem_wait_ld();
-      float crow = 0.f;
-#pragma unroll
-      for (int c = 0; c < Cfg::NPIECE; ++c) crow += cs[c] * p.wscale[(size_t)tile_n * 16 + c];
-      crow += cr_adj;
-      T.crow[r] = crow;
-      // column checksums: lane quarter lq holds columns lq*32.. of each half
-      tmem_ld16(tl + Cfg::COL_CC0, cs);
-      tmem_wait_ld();
-      float cc0 = 0.f;
-#pragma unroll
-      for (int c = 0; c < Cfg::NPIECE; ++c) cc0 += cs[c] * p.vscale[(size_t)tile_m * 16 + c];
-      tmem_ld16(tl + Cfg::COL_CC1, cs);
-      tmem_wait_ld();
-      float cc1 = 0.f;
-#pragma unroll
-      for (int c = 0; c < Cfg::NPIECE; ++c) cc1 += cs[c] * p.vscale[(size_t)tile_m * 16 + c];
-      T.ccol[r] = cc0 + cc_adj0;
-      T.ccol[128 + r] = cc1 + cc_adj1;
-      // row sums (two-term fp32 summation) and partial column sums
-      float rs = 0.f, rc = 0.f;
+      float rs = 0.f, rc = 0.f, crow = 0.f;
       for (int ch = 0; ch < BN / 16; ++ch) {
         float v[16];
-        tmem_ld16(tl + Cfg::COL_ACC + ch * 16, v);
+        tmem_ld16(tl + ch * 16, v);
         tmem_wait_ld();
+        // row sum over the data columns (two-term fp32 summation); the row
+        // checksum pieces sit in columns DN..DN+NPIECE-1
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const float y = v[q] - rc;
-          const float t = rs + y;
-          rc = (t - rs) - y;
-          rs = t;
+          const int c = ch * 16 + q;
+          if (c < DN) {
+            const float y = v[q] - rc;
+            const float t = rs + y;
+            rc = (t - rs) - y;
+            rs = t;
+          } else if (c - DN < Cfg::NPIECE) {
+            crow = fmaf(v[q], p.wscale[(size_t)tile_n * CSR + (c - DN)], crow);
+          }
         }
-        // warp partial column sums of these 16 columns: a reduce-scatter
-        // over the lanes leaves lanes 2q and 2q+1 with column idx(q)
+        // the column checksum pieces sit in lanes DM..DM+NPIECE-1
+        if (r >= DM && r - DM < Cfg::NPIECE) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
+        }
+        // warp partial column sums over the data rows: a reduce-scatter over
+        // the lanes leaves lanes 2q and 2q+1 with column idx(q)
         float w[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) w[q] = v[q];
+        for (int q = 0; q < 16; ++q) w[q] = data_row ? v[q] : 0.f;
 #pragma unroll
         for (int lev = 16, half = 8; lev >= 2; lev >>= 1, half >>= 1) {
           const bool up = (lane & lev) != 0;
@@ -266,45 +263,53 @@ __global__ void __launch_bounds__(192, 1)
           T.colpart[lq][ch * 16 + idx] = w[0];
         }
       }
-      // thresholds
-      const float nAr = (gr < p.M) ? p.nA[gr] : 0.f;
-      T.tr[r] = p.lam_u * nAr * p.froB[tile_n];
+      crow += T.cradj[r];
+      T.crow[r] = crow;
+      T.tr[r] = (data_row && gr < p.M) ? p.lam_u * p.nA[gr] * p.froB[tile_n] : 0.f;
+      T.flag_r[r] = data_row && fabsf(rs - crow) > T.tr[r];
+      epi_bar();
       for (int c = r; c < BN; c += 128) {
-        const int gc = col0 + c;
-        T.tc[c] = p.lam_u * p.froA[tile_m] * ((gc < p.N) ? p.nB[gc] : 0.f);
+        int fl = 0;
+        float cc = 0.f, tcv = 0.f;
+        if (c < DN) {
+#pragma unroll
+          for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], p.vscale[(size_t)tile_m * CSR + q], cc);
+          cc += T.ccadj[c];
+          const int gc = col0 + c;
+          tcv = gc < p.N ? p.lam_u * p.froA[tile_m] * p.nB[gc] : 0.f;
+          const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
+          fl = fabsf(s - cc) > tcv;
+        }
+        T.ccol[c] = cc;
+        T.tc[c] = tcv;
+        T.flag_c[c] = fl;
       }
-      T.flag_r[r] = fabsf(rs - crow) > T.tr[r];
-    }
-    // epilogue-only named barrier among the 4 epilogue warps
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if constexpr (ABFT) {
-      for (int c = r; c < BN; c += 128) {
-        const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
-        T.flag_c[c] = fabsf(s - T.ccol[c]) > T.tc[c];
-      }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      epi_bar();
       int any = 0;
       for (int c = lane; c < 128; c += 32) any |= T.flag_r[c];
       for (int c = lane; c < 256; c += 32) any |= T.flag_c[c];
       any = __any_sync(0xffffffffu, any);
-      if (any) {
+      if (any) {  // the same in all four epilogue warps: the flags are shared
         // ----- fp64 confirmation of every screened row / column -----
-        if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; T.fix_row = -1; T.reset_side = -1; }
+        if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
         for (int c = r; c < BN; c += 128) T.sum_c[c] = 0.0;
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        epi_bar();
         double sr = 0.0;
         for (int ch = 0; ch < BN / 16; ++ch) {
           float v[16];
-          tmem_ld16(tl + Cfg::COL_ACC + ch * 16, v);
+          tmem_ld16(tl + ch * 16, v);
           tmem_wait_ld();
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
-            sr += (double)v[q];
-            if (T.flag_c[ch * 16 + q]) atomicAdd(&T.sum_c[ch * 16 + q], (double)v[q]);
+            const int c = ch * 16 + q;
+            if (c < DN) {
+              sr += (double)v[q];
+              if (data_row && T.flag_c[c]) atomicAdd(&T.sum_c[c], (double)v[q]);
+            }
           }
         }
         T.sum_r[r] = sr;
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        epi_bar();
         if (T.flag_r[r]) {
           const double d = sr - (double)T.crow[r];
           if (fabs(d) > (double)T.tr[r]) {
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(192, 1)
             atomicMax(&T.bestr, flag_key(flag_score((float)d, T.tr[r]), r));
           }
         }
-        for (int c = r; c < BN; c += 128) {
+        for (int c = r; c < DN; c += 128) {
           if (T.flag_c[c]) {
             const double d = T.sum_c[c] - (double)T.ccol[c];
             if (fabs(d) > (double)T.tc[c]) {
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(192, 1)
             }
           }
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        epi_bar();
         if (r == 0 && (T.nr | T.nc)) {
           const int nr = T.nr, nc = T.nc;
           const int ir = nr ? key_index(T.bestr) : -1, jc = nc ? key_index(T.bestc) : -1;
@@ -348,51 +353,49 @@ __global__ void __launch_bounds__(192, 1)
           }
           report_event(p.rep, p.recs, rec);
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        epi_bar();
       }
     }
     // ----- alpha * acc + beta * C, store -----
+    // every lane reads tensor memory (the loads are warp-collective); only
+    // data rows inside the matrix store, and only data columns
     const int fr = ABFT ? T.fix_row : -1;
     const int fc = ABFT ? T.fix_col : -1;
     const double fd = ABFT ? T.fix_delta : 0.0;
-    // every lane reads tensor memory (the loads are warp-collective); only
-    // rows inside the matrix store
-    {
-      const bool row_ok = gr < p.M;
-      float* crow_ptr = p.C + (long long)(row_ok ? gr : 0) * p.ldc + col0;
-      for (int ch = 0; ch < BN / 16; ++ch) {
-        float v[16];
-        tmem_ld16(tl + Cfg::COL_ACC + ch * 16, v);
-        tmem_wait_ld();
-        if (!row_ok) continue;
-        if (ABFT && r == fr && fc >= ch * 16 && fc < ch * 16 + 16) {
+    const bool row_ok = data_row && gr < p.M;
+    float* crow_ptr = p.C + (long long)(row_ok ? gr : 0) * p.ldc + col0;
+    const float sc = alpha * acc_scale;
+    for (int ch = 0; ch < BN / 16; ++ch) {
+      float v[16];
+      tmem_ld16(tl + ch * 16, v);
+      tmem_wait_ld();
+      if (!row_ok) continue;
+      if (ABFT && r == fr && fc >= ch * 16 && fc < ch * 16 + 16) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (ch * 16 + q == fc) v[q] = (float)((double)v[q] - fd);
-        }
-        const int c0 = col0 + ch * 16;
-        if (p.c_vec && c0 + 15 < p.N) {
+        for (int q = 0; q < 16; ++q)
+          if (ch * 16 + q == fc) v[q] = (float)((double)v[q] - fd);
+      }
 #pragma unroll
-          for (int q = 0; q < 16; q += 4) {
-            float4 o;
-            if (beta != 0.f) {
-              const float4 ci = *reinterpret_cast<const float4*>(crow_ptr + ch * 16 + q);
-              o = make_float4(fmaf(beta, ci.x, alpha * acc_scale * v[q]),
-                              fmaf(beta, ci.y, alpha * acc_scale * v[q + 1]),
-                              fmaf(beta, ci.z, alpha * acc_scale * v[q + 2]),
-                              fmaf(beta, ci.w, alpha * acc_scale * v[q + 3]));
-            } else {
-              o = make_float4(alpha * acc_scale * v[q], alpha * acc_scale * v[q + 1],
-                              alpha * acc_scale * v[q + 2], alpha * acc_scale * v[q + 3]);
-            }
-            *reinterpret_cast<float4*>(crow_ptr + ch * 16 + q) = o;
+      for (int q = 0; q < 16; q += 4) {
+        const int c = ch * 16 + q;  // tile column of this group of 4
+        if (c >= DN) break;
+        const int gc = col0 + c;
+        float* dst = crow_ptr + c;
+        // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
+        if (p.c_vec && c + 3 < DN && gc + 3 < p.N) {
+          float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
+          if (beta != 0.f) {
+            const float4 ci = *reinterpret_cast<const float4*>(dst);
+            o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
+            o.z = fmaf(beta, ci.z, o.z); o.w = fmaf(beta, ci.w, o.w);
           }
+          *reinterpret_cast<float4*>(dst) = o;
         } else {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            if (c0 + q < p.N) {
-              const float o = alpha * acc_scale * v[q];
-              crow_ptr[ch * 16 + q] = beta != 0.f ? fmaf(beta, crow_ptr[ch * 16 + q], o) : o;
+          for (int e = 0; e < 4; ++e) {
+            if (c + e < DN && gc + e < p.N) {
+              const float o = sc * v[q + e];
+              dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
             }
           }
         }
@@ -411,12 +414,12 @@ __global__ void __launch_bounds__(192, 1)
 
 template <int DT, bool ABFT>
 cudaError_t launch_tc_impl(const TcMaps& maps, const TcParams& p, cudaStream_t st) {
-  using Cfg = TcCfg<DT>;
+  using Cfg = TcCfg<DT, ABFT>;
   const size_t smem = 1024 + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES + sizeof(TcSmemTail);
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<DT, ABFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((p.N + Cfg::BN - 1) / Cfg::BN, (p.M + Cfg::BM - 1) / Cfg::BM);
+  dim3 grid((p.N + Cfg::DN - 1) / Cfg::DN, (p.M + Cfg::DM - 1) / Cfg::DM);
   tc_gemm_kernel<DT, ABFT><<<grid, Cfg::THREADS, smem, st>>>(maps.A, maps.B, maps.W, maps.V, p);
   return cudaGetLastError();
 }
@@ -424,11 +427,6 @@ cudaError_t launch_tc_impl(const TcMaps& maps, const TcParams& p, cudaStream_t s
 cudaError_t launch_tc_gemm(int dt, bool abft, const TcMaps& maps, const TcParams& p, cudaStream_t st) {
   if (dt == 0) return abft ? launch_tc_impl<0, true>(maps, p, st) : launch_tc_impl<0, false>(maps, p, st);
   return abft ? launch_tc_impl<1, true>(maps, p, st) : launch_tc_impl<1, false>(maps, p, st);
-}
-
-size_t tc_smem_bytes(int dt) {
-  return dt == 0 ? 1024 + (size_t)TcCfg<0>::STAGES * TcCfg<0>::STAGE_BYTES + sizeof(TcSmemTail)
-                 : 1024 + (size_t)TcCfg<1>::STAGES * TcCfg<1>::STAGE_BYTES + sizeof(TcSmemTail);
 }
 
 }  // namespace ftg

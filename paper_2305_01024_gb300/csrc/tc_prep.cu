@@ -1,9 +1,10 @@
 // tc_prep.cu -- encoding pass of the tensor-core path and the operand
 // quantizer.
 //
-// Encoding (Eq. 1-2 of Wu, Zhai et al., ICS'23) for a 128 x 256 output tile:
-//   v_I[k] = sum_{i in I} A[i][k]   (e^T A per 128-row block of A)
-//   w_J[k] = sum_{j in J} B[k][j]   (B e per 256-column block of B)
+// Encoding (Eq. 1-2 of Wu, Zhai et al., ICS'23) for a TC_DM x TC_DN
+// (120 x 248) data tile of C:
+//   v_I[k] = sum_{i in I} A[i][k]   (e^T A per 120-row block of A)
+//   w_J[k] = sum_{j in J} B[k][j]   (B e per 248-column block of B)
 // accumulated in fp32 from the operand values as stored, then split into
 // pieces representable in the operand type so the MMA can carry them:
 //   bf16: x = hi + mid + lo, each piece a bf16 (24 significant bits in all);
@@ -116,14 +117,15 @@ __global__ void tc_blockscale_kernel(const float* __restrict__ S, int K, float* 
   }
 }
 
-// Pieces of S[b][k] into P[(b*16 + c)][k] (c < 16, unused pieces zero) and
-// their multipliers scale[b*16 + c].
+// Pieces of S[b][k] into P[(b*TC_CS_SLOTS + c)][k] (unused slots zero) and
+// their multipliers scale[b*TC_CS_SLOTS + c].
 template <int DT>
 __global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, long long ldp,
                                  void* __restrict__ P, float* __restrict__ scale, const float* __restrict__ s0) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
-  if (blockIdx.x == 0 && threadIdx.x < 16) {
+  constexpr int NS = TC_CS_SLOTS;
+  if (blockIdx.x == 0 && threadIdx.x < NS) {
     const int c = threadIdx.x;
     float m = 0.f;
     if (DT == 0) {
@@ -133,7 +135,7 @@ __global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, lon
       for (int q = 0; q < c; ++q) m *= 16.f;
       m = 1.f / m;
     }
-    scale[b * 16 + c] = m;
+    scale[b * NS + c] = m;
   }
   if (k >= K) return;
   float x = S[(long long)b * K + k];
@@ -144,14 +146,14 @@ __global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, lon
     const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
     const float r2 = r1 - __bfloat162float(mid);
     const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < NS; ++c) {
       const __nv_bfloat16 v = c == 0 ? hi : c == 1 ? mid : c == 2 ? lo : __float2bfloat16_rn(0.f);
-      out[(long long)(b * 16 + c) * ldp + k] = v;
+      out[(long long)(b * NS + c) * ldp + k] = v;
     }
   } else {
     __nv_fp8_storage_t* out = reinterpret_cast<__nv_fp8_storage_t*>(P);
     float sc = s0[b];
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < NS; ++c) {
       __nv_fp8_storage_t q = 0;
       if (c < 5) {
         q = __nv_cvt_float_to_fp8(x * sc, __NV_SATFINITE, __NV_E4M3);
@@ -160,7 +162,7 @@ __global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, lon
         x -= float(qq) / sc;
         sc *= 16.f;
       }
-      out[(long long)(b * 16 + c) * ldp + k] = q;
+      out[(long long)(b * NS + c) * ldp + k] = q;
     }
   }
 }
@@ -196,7 +198,6 @@ __global__ void cast_e4m3_kernel(const float* __restrict__ x, long long n, const
 // caller's buffers (see TcPrepBuffers).
 cudaError_t launch_tc_prep(int dt, const void* A, long long lda, const void* B, long long ldb, int M, int N,
                            int K, bool abft, const TcPrepBuffers& w, int* launches, cudaStream_t st) {
-  const int tiles_m = (M + 127) / 128, tiles_n = (N + 255) / 256;
   {
     dim3 g((N + 31) / 32, (K + 31) / 32);
     if (dt == 0)
@@ -206,6 +207,7 @@ cudaError_t launch_tc_prep(int dt, const void* A, long long lda, const void* B, 
     ++*launches;
   }
   if (!abft) return cudaGetLastError();
+  const int tiles_m = (M + TC_DM - 1) / TC_DM, tiles_n = (N + TC_DN - 1) / TC_DN;
   auto blocksum = [&](const void* X, long long ldx, int R, int bs, float* S) {
     dim3 g((K + 255) / 256, (R + bs - 1) / bs);
     if (dt == 0) tc_blocksum_kernel<0><<<g, 256, 0, st>>>(X, ldx, R, K, bs, S);
@@ -227,12 +229,12 @@ cudaError_t launch_tc_prep(int dt, const void* A, long long lda, const void* B, 
     else tc_pieces_kernel<1><<<g, 256, 0, st>>>(S, nb, K, w.ldk, P, scale, s0);
     ++*launches;
   };
-  blocksum(A, lda, M, 128, w.Vf);
-  blocksum(w.Bt, w.ldk, N, 256, w.Wf);
+  blocksum(A, lda, M, TC_DM, w.Vf);
+  blocksum(w.Bt, w.ldk, N, TC_DN, w.Wf);
   rownorm(A, lda, M, w.nA);
   rownorm(w.Bt, w.ldk, N, w.nB);
-  tc_blockfro_kernel<<<(tiles_m + 127) / 128, 128, 0, st>>>(w.nA, M, 128, tiles_m, w.froA);
-  tc_blockfro_kernel<<<(tiles_n + 127) / 128, 128, 0, st>>>(w.nB, N, 256, tiles_n, w.froB);
+  tc_blockfro_kernel<<<(tiles_m + 127) / 128, 128, 0, st>>>(w.nA, M, TC_DM, tiles_m, w.froA);
+  tc_blockfro_kernel<<<(tiles_n + 127) / 128, 128, 0, st>>>(w.nB, N, TC_DN, tiles_n, w.froB);
   *launches += 2;
   pieces(w.Vf, tiles_m, w.Vt, w.vscale, w.s0v);
   pieces(w.Wf, tiles_n, w.Wt, w.wscale, w.s0w);

@@ -27,10 +27,15 @@ def handle(ft):
     h.close()
 
 
+# With checksums on, 8 rows and 8 columns of the 128 x 256 MMA tile carry the
+# checksum pieces: a CTA computes a 120 x 248 tile of C.
+TDM, TDN = 120, 248
+
+
 def _tc_sched(orc, K, dt):
     bk = 64 if dt == "bf16" else 128
     nks = -(-K // bk)
-    return orc.Schedule(m_tb=128, n_tb=256, k_tb=bk, m_w=128, n_w=256, m_t=128, n_t=256,
+    return orc.Schedule(m_tb=TDM, n_tb=TDN, k_tb=bk, m_w=TDM, n_w=TDN, m_t=TDM, n_t=TDN,
                         cadence=nks, split_k=1, level=orc.TILE, lam=32.0, u=U32)
 
 
@@ -145,11 +150,11 @@ def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
     sched = _tc_sched(orc, K, dt)
     ksteps = -(-K // sched.k_tb)
     AB = Aq.astype(np.float64) @ Bq.astype(np.float64)
-    pos = synth.fault_positions(synth.config_seed(4, 22), 5, 3, 3, ksteps, 128, 256, M, N, ksteps)
+    pos = synth.fault_positions(synth.config_seed(4, 22), 5, 3, 3, ksteps, TDM, TDN, M, N, ksteps)
     mags = synth.log_uniform(synth.config_seed(4, 23), 5, 1e-2, 1e3)
     faults = []
     for (tm, tn, ks, r, c), g in zip(pos, mags):
-        tmax = np.abs(AB[tm * 128:(tm + 1) * 128, tn * 256:(tn + 1) * 256]).max()
+        tmax = np.abs(AB[tm * TDM:(tm + 1) * TDM, tn * TDN:(tn + 1) * TDN]).max()
         faults.append((tm, tn, ks, r, c, float(np.float32(g * tmax))))
     dC = torch.zeros(M, N, device="cuda")
     rep = handle.gemm(dA, dB, dC, level=ft.FT_TILE, dtype=dtype, inject=faults)
