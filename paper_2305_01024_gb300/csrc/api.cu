@@ -391,7 +391,7 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   p.lam_u = (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24));
   p.faults = nf > 0 ? h->d_faults : nullptr;
   p.nfaults = nf;
-  p.tiles_n = tiles_n;
+  p.tiles_m = tiles_m; p.tiles_n = tiles_n;
   p.rep = h->rep; p.recs = h->recs;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (h->timing) {

@@ -98,6 +98,7 @@ struct SimtMaps {
 // columns the pieces of B e, leaving a TC_DM x TC_DN data tile of C.
 constexpr int TC_BM = 128, TC_BN = 256, TC_CS_SLOTS = 8;
 constexpr int TC_DM = TC_BM - TC_CS_SLOTS, TC_DN = TC_BN - TC_CS_SLOTS;  // 120, 248
+constexpr int TC_GROUP_M = 16;  // tile rows per raster group
 
 // Parameters of the tensor-core GEMM (operands through TcMaps).
 struct TcParams {
@@ -113,7 +114,7 @@ struct TcParams {
   const float* wscale;    // [tiles_n * TC_CS_SLOTS] multiplier of each B e piece
   const float* vscale;    // [tiles_m * TC_CS_SLOTS] multiplier of each e^T A piece
   float lam_u;
-  const Fault* faults; int nfaults; int tiles_n;
+  const Fault* faults; int nfaults; int tiles_m, tiles_n;
   DevReport* rep; ftgemm_fault_record* recs;
 };
 

@@ -102,7 +102,16 @@ __global__ void __launch_bounds__(192, 1)
                                                          ~uintptr_t(1023));
   TcSmemTail& T = *reinterpret_cast<TcSmemTail*>(base + S * Cfg::STAGE_BYTES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile_m = blockIdx.y, tile_n = blockIdx.x;
+  // grouped raster: consecutive CTAs walk down TC_GROUP_M tile rows before
+  // moving one tile column right, so a wave shares k-slices of A and B in L2
+  int tile_m, tile_n;
+  {
+    const int id = blockIdx.x, per_group = TC_GROUP_M * p.tiles_n;
+    const int first_m = (id / per_group) * TC_GROUP_M;
+    const int gsize = min(p.tiles_m - first_m, TC_GROUP_M);
+    tile_m = first_m + (id % per_group) % gsize;
+    tile_n = (id % per_group) / gsize;
+  }
   const int row0 = tile_m * DM, col0 = tile_n * DN;
   const int nkb = (p.K + BK - 1) / BK;
   auto sA = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
@@ -419,7 +428,7 @@ cudaError_t launch_tc_impl(const TcMaps& maps, const TcParams& p, cudaStream_t s
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<DT, ABFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((p.N + Cfg::DN - 1) / Cfg::DN, (p.M + Cfg::DM - 1) / Cfg::DM);
+  const int grid = p.tiles_m * p.tiles_n;
   tc_gemm_kernel<DT, ABFT><<<grid, Cfg::THREADS, smem, st>>>(maps.A, maps.B, maps.W, maps.V, p);
   return cudaGetLastError();
 }
