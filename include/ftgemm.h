@@ -106,16 +106,18 @@ typedef struct {
  *         was corrupted; it is reset from the data and C is left alone).
  * delta: the amount subtracted (kind 0) or the checksum's offset (kind 2).
  * residual_r / residual_c: the residuals of the flagged row / column.
- * tau: the sum of the thresholds of the flagged row and column.            */
+ * tau: the sum of the thresholds of the flagged row and column.
+ * problem: index of the problem in a grouped call (0 otherwise).           */
 typedef struct {
   int32_t tile_m, tile_n, kstep, row, col, kind;
+  int32_t problem, reserved;
   double delta, residual_r, residual_c, tau;
 } ftgemm_fault_record;
 
 /* Caller-owned report.  records points to `capacity` caller-owned slots.
  * On return n_records is the number of events (may exceed capacity, then
  * overflow = 1 and only the first `capacity` in sorted order are written).
- * Records are sorted by (tile_m, tile_n, kstep, row, col, kind).            */
+ * Records are sorted by (problem, tile_m, tile_n, kstep, row, col, kind).   */
 typedef struct {
   int64_t detected;      /* unit-periods with at least one flagged residual */
   int64_t corrected;     /* kind 0 */
@@ -195,6 +197,59 @@ int ftgemm_gemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                 int64_t ldb, double beta, float* C, int64_t ldc,
                 ftgemm_dtype dtype, ftgemm_ft_level ft_level,
                 const ftgemm_inject_spec* inject, ftgemm_report* report);
+
+/* ---- grouped GEMM (tensor-core path) ----------------------------------- */
+
+/* One GEMM of a group: C = alpha * A * B + beta * C, all device pointers,
+ * row-major; A is m x k and B is k x n of the group's dtype, C is fp32. */
+typedef struct {
+  int64_t m, n, k;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  float* C;
+  int64_t ldc;
+  double alpha, beta;
+  float scale_a, scale_b; /* E4M3: per-tensor scales of A and B (ignored for BF16) */
+} ftgemm_problem;
+
+typedef struct ftgemm_group* ftgemm_group_t;
+
+/* Prepare a group of GEMMs for one persistent launch (no counterpart in the
+ * paper, whose experiments run one GEMM at a time; the tile shapes and the
+ * online ABFT per tile are those of ftgemm_gemm's tensor-core path).  The
+ * problems (host array, copied) fix the operand pointers and shapes; the
+ * group owns the device problem table, the TMA descriptors and the encode
+ * workspace (allocated here, synchronously).  dtype: BF16 or E4M3; level:
+ * OFF or TILE.  The threshold in force on the handle is captured here.
+ * Problems are scheduled longest-K first; records report the caller's
+ * problem index.  Errors: FTGEMM_ERR_ARG (sizes, NULL, leading dimensions),
+ * FTGEMM_ERR_ALIGN (A not 16-byte aligned), FTGEMM_ERR_UNSUPPORTED,
+ * FTGEMM_ERR_CUDA (allocation). */
+int ftgemm_group_create(ftgemm_handle_t handle, int32_t count, const ftgemm_problem* problems,
+                        ftgemm_dtype dtype, ftgemm_ft_level ft_level, ftgemm_group_t* out);
+
+/* Tile grid of each problem (caller arrays of `count`): 120 x 248 tiles of C
+ * at level TILE, 128 x 256 at OFF. */
+int ftgemm_group_tiles(ftgemm_group_t group, int32_t* tiles_m, int32_t* tiles_n);
+
+/* Faults applied by every later ftgemm_grouped_gemm of the group: problem[i]
+ * is the problem of fault i, the other fields as in ftgemm_gemm's inject
+ * (tile indices and in-tile offsets on that problem's grid).  NULL or n = 0
+ * clears them.  Synchronises the handle's stream; not for use while a
+ * stream capture is in progress. */
+int ftgemm_group_set_faults(ftgemm_group_t group, const int32_t* problem, const ftgemm_inject_spec* inject);
+
+/* Enqueue the group on the handle's stream: the batched encode pass and one
+ * persistent tensor-core launch over every tile of every problem.  No host
+ * synchronisation and no allocation, so the call can be captured into a CUDA
+ * graph and replayed; each replay recomputes every C.  Fault events
+ * accumulate in the handle; read them with ftgemm_report_fetch. */
+int ftgemm_grouped_gemm(ftgemm_handle_t handle, ftgemm_group_t group);
+
+/* Release a group (synchronises the handle's stream first). */
+int ftgemm_group_destroy(ftgemm_group_t group);
 
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them. */

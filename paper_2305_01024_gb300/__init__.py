@@ -50,8 +50,15 @@ class InjectSpec(C.Structure):
 class FaultRecord(C.Structure):
     _fields_ = [("tile_m", C.c_int32), ("tile_n", C.c_int32), ("kstep", C.c_int32),
                 ("row", C.c_int32), ("col", C.c_int32), ("kind", C.c_int32),
-                ("delta", C.c_double), ("residual_r", C.c_double),
+                ("problem", C.c_int32), ("reserved", C.c_int32), ("delta", C.c_double), ("residual_r", C.c_double),
                 ("residual_c", C.c_double), ("tau", C.c_double)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("k", C.c_int64),
+                ("A", C.c_void_p), ("lda", C.c_int64), ("B", C.c_void_p), ("ldb", C.c_int64),
+                ("C", C.c_void_p), ("ldc", C.c_int64), ("alpha", C.c_double), ("beta", C.c_double),
+                ("scale_a", C.c_float), ("scale_b", C.c_float)]
 
 
 class Stats(C.Structure):
@@ -103,13 +110,20 @@ def lib():
     L.ftgemm_quantize.argtypes = [vp, i64, vp, vp, C.c_int, C.POINTER(C.c_float)]
     L.ftgemm_enable_timing.argtypes = [vp, C.c_int]
     L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
+    L.ftgemm_group_create.argtypes = [vp, i32, C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(vp)]
+    L.ftgemm_group_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.ftgemm_group_set_faults.argtypes = [vp, C.POINTER(i32), C.POINTER(InjectSpec)]
+    L.ftgemm_grouped_gemm.argtypes = [vp, vp]
+    L.ftgemm_group_destroy.argtypes = [vp]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
     for fn in ("ftgemm_create", "ftgemm_destroy", "ftgemm_set_stream", "ftgemm_set_schedule",
                "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
-               "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize"):
+               "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
+               "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
+               "ftgemm_grouped_gemm", "ftgemm_group_destroy"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -136,7 +150,8 @@ def _records(rep: Report, cap: int) -> list:
     out = []
     for q in range(min(rep.n_records, cap)):
         r = rep.records[q]
-        out.append(dict(tile_m=r.tile_m, tile_n=r.tile_n, kstep=r.kstep, row=r.row, col=r.col,
+        out.append(dict(problem=r.problem, tile_m=r.tile_m, tile_n=r.tile_n, kstep=r.kstep,
+                        row=r.row, col=r.col,
                         kind=r.kind, delta=r.delta, residual_r=r.residual_r,
                         residual_c=r.residual_c, tau=r.tau))
     return out
@@ -262,3 +277,59 @@ class Handle:
         _, N = B.shape
         _check(lib().ftgemm_encode(self._h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
                                    m_u, n_u, _ptr(V), _ptr(W), _ptr(nA), _ptr(nB)))
+
+
+class Group:
+    """A prepared group of tensor-core GEMMs (ftgemm_group_create).
+
+    problems: list of (A, B, C) CUDA tensors, or (A, B, C, alpha, beta[,
+    scale_a, scale_b]); A m x k and B k x n of `dtype` (bf16 tensors, or
+    uint8 E4M3 codes), C fp32 m x n.  The tensors must outlive the group."""
+
+    def __init__(self, handle: "Handle", problems, dtype=BF16, level=FT_TILE):
+        self.handle = handle
+        self.count = len(problems)
+        arr = (Problem * self.count)()
+        for q, pr in enumerate(problems):
+            A, B, Cm = pr[:3]
+            alpha = float(pr[3]) if len(pr) > 3 else 1.0
+            beta = float(pr[4]) if len(pr) > 4 else 0.0
+            sa = float(pr[5]) if len(pr) > 5 else 1.0
+            sb = float(pr[6]) if len(pr) > 6 else 1.0
+            m, k = A.shape
+            n = B.shape[1]
+            arr[q] = Problem(m, n, k, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                             Cm.data_ptr(), Cm.stride(0), alpha, beta, sa, sb)
+        self._keep = list(problems)
+        self._g = C.c_void_p()
+        _check(lib().ftgemm_group_create(handle._h, self.count, arr, dtype, level, C.byref(self._g)))
+
+    def tiles(self):
+        tm = (C.c_int32 * self.count)()
+        tn = (C.c_int32 * self.count)()
+        _check(lib().ftgemm_group_tiles(self._g, tm, tn))
+        return list(tm), list(tn)
+
+    def set_faults(self, faults):
+        """faults: tuples (problem, tile_m, tile_n, kstep, row, col, delta[, target])."""
+        if not faults:
+            _check(lib().ftgemm_group_set_faults(self._g, None, None))
+            return
+        prob = (C.c_int32 * len(faults))(*[int(f[0]) for f in faults])
+        spec = make_inject([tuple(f[1:]) for f in faults])
+        _check(lib().ftgemm_group_set_faults(self._g, prob, C.byref(spec)))
+
+    def run(self):
+        """Enqueue the whole group on the handle's stream (no host sync)."""
+        _check(lib().ftgemm_grouped_gemm(self.handle._h, self._g))
+
+    def close(self):
+        if getattr(self, "_g", None) and self._g.value:
+            lib().ftgemm_group_destroy(self._g)
+            self._g = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

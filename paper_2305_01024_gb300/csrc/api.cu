@@ -27,9 +27,11 @@ cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*,
                                  float*, int*, cudaStream_t);
 cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, float*, long long,
                                  cudaStream_t);
-cudaError_t launch_tc_prep(int dt, const void* A, long long lda, const void* B, long long ldb, int M, int N,
-                           int K, bool abft, const TcPrepBuffers& w, int* launches, cudaStream_t st);
-cudaError_t launch_tc_gemm(int dt, bool abft, const TcMaps& maps, const TcParams& p, cudaStream_t st);
+void tc_prep_blocks(const TcProblem& P, int out[P_KINDS]);
+cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
+                           cudaStream_t st);
+cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
+                           cudaStream_t st);
 cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
                             int* launches, cudaStream_t st);
 
@@ -310,96 +312,135 @@ static int clear_report(ftgemm_ctx* h) {
 }
 extern "C" int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out);
 
-// Tensor-core path of ftgemm_gemm (BF16 / E4M3 operands, levels OFF and TILE).
+// ---- tensor-core path: problem layout shared by ftgemm_gemm and groups ----
+
+// Shape, tiling and epilogue fields of a tensor-core problem.
+static void tc_set_problem(TcProblem& P, int dt, bool abft, int M, int N, int K, const void* A, int64_t lda,
+                           const void* B, int64_t ldb, float* C, int64_t ldc, double alpha, double beta,
+                           float acc_scale, float lam_u) {
+  memset(&P, 0, sizeof(P));
+  const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
+  const int kblk = dt == 0 ? 64 : 128;
+  P.M = M; P.N = N; P.K = K;
+  P.tiles_m = (M + dm - 1) / dm;
+  P.tiles_n = (N + dn - 1) / dn;
+  P.nkb = (K + kblk - 1) / kblk;
+  P.A = A; P.lda = lda; P.B = B; P.ldb = ldb;
+  P.ldk = (K + 127) / 128 * 128;  // elements; a 16-byte multiple for both types
+  P.C = C; P.ldc = ldc;
+  P.c_vec = (ldc % 4 == 0) && (((uintptr_t)C & 15) == 0);
+  P.alpha = (float)alpha; P.beta = (float)beta;
+  P.acc_scale = acc_scale;
+  P.lam_u = lam_u;
+}
+
+// Encode buffers of one problem laid out from `ws` (floats); with ws null
+// only the size is computed.  Returns the floats used.
+static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
+  const size_t eb = dt == 0 ? 2 : 1, ns = TC_CS_SLOTS;
+  const size_t tm = P.tiles_m, tn = P.tiles_n, K = P.K;
+  auto fl = [&](size_t bytes) { return (bytes + 3) / 4; };
+  size_t o = 0;
+  auto take = [&](size_t floats) {
+    const size_t at = o;
+    o = align64(o + floats);
+    return ws ? ws + at : nullptr;
+  };
+  P.Bt = take(fl(eb * (size_t)P.N * P.ldk));
+  if (abft) {
+    P.Vf = take(tm * K);
+    P.Wf = take(tn * K);
+    P.Vt = take(fl(eb * tm * ns * P.ldk));
+    P.Wt = take(fl(eb * tn * ns * P.ldk));
+    P.vscale = take(tm * ns);
+    P.wscale = take(tn * ns);
+    P.s0v = take(tm);
+    P.s0w = take(tn);
+    P.nA = take(P.M);
+    P.nB = take(P.N);
+    P.froA = take(tm);
+    P.froB = take(tn);
+  }
+  return o;
+}
+
+static int tc_make_maps(TcProbMaps& mp, const TcProblem& P, int dt, bool abft) {
+  const int elem = dt == 0 ? 2 : 1, BK = 128 / elem;
+  const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
+  const uint32_t ns = TC_CS_SLOTS;
+  memset(&mp, 0, sizeof(mp));
+  int rc = make_map_sw128(&mp.A, P.A, elem, P.K, P.M, P.lda, BK, dm);
+  if (!rc) rc = make_map_sw128(&mp.B, P.Bt, elem, P.K, P.N, P.ldk, BK, dn);
+  if (!rc && abft) rc = make_map_sw128(&mp.W, P.Wt, elem, P.K, (uint64_t)P.tiles_n * ns, P.ldk, BK, ns);
+  if (!rc && abft) rc = make_map_sw128(&mp.V, P.Vt, elem, P.K, (uint64_t)P.tiles_m * ns, P.ldk, BK, ns);
+  if (rc) return rc;
+  if (!abft) { mp.W = mp.A; mp.V = mp.A; }
+  return FTGEMM_OK;
+}
+
+static int tc_check_operand_a(const void* A, int64_t lda, int elem, const char* who) {
+  if (((uintptr_t)A & 15) || (lda * elem) % 16)
+    FAIL(FTGEMM_ERR_ALIGN, "%s: A needs a 16-byte aligned base and row stride for TMA", who);
+  return FTGEMM_OK;
+}
+
+// Tensor-core path of ftgemm_gemm (BF16 / E4M3 operands, levels OFF and TILE):
+// one problem passed inline to the batched encode and the persistent GEMM.
 static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda,
                    const void* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_dtype dtype,
                    ftgemm_ft_level level, const ftgemm_inject_spec* inject, ftgemm_report* report) {
   if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE)
     FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: bf16/e4m3 take level OFF or TILE, not %d", (int)level);
   const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
-  const int elem = dt == 0 ? 2 : 1;
-  if (((uintptr_t)A & 15) || (lda * elem) % 16)
-    FAIL(FTGEMM_ERR_ALIGN, "ftgemm_gemm: A needs a 16-byte aligned base and row stride for TMA");
+  {
+    int rc = tc_check_operand_a(A, lda, dt == 0 ? 2 : 1, "ftgemm_gemm");
+    if (rc) return rc;
+  }
   CK(cudaSetDevice(h->device));
-  const int M = (int)m, N = (int)n, K = (int)k;
   const bool abft = level == FTGEMM_FT_TILE;
-  // data tile of C per CTA: 128 x 256, or 120 x 248 when 8 rows and 8
-  // columns of the MMA tile carry the checksums
-  const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
-  const int tiles_m = (M + dm - 1) / dm, tiles_n = (N + dn - 1) / dn;
-  const int kblk = 128 / (dtype == FTGEMM_BF16 ? 2 : 1);
-  const int ksteps = (K + kblk - 1) / kblk;
+  TcBatch b;
+  memset(&b, 0, sizeof(b));
+  TcProblem& P = b.one;
+  tc_set_problem(P, dt, abft, (int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, alpha, beta,
+                 dt == 1 ? h->fp8_sa * h->fp8_sb : 1.f, (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24)));
+  b.table = nullptr;
+  b.nprob = 1;
+  b.total_tiles = P.tiles_m * P.tiles_n;
   int nf = 0;
   {
-    ftgemm_schedule tcs{dm, dn, kblk, dm, dn, dm, dn, 0, 1};
-    int rc = upload_faults(h, inject, tcs, M, N, ksteps, tiles_m, tiles_n, level, &nf);
+    const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
+    ftgemm_schedule tcs{dm, dn, dt == 0 ? 64 : 128, dm, dn, dm, dn, 0, 1};
+    int rc = upload_faults(h, inject, tcs, P.M, P.N, P.nkb, P.tiles_m, P.tiles_n, level, &nf);
     if (rc) return rc;
   }
-  const long long ldk = (K + 127) / 128 * 128;  // elements; 16-byte multiple for both types
-  const size_t eb = (size_t)elem;
-  // workspace layout (floats)
-  auto fl = [&](size_t bytes) { return (bytes + 3) / 4; };
-  const size_t oBt = 0;
-  const size_t oVf = align64(oBt + fl(eb * (size_t)N * ldk));
-  const size_t oWf = align64(oVf + (abft ? (size_t)tiles_m * K : 0));
-  const size_t ns = TC_CS_SLOTS;
-  const size_t oVt = align64(oWf + (abft ? (size_t)tiles_n * K : 0));
-  const size_t oWt = align64(oVt + (abft ? fl(eb * (size_t)tiles_m * ns * ldk) : 0));
-  const size_t oVs = align64(oWt + (abft ? fl(eb * (size_t)tiles_n * ns * ldk) : 0));
-  const size_t oWs = align64(oVs + (size_t)tiles_m * ns);
-  const size_t oS0 = align64(oWs + (size_t)tiles_n * ns);
-  const size_t oNa = align64(oS0 + (size_t)tiles_m + tiles_n);
-  const size_t oNb = align64(oNa + (size_t)M);
-  const size_t oFa = align64(oNb + (size_t)N);
-  const size_t oFb = align64(oFa + (size_t)tiles_m);
-  const size_t total = align64(oFb + (size_t)tiles_n);
   {
-    int rc = ensure_ws(h, total);
+    int rc = ensure_ws(h, tc_layout(P, dt, abft, nullptr));
     if (rc) return rc;
   }
-  float* ws = h->ws;
+  tc_layout(P, dt, abft, h->ws);
   if (report) {
     int rc = clear_report(h);
     if (rc) return rc;
   }
-  TcPrepBuffers w;
-  w.Bt = ws + oBt; w.ldk = ldk;
-  w.Vf = ws + oVf; w.Wf = ws + oWf; w.Vt = ws + oVt; w.Wt = ws + oWt;
-  w.vscale = ws + oVs; w.wscale = ws + oWs; w.s0v = ws + oS0; w.s0w = ws + oS0 + tiles_m;
-  w.nA = ws + oNa; w.nB = ws + oNb; w.froA = ws + oFa; w.froB = ws + oFb;
+  int total[P_KINDS];
+  tc_prep_blocks(P, total);
   int launches = 0;
-  CK(launch_tc_prep(dt, A, lda, B, ldb, M, N, K, abft, w, &launches, h->stream));
-  const int BK = 128 / elem;
-  TcMaps maps;
+  CK(launch_tc_prep(dt, abft, b, total, &launches, h->stream));
+  TcMapsBatch mb;
+  memset(&mb, 0, sizeof(mb));
   {
-    int rc = make_map_sw128(&maps.A, A, elem, K, M, lda, BK, dm);
-    if (!rc) rc = make_map_sw128(&maps.B, w.Bt, elem, K, N, ldk, BK, dn);
-    if (!rc && abft) rc = make_map_sw128(&maps.W, w.Wt, elem, K, (uint64_t)tiles_n * ns, ldk, BK, ns);
-    if (!rc && abft) rc = make_map_sw128(&maps.V, w.Vt, elem, K, (uint64_t)tiles_m * ns, ldk, BK, ns);
+    int rc = tc_make_maps(mb.one, P, dt, abft);
     if (rc) return rc;
-    if (!abft) { maps.W = maps.A; maps.V = maps.A; }
   }
-  TcParams p;
-  memset(&p, 0, sizeof(p));
-  p.M = M; p.N = N; p.K = K;
-  p.C = C; p.ldc = ldc;
-  p.c_vec = (ldc % 4 == 0) && (((uintptr_t)C & 15) == 0);
-  p.alpha = (float)alpha; p.beta = (float)beta;
-  p.acc_scale = dt == 1 ? h->fp8_sa * h->fp8_sb : 1.f;
-  p.nA = w.nA; p.nB = w.nB; p.froA = w.froA; p.froB = w.froB;
-  p.wscale = w.wscale; p.vscale = w.vscale;
-  p.lam_u = (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24));
-  p.faults = nf > 0 ? h->d_faults : nullptr;
-  p.nfaults = nf;
-  p.tiles_m = tiles_m; p.tiles_n = tiles_n;
-  p.rep = h->rep; p.recs = h->recs;
+  TcRun run{nf > 0 ? h->d_faults : nullptr, nf, h->rep, h->recs};
+  const int grid = std::max(1, std::min(b.total_tiles, h->num_sms > 0 ? h->num_sms : 148));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (h->timing) {
     int rc = take_events(h, &ev);
     if (rc) return rc;
     CK(cudaEventRecord(ev.first, h->stream));
   }
-  CK(launch_tc_gemm(dt, abft, maps, p, h->stream));
+  CK(launch_tc_gemm(dt, abft, b, mb, run, grid, h->stream));
   ++launches;
   if (h->timing) {
     CK(cudaEventRecord(ev.second, h->stream));
@@ -410,7 +451,218 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   return FTGEMM_OK;
 }
 
+// A prepared group of tensor-core problems (ftgemm_group_create): device
+// problem table in schedule order, tensor maps, encode workspace, faults.
+struct ftgemm_group {
+  ftgemm_ctx* h = nullptr;
+  int dt = 0;
+  bool abft = false;
+  int count = 0;
+  std::vector<TcProblem> probs;  // schedule order
+  std::vector<int> pos;          // user index -> schedule position
+  TcProblem* d_probs = nullptr;
+  TcProbMaps* d_maps = nullptr;
+  float* ws = nullptr;
+  int total[P_KINDS] = {};
+  int total_tiles = 0;
+  Fault* d_faults = nullptr;
+  int nfaults = 0;
+};
+
+static void group_free(ftgemm_group* g) {
+  if (!g) return;
+  if (g->d_probs) cudaFree(g->d_probs);
+  if (g->d_maps) cudaFree(g->d_maps);
+  if (g->ws) cudaFree(g->ws);
+  if (g->d_faults) cudaFree(g->d_faults);
+  delete g;
+}
+
 extern "C" {
+
+int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* pr, ftgemm_dtype dtype,
+                        ftgemm_ft_level level, ftgemm_group_t* out) {
+  if (!h || !pr || !out || count <= 0) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_create: bad argument");
+  *out = nullptr;
+  if (dtype != FTGEMM_BF16 && dtype != FTGEMM_E4M3)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_group_create: bf16 or e4m3 operands only");
+  if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_group_create: level OFF or TILE, not %d", (int)level);
+  const int dt = dtype == FTGEMM_BF16 ? 0 : 1, elem = dt == 0 ? 2 : 1;
+  const bool abft = level == FTGEMM_FT_TILE;
+  for (int i = 0; i < count; ++i) {
+    const ftgemm_problem& q = pr[i];
+    if (q.m <= 0 || q.n <= 0 || q.k <= 0 || q.m > INT32_MAX || q.n > INT32_MAX || q.k > INT32_MAX)
+      FAIL(FTGEMM_ERR_ARG, "problem %d: sizes %lld x %lld x %lld", i, (long long)q.m, (long long)q.n,
+           (long long)q.k);
+    if (!q.A || !q.B || !q.C || q.lda < q.k || q.ldb < q.n || q.ldc < q.n)
+      FAIL(FTGEMM_ERR_ARG, "problem %d: NULL operand or leading dimension too small", i);
+    if (dt == 1 && !(q.scale_a > 0.f && q.scale_b > 0.f))
+      FAIL(FTGEMM_ERR_ARG, "problem %d: e4m3 scales must be positive", i);
+    char who[48];
+    snprintf(who, sizeof(who), "problem %d", i);
+    int rc = tc_check_operand_a(q.A, q.lda, elem, who);
+    if (rc) return rc;
+  }
+  CK(cudaSetDevice(h->device));
+  ftgemm_group* g = new ftgemm_group;
+  g->h = h; g->dt = dt; g->abft = abft; g->count = count;
+  // schedule order: longer K first, so each CTA's static tile list ends on
+  // the cheap tiles
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pr[a].k > pr[c].k; });
+  g->probs.resize(count);
+  g->pos.resize(count);
+  const float lam_u = (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24));
+  long long tiles = 0, blocks[P_KINDS] = {};
+  size_t ws_floats = 0;
+  std::vector<size_t> ws_at(count);
+  for (int q = 0; q < count; ++q) {
+    const ftgemm_problem& u = pr[order[q]];
+    TcProblem& P = g->probs[q];
+    tc_set_problem(P, dt, abft, (int)u.m, (int)u.n, (int)u.k, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.alpha, u.beta,
+                   dt == 1 ? u.scale_a * u.scale_b : 1.f, lam_u);
+    P.id = order[q];
+    g->pos[order[q]] = q;
+    P.tile_start = (int)tiles;
+    tiles += (long long)P.tiles_m * P.tiles_n;
+    int nb[P_KINDS];
+    tc_prep_blocks(P, nb);
+    for (int kd = 0; kd < P_KINDS; ++kd) {
+      P.blk_start[kd] = (int)blocks[kd];
+      blocks[kd] += nb[kd];
+    }
+    ws_at[q] = ws_floats;
+    ws_floats += tc_layout(P, dt, abft, nullptr);
+    if (tiles > INT32_MAX) { group_free(g); FAIL(FTGEMM_ERR_ARG, "ftgemm_group_create: too many tiles"); }
+  }
+  for (int kd = 0; kd < P_KINDS; ++kd) {
+    if (blocks[kd] > INT32_MAX) { group_free(g); FAIL(FTGEMM_ERR_ARG, "ftgemm_group_create: group too large"); }
+    g->total[kd] = (int)blocks[kd];
+  }
+  g->total_tiles = (int)tiles;
+  cudaError_t e = cudaMalloc(&g->ws, ws_floats * sizeof(float));
+  if (e != cudaSuccess) {
+    group_free(g);
+    FAIL(FTGEMM_ERR_CUDA, "ftgemm_group_create: %zu bytes of workspace: %s", ws_floats * sizeof(float),
+         cudaGetErrorString(e));
+  }
+  std::vector<TcProbMaps> maps(count);
+  for (int q = 0; q < count; ++q) {
+    tc_layout(g->probs[q], dt, abft, g->ws + ws_at[q]);
+    int rc = tc_make_maps(maps[q], g->probs[q], dt, abft);
+    if (rc) { group_free(g); return rc; }
+  }
+  e = cudaMalloc(&g->d_probs, sizeof(TcProblem) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_maps, sizeof(TcProbMaps) * count);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_probs, g->probs.data(), sizeof(TcProblem) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_maps, maps.data(), sizeof(TcProbMaps) * count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    group_free(g);
+    FAIL(FTGEMM_ERR_CUDA, "ftgemm_group_create: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return FTGEMM_OK;
+}
+
+int ftgemm_group_tiles(ftgemm_group_t g, int32_t* tiles_m, int32_t* tiles_n) {
+  if (!g || !tiles_m || !tiles_n) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_tiles: NULL argument");
+  for (int i = 0; i < g->count; ++i) {
+    const TcProblem& P = g->probs[g->pos[i]];
+    tiles_m[i] = P.tiles_m;
+    tiles_n[i] = P.tiles_n;
+  }
+  return FTGEMM_OK;
+}
+
+int ftgemm_group_set_faults(ftgemm_group_t g, const int32_t* problem, const ftgemm_inject_spec* inject) {
+  if (!g) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_set_faults: NULL group");
+  const int nf = inject ? inject->n : 0;
+  if (nf < 0) FAIL(FTGEMM_ERR_ARG, "inject->n < 0");
+  if (nf > 0 && (!problem || !inject->tile_m || !inject->tile_n || !inject->kstep || !inject->row || !inject->col ||
+                 !inject->delta))
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_group_set_faults: NULL array");
+  std::vector<Fault> fv(nf);
+  const int dm = g->abft ? TC_DM : TC_BM, dn = g->abft ? TC_DN : TC_BN;
+  for (int i = 0; i < nf; ++i) {
+    const int pi = problem[i];
+    if (pi < 0 || pi >= g->count) FAIL(FTGEMM_ERR_ARG, "inject[%d]: problem %d outside [0,%d)", i, pi, g->count);
+    const TcProblem& P = g->probs[g->pos[pi]];
+    const int tm = inject->tile_m[i], tn = inject->tile_n[i], r = inject->row[i], c = inject->col[i];
+    const int tg = inject->target ? inject->target[i] : 0;
+    int ks = inject->kstep[i];
+    if (tm < 0 || tm >= P.tiles_m || tn < 0 || tn >= P.tiles_n)
+      FAIL(FTGEMM_ERR_ARG, "inject[%d]: tile (%d,%d) outside problem %d's %dx%d grid", i, tm, tn, pi, P.tiles_m,
+           P.tiles_n);
+    if (ks == -1) ks = P.nkb - 1;
+    if (ks < 0 || ks >= P.nkb) FAIL(FTGEMM_ERR_ARG, "inject[%d]: k-step %d outside [0,%d)", i, ks, P.nkb);
+    const int rows = std::min(dm, P.M - tm * dm), cols = std::min(dn, P.N - tn * dn);
+    if (r < 0 || r >= rows || c < 0 || c >= cols)
+      FAIL(FTGEMM_ERR_ARG, "inject[%d]: element (%d,%d) outside tile (%d x %d)", i, r, c, rows, cols);
+    if (tg < 0 || tg > 2) FAIL(FTGEMM_ERR_ARG, "inject[%d]: target %d", i, tg);
+    if (!g->abft && tg != 0) FAIL(FTGEMM_ERR_ARG, "inject[%d]: no checksums at level OFF", i);
+    fv[i] = Fault{P.tile_start + tm * P.tiles_n + tn, ks, r, c, tg, inject->delta[i]};
+  }
+  std::stable_sort(fv.begin(), fv.end(), [](const Fault& a, const Fault& b) {
+    return a.tile != b.tile ? a.tile < b.tile : a.kstep < b.kstep;
+  });
+  CK(cudaSetDevice(g->h->device));
+  CK(cudaStreamSynchronize(g->h->stream));  // a launch in flight may read the old table
+  if (g->d_faults) cudaFree(g->d_faults);
+  g->d_faults = nullptr;
+  g->nfaults = 0;
+  if (nf > 0) {
+    CK(cudaMalloc(&g->d_faults, sizeof(Fault) * nf));
+    CK(cudaMemcpy(g->d_faults, fv.data(), sizeof(Fault) * nf, cudaMemcpyHostToDevice));
+  }
+  g->nfaults = nf;
+  return FTGEMM_OK;
+}
+
+int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
+  if (!h || !g) FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm: NULL argument");
+  if (g->h != h) FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm: the group was created on another handle");
+  CK(cudaSetDevice(h->device));
+  TcBatch b;
+  memset(&b, 0, sizeof(b));
+  b.table = g->d_probs;
+  b.nprob = g->count;
+  b.total_tiles = g->total_tiles;
+  int launches = 0;
+  CK(launch_tc_prep(g->dt, g->abft, b, g->total, &launches, h->stream));
+  TcMapsBatch mb;
+  memset(&mb, 0, sizeof(mb));
+  mb.table = g->d_maps;
+  TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, h->rep, h->recs};
+  const int grid = std::max(1, std::min(b.total_tiles, h->num_sms > 0 ? h->num_sms : 148));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(h->stream, &cs));
+  const bool timed = h->timing && cs == cudaStreamCaptureStatusNone;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (timed) {
+    int rc = take_events(h, &ev);
+    if (rc) return rc;
+    CK(cudaEventRecord(ev.first, h->stream));
+  }
+  CK(launch_tc_gemm(g->dt, g->abft, b, mb, run, grid, h->stream));
+  ++launches;
+  if (timed) {
+    CK(cudaEventRecord(ev.second, h->stream));
+    h->pending.push_back(ev);
+  }
+  h->launches += launches;
+  return FTGEMM_OK;
+}
+
+int ftgemm_group_destroy(ftgemm_group_t g) {
+  if (!g) return FTGEMM_OK;
+  cudaSetDevice(g->h->device);
+  cudaStreamSynchronize(g->h->stream);
+  group_free(g);
+  return FTGEMM_OK;
+}
 
 int ftgemm_enable_timing(ftgemm_handle_t h, int enable) {
   if (!h) FAIL(FTGEMM_ERR_ARG, "ftgemm_enable_timing: NULL handle");
@@ -570,6 +822,7 @@ int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out) {
     CK(cudaStreamSynchronize(h->stream));
   }
   std::sort(v.begin(), v.end(), [](const ftgemm_fault_record& a, const ftgemm_fault_record& b) {
+    if (a.problem != b.problem) return a.problem < b.problem;
     if (a.tile_m != b.tile_m) return a.tile_m < b.tile_m;
     if (a.tile_n != b.tile_n) return a.tile_n < b.tile_n;
     if (a.kstep != b.kstep) return a.kstep < b.kstep;

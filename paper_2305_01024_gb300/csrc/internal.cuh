@@ -29,7 +29,7 @@ struct DevReport {
   int pad;
 };
 
-static_assert(sizeof(ftgemm_fault_record) == 56, "record layout");
+static_assert(sizeof(ftgemm_fault_record) == 64, "record layout");
 
 __device__ __forceinline__ void report_event(DevReport* rep, ftgemm_fault_record* recs,
                                              const ftgemm_fault_record& r) {
@@ -100,40 +100,81 @@ constexpr int TC_BM = 128, TC_BN = 256, TC_CS_SLOTS = 8;
 constexpr int TC_DM = TC_BM - TC_CS_SLOTS, TC_DN = TC_BN - TC_CS_SLOTS;  // 120, 248
 constexpr int TC_GROUP_M = 16;  // tile rows per raster group
 
-// Parameters of the tensor-core GEMM (operands through TcMaps).
-struct TcParams {
-  int M, N, K;
+// Batched encode launches of the tensor-core path; a problem's first block
+// in launch `kind` is TcProblem::blk_start[kind].
+enum TcPrepKind { P_TRANSPOSE = 0, P_SUM_A, P_SUM_B, P_NORM_A, P_NORM_B, P_FRO, P_SCALE, P_PIECES, P_KINDS };
+
+// One GEMM of the tensor-core path: operands, encode buffers, epilogue.
+// A table of these drives the encode launches and the persistent GEMM; a
+// single GEMM passes one inline (kernel parameter space).
+struct TcProblem {
+  int M, N, K, id;                // id: index reported in fault records
+  int tiles_m, tiles_n, tile_start, nkb;
+  int blk_start[P_KINDS];
+  const void* A; long long lda;   // M x K, operand type, K contiguous
+  const void* B; long long ldb;   // K x N, operand type, N contiguous
+  void* Bt; long long ldk;        // B^T (N x ldk); ldk also the row stride of Vt / Wt
+  float* Vf; float* Wf;           // fp32 e^T A [tiles_m][K], B e [tiles_n][K]
+  void* Vt; void* Wt;             // pieces [tiles * TC_CS_SLOTS][ldk], operand type
+  float* vscale; float* wscale;   // [tiles * TC_CS_SLOTS] multiplier of each piece
+  float* s0v; float* s0w;         // [tiles] fp8 piece base scales
+  float* nA; float* nB;           // [M] row 2-norms of A, [N] column 2-norms of B
+  float* froA; float* froB;       // [tiles_m], [tiles_n] Frobenius norms of the blocks
   float* C; long long ldc;
-  int c_vec;
+  int c_vec;                      // C rows 16-byte aligned (float4 stores)
   float alpha, beta;
-  float acc_scale;        // fp8: product of the per-tensor scales; bf16: 1
-  const float* nA;        // [M] row 2-norms of A (operand values as stored)
-  const float* nB;        // [N] column 2-norms of B
-  const float* froA;      // [tiles_m] Frobenius norm of each data-row block of A
-  const float* froB;      // [tiles_n] Frobenius norm of each data-column block of B
-  const float* wscale;    // [tiles_n * TC_CS_SLOTS] multiplier of each B e piece
-  const float* vscale;    // [tiles_m * TC_CS_SLOTS] multiplier of each e^T A piece
-  float lam_u;
-  const Fault* faults; int nfaults; int tiles_m, tiles_n;
-  DevReport* rep; ftgemm_fault_record* recs;
+  float acc_scale;                // fp8: product of the per-tensor scales; bf16: 1
+  float lam_u;                    // analytic threshold factor lambda * u
+  const float* lam_tile;          // per-tile lambda * u (learned threshold), or null
 };
 
-// Buffers of the tensor-core encoding pass.
-struct TcPrepBuffers {
-  void* Bt; long long ldk;  // B^T (N x ldk), operand type; ldk also the row stride of Vt/Wt
-  float* Vf; float* Wf;     // fp32 e^T A [tiles_m][K] and B e [tiles_n][K]
-  void* Vt; void* Wt;       // pieces [tiles * TC_CS_SLOTS][ldk], operand type
-  float* vscale; float* wscale;  // [tiles * TC_CS_SLOTS]
-  float* s0v; float* s0w;        // [tiles] fp8 piece base scales
-  float* nA; float* nB;          // [M], [N]
-  float* froA; float* froB;      // [tiles_m], [tiles_n]
+struct TcBatch {
+  const TcProblem* table;  // device table of nprob problems, or null: use `one`
+  int nprob;
+  int total_tiles;
+  TcProblem one;
 };
 
-struct TcMaps {
+struct alignas(128) TcProbMaps {
   CUtensorMap A;  // A:   dims {K, M}, box {k-block, data rows}, 128-byte swizzle
   CUtensorMap B;  // B^T: dims {K, N}, box {k-block, data columns}
   CUtensorMap W;  // pieces of B e:   dims {K, 8 * tiles_n}, box {k-block, 8}
   CUtensorMap V;  // pieces of e^T A: dims {K, 8 * tiles_m}, box {k-block, 8}
 };
+
+struct TcMapsBatch {
+  const TcProbMaps* table;  // device table (128-byte aligned), or null: use `one`
+  TcProbMaps one;
+};
+
+struct TcRun {
+  const Fault* faults; int nfaults;  // sorted by global tile (tile_start + local)
+  DevReport* rep; ftgemm_fault_record* recs;
+};
+
+__device__ __forceinline__ const TcProblem& tc_problem(const TcBatch& b, int pi) {
+  return b.table ? b.table[pi] : b.one;
+}
+
+// Problem owning block `blk` of a batched launch of `kind`: the last problem
+// whose first block is <= blk.
+__device__ __forceinline__ int tc_find_block(const TcBatch& b, int kind, int blk) {
+  if (!b.table) return 0;
+  int lo = 0, hi = b.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.table[mid].blk_start[kind] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int tc_find_tile(const TcBatch& b, int t) {
+  if (!b.table) return 0;
+  int lo = 0, hi = b.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 }  // namespace ftg

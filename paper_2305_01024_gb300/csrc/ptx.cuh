@@ -70,6 +70,26 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Order earlier generic-proxy writes of a tensor map in global memory before
+// its use by TMA (the tensormap proxy).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
+// Barrier `id` over `n` threads that also ORs a predicate across them: every
+// participating thread gets the same result.
+__device__ __forceinline__ int bar_red_or(int id, int n, int pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, %3, pi;\n"
+      " selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(out)
+      : "r"(pred), "r"(id), "r"(n)
+      : "memory");
+  return (int)out;
+}
+
 }  // namespace ftg
 
 // ---------------------------------------------------------------------------

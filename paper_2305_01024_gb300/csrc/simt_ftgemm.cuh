@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
             if (nr | nc) {
               ftgemm_fault_record rec;
               rec.tile_m = tile_m; rec.tile_n = tile_n; rec.kstep = ks;
+              rec.problem = 0; rec.reserved = 0;
               rec.row = ir >= 0 ? row0 + FROW(ir) : -1;
               rec.col = jc >= 0 ? col0 + FCOL(jc) : -1;
               rec.residual_r = dR; rec.residual_c = dC; rec.tau = (double)tR + (double)tC;
@@ -824,6 +825,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                 if (lane == 0) {
                   ftgemm_fault_record rec;
                   rec.tile_m = tile_m; rec.tile_n = tile_n; rec.kstep = ks;
+                  rec.problem = 0; rec.reserved = 0;
                   rec.row = ir >= 0 ? row0 + ir : -1;
                   rec.col = jc >= 0 ? col0 + jc : -1;
                   rec.kind = kind; rec.delta = delta;
@@ -935,6 +937,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                 const float tR = nr ? X.tres[NT + ir] : 0.f, tC = nc ? X.tres[jc] : 0.f;
                 ftgemm_fault_record rec;
                 rec.tile_m = tile_m; rec.tile_n = tile_n; rec.kstep = ks;
+                rec.problem = 0; rec.reserved = 0;
                 rec.row = ir >= 0 ? row0 + ir : -1;
                 rec.col = jc >= 0 ? col0 + jc : -1;
                 rec.residual_r = dR; rec.residual_c = dC;

@@ -21,10 +21,14 @@
 // last k-step, from TMEM: fp32 sums screen every row and column, fp64 sums
 // confirm the flagged ones.
 //
-// CTA: warp 0 issues TMA loads, warp 1 allocates TMEM and issues MMAs,
-// warps 2..5 read TMEM (each warp the 32 lanes its index allows), verify,
-// correct and store.  k-block = one 128-byte swizzle row (64 bf16 or 128
-// fp8 elements), STAGES-deep ring.
+// The kernel is persistent: one CTA per SM walks a static list of output
+// tiles over a table of problems (one problem for ftgemm_gemm, many for the
+// grouped call), tiles of one problem in a grouped raster.  Warp 0 issues
+// TMA loads into a STAGES-deep ring, warp 1 allocates TMEM and issues MMAs
+// into one of two 256-column accumulators, warps 2..5 read the other
+// accumulator (each warp the 32 lanes its index allows), verify, correct and
+// store -- so the epilogue of one tile overlaps the main loop of the next.
+// k-block = one 128-byte swizzle row (64 bf16 or 128 fp8 elements).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -48,7 +52,7 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * 128;            // 32 KB
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int THREADS = 192;
-  static constexpr uint32_t TMEM_COLS = 256;
+  static constexpr uint32_t TMEM_COLS = 2 * BN;       // two fp32 accumulators
   static constexpr int NPIECE = DT == 0 ? 3 : 5;      // checksum pieces in use
   static_assert(!ABFT || NPIECE <= CSR, "pieces must fit the checksum slots");
   // the checksum rows start on a 1024-byte (8-row) swizzle boundary
@@ -69,14 +73,17 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
   else tc_mma_f8(d, a, b, idesc, acc);
 }
 
+constexpr int TC_STAGES = 4;
+
 struct TcSmemTail {
-  uint64_t full[4], empty[4], acc_full;
+  uint64_t full[TC_STAGES], empty[TC_STAGES];
+  uint64_t acc_full[2], acc_empty[2];
   uint32_t tmem_base;
   int abort;
   int nr, nc;
   unsigned long long bestr, bestc;
-  int fix_row, fix_col;
-  double fix_delta;
+  int fix_row[2], fix_col[2];      // per accumulator parity
+  double fix_delta[2];
   float colpart[4][256];           // per epilogue warp partial column sums (data rows)
   float ccp[TC_CS_SLOTS][256];     // column-checksum pieces, TMEM lanes 120..127
   float crow[128];                 // row checksums
@@ -89,31 +96,36 @@ struct TcSmemTail {
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// Problem, tile row and tile column of list entry t: problems in table
+// order, tiles of a problem in a raster of TC_GROUP_M tile rows by all its
+// tile columns, column-major inside a group.
+struct TcTile {
+  int pi, tm, tn;
+};
+__device__ __forceinline__ TcTile tc_tile(const TcBatch& b, int t) {
+  TcTile x;
+  x.pi = tc_find_tile(b, t);
+  const TcProblem& P = tc_problem(b, x.pi);
+  const int id = t - P.tile_start, per_group = TC_GROUP_M * P.tiles_n;
+  const int first_m = (id / per_group) * TC_GROUP_M;
+  const int gsize = min(P.tiles_m - first_m, TC_GROUP_M);
+  x.tm = first_m + (id % per_group) % gsize;
+  x.tn = (id % per_group) / gsize;
+  return x;
+}
+
 template <int DT, bool ABFT>
 __global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmV,
-                   const TcParams p) {
+    tc_gemm_kernel(const __grid_constant__ TcBatch b, const __grid_constant__ TcMapsBatch mb, const TcRun run) {
   using Cfg = TcCfg<DT, ABFT>;
   constexpr int BM = Cfg::BM, BN = Cfg::BN, DM = Cfg::DM, DN = Cfg::DN, BK = Cfg::BK, UK = Cfg::UK;
   constexpr int S = Cfg::STAGES, CSR = Cfg::CSR;
+  static_assert(S == TC_STAGES, "ring depth");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~uintptr_t(1023));
   TcSmemTail& T = *reinterpret_cast<TcSmemTail*>(base + S * Cfg::STAGE_BYTES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // grouped raster: consecutive CTAs walk down TC_GROUP_M tile rows before
-  // moving one tile column right, so a wave shares k-slices of A and B in L2
-  int tile_m, tile_n;
-  {
-    const int id = blockIdx.x, per_group = TC_GROUP_M * p.tiles_n;
-    const int first_m = (id / per_group) * TC_GROUP_M;
-    const int gsize = min(p.tiles_m - first_m, TC_GROUP_M);
-    tile_m = first_m + (id % per_group) % gsize;
-    tile_n = (id % per_group) / gsize;
-  }
-  const int row0 = tile_m * DM, col0 = tile_n * DN;
-  const int nkb = (p.K + BK - 1) / BK;
   auto sA = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
   auto sB = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
 
@@ -122,11 +134,11 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&T.full[s], 1);
       mbar_init(&T.empty[s], 1);
     }
-    mbar_init(&T.acc_full, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&T.acc_full[a], 1);
+      mbar_init(&T.acc_empty[a], 4);  // one arrival per epilogue warp
+    }
     T.abort = 0;
-    T.fix_row = -1;
-    T.fix_col = -1;
-    T.fix_delta = 0.0;
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -140,280 +152,343 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: data rows of A and B^T, then the checksum slots -----
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (kb >= S && !mbar_wait(&T.empty[s], (uint32_t)((kb / S) - 1) & 1u)) {
-        atomicExch(&T.abort, 1);
-        break;
+    uint32_t it = 0;  // k-blocks issued, over all tiles of this CTA
+    int last_pi = -1;
+    bool dead = false;
+    for (int t = blockIdx.x; t < b.total_tiles && !dead; t += gridDim.x) {
+      const TcTile x = tc_tile(b, t);
+      const TcProblem& P = tc_problem(b, x.pi);
+      const TcProbMaps* mp = mb.table ? &mb.table[x.pi] : &mb.one;
+      if (x.pi != last_pi) {
+        if (mb.table) {
+          tensormap_acquire(&mp->A);
+          tensormap_acquire(&mp->B);
+          if constexpr (ABFT) {
+            tensormap_acquire(&mp->W);
+            tensormap_acquire(&mp->V);
+          }
+        }
+        prefetch_tmap(&mp->A);
+        prefetch_tmap(&mp->B);
+        last_pi = x.pi;
       }
-      mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
-      tma_load_2d(sA(s), &tmA, &T.full[s], kb * BK, row0);
-      tma_load_2d(sB(s), &tmB, &T.full[s], kb * BK, col0);
-      if constexpr (ABFT) {
-        tma_load_2d(sA(s) + DM * 128, &tmV, &T.full[s], kb * BK, tile_m * CSR);
-        tma_load_2d(sB(s) + DN * 128, &tmW, &T.full[s], kb * BK, tile_n * CSR);
+      const int row0 = x.tm * DM, col0 = x.tn * DN;
+      for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+        const int s = it % S;
+        if (it >= S && !mbar_wait(&T.empty[s], ((it / S) & 1u) ^ 1u)) {
+          dead = true;
+          break;
+        }
+        mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
+        tma_load_2d(sA(s), &mp->A, &T.full[s], kb * BK, row0);
+        tma_load_2d(sB(s), &mp->B, &T.full[s], kb * BK, col0);
+        if constexpr (ABFT) {
+          tma_load_2d(sA(s) + DM * 128, &mp->V, &T.full[s], kb * BK, x.tm * CSR);
+          tma_load_2d(sB(s) + DN * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
+        }
       }
     }
+    if (dead) atomicExch(&T.abort, 1);
+    // let the last loads land before the CTA may exit (bounded)
+    for (uint32_t j = it > (uint32_t)S ? it - S : 0; j < it; ++j) mbar_wait(&T.full[j % S], (j / S) & 1u);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: one 128 x 256 MMA per 32-byte k-slice ----------------
     constexpr uint32_t idesc = tc_idesc(DT, BM, BN);
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait(&T.full[s], (uint32_t)(kb / S) & 1u)) { ok = false; break; }
-      tc_fence_after();
-      const uint64_t da = smem_desc_sw128(sA(s)), db = smem_desc_sw128(sB(s));
-#pragma unroll
-      for (int kk = 0; kk < BK / UK; ++kk) {
-        const uint64_t step = (uint64_t)(kk * 32) >> 4;  // 32 bytes per instruction
-        tc_mma<DT>(tmem, da + step, db + step, idesc, (kb | kk) != 0);
+    uint32_t it = 0;
+    int lt = 0;  // tiles of this CTA so far
+    bool dead = false;
+    for (int t = blockIdx.x; t < b.total_tiles && !dead; t += gridDim.x, ++lt) {
+      const TcProblem& P = tc_problem(b, tc_find_tile(b, t));
+      const int ab = lt & 1;
+      if (lt >= 2 && !mbar_wait(&T.acc_empty[ab], ((lt >> 1) - 1) & 1)) {
+        dead = true;
+        break;
       }
-      tc_commit(&T.empty[s]);  // the stage is free once these MMAs completed
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(ab * BN);
+      for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+        const int s = it % S;
+        if (!mbar_wait(&T.full[s], (it / S) & 1u)) {
+          dead = true;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da = smem_desc_sw128(sA(s)), db = smem_desc_sw128(sB(s));
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          const uint64_t step = (uint64_t)(kk * 32) >> 4;  // 32 bytes per instruction
+          tc_mma<DT>(d, da + step, db + step, idesc, (kb | kk) != 0);
+        }
+        tc_commit(&T.empty[s]);  // the stage is free once these MMAs completed
+      }
+      tc_commit(&T.acc_full[ab]);
     }
-    if (!ok) atomicExch(&T.abort, 1);
-    tc_commit(&T.acc_full);
+    if (dead) atomicExch(&T.abort, 1);
+    // let the last MMAs finish before TMEM may be released (bounded)
+    if (lt > 0) mbar_wait(&T.acc_full[(lt - 1) & 1], ((lt - 1) >> 1) & 1);
   } else if (warp >= 2) {
     // ---- epilogue -------------------------------------------------------
     const int lq = warp & 3;            // TMEM lane quarter this warp may access
     const int r = lq * 32 + lane;       // tile row == TMEM lane
-    const int gr = row0 + r;
     const bool data_row = r < DM;
-    const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
-    if (!mbar_wait(&T.acc_full, 0)) atomicExch(&T.abort, 1);
-    tc_fence_after();
-    const float alpha = p.alpha, beta = p.beta;
-    const float acc_scale = p.acc_scale;  // fp8: product of the per-tensor scales
+    bool dead = false;
+    int lt = 0;
+    for (int t = blockIdx.x; t < b.total_tiles; t += gridDim.x, ++lt) {
+      const TcTile x = tc_tile(b, t);
+      const TcProblem& P = tc_problem(b, x.pi);
+      const int ab = lt & 1;
+      const int row0 = x.tm * DM, col0 = x.tn * DN, gr = row0 + r;
+      const uint32_t tl = tmem + (uint32_t)(ab * BN) + ((uint32_t)(lq * 32) << 16);
+      // after one wait gave up the remaining tiles are walked without waits
+      // (and without stores), so the barriers below still line up
+      const bool ok = !dead && mbar_wait(&T.acc_full[ab], (lt >> 1) & 1);
+      if (!ok && !dead) {
+        dead = true;
+        atomicExch(&T.abort, 1);
+      }
+      tc_fence_after();
+      const float sc = P.alpha * P.acc_scale;  // fp8: product of the per-tensor scales
+      const float beta = P.beta;
+      const int my_tile = P.tile_start + x.tm * P.tiles_n + x.tn;
 
-    if constexpr (ABFT) {
-      T.cradj[r] = 0.f;
-      T.ccadj[r] = 0.f;
-      T.ccadj[128 + r] = 0.f;
-      epi_bar();
-    }
-    // ----- scheduled faults of this tile (Section 5.3) -----
-    // Verification runs once per tile after its last k-step; the accumulation
-    // being additive, an offset is applied to the tensor-memory accumulator
-    // here, where the k-step it was scheduled for only changes rounding.
-    if (p.nfaults > 0) {
-      const int my_tile = tile_m * p.tiles_n + tile_n;
-      for (int f = first_fault(p.faults, p.nfaults, my_tile); f < p.nfaults && p.faults[f].tile == my_tile; ++f) {
-        const Fault F = p.faults[f];
-        if (F.target == T_ACC) {
-          if ((F.row >> 5) == lq) {  // warp-uniform: this warp owns the lane
-            const uint32_t a = tl + (uint32_t)(F.col & ~15);
-            float v[16];
-            tmem_ld16(a, v);
-            tmem_wait_ld();
-            if (lane == (F.row & 31)) {
-#pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (q == (F.col & 15)) v[q] += F.delta;
-            }
-            tmem_st16(a, v);
-            tmem_wait_st();
-          }
-        } else if constexpr (ABFT) {
-          if (r == 0) {
-            if (F.target == T_ROWSUM) T.cradj[F.row] += F.delta;
-            else T.ccadj[F.col] += F.delta;
-          }
+      if constexpr (ABFT) {
+        T.cradj[r] = 0.f;
+        T.ccadj[r] = 0.f;
+        T.ccadj[128 + r] = 0.f;
+        if (r == 0) {
+          T.fix_row[ab] = -1;
+          T.fix_col[ab] = -1;
+          T.fix_delta[ab] = 0.0;
         }
-      }
-    }
-
-    if constexpr (ABFT) {
-      epi_bar();
-      // ----- fp32 screen -----
-      float rs = 0.f, rc = 0.f, crow = 0.f;
-      for (int ch = 0; ch < BN / 16; ++ch) {
-        float v[16];
-        tmem_ld16(tl + ch * 16, v);
-        tmem_wait_ld();
-        // row sum over the data columns (two-term fp32 summation); the row
-        // checksum pieces sit in columns DN..DN+NPIECE-1
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int c = ch * 16 + q;
-          if (c < DN) {
-            const float y = v[q] - rc;
-            const float t = rs + y;
-            rc = (t - rs) - y;
-            rs = t;
-          } else if (c - DN < Cfg::NPIECE) {
-            crow = fmaf(v[q], p.wscale[(size_t)tile_n * CSR + (c - DN)], crow);
-          }
-        }
-        // the column checksum pieces sit in lanes DM..DM+NPIECE-1
-        if (r >= DM && r - DM < Cfg::NPIECE) {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
-        }
-        // warp partial column sums over the data rows: a reduce-scatter over
-        // the lanes leaves lanes 2q and 2q+1 with column idx(q)
-        float w[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) w[q] = data_row ? v[q] : 0.f;
-#pragma unroll
-        for (int lev = 16, half = 8; lev >= 2; lev >>= 1, half >>= 1) {
-          const bool up = (lane & lev) != 0;
-#pragma unroll
-          for (int q = 0; q < half; ++q) {
-            const float snd = up ? w[q] : w[q + half];
-            const float kp = up ? w[q + half] : w[q];
-            w[q] = kp + __shfl_xor_sync(0xffffffffu, snd, lev);
-          }
-        }
-        w[0] += __shfl_xor_sync(0xffffffffu, w[0], 1);
-        if ((lane & 1) == 0) {
-          const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                          ((lane >> 1) & 1);
-          T.colpart[lq][ch * 16 + idx] = w[0];
-        }
-      }
-      crow += T.cradj[r];
-      T.crow[r] = crow;
-      T.tr[r] = (data_row && gr < p.M) ? p.lam_u * p.nA[gr] * p.froB[tile_n] : 0.f;
-      T.flag_r[r] = data_row && fabsf(rs - crow) > T.tr[r];
-      epi_bar();
-      for (int c = r; c < BN; c += 128) {
-        int fl = 0;
-        float cc = 0.f, tcv = 0.f;
-        if (c < DN) {
-#pragma unroll
-          for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], p.vscale[(size_t)tile_m * CSR + q], cc);
-          cc += T.ccadj[c];
-          const int gc = col0 + c;
-          tcv = gc < p.N ? p.lam_u * p.froA[tile_m] * p.nB[gc] : 0.f;
-          const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
-          fl = fabsf(s - cc) > tcv;
-        }
-        T.ccol[c] = cc;
-        T.tc[c] = tcv;
-        T.flag_c[c] = fl;
-      }
-      epi_bar();
-      int any = 0;
-      for (int c = lane; c < 128; c += 32) any |= T.flag_r[c];
-      for (int c = lane; c < 256; c += 32) any |= T.flag_c[c];
-      any = __any_sync(0xffffffffu, any);
-      if (any) {  // the same in all four epilogue warps: the flags are shared
-        // ----- fp64 confirmation of every screened row / column -----
-        if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
-        for (int c = r; c < BN; c += 128) T.sum_c[c] = 0.0;
         epi_bar();
-        double sr = 0.0;
+      }
+      // ----- scheduled faults of this tile (Section 5.3) -----
+      // Verification runs once per tile after its last k-step; the
+      // accumulation being additive, an offset is applied to the
+      // tensor-memory accumulator here, where the k-step it was scheduled
+      // for only changes rounding.
+      if (run.nfaults > 0) {
+        for (int f = first_fault(run.faults, run.nfaults, my_tile); f < run.nfaults && run.faults[f].tile == my_tile;
+             ++f) {
+          const Fault F = run.faults[f];
+          if (F.target == T_ACC) {
+            if ((F.row >> 5) == lq) {  // warp-uniform: this warp owns the lane
+              const uint32_t a = tl + (uint32_t)(F.col & ~15);
+              float v[16];
+              tmem_ld16(a, v);
+              tmem_wait_ld();
+              if (lane == (F.row & 31)) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                  if (q == (F.col & 15)) v[q] += F.delta;
+              }
+              tmem_st16(a, v);
+              tmem_wait_st();
+            }
+          } else if constexpr (ABFT) {
+            if (r == 0) {
+              if (F.target == T_ROWSUM) T.cradj[F.row] += F.delta;
+              else T.ccadj[F.col] += F.delta;
+            }
+          }
+        }
+      }
+
+      if constexpr (ABFT) {
+        epi_bar();
+        const float lam_u = P.lam_tile ? P.lam_tile[x.tm * P.tiles_n + x.tn] : P.lam_u;
+        // ----- fp32 screen -----
+        float rs = 0.f, rc = 0.f, crow = 0.f;
         for (int ch = 0; ch < BN / 16; ++ch) {
           float v[16];
           tmem_ld16(tl + ch * 16, v);
           tmem_wait_ld();
+          // row sum over the data columns (two-term fp32 summation); the row
+          // checksum pieces sit in columns DN..DN+NPIECE-1
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int c = ch * 16 + q;
             if (c < DN) {
-              sr += (double)v[q];
-              if (data_row && T.flag_c[c]) atomicAdd(&T.sum_c[c], (double)v[q]);
+              const float y = v[q] - rc;
+              const float tt = rs + y;
+              rc = (tt - rs) - y;
+              rs = tt;
+            } else if (c - DN < Cfg::NPIECE) {
+              crow = fmaf(v[q], P.wscale[(size_t)x.tn * CSR + (c - DN)], crow);
             }
           }
-        }
-        T.sum_r[r] = sr;
-        epi_bar();
-        if (T.flag_r[r]) {
-          const double d = sr - (double)T.crow[r];
-          if (fabs(d) > (double)T.tr[r]) {
-            atomicAdd(&T.nr, 1);
-            atomicMax(&T.bestr, flag_key(flag_score((float)d, T.tr[r]), r));
+          // the column checksum pieces sit in lanes DM..DM+NPIECE-1
+          if (r >= DM && r - DM < Cfg::NPIECE) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
           }
-        }
-        for (int c = r; c < DN; c += 128) {
-          if (T.flag_c[c]) {
-            const double d = T.sum_c[c] - (double)T.ccol[c];
-            if (fabs(d) > (double)T.tc[c]) {
-              atomicAdd(&T.nc, 1);
-              atomicMax(&T.bestc, flag_key(flag_score((float)d, T.tc[c]), c));
+          // warp partial column sums over the data rows: a reduce-scatter
+          // over the lanes leaves lanes 2q and 2q+1 with column idx(q)
+          float w[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) w[q] = data_row ? v[q] : 0.f;
+#pragma unroll
+          for (int lev = 16, half = 8; lev >= 2; lev >>= 1, half >>= 1) {
+            const bool up = (lane & lev) != 0;
+#pragma unroll
+            for (int q = 0; q < half; ++q) {
+              const float snd = up ? w[q] : w[q + half];
+              const float kp = up ? w[q + half] : w[q];
+              w[q] = kp + __shfl_xor_sync(0xffffffffu, snd, lev);
             }
           }
+          w[0] += __shfl_xor_sync(0xffffffffu, w[0], 1);
+          if ((lane & 1) == 0) {
+            const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                            ((lane >> 1) & 1);
+            T.colpart[lq][ch * 16 + idx] = w[0];
+          }
         }
+        crow += T.cradj[r];
+        T.crow[r] = crow;
+        T.tr[r] = (data_row && gr < P.M) ? lam_u * P.nA[gr] * P.froB[x.tn] : 0.f;
+        int flagged = data_row && fabsf(rs - crow) > T.tr[r];
+        T.flag_r[r] = flagged;
         epi_bar();
-        if (r == 0 && (T.nr | T.nc)) {
-          const int nr = T.nr, nc = T.nc;
-          const int ir = nr ? key_index(T.bestr) : -1, jc = nc ? key_index(T.bestc) : -1;
-          const double dR = nr ? T.sum_r[ir] - (double)T.crow[ir] : 0.0;
-          const double dC = nc ? T.sum_c[jc] - (double)T.ccol[jc] : 0.0;
-          const float tR = nr ? T.tr[ir] : 0.f, tC = nc ? T.tc[jc] : 0.f;
-          ftgemm_fault_record rec;
-          rec.tile_m = tile_m; rec.tile_n = tile_n; rec.kstep = nkb - 1;
-          rec.row = ir >= 0 ? row0 + ir : -1;
-          rec.col = jc >= 0 ? col0 + jc : -1;
-          rec.residual_r = dR; rec.residual_c = dC; rec.tau = (double)tR + (double)tC;
-          rec.delta = 0.0;
-          if (nr == 1 && nc == 1) {
-            if (fabs(dR - dC) <= (double)tR + (double)tC) {
-              rec.kind = K_CORRECTED; rec.delta = dR;
-              T.fix_row = ir; T.fix_col = jc; T.fix_delta = dR;
+        for (int c = r; c < BN; c += 128) {
+          int fl = 0;
+          float cc = 0.f, tcv = 0.f;
+          if (c < DN) {
+#pragma unroll
+            for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], P.vscale[(size_t)x.tm * CSR + q], cc);
+            cc += T.ccadj[c];
+            const int gc = col0 + c;
+            tcv = gc < P.N ? lam_u * P.froA[x.tm] * P.nB[gc] : 0.f;
+            const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
+            fl = fabsf(s - cc) > tcv;
+          }
+          T.ccol[c] = cc;
+          T.tc[c] = tcv;
+          T.flag_c[c] = fl;
+          flagged |= fl;
+        }
+        // barrier + OR over the four epilogue warps: the same answer in all
+        if (bar_red_or(1, 128, flagged)) {
+          // ----- fp64 confirmation of every screened row / column -----
+          if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
+          for (int c = r; c < BN; c += 128) T.sum_c[c] = 0.0;
+          epi_bar();
+          double sr = 0.0;
+          for (int ch = 0; ch < BN / 16; ++ch) {
+            float v[16];
+            tmem_ld16(tl + ch * 16, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int c = ch * 16 + q;
+              if (c < DN) {
+                sr += (double)v[q];
+                if (data_row && T.flag_c[c]) atomicAdd(&T.sum_c[c], (double)v[q]);
+              }
+            }
+          }
+          T.sum_r[r] = sr;
+          epi_bar();
+          if (T.flag_r[r]) {
+            const double dd = sr - (double)T.crow[r];
+            if (fabs(dd) > (double)T.tr[r]) {
+              atomicAdd(&T.nr, 1);
+              atomicMax(&T.bestr, flag_key(flag_score((float)dd, T.tr[r]), r));
+            }
+          }
+          for (int c = r; c < DN; c += 128) {
+            if (T.flag_c[c]) {
+              const double dd = T.sum_c[c] - (double)T.ccol[c];
+              if (fabs(dd) > (double)T.tc[c]) {
+                atomicAdd(&T.nc, 1);
+                atomicMax(&T.bestc, flag_key(flag_score((float)dd, T.tc[c]), c));
+              }
+            }
+          }
+          epi_bar();
+          if (r == 0 && (T.nr | T.nc)) {
+            const int nr = T.nr, nc = T.nc;
+            const int ir = nr ? key_index(T.bestr) : -1, jc = nc ? key_index(T.bestc) : -1;
+            const double dR = nr ? T.sum_r[ir] - (double)T.crow[ir] : 0.0;
+            const double dC = nc ? T.sum_c[jc] - (double)T.ccol[jc] : 0.0;
+            const float tR = nr ? T.tr[ir] : 0.f, tC = nc ? T.tc[jc] : 0.f;
+            ftgemm_fault_record rec;
+            rec.tile_m = x.tm; rec.tile_n = x.tn; rec.kstep = P.nkb - 1;
+            rec.problem = P.id; rec.reserved = 0;
+            rec.row = ir >= 0 ? row0 + ir : -1;
+            rec.col = jc >= 0 ? col0 + jc : -1;
+            rec.residual_r = dR; rec.residual_c = dC; rec.tau = (double)tR + (double)tC;
+            rec.delta = 0.0;
+            if (nr == 1 && nc == 1) {
+              if (fabs(dR - dC) <= (double)tR + (double)tC) {
+                rec.kind = K_CORRECTED; rec.delta = dR;
+                T.fix_row[ab] = ir; T.fix_col[ab] = jc; T.fix_delta[ab] = dR;
+              } else {
+                rec.kind = K_UNCORRECTABLE;
+              }
+            } else if ((nr == 1 && nc == 0) || (nr == 0 && nc == 1)) {
+              rec.kind = K_CHECKSUM; rec.delta = nr ? -dR : -dC;
             } else {
               rec.kind = K_UNCORRECTABLE;
             }
-          } else if ((nr == 1 && nc == 0) || (nr == 0 && nc == 1)) {
-            rec.kind = K_CHECKSUM; rec.delta = nr ? -dR : -dC;
-          } else {
-            rec.kind = K_UNCORRECTABLE;
+            report_event(run.rep, run.recs, rec);
           }
-          report_event(p.rep, p.recs, rec);
+          epi_bar();
         }
-        epi_bar();
       }
-    }
-    // ----- alpha * acc + beta * C, store -----
-    // every lane reads tensor memory (the loads are warp-collective); only
-    // data rows inside the matrix store, and only data columns
-    const int fr = ABFT ? T.fix_row : -1;
-    const int fc = ABFT ? T.fix_col : -1;
-    const double fd = ABFT ? T.fix_delta : 0.0;
-    const bool row_ok = data_row && gr < p.M;
-    float* crow_ptr = p.C + (long long)(row_ok ? gr : 0) * p.ldc + col0;
-    const float sc = alpha * acc_scale;
-    for (int ch = 0; ch < BN / 16; ++ch) {
-      float v[16];
-      tmem_ld16(tl + ch * 16, v);
-      tmem_wait_ld();
-      if (!row_ok) continue;
-      if (ABFT && r == fr && fc >= ch * 16 && fc < ch * 16 + 16) {
+      // ----- alpha * acc + beta * C, store -----
+      // every lane reads tensor memory (the loads are warp-collective); only
+      // data rows inside the matrix store, and only data columns
+      const int fr = ABFT ? T.fix_row[ab] : -1;
+      const int fc = ABFT ? T.fix_col[ab] : -1;
+      const double fd = ABFT ? T.fix_delta[ab] : 0.0;
+      const bool row_ok = ok && data_row && gr < P.M;
+      float* crow_ptr = P.C + (long long)(row_ok ? gr : 0) * P.ldc + col0;
+      for (int ch = 0; ch < BN / 16; ++ch) {
+        float v[16];
+        tmem_ld16(tl + ch * 16, v);
+        tmem_wait_ld();
+        if (!row_ok) continue;
+        if (ABFT && r == fr && fc >= ch * 16 && fc < ch * 16 + 16) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (ch * 16 + q == fc) v[q] = (float)((double)v[q] - fd);
-      }
+          for (int q = 0; q < 16; ++q)
+            if (ch * 16 + q == fc) v[q] = (float)((double)v[q] - fd);
+        }
 #pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        const int c = ch * 16 + q;  // tile column of this group of 4
-        if (c >= DN) break;
-        const int gc = col0 + c;
-        float* dst = crow_ptr + c;
-        // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
-        if (p.c_vec && c + 3 < DN && gc + 3 < p.N) {
-          float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
-          if (beta != 0.f) {
-            const float4 ci = *reinterpret_cast<const float4*>(dst);
-            o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
-            o.z = fmaf(beta, ci.z, o.z); o.w = fmaf(beta, ci.w, o.w);
-          }
-          *reinterpret_cast<float4*>(dst) = o;
-        } else {
+        for (int q = 0; q < 16; q += 4) {
+          const int c = ch * 16 + q;  // tile column of this group of 4
+          if (c >= DN) break;
+          const int gc = col0 + c;
+          float* dst = crow_ptr + c;
+          // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
+          if (P.c_vec && c + 3 < DN && gc + 3 < P.N) {
+            float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
+            if (beta != 0.f) {
+              const float4 ci = *reinterpret_cast<const float4*>(dst);
+              o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
+              o.z = fmaf(beta, ci.z, o.z); o.w = fmaf(beta, ci.w, o.w);
+            }
+            *reinterpret_cast<float4*>(dst) = o;
+          } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (c + e < DN && gc + e < p.N) {
-              const float o = sc * v[q + e];
-              dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
+            for (int e = 0; e < 4; ++e) {
+              if (c + e < DN && gc + e < P.N) {
+                const float o = sc * v[q + e];
+                dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
+              }
             }
           }
         }
       }
+      // this warp is done with the accumulator: hand it back to the MMA warp
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&T.acc_empty[ab]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (tid == 0 && T.abort) atomicAdd(&p.rep->timeouts, 1);
+  if (tid == 0 && T.abort) atomicAdd(&run.rep->timeouts, 1);
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -422,20 +497,21 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 template <int DT, bool ABFT>
-cudaError_t launch_tc_impl(const TcMaps& maps, const TcParams& p, cudaStream_t st) {
+cudaError_t launch_tc_impl(const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid, cudaStream_t st) {
   using Cfg = TcCfg<DT, ABFT>;
   const size_t smem = 1024 + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES + sizeof(TcSmemTail);
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<DT, ABFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = p.tiles_m * p.tiles_n;
-  tc_gemm_kernel<DT, ABFT><<<grid, Cfg::THREADS, smem, st>>>(maps.A, maps.B, maps.W, maps.V, p);
+  tc_gemm_kernel<DT, ABFT><<<grid, Cfg::THREADS, smem, st>>>(b, mb, run);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(int dt, bool abft, const TcMaps& maps, const TcParams& p, cudaStream_t st) {
-  if (dt == 0) return abft ? launch_tc_impl<0, true>(maps, p, st) : launch_tc_impl<0, false>(maps, p, st);
-  return abft ? launch_tc_impl<1, true>(maps, p, st) : launch_tc_impl<1, false>(maps, p, st);
+// Persistent launch over b.total_tiles tiles with `grid` CTAs (<= one per SM).
+cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
+                           cudaStream_t st) {
+  if (dt == 0) return abft ? launch_tc_impl<0, true>(b, mb, run, grid, st) : launch_tc_impl<0, false>(b, mb, run, grid, st);
+  return abft ? launch_tc_impl<1, true>(b, mb, run, grid, st) : launch_tc_impl<1, false>(b, mb, run, grid, st);
 }
 
 }  // namespace ftg

@@ -36,46 +36,66 @@ __device__ __forceinline__ float ld_elem(const void* base, long long idx) {
   }
 }
 
+// Every encode kernel runs over a batch of problems (TcBatch): a problem's
+// blocks of launch `kind` start at blk_start[kind], found by binary search.
+#define TC_BLOCK_OF(KIND)                                  \
+  const int pi = tc_find_block(b, KIND, blockIdx.x);       \
+  const TcProblem& P = tc_problem(b, pi);                  \
+  const int lb = (int)blockIdx.x - P.blk_start[KIND]
+
 // B (K x N, ldb elements) -> Bt (N x ldk): 32 x 32 tiles through shared memory
 template <typename E>
-__global__ void tc_transpose_kernel(const E* __restrict__ B, long long ldb, int K, int N, E* __restrict__ Bt,
-                                    long long ldk) {
+__global__ void tc_transpose_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_TRANSPOSE);
   __shared__ E tile[32][33];
-  const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const E* B = reinterpret_cast<const E*>(P.B);
+  E* Bt = reinterpret_cast<E*>(P.Bt);
+  const int nbx = (P.N + 31) / 32;
+  const int n0 = (lb % nbx) * 32, k0 = (lb / nbx) * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int r = ty; r < 32; r += 8) {
     const int k = k0 + r, n = n0 + tx;
-    tile[r][tx] = (k < K && n < N) ? B[(long long)k * ldb + n] : E(0);
+    tile[r][tx] = (k < P.K && n < P.N) ? B[(long long)k * P.ldb + n] : E(0);
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     const int n = n0 + r, k = k0 + tx;
-    if (n < N && k < K) Bt[(long long)n * ldk + k] = tile[tx][r];
+    if (n < P.N && k < P.K) Bt[(long long)n * P.ldk + k] = tile[tx][r];
   }
 }
 
-// S[b][k] = sum over rows r in block b (bs rows) of X[r][k]; X is R x K (K-major)
-template <int DT>
-__global__ void tc_blocksum_kernel(const void* __restrict__ X, long long ldx, int R, int K, int bs,
-                                   float* __restrict__ S) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (k >= K) return;
-  const int r1 = min(R, (b + 1) * bs);
+// S[blk][k] = sum over the rows r of block blk (bs rows) of X[r][k]; X is
+// R x K, K contiguous.  side 0: A, 120-row blocks -> Vf; side 1: B^T,
+// 248-row blocks -> Wf.
+template <int DT, int SIDE>
+__global__ void tc_blocksum_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(SIDE == 0 ? P_SUM_A : P_SUM_B);
+  const void* X = SIDE == 0 ? P.A : P.Bt;
+  const long long ldx = SIDE == 0 ? P.lda : P.ldk;
+  const int R = SIDE == 0 ? P.M : P.N, bs = SIDE == 0 ? TC_DM : TC_DN;
+  float* S = SIDE == 0 ? P.Vf : P.Wf;
+  const int nkx = (P.K + 255) / 256;
+  const int k = (lb % nkx) * 256 + threadIdx.x, blk = lb / nkx;
+  if (k >= P.K) return;
+  const int r1 = min(R, (blk + 1) * bs);
   float s = 0.f;
-  for (int r = b * bs; r < r1; ++r) s += ld_elem<DT>(X, (long long)r * ldx + k);
-  S[(long long)b * K + k] = s;
+  for (int r = blk * bs; r < r1; ++r) s += ld_elem<DT>(X, (long long)r * ldx + k);
+  S[(long long)blk * P.K + k] = s;
 }
 
-// n[r] = ||X[r][:]||_2, one warp per row
-template <int DT>
-__global__ void tc_rownorm_kernel(const void* __restrict__ X, long long ldx, int R, int K,
-                                  float* __restrict__ nrm) {
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// n[r] = ||X[r][:]||_2, one warp per row (side 0: rows of A; 1: rows of B^T)
+template <int DT, int SIDE>
+__global__ void tc_rownorm_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(SIDE == 0 ? P_NORM_A : P_NORM_B);
+  const void* X = SIDE == 0 ? P.A : P.Bt;
+  const long long ldx = SIDE == 0 ? P.lda : P.ldk;
+  const int R = SIDE == 0 ? P.M : P.N;
+  float* nrm = SIDE == 0 ? P.nA : P.nB;
+  const int r = lb * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= R) return;
   float s = 0.f;
-  for (int k = lane; k < K; k += 32) {
+  for (int k = lane; k < P.K; k += 32) {
     const float v = ld_elem<DT>(X, (long long)r * ldx + k);
     s = fmaf(v, v, s);
   }
@@ -84,22 +104,30 @@ __global__ void tc_rownorm_kernel(const void* __restrict__ X, long long ldx, int
   if (lane == 0) nrm[r] = sqrtf(s);
 }
 
-// fro[b] = sqrt(sum_{r in block b} n[r]^2)
-__global__ void tc_blockfro_kernel(const float* __restrict__ nrm, int R, int bs, int nb,
-                                   float* __restrict__ fro) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+// fro[blk] = sqrt(sum_{r in blk} n[r]^2) for the row blocks of A (first
+// tiles_m indices) and the column blocks of B (next tiles_n)
+__global__ void tc_blockfro_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_FRO);
+  const int i = lb * blockDim.x + threadIdx.x;
+  if (i >= P.tiles_m + P.tiles_n) return;
+  const bool side_a = i < P.tiles_m;
+  const int blk = side_a ? i : i - P.tiles_m;
+  const int R = side_a ? P.M : P.N, bs = side_a ? TC_DM : TC_DN;
+  const float* nrm = side_a ? P.nA : P.nB;
   float s = 0.f;
-  for (int r = b * bs; r < min(R, (b + 1) * bs); ++r) s = fmaf(nrm[r], nrm[r], s);
-  fro[b] = sqrtf(s);
+  for (int r = blk * bs; r < min(R, (blk + 1) * bs); ++r) s = fmaf(nrm[r], nrm[r], s);
+  (side_a ? P.froA : P.froB)[blk] = sqrtf(s);
 }
 
-// s0[b]: power of two with max_k |S[b][k]| * s0 in (224, 448]  (fp8 only)
-__global__ void tc_blockscale_kernel(const float* __restrict__ S, int K, float* __restrict__ s0) {
+// s0[blk]: power of two with max_k |S[blk][k]| * s0 in (224, 448]  (fp8 only)
+__global__ void tc_blockscale_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_SCALE);
   __shared__ float red[32];
-  const int b = blockIdx.x;
+  const bool side_a = lb < P.tiles_m;
+  const int blk = side_a ? lb : lb - P.tiles_m;
+  const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.K;
   float m = 0.f;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) m = fmaxf(m, fabsf(S[(long long)b * K + k]));
+  for (int k = threadIdx.x; k < P.K; k += blockDim.x) m = fmaxf(m, fabsf(S[k]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -113,34 +141,41 @@ __global__ void tc_blockscale_kernel(const float* __restrict__ S, int K, float* 
       frexpf(448.f / t, &e);  // 448/t in [2^(e-1), 2^e)
       sc = ldexpf(1.f, e - 1);
     }
-    s0[b] = sc;
+    (side_a ? P.s0v : P.s0w)[blk] = sc;
   }
 }
 
-// Pieces of S[b][k] into P[(b*TC_CS_SLOTS + c)][k] (unused slots zero) and
-// their multipliers scale[b*TC_CS_SLOTS + c].
+// Pieces of S[blk][k] into Pc[(blk*TC_CS_SLOTS + c)][k] (unused slots zero)
+// and their multipliers scale[blk*TC_CS_SLOTS + c]; row blocks of A first,
+// then column blocks of B.
 template <int DT>
-__global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, long long ldp,
-                                 void* __restrict__ P, float* __restrict__ scale, const float* __restrict__ s0) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
+__global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_PIECES);
   constexpr int NS = TC_CS_SLOTS;
-  if (blockIdx.x == 0 && threadIdx.x < NS) {
+  const int nkx = (P.K + 255) / 256;
+  const int k = (lb % nkx) * 256 + threadIdx.x, bi = lb / nkx;
+  const bool side_a = bi < P.tiles_m;
+  const int blk = side_a ? bi : bi - P.tiles_m;
+  const float* S = side_a ? P.Vf : P.Wf;
+  void* Pc = side_a ? P.Vt : P.Wt;
+  float* scale = side_a ? P.vscale : P.wscale;
+  const float* s0 = side_a ? P.s0v : P.s0w;
+  if (lb % nkx == 0 && threadIdx.x < NS) {
     const int c = threadIdx.x;
     float m = 0.f;
     if (DT == 0) {
       m = c < 3 ? 1.f : 0.f;
     } else if (c < 5) {
-      m = s0[b];
+      m = s0[blk];
       for (int q = 0; q < c; ++q) m *= 16.f;
       m = 1.f / m;
     }
-    scale[b * NS + c] = m;
+    scale[blk * NS + c] = m;
   }
-  if (k >= K) return;
-  float x = S[(long long)b * K + k];
+  if (k >= P.K) return;
+  float x = S[(long long)blk * P.K + k];
   if constexpr (DT == 0) {
-    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P);
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Pc);
     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
     const float r1 = x - __bfloat162float(hi);
     const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
@@ -148,11 +183,11 @@ __global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, lon
     const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
     for (int c = 0; c < NS; ++c) {
       const __nv_bfloat16 v = c == 0 ? hi : c == 1 ? mid : c == 2 ? lo : __float2bfloat16_rn(0.f);
-      out[(long long)(b * NS + c) * ldp + k] = v;
+      out[(long long)(blk * NS + c) * P.ldk + k] = v;
     }
   } else {
-    __nv_fp8_storage_t* out = reinterpret_cast<__nv_fp8_storage_t*>(P);
-    float sc = s0[b];
+    __nv_fp8_storage_t* out = reinterpret_cast<__nv_fp8_storage_t*>(Pc);
+    float sc = s0[blk];
     for (int c = 0; c < NS; ++c) {
       __nv_fp8_storage_t q = 0;
       if (c < 5) {
@@ -162,7 +197,7 @@ __global__ void tc_pieces_kernel(const float* __restrict__ S, int nb, int K, lon
         x -= float(qq) / sc;
         sc *= 16.f;
       }
-      out[(long long)(b * NS + c) * ldp + k] = q;
+      out[(long long)(blk * NS + c) * P.ldk + k] = q;
     }
   }
 }
@@ -194,50 +229,51 @@ __global__ void cast_e4m3_kernel(const float* __restrict__ x, long long n, const
 
 // ---------------------------------------------------------------------------
 
-// Everything the tensor-core kernel needs besides A and B, written into the
-// caller's buffers (see TcPrepBuffers).
-cudaError_t launch_tc_prep(int dt, const void* A, long long lda, const void* B, long long ldb, int M, int N,
-                           int K, bool abft, const TcPrepBuffers& w, int* launches, cudaStream_t st) {
-  {
-    dim3 g((N + 31) / 32, (K + 31) / 32);
-    if (dt == 0)
-      tc_transpose_kernel<uint16_t><<<g, dim3(32, 8), 0, st>>>((const uint16_t*)B, ldb, K, N, (uint16_t*)w.Bt, w.ldk);
-    else
-      tc_transpose_kernel<uint8_t><<<g, dim3(32, 8), 0, st>>>((const uint8_t*)B, ldb, K, N, (uint8_t*)w.Bt, w.ldk);
+// Blocks each batched encode launch gives one problem.
+void tc_prep_blocks(const TcProblem& P, int out[P_KINDS]) {
+  const int nkx = (P.K + 255) / 256;
+  out[P_TRANSPOSE] = ((P.N + 31) / 32) * ((P.K + 31) / 32);
+  out[P_SUM_A] = nkx * P.tiles_m;
+  out[P_SUM_B] = nkx * P.tiles_n;
+  out[P_NORM_A] = (P.M + 7) / 8;
+  out[P_NORM_B] = (P.N + 7) / 8;
+  out[P_FRO] = (P.tiles_m + P.tiles_n + 127) / 128;
+  out[P_SCALE] = P.tiles_m + P.tiles_n;
+  out[P_PIECES] = nkx * (P.tiles_m + P.tiles_n);
+}
+
+// The encode pass of a batch: B^T for every problem; with checksums also
+// the block sums, norms, Frobenius norms and pieces.  total[kind] = blocks
+// of each launch over the batch.
+cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
+                           cudaStream_t st) {
+  auto go = [&](int kind) { return total[kind] > 0; };
+  if (go(P_TRANSPOSE)) {
+    if (dt == 0) tc_transpose_kernel<uint16_t><<<total[P_TRANSPOSE], dim3(32, 8), 0, st>>>(b);
+    else tc_transpose_kernel<uint8_t><<<total[P_TRANSPOSE], dim3(32, 8), 0, st>>>(b);
     ++*launches;
   }
   if (!abft) return cudaGetLastError();
-  const int tiles_m = (M + TC_DM - 1) / TC_DM, tiles_n = (N + TC_DN - 1) / TC_DN;
-  auto blocksum = [&](const void* X, long long ldx, int R, int bs, float* S) {
-    dim3 g((K + 255) / 256, (R + bs - 1) / bs);
-    if (dt == 0) tc_blocksum_kernel<0><<<g, 256, 0, st>>>(X, ldx, R, K, bs, S);
-    else tc_blocksum_kernel<1><<<g, 256, 0, st>>>(X, ldx, R, K, bs, S);
+  if (dt == 0) {
+    tc_blocksum_kernel<0, 0><<<total[P_SUM_A], 256, 0, st>>>(b);
+    tc_blocksum_kernel<0, 1><<<total[P_SUM_B], 256, 0, st>>>(b);
+    tc_rownorm_kernel<0, 0><<<total[P_NORM_A], 256, 0, st>>>(b);
+    tc_rownorm_kernel<0, 1><<<total[P_NORM_B], 256, 0, st>>>(b);
+  } else {
+    tc_blocksum_kernel<1, 0><<<total[P_SUM_A], 256, 0, st>>>(b);
+    tc_blocksum_kernel<1, 1><<<total[P_SUM_B], 256, 0, st>>>(b);
+    tc_rownorm_kernel<1, 0><<<total[P_NORM_A], 256, 0, st>>>(b);
+    tc_rownorm_kernel<1, 1><<<total[P_NORM_B], 256, 0, st>>>(b);
+  }
+  tc_blockfro_kernel<<<total[P_FRO], 128, 0, st>>>(b);
+  *launches += 5;
+  if (dt == 1) {
+    tc_blockscale_kernel<<<total[P_SCALE], 256, 0, st>>>(b);
     ++*launches;
-  };
-  auto rownorm = [&](const void* X, long long ldx, int R, float* n) {
-    if (dt == 0) tc_rownorm_kernel<0><<<(R + 7) / 8, 256, 0, st>>>(X, ldx, R, K, n);
-    else tc_rownorm_kernel<1><<<(R + 7) / 8, 256, 0, st>>>(X, ldx, R, K, n);
-    ++*launches;
-  };
-  auto pieces = [&](const float* S, int nb, void* P, float* scale, float* s0) {
-    if (dt == 1) {
-      tc_blockscale_kernel<<<nb, 256, 0, st>>>(S, K, s0);
-      ++*launches;
-    }
-    dim3 g((K + 255) / 256, nb);
-    if (dt == 0) tc_pieces_kernel<0><<<g, 256, 0, st>>>(S, nb, K, w.ldk, P, scale, s0);
-    else tc_pieces_kernel<1><<<g, 256, 0, st>>>(S, nb, K, w.ldk, P, scale, s0);
-    ++*launches;
-  };
-  blocksum(A, lda, M, TC_DM, w.Vf);
-  blocksum(w.Bt, w.ldk, N, TC_DN, w.Wf);
-  rownorm(A, lda, M, w.nA);
-  rownorm(w.Bt, w.ldk, N, w.nB);
-  tc_blockfro_kernel<<<(tiles_m + 127) / 128, 128, 0, st>>>(w.nA, M, TC_DM, tiles_m, w.froA);
-  tc_blockfro_kernel<<<(tiles_n + 127) / 128, 128, 0, st>>>(w.nB, N, TC_DN, tiles_n, w.froB);
-  *launches += 2;
-  pieces(w.Vf, tiles_m, w.Vt, w.vscale, w.s0v);
-  pieces(w.Wf, tiles_n, w.Wt, w.wscale, w.s0w);
+  }
+  if (dt == 0) tc_pieces_kernel<0><<<total[P_PIECES], 256, 0, st>>>(b);
+  else tc_pieces_kernel<1><<<total[P_PIECES], 256, 0, st>>>(b);
+  ++*launches;
   return cudaGetLastError();
 }
 

@@ -30,7 +30,9 @@ def test_header_declares_the_boundary():
     names = _declared_symbols()
     for must in ("ftgemm_create", "ftgemm_destroy", "ftgemm_gemm", "ftgemm_report_fetch",
                  "ftgemm_encode", "ftgemm_set_schedule", "ftgemm_get_schedule",
-                 "ftgemm_set_threshold", "ftgemm_status_string"):
+                 "ftgemm_set_threshold", "ftgemm_status_string", "ftgemm_group_create",
+                 "ftgemm_group_tiles", "ftgemm_group_set_faults", "ftgemm_grouped_gemm",
+                 "ftgemm_group_destroy"):
         assert must in names
 
 
@@ -49,4 +51,10 @@ def test_host_side_argument_checks(libpath):
     assert L.ftgemm_create(None, 0, None) == -1
     assert L.ftgemm_report_fetch(None, None) == -1
     assert L.ftgemm_set_schedule(None, None) == -1
+    out = ctypes.c_void_p()
+    assert L.ftgemm_group_create(None, 1, None, ft.BF16, ft.FT_TILE, ctypes.byref(out)) == -1
+    assert L.ftgemm_grouped_gemm(None, None) == -1
+    assert L.ftgemm_group_set_faults(None, None, None) == -1
+    assert L.ftgemm_group_tiles(None, None, None) == -1
+    assert L.ftgemm_group_destroy(None) == 0
     assert b"NULL" in L.ftgemm_last_error() or len(L.ftgemm_last_error()) > 0
