@@ -27,7 +27,7 @@ cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*,
                                  float*, int*, cudaStream_t);
 cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, float*, long long,
                                  cudaStream_t);
-void tc_prep_blocks(const TcProblem& P, int out[P_KINDS]);
+void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]);
 cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
                            cudaStream_t st);
 cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
@@ -358,6 +358,8 @@ static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
     P.s0w = take(tn);
     P.nA = take(P.M);
     P.nB = take(P.N);
+    P.nA_part = take((size_t)((K + 255) / 256) * P.M);
+    P.nB_part = take((size_t)((K + (dt == 0 ? 63 : 127)) / (dt == 0 ? 64 : 128)) * P.N);
     P.froA = take(tm);
     P.froB = take(tn);
   }
@@ -423,7 +425,7 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
     if (rc) return rc;
   }
   int total[P_KINDS];
-  tc_prep_blocks(P, total);
+  tc_prep_blocks(P, dt, total);
   int launches = 0;
   CK(launch_tc_prep(dt, abft, b, total, &launches, h->stream));
   TcMapsBatch mb;
@@ -462,6 +464,9 @@ struct ftgemm_group {
   std::vector<int> pos;          // user index -> schedule position
   TcProblem* d_probs = nullptr;
   TcProbMaps* d_maps = nullptr;
+  int4* d_tiles = nullptr;      // the schedule: per-CTA tile lists, concatenated
+  int* d_cta_start = nullptr;   // [ncta + 1]
+  int ncta = 0;
   float* ws = nullptr;
   int total[P_KINDS] = {};
   int total_tiles = 0;
@@ -469,10 +474,51 @@ struct ftgemm_group {
   int nfaults = 0;
 };
 
+// Static schedule of a group's tiles over `ncta` persistent CTAs: tiles in
+// order (problems longest-K first, each in the kernel's raster), each given
+// to the CTA with the least work so far (longest-processing-time greedy).
+// A tile's cost is its k-blocks, but at least kEpilogueKb: with the
+// accumulator double-buffered a CTA's time per tile is about the larger of
+// its main loop and its epilogue.
+static void tc_schedule(const std::vector<TcProblem>& probs, int ncta, std::vector<int4>& tiles,
+                        std::vector<int>& cta_start) {
+  constexpr long long kEpilogueKb = 6;
+  std::vector<std::vector<int4>> per(ncta);
+  // min-heap of (load, cta)
+  std::vector<std::pair<long long, int>> heap;
+  for (int c = 0; c < ncta; ++c) heap.push_back({0, c});
+  auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  for (int pi = 0; pi < (int)probs.size(); ++pi) {
+    const TcProblem& P = probs[pi];
+    const long long cost = std::max<long long>(P.nkb, kEpilogueKb);
+    const int ntile = P.tiles_m * P.tiles_n, per_group = TC_GROUP_M * P.tiles_n;
+    for (int id = 0; id < ntile; ++id) {
+      const int first_m = (id / per_group) * TC_GROUP_M;
+      const int gsize = std::min(P.tiles_m - first_m, TC_GROUP_M);
+      const int tm = first_m + (id % per_group) % gsize, tn = (id % per_group) / gsize;
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto& top = heap.back();
+      per[top.second].push_back(make_int4(pi, tm, tn, P.nkb));
+      top.first += cost;
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+  }
+  tiles.clear();
+  cta_start.assign(ncta + 1, 0);
+  for (int c = 0; c < ncta; ++c) {
+    cta_start[c] = (int)tiles.size();
+    tiles.insert(tiles.end(), per[c].begin(), per[c].end());
+  }
+  cta_start[ncta] = (int)tiles.size();
+}
+
 static void group_free(ftgemm_group* g) {
   if (!g) return;
   if (g->d_probs) cudaFree(g->d_probs);
   if (g->d_maps) cudaFree(g->d_maps);
+  if (g->d_tiles) cudaFree(g->d_tiles);
+  if (g->d_cta_start) cudaFree(g->d_cta_start);
   if (g->ws) cudaFree(g->ws);
   if (g->d_faults) cudaFree(g->d_faults);
   delete g;
@@ -528,7 +574,7 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
     P.tile_start = (int)tiles;
     tiles += (long long)P.tiles_m * P.tiles_n;
     int nb[P_KINDS];
-    tc_prep_blocks(P, nb);
+    tc_prep_blocks(P, dt, nb);
     for (int kd = 0; kd < P_KINDS; ++kd) {
       P.blk_start[kd] = (int)blocks[kd];
       blocks[kd] += nb[kd];
@@ -554,11 +600,20 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
     int rc = tc_make_maps(maps[q], g->probs[q], dt, abft);
     if (rc) { group_free(g); return rc; }
   }
+  g->ncta = std::max(1, std::min(g->total_tiles, h->num_sms > 0 ? h->num_sms : 148));
+  std::vector<int4> sched;
+  std::vector<int> cta_start;
+  tc_schedule(g->probs, g->ncta, sched, cta_start);
   e = cudaMalloc(&g->d_probs, sizeof(TcProblem) * count);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_maps, sizeof(TcProbMaps) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_tiles, sizeof(int4) * sched.size());
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_cta_start, sizeof(int) * cta_start.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(g->d_probs, g->probs.data(), sizeof(TcProblem) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_maps, maps.data(), sizeof(TcProbMaps) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_tiles, sched.data(), sizeof(int4) * sched.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_cta_start, cta_start.data(), sizeof(int) * cta_start.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     group_free(g);
     FAIL(FTGEMM_ERR_CUDA, "ftgemm_group_create: %s", cudaGetErrorString(e));
@@ -628,6 +683,8 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   TcBatch b;
   memset(&b, 0, sizeof(b));
   b.table = g->d_probs;
+  b.tile_list = g->d_tiles;
+  b.cta_start = g->d_cta_start;
   b.nprob = g->count;
   b.total_tiles = g->total_tiles;
   int launches = 0;
@@ -636,7 +693,7 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   memset(&mb, 0, sizeof(mb));
   mb.table = g->d_maps;
   TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, h->rep, h->recs};
-  const int grid = std::max(1, std::min(b.total_tiles, h->num_sms > 0 ? h->num_sms : 148));
+  const int grid = g->ncta;  // the schedule was built for this many CTAs
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(h->stream, &cs));
   const bool timed = h->timing && cs == cudaStreamCaptureStatusNone;

@@ -102,7 +102,7 @@ constexpr int TC_GROUP_M = 16;  // tile rows per raster group
 
 // Batched encode launches of the tensor-core path; a problem's first block
 // in launch `kind` is TcProblem::blk_start[kind].
-enum TcPrepKind { P_TRANSPOSE = 0, P_SUM_A, P_SUM_B, P_NORM_A, P_NORM_B, P_FRO, P_SCALE, P_PIECES, P_KINDS };
+enum TcPrepKind { P_ENC_A = 0, P_ENC_B, P_FIN, P_SCALE, P_PIECES, P_KINDS };
 
 // One GEMM of the tensor-core path: operands, encode buffers, epilogue.
 // A table of these drives the encode launches and the persistent GEMM; a
@@ -119,6 +119,7 @@ struct TcProblem {
   float* vscale; float* wscale;   // [tiles * TC_CS_SLOTS] multiplier of each piece
   float* s0v; float* s0w;         // [tiles] fp8 piece base scales
   float* nA; float* nB;           // [M] row 2-norms of A, [N] column 2-norms of B
+  float* nA_part; float* nB_part; // squared-norm partials per k-chunk: [ceil(K/256)][M], [ceil(K/kc)][N]
   float* froA; float* froB;       // [tiles_m], [tiles_n] Frobenius norms of the blocks
   float* C; long long ldc;
   int c_vec;                      // C rows 16-byte aligned (float4 stores)
@@ -130,6 +131,11 @@ struct TcProblem {
 
 struct TcBatch {
   const TcProblem* table;  // device table of nprob problems, or null: use `one`
+  // With a table: CTA c runs tile_list[cta_start[c] .. cta_start[c+1]), each
+  // entry {problem, tile_m, tile_n, k-blocks} (a host-built schedule).
+  // Without: CTA c runs raster tiles c, c + gridDim.x, ... of `one`.
+  const int4* tile_list;
+  const int* cta_start;
   int nprob;
   int total_tiles;
   TcProblem one;
@@ -164,15 +170,6 @@ __device__ __forceinline__ int tc_find_block(const TcBatch& b, int kind, int blk
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (b.table[mid].blk_start[kind] <= blk) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-__device__ __forceinline__ int tc_find_tile(const TcBatch& b, int t) {
-  if (!b.table) return 0;
-  int lo = 0, hi = b.nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (b.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
   }
   return lo;
 }

@@ -96,21 +96,32 @@ struct TcSmemTail {
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Problem, tile row and tile column of list entry t: problems in table
-// order, tiles of a problem in a raster of TC_GROUP_M tile rows by all its
-// tile columns, column-major inside a group.
+// The tiles one CTA runs.  With a problem table: the CTA's slice of the
+// host-built tile list.  With one inline problem: every gridDim.x-th entry
+// of a raster of TC_GROUP_M tile rows by all tile columns, column-major
+// inside a group.
 struct TcTile {
-  int pi, tm, tn;
+  int pi, tm, tn, nkb;
 };
-__device__ __forceinline__ TcTile tc_tile(const TcBatch& b, int t) {
+__device__ __forceinline__ int tc_my_count(const TcBatch& b) {
+  if (b.table) return b.cta_start[blockIdx.x + 1] - b.cta_start[blockIdx.x];
+  return (int)blockIdx.x < b.total_tiles ? (b.total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+}
+__device__ __forceinline__ TcTile tc_my_tile(const TcBatch& b, int my0, int j) {
   TcTile x;
-  x.pi = tc_find_tile(b, t);
-  const TcProblem& P = tc_problem(b, x.pi);
-  const int id = t - P.tile_start, per_group = TC_GROUP_M * P.tiles_n;
+  if (b.table) {
+    const int4 e = b.tile_list[my0 + j];
+    x.pi = e.x; x.tm = e.y; x.tn = e.z; x.nkb = e.w;
+    return x;
+  }
+  const TcProblem& P = b.one;
+  const int id = (int)blockIdx.x + j * (int)gridDim.x, per_group = TC_GROUP_M * P.tiles_n;
   const int first_m = (id / per_group) * TC_GROUP_M;
   const int gsize = min(P.tiles_m - first_m, TC_GROUP_M);
+  x.pi = 0;
   x.tm = first_m + (id % per_group) % gsize;
   x.tn = (id % per_group) / gsize;
+  x.nkb = P.nkb;
   return x;
 }
 
@@ -155,9 +166,10 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t it = 0;  // k-blocks issued, over all tiles of this CTA
     int last_pi = -1;
     bool dead = false;
-    for (int t = blockIdx.x; t < b.total_tiles && !dead; t += gridDim.x) {
-      const TcTile x = tc_tile(b, t);
-      const TcProblem& P = tc_problem(b, x.pi);
+    const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
+    TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
+    for (int j = 0; j < n_my && !dead; ++j) {
+      const TcTile x = nx;
       const TcProbMaps* mp = mb.table ? &mb.table[x.pi] : &mb.one;
       if (x.pi != last_pi) {
         if (mb.table) {
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(192, 1)
         last_pi = x.pi;
       }
       const int row0 = x.tm * DM, col0 = x.tn * DN;
-      for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+      for (int kb = 0; kb < x.nkb; ++kb, ++it) {
         const int s = it % S;
         if (it >= S && !mbar_wait(&T.empty[s], ((it / S) & 1u) ^ 1u)) {
           dead = true;
@@ -186,19 +198,23 @@ __global__ void __launch_bounds__(192, 1)
           tma_load_2d(sA(s) + DM * 128, &mp->V, &T.full[s], kb * BK, x.tm * CSR);
           tma_load_2d(sB(s) + DN * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
         }
+        // look one tile ahead while this tile's loads are in flight
+        if (kb == 0 && j + 1 < n_my) nx = tc_my_tile(b, my0, j + 1);
       }
     }
     if (dead) atomicExch(&T.abort, 1);
     // let the last loads land before the CTA may exit (bounded)
-    for (uint32_t j = it > (uint32_t)S ? it - S : 0; j < it; ++j) mbar_wait(&T.full[j % S], (j / S) & 1u);
+    for (uint32_t q = it > (uint32_t)S ? it - S : 0; q < it; ++q) mbar_wait(&T.full[q % S], (q / S) & 1u);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: one 128 x 256 MMA per 32-byte k-slice ----------------
     constexpr uint32_t idesc = tc_idesc(DT, BM, BN);
     uint32_t it = 0;
     int lt = 0;  // tiles of this CTA so far
     bool dead = false;
-    for (int t = blockIdx.x; t < b.total_tiles && !dead; t += gridDim.x, ++lt) {
-      const TcProblem& P = tc_problem(b, tc_find_tile(b, t));
+    const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
+    TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
+    for (; lt < n_my && !dead; ++lt) {
+      const int nkb = nx.nkb;
       const int ab = lt & 1;
       if (lt >= 2 && !mbar_wait(&T.acc_empty[ab], ((lt >> 1) - 1) & 1)) {
         dead = true;
@@ -206,7 +222,7 @@ __global__ void __launch_bounds__(192, 1)
       }
       tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(ab * BN);
-      for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = it % S;
         if (!mbar_wait(&T.full[s], (it / S) & 1u)) {
           dead = true;
@@ -220,6 +236,7 @@ __global__ void __launch_bounds__(192, 1)
           tc_mma<DT>(d, da + step, db + step, idesc, (kb | kk) != 0);
         }
         tc_commit(&T.empty[s]);  // the stage is free once these MMAs completed
+        if (kb == 0 && lt + 1 < n_my) nx = tc_my_tile(b, my0, lt + 1);
       }
       tc_commit(&T.acc_full[ab]);
     }
@@ -231,10 +248,12 @@ __global__ void __launch_bounds__(192, 1)
     const int lq = warp & 3;            // TMEM lane quarter this warp may access
     const int r = lq * 32 + lane;       // tile row == TMEM lane
     const bool data_row = r < DM;
+    const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
+    TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
     bool dead = false;
-    int lt = 0;
-    for (int t = blockIdx.x; t < b.total_tiles; t += gridDim.x, ++lt) {
-      const TcTile x = tc_tile(b, t);
+    for (int lt = 0; lt < n_my; ++lt) {
+      const TcTile x = nx;
+      if (lt + 1 < n_my) nx = tc_my_tile(b, my0, lt + 1);  // consumed next tile
       const TcProblem& P = tc_problem(b, x.pi);
       const int ab = lt & 1;
       const int row0 = x.tm * DM, col0 = x.tn * DN, gr = row0 + r;
@@ -250,6 +269,37 @@ __global__ void __launch_bounds__(192, 1)
       const float sc = P.alpha * P.acc_scale;  // fp8: product of the per-tensor scales
       const float beta = P.beta;
       const int my_tile = P.tile_start + x.tm * P.tiles_n + x.tn;
+      const bool row_ok = ok && data_row && gr < P.M;
+      float* crow_ptr = P.C + (long long)(row_ok ? gr : 0) * P.ldc + col0;
+      // alpha * acc + beta * C of one 16-column chunk of this row, data
+      // columns inside the matrix only
+      auto store16 = [&](int ch, const float* v) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4) {
+          const int c = ch * 16 + q;  // tile column of this group of 4
+          if (c >= DN) break;
+          const int gc = col0 + c;
+          float* dst = crow_ptr + c;
+          // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
+          if (P.c_vec && c + 3 < DN && gc + 3 < P.N) {
+            float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
+            if (beta != 0.f) {
+              const float4 ci = *reinterpret_cast<const float4*>(dst);
+              o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
+              o.z = fmaf(beta, ci.z, o.z); o.w = fmaf(beta, ci.w, o.w);
+            }
+            *reinterpret_cast<float4*>(dst) = o;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (c + e < DN && gc + e < P.N) {
+                const float o = sc * v[q + e];
+                dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
+              }
+            }
+          }
+        }
+      };
 
       if constexpr (ABFT) {
         T.cradj[r] = 0.f;
@@ -294,10 +344,22 @@ __global__ void __launch_bounds__(192, 1)
         }
       }
 
-      if constexpr (ABFT) {
+      if constexpr (!ABFT) {
+        // ----- alpha * acc + beta * C, store -----
+        // every lane reads tensor memory (the loads are warp-collective);
+        // only rows inside the matrix store
+        for (int ch = 0; ch < BN / 16; ++ch) {
+          float v[16];
+          tmem_ld16(tl + ch * 16, v);
+          tmem_wait_ld();
+          if (row_ok) store16(ch, v);
+        }
+      } else {
         epi_bar();
         const float lam_u = P.lam_tile ? P.lam_tile[x.tm * P.tiles_n + x.tn] : P.lam_u;
-        // ----- fp32 screen -----
+        // ----- one pass over the accumulator: fp32 screen sums and the store -----
+        // C is written before verification; a confirmed fault is then
+        // patched in place (a single element, below).
         float rs = 0.f, rc = 0.f, crow = 0.f;
         for (int ch = 0; ch < BN / 16; ++ch) {
           float v[16];
@@ -322,6 +384,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
           }
+          if (row_ok) store16(ch, v);
           // warp partial column sums over the data rows: a reduce-scatter
           // over the lanes leaves lanes 2q and 2q+1 with column idx(q)
           float w[16];
@@ -413,7 +476,7 @@ __global__ void __launch_bounds__(192, 1)
             const double dC = nc ? T.sum_c[jc] - (double)T.ccol[jc] : 0.0;
             const float tR = nr ? T.tr[ir] : 0.f, tC = nc ? T.tc[jc] : 0.f;
             ftgemm_fault_record rec;
-            rec.tile_m = x.tm; rec.tile_n = x.tn; rec.kstep = P.nkb - 1;
+            rec.tile_m = x.tm; rec.tile_n = x.tn; rec.kstep = x.nkb - 1;
             rec.problem = P.id; rec.reserved = 0;
             rec.row = ir >= 0 ? row0 + ir : -1;
             rec.col = jc >= 0 ? col0 + jc : -1;
@@ -434,48 +497,26 @@ __global__ void __launch_bounds__(192, 1)
             report_event(run.rep, run.recs, rec);
           }
           epi_bar();
-        }
-      }
-      // ----- alpha * acc + beta * C, store -----
-      // every lane reads tensor memory (the loads are warp-collective); only
-      // data rows inside the matrix store, and only data columns
-      const int fr = ABFT ? T.fix_row[ab] : -1;
-      const int fc = ABFT ? T.fix_col[ab] : -1;
-      const double fd = ABFT ? T.fix_delta[ab] : 0.0;
-      const bool row_ok = ok && data_row && gr < P.M;
-      float* crow_ptr = P.C + (long long)(row_ok ? gr : 0) * P.ldc + col0;
-      for (int ch = 0; ch < BN / 16; ++ch) {
-        float v[16];
-        tmem_ld16(tl + ch * 16, v);
-        tmem_wait_ld();
-        if (!row_ok) continue;
-        if (ABFT && r == fr && fc >= ch * 16 && fc < ch * 16 + 16) {
+          // ----- correct the located element of C (Section 4.2.1) -----
+          // The warp owning its TMEM lane rereads the accumulator: with
+          // beta == 0 the value is recomputed from acc - delta; otherwise C
+          // already holds alpha * acc + beta * C_in and alpha * delta is
+          // taken off it.
+          const int fr = T.fix_row[ab];
+          if (fr >= 0 && (fr >> 5) == lq) {  // warp-uniform
+            const int fc = T.fix_col[ab];
+            const double fd = T.fix_delta[ab];
+            float v[16];
+            tmem_ld16(tl + (uint32_t)(fc & ~15), v);
+            tmem_wait_ld();
+            if (lane == (fr & 31) && row_ok) {
+              float a = 0.f;
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (ch * 16 + q == fc) v[q] = (float)((double)v[q] - fd);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; q += 4) {
-          const int c = ch * 16 + q;  // tile column of this group of 4
-          if (c >= DN) break;
-          const int gc = col0 + c;
-          float* dst = crow_ptr + c;
-          // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
-          if (P.c_vec && c + 3 < DN && gc + 3 < P.N) {
-            float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
-            if (beta != 0.f) {
-              const float4 ci = *reinterpret_cast<const float4*>(dst);
-              o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
-              o.z = fmaf(beta, ci.z, o.z); o.w = fmaf(beta, ci.w, o.w);
-            }
-            *reinterpret_cast<float4*>(dst) = o;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (c + e < DN && gc + e < P.N) {
-                const float o = sc * v[q + e];
-                dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
-              }
+              for (int q = 0; q < 16; ++q)
+                if (q == (fc & 15)) a = v[q];
+              float* dst = crow_ptr + fc;
+              if (beta == 0.f) *dst = sc * (float)((double)a - fd);
+              else *dst = (float)((double)*dst - (double)sc * fd);
             }
           }
         }

@@ -10,9 +10,11 @@
 //   bf16: x = hi + mid + lo, each piece a bf16 (24 significant bits in all);
 //   e4m3: x = sum_c q_c / s_c with s_c = s_0 * 16^c, q_c = e4m3(residual * s_c)
 //         and s_0 a power of two putting the block's largest |x| near 448.
-// Norms of the rows of A and of the columns of B (through B^T) scale the
-// detection threshold.  B is also transposed to the K-major layout the MMA
-// reads.
+// Norms of the rows of A and of the columns of B scale the detection
+// threshold.  B is also transposed to the K-major layout the MMA reads.
+// Each operand is read once: one kernel reads A for its block sums and row
+// norms, one reads B for B^T, its block sums and column norms (partial
+// norms per k-chunk, finished without atomics so results are reproducible).
 //
 // Quantizer: bf16 by round-to-nearest-even; e4m3 with a per-tensor scale
 // amax / 448 and round-to-nearest-even with saturation (OCP FP8).
@@ -20,6 +22,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -43,80 +46,191 @@ __device__ __forceinline__ float ld_elem(const void* base, long long idx) {
   const TcProblem& P = tc_problem(b, pi);                  \
   const int lb = (int)blockIdx.x - P.blk_start[KIND]
 
-// B (K x N, ldb elements) -> Bt (N x ldk): 32 x 32 tiles through shared memory
-template <typename E>
-__global__ void tc_transpose_kernel(const __grid_constant__ TcBatch b) {
-  TC_BLOCK_OF(P_TRANSPOSE);
-  __shared__ E tile[32][33];
-  const E* B = reinterpret_cast<const E*>(P.B);
-  E* Bt = reinterpret_cast<E*>(P.Bt);
-  const int nbx = (P.N + 31) / 32;
-  const int n0 = (lb % nbx) * 32, k0 = (lb / nbx) * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int r = ty; r < 32; r += 8) {
-    const int k = k0 + r, n = n0 + tx;
-    tile[r][tx] = (k < P.K && n < P.N) ? B[(long long)k * P.ldb + n] : E(0);
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int n = n0 + r, k = k0 + tx;
-    if (n < P.N && k < P.K) Bt[(long long)n * P.ldk + k] = tile[tx][r];
-  }
-}
-
-// S[blk][k] = sum over the rows r of block blk (bs rows) of X[r][k]; X is
-// R x K, K contiguous.  side 0: A, 120-row blocks -> Vf; side 1: B^T,
-// 248-row blocks -> Wf.
-template <int DT, int SIDE>
-__global__ void tc_blocksum_kernel(const __grid_constant__ TcBatch b) {
-  TC_BLOCK_OF(SIDE == 0 ? P_SUM_A : P_SUM_B);
-  const void* X = SIDE == 0 ? P.A : P.Bt;
-  const long long ldx = SIDE == 0 ? P.lda : P.ldk;
-  const int R = SIDE == 0 ? P.M : P.N, bs = SIDE == 0 ? TC_DM : TC_DN;
-  float* S = SIDE == 0 ? P.Vf : P.Wf;
-  const int nkx = (P.K + 255) / 256;
-  const int k = (lb % nkx) * 256 + threadIdx.x, blk = lb / nkx;
-  if (k >= P.K) return;
-  const int r1 = min(R, (blk + 1) * bs);
-  float s = 0.f;
-  for (int r = blk * bs; r < r1; ++r) s += ld_elem<DT>(X, (long long)r * ldx + k);
-  S[(long long)blk * P.K + k] = s;
-}
-
-// n[r] = ||X[r][:]||_2, one warp per row (side 0: rows of A; 1: rows of B^T)
-template <int DT, int SIDE>
-__global__ void tc_rownorm_kernel(const __grid_constant__ TcBatch b) {
-  TC_BLOCK_OF(SIDE == 0 ? P_NORM_A : P_NORM_B);
-  const void* X = SIDE == 0 ? P.A : P.Bt;
-  const long long ldx = SIDE == 0 ? P.lda : P.ldk;
-  const int R = SIDE == 0 ? P.M : P.N;
-  float* nrm = SIDE == 0 ? P.nA : P.nB;
-  const int r = lb * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= R) return;
-  float s = 0.f;
-  for (int k = lane; k < P.K; k += 32) {
-    const float v = ld_elem<DT>(X, (long long)r * ldx + k);
-    s = fmaf(v, v, s);
+// Eight consecutive elements of row `row` (columns c0..c0+7, zero past
+// `ncols`) as floats, and their raw codes; one vector load when aligned.
+template <int DT>
+__device__ __forceinline__ void ld8(const void* base, long long ld, long long row, int c0, int ncols, bool vec_ok,
+                                    float* v, uint16_t* raw) {
+  using E = typename std::conditional<DT == 0, uint16_t, uint8_t>::type;
+  const E* p = reinterpret_cast<const E*>(base) + row * ld + c0;
+  E e[8];
+  if (vec_ok && c0 + 8 <= ncols) {
+    if constexpr (DT == 0) {
+      const uint4 q = *reinterpret_cast<const uint4*>(p);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { e[2 * i] = (E)(w[i] & 0xFFFF); e[2 * i + 1] = (E)(w[i] >> 16); }
+    } else {
+      const uint2 q = *reinterpret_cast<const uint2*>(p);
+      const uint32_t w[2] = {q.x, q.y};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) e[i] = (E)((w[i >> 2] >> (8 * (i & 3))) & 0xFF);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) e[i] = c0 + i < ncols ? p[i] : E(0);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) nrm[r] = sqrtf(s);
+  for (int i = 0; i < 8; ++i) {
+    raw[i] = e[i];
+    if constexpr (DT == 0) {
+      v[i] = __uint_as_float((uint32_t)e[i] << 16);  // bf16 -> fp32 is exact
+    } else {
+      __nv_fp8_e4m3 q;
+      q.__x = (__nv_fp8_storage_t)e[i];
+      v[i] = float(q);
+    }
+  }
 }
 
-// fro[blk] = sqrt(sum_{r in blk} n[r]^2) for the row blocks of A (first
-// tiles_m indices) and the column blocks of B (next tiles_n)
-__global__ void tc_blockfro_kernel(const __grid_constant__ TcBatch b) {
-  TC_BLOCK_OF(P_FRO);
-  const int i = lb * blockDim.x + threadIdx.x;
-  if (i >= P.tiles_m + P.tiles_n) return;
-  const bool side_a = i < P.tiles_m;
-  const int blk = side_a ? i : i - P.tiles_m;
+// A: block sums over TC_DM-row blocks (-> Vf) and squared row-norm partials
+// over 256-wide k-chunks (-> nA_part), one pass.  Block = (row block, chunk);
+// warp w takes rows w, w+8, ..., lane l the 8 columns 8l..8l+7 of the chunk.
+template <int DT>
+__global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_ENC_A);
+  __shared__ float part[8][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkx = (P.K + 255) / 256;
+  const int kx = lb % nkx, blk = lb / nkx;
+  const int k0 = kx * 256, r0 = blk * TC_DM;
+  const int elem = DT == 0 ? 2 : 1;
+  const bool vec_ok = ((uintptr_t)P.A % (8 * elem) == 0) && ((P.lda * elem) % (8 * elem) == 0);
+  float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int rr = warp; rr < TC_DM; rr += 8) {
+    const int r = r0 + rr;
+    if (r >= P.M) break;  // warp-uniform
+    float v[8];
+    uint16_t raw[8];
+    ld8<DT>(P.A, P.lda, r, k0 + lane * 8, P.K, vec_ok, v, raw);
+    float sq = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      cs[e] += v[e];
+      sq = fmaf(v[e], v[e], sq);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) P.nA_part[(long long)kx * P.M + r] = sq;
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) part[warp][lane * 8 + e] = cs[e];
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (k0 + t < P.K) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += part[w][t];
+    P.Vf[(long long)blk * P.K + k0 + t] = s;
+  }
+}
+
+// B (K x N, N contiguous): B^T (N x ldk, K contiguous) in KC x NBW tiles
+// through shared memory; with checksums also the block sums over NBW-column
+// blocks (-> Wf) and squared column-norm partials per k-chunk (-> nB_part).
+// KC is one 128-byte k-block of the operand type.
+template <int DT, bool ABFT>
+__global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_ENC_B);
+  using E = typename std::conditional<DT == 0, uint16_t, uint8_t>::type;
+  constexpr int KC = 128 / (int)sizeof(E);
+  constexpr int NBW = ABFT ? TC_DN : TC_BN;
+  constexpr int PITCH = NBW + (DT == 0 ? 10 : 20);  // elements; staggers the banks
+  __shared__ __align__(16) E tile[KC][PITCH];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkc = (P.K + KC - 1) / KC;
+  const int kc = lb % nkc, nb = lb / nkc;
+  const int k0 = kc * KC, n0 = nb * NBW;
+  const bool vec_ok = ((uintptr_t)P.B % (8 * sizeof(E)) == 0) && ((P.ldb * (long long)sizeof(E)) % (8 * sizeof(E)) == 0);
+  const bool in_cols = lane * 8 < NBW;  // 31 of 32 lanes for 248 columns
+  float sq[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int kk = warp; kk < KC; kk += 8) {
+    const int k = k0 + kk;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    uint16_t raw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < P.K && in_cols) ld8<DT>(P.B, P.ldb, k, n0 + lane * 8, P.N, vec_ok, v, raw);
+    if (in_cols) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) tile[kk][lane * 8 + e] = (E)raw[e];
+    }
+    if constexpr (ABFT) {
+      float rs = 0.f;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        rs += v[e];
+        sq[e] = fmaf(v[e], v[e], sq[e]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+      if (lane == 0 && k < P.K) P.Wf[(long long)nb * P.K + k] = rs;
+    }
+  }
+  if constexpr (ABFT) {
+    if (in_cols) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int n = n0 + lane * 8 + e;
+        if (n < P.N) P.nB_part[(long long)kc * P.N + n] = sq[e];
+      }
+    }
+  }
+  __syncthreads();
+  // B^T rows n0..n0+NBW-1, k0..k0+KC-1: 8 threads write one 128-byte row
+  // segment (the k-range past K is zero, inside the padded row)
+  E* Bt = reinterpret_cast<E*>(P.Bt);
+  constexpr int EPV = 16 / (int)sizeof(E);  // elements per 16-byte vector
+  for (int i = threadIdx.x; i < NBW * 8; i += 256) {
+    const int nn = i >> 3, vq = i & 7;
+    const int n = n0 + nn;
+    if (n >= P.N) continue;
+    E o[EPV];
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) o[e] = tile[vq * EPV + e][nn];
+    uint4 w;
+    if constexpr (DT == 0) {
+      w.x = (uint32_t)o[0] | ((uint32_t)o[1] << 16); w.y = (uint32_t)o[2] | ((uint32_t)o[3] << 16);
+      w.z = (uint32_t)o[4] | ((uint32_t)o[5] << 16); w.w = (uint32_t)o[6] | ((uint32_t)o[7] << 16);
+    } else {
+      uint32_t q[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        q[j] = (uint32_t)o[4 * j] | ((uint32_t)o[4 * j + 1] << 8) | ((uint32_t)o[4 * j + 2] << 16) |
+               ((uint32_t)o[4 * j + 3] << 24);
+      w = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+    *reinterpret_cast<uint4*>(Bt + (long long)n * P.ldk + k0 + vq * EPV) = w;
+  }
+}
+
+// Norms from the partials: nA / nB and the Frobenius norm of each row block
+// of A (first tiles_m blocks) and column block of B (next tiles_n).
+template <int DT>
+__global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ TcBatch b) {
+  TC_BLOCK_OF(P_FIN);
+  __shared__ float red[8];
+  constexpr int KC = DT == 0 ? 64 : 128;
+  const bool side_a = lb < P.tiles_m;
+  const int blk = side_a ? lb : lb - P.tiles_m;
   const int R = side_a ? P.M : P.N, bs = side_a ? TC_DM : TC_DN;
-  const float* nrm = side_a ? P.nA : P.nB;
+  const int nparts = side_a ? (P.K + 255) / 256 : (P.K + KC - 1) / KC;
+  const float* part = side_a ? P.nA_part : P.nB_part;
+  float* nrm = side_a ? P.nA : P.nB;
+  const int t = threadIdx.x, r = blk * bs + t;
   float s = 0.f;
-  for (int r = blk * bs; r < min(R, (blk + 1) * bs); ++r) s = fmaf(nrm[r], nrm[r], s);
-  (side_a ? P.froA : P.froB)[blk] = sqrtf(s);
+  if (t < bs && r < R) {
+    for (int c = 0; c < nparts; ++c) s += part[(long long)c * R + r];
+    nrm[r] = sqrtf(s);
+  }
+  float f = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if ((t & 31) == 0) red[t >> 5] = f;
+  __syncthreads();
+  if (t == 0) {
+    float tot = 0.f;
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    (side_a ? P.froA : P.froB)[blk] = sqrtf(tot);
+  }
 }
 
 // s0[blk]: power of two with max_k |S[blk][k]| * s0 in (224, 448]  (fp8 only)
@@ -230,14 +344,11 @@ __global__ void cast_e4m3_kernel(const float* __restrict__ x, long long n, const
 // ---------------------------------------------------------------------------
 
 // Blocks each batched encode launch gives one problem.
-void tc_prep_blocks(const TcProblem& P, int out[P_KINDS]) {
-  const int nkx = (P.K + 255) / 256;
-  out[P_TRANSPOSE] = ((P.N + 31) / 32) * ((P.K + 31) / 32);
-  out[P_SUM_A] = nkx * P.tiles_m;
-  out[P_SUM_B] = nkx * P.tiles_n;
-  out[P_NORM_A] = (P.M + 7) / 8;
-  out[P_NORM_B] = (P.N + 7) / 8;
-  out[P_FRO] = (P.tiles_m + P.tiles_n + 127) / 128;
+void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]) {
+  const int nkx = (P.K + 255) / 256, kc = dt == 0 ? 64 : 128;
+  out[P_ENC_A] = nkx * P.tiles_m;
+  out[P_ENC_B] = ((P.K + kc - 1) / kc) * P.tiles_n;
+  out[P_FIN] = P.tiles_m + P.tiles_n;
   out[P_SCALE] = P.tiles_m + P.tiles_n;
   out[P_PIECES] = nkx * (P.tiles_m + P.tiles_n);
 }
@@ -247,33 +358,26 @@ void tc_prep_blocks(const TcProblem& P, int out[P_KINDS]) {
 // of each launch over the batch.
 cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
                            cudaStream_t st) {
-  auto go = [&](int kind) { return total[kind] > 0; };
-  if (go(P_TRANSPOSE)) {
-    if (dt == 0) tc_transpose_kernel<uint16_t><<<total[P_TRANSPOSE], dim3(32, 8), 0, st>>>(b);
-    else tc_transpose_kernel<uint8_t><<<total[P_TRANSPOSE], dim3(32, 8), 0, st>>>(b);
+  if (!abft) {
+    if (dt == 0) tc_encode_b_kernel<0, false><<<total[P_ENC_B], 256, 0, st>>>(b);
+    else tc_encode_b_kernel<1, false><<<total[P_ENC_B], 256, 0, st>>>(b);
     ++*launches;
+    return cudaGetLastError();
   }
-  if (!abft) return cudaGetLastError();
   if (dt == 0) {
-    tc_blocksum_kernel<0, 0><<<total[P_SUM_A], 256, 0, st>>>(b);
-    tc_blocksum_kernel<0, 1><<<total[P_SUM_B], 256, 0, st>>>(b);
-    tc_rownorm_kernel<0, 0><<<total[P_NORM_A], 256, 0, st>>>(b);
-    tc_rownorm_kernel<0, 1><<<total[P_NORM_B], 256, 0, st>>>(b);
+    tc_encode_b_kernel<0, true><<<total[P_ENC_B], 256, 0, st>>>(b);
+    tc_encode_a_kernel<0><<<total[P_ENC_A], 256, 0, st>>>(b);
+    tc_norms_kernel<0><<<total[P_FIN], 256, 0, st>>>(b);
   } else {
-    tc_blocksum_kernel<1, 0><<<total[P_SUM_A], 256, 0, st>>>(b);
-    tc_blocksum_kernel<1, 1><<<total[P_SUM_B], 256, 0, st>>>(b);
-    tc_rownorm_kernel<1, 0><<<total[P_NORM_A], 256, 0, st>>>(b);
-    tc_rownorm_kernel<1, 1><<<total[P_NORM_B], 256, 0, st>>>(b);
-  }
-  tc_blockfro_kernel<<<total[P_FRO], 128, 0, st>>>(b);
-  *launches += 5;
-  if (dt == 1) {
+    tc_encode_b_kernel<1, true><<<total[P_ENC_B], 256, 0, st>>>(b);
+    tc_encode_a_kernel<1><<<total[P_ENC_A], 256, 0, st>>>(b);
+    tc_norms_kernel<1><<<total[P_FIN], 256, 0, st>>>(b);
     tc_blockscale_kernel<<<total[P_SCALE], 256, 0, st>>>(b);
     ++*launches;
   }
   if (dt == 0) tc_pieces_kernel<0><<<total[P_PIECES], 256, 0, st>>>(b);
   else tc_pieces_kernel<1><<<total[P_PIECES], 256, 0, st>>>(b);
-  ++*launches;
+  *launches += 4;
   return cudaGetLastError();
 }
 
