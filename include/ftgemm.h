@@ -155,10 +155,52 @@ int ftgemm_get_schedule(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
  * mode 0, analytic:  tau_row(i) = lambda * u * ||A(i,:)||_2 * ||B(:,J)||_F and
  *                    tau_col(j) = lambda * u * ||A(I,:)||_F * ||B(:,j)||_2,
  *   J (I) the columns (rows) of the verification unit, u = 2^-24.  lambda <= 0
- *   keeps the current value (default 32).
- * Other modes are rejected with FTGEMM_ERR_UNSUPPORTED. */
+ *   keeps the current value (default 32).  Turns the learned threshold off.
+ * mode 1, learned (tensor-core path, level TILE; no counterpart in the
+ *   paper): each tile uses lambda_t = lambda * 2^f(x_t) in the same formulas,
+ *   f the 5 -> 32 -> 32 -> 1 ReLU network whose FTGEMM_MLP_PARAMS parameters
+ *   mlp_weights holds (host array, copied; layout W1[32][5], b1[32],
+ *   W2[32][32], b2[32], W3[32], b3), x_t the tile's features: log2(K)/16,
+ *   the coherence ||e^T A_I||_2 / (sqrt|I| ||A_I||_F) of its row block, the
+ *   same ||B_J e||_2 / (sqrt|J| ||B_J||_F) of its column block, the operand
+ *   type (0.5 bf16, 1 e4m3) and log2(|I| |J|)/16.  f is evaluated in the GEMM
+ *   epilogue; a non-finite or non-positive lambda_t falls back to the
+ *   analytic one.  lambda (the calibration scale) must be > 0.  The SIMT
+ *   path keeps the analytic threshold.  Synchronises the handle's stream.
+ * Other modes: FTGEMM_ERR_UNSUPPORTED. */
+#define FTGEMM_MLP_INPUTS 5
+#define FTGEMM_MLP_PARAMS 1281
 int ftgemm_set_threshold(ftgemm_handle_t handle, int mode, double lambda,
                          const float* mlp_weights, size_t n_weights);
+
+/* Residual sink for training the learned threshold (no counterpart in the
+ * paper): while set, every tensor-core call at level TILE writes, for each
+ * of its tiles t (t = tile_m * tiles_n + tile_n; in a group, offset by the
+ * tiles of the problems scheduled before it), lam_needed[t] = the largest
+ * |residual| / (u * norm product) over the tile's rows and columns -- the
+ * smallest analytic lambda that flags nothing there -- and its 5 features
+ * into features[5t .. 5t+4] (device arrays of `capacity` tiles, owned by the
+ * caller).  lam_needed = NULL removes the sink.  A call with more tiles than
+ * `capacity` fails with FTGEMM_ERR_ARG. */
+int ftgemm_set_residual_sink(ftgemm_handle_t handle, float* lam_needed, float* features,
+                             int64_t capacity);
+
+/* The threshold network on the GPU (no counterpart in the paper).
+ * X: n x 5 features, t: n targets, theta: FTGEMM_MLP_PARAMS parameters,
+ * all device fp32.  ftgemm_mlp_forward writes the n outputs to y (device).
+ * ftgemm_mlp_grad writes the gradient of the mean squared error
+ * (1/n) sum (f(x_i) - t_i)^2 to grad (device) and, if loss is not NULL, the
+ * loss to *loss (host; synchronises).  ftgemm_mlp_train runs `epochs`
+ * passes of minibatch Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate
+ * lr) over the samples in order, `batch` per step, updating theta in place;
+ * losses (host, may be NULL) receives the mean minibatch loss of each epoch
+ * (synchronises).  Gradients are reduced in a fixed order: runs repeat bit
+ * for bit. */
+int ftgemm_mlp_forward(ftgemm_handle_t handle, int64_t n, const float* X, const float* theta, float* y);
+int ftgemm_mlp_grad(ftgemm_handle_t handle, int64_t n, const float* X, const float* t,
+                    const float* theta, float* grad, float* loss);
+int ftgemm_mlp_train(ftgemm_handle_t handle, int64_t n, const float* X, const float* t,
+                     int32_t epochs, int32_t batch, float lr, float* theta, float* losses);
 
 /* Per-tensor scales of E4M3 operands: the product is scale_a * scale_b *
  * (A_q B_q) with A_q, B_q the stored codes (see ftgemm_quantize). */

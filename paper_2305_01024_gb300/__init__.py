@@ -30,6 +30,10 @@ class FtgemmError(RuntimeError):
         self.status = status
 
 
+MLP_INPUTS = 5
+MLP_PARAMS = 1281
+
+
 class Schedule(C.Structure):
     """ftgemm_schedule: Table 1 tile tuple + cadence + split_k."""
     _fields_ = [("m_tb", C.c_int32), ("n_tb", C.c_int32), ("k_tb", C.c_int32),
@@ -115,6 +119,10 @@ def lib():
     L.ftgemm_group_set_faults.argtypes = [vp, C.POINTER(i32), C.POINTER(InjectSpec)]
     L.ftgemm_grouped_gemm.argtypes = [vp, vp]
     L.ftgemm_group_destroy.argtypes = [vp]
+    L.ftgemm_set_residual_sink.argtypes = [vp, vp, vp, i64]
+    L.ftgemm_mlp_forward.argtypes = [vp, i64, vp, vp, vp]
+    L.ftgemm_mlp_grad.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(C.c_float)]
+    L.ftgemm_mlp_train.argtypes = [vp, i64, vp, vp, i32, i32, C.c_float, vp, C.POINTER(C.c_float)]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
@@ -123,7 +131,8 @@ def lib():
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
                "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
-               "ftgemm_grouped_gemm", "ftgemm_group_destroy"):
+               "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
+               "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -248,6 +257,39 @@ class Handle:
         _check(lib().ftgemm_report_fetch(self._h, C.byref(rep)))
         return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
                         rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def set_residual_sink(self, lam_needed=None, features=None):
+        """Route every later TILE-level tensor-core call's per-tile residual
+        ratios and features into the given CUDA tensors (None removes it)."""
+        if lam_needed is None:
+            _check(lib().ftgemm_set_residual_sink(self._h, None, None, 0))
+            return
+        assert features.numel() == MLP_INPUTS * lam_needed.numel()
+        _check(lib().ftgemm_set_residual_sink(self._h, _ptr(lam_needed), _ptr(features),
+                                              lam_needed.numel()))
+
+    def mlp_forward(self, X, theta):
+        import torch
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(lib().ftgemm_mlp_forward(self._h, X.shape[0], _ptr(X), _ptr(theta), _ptr(y)))
+        return y
+
+    def mlp_grad(self, X, t, theta):
+        """(loss, gradient tensor) of the mean squared error."""
+        import torch
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        L = C.c_float(0.0)
+        _check(lib().ftgemm_mlp_grad(self._h, X.shape[0], _ptr(X), _ptr(t), _ptr(theta), _ptr(g),
+                                     C.byref(L)))
+        return L.value, g
+
+    def mlp_train(self, X, t, theta, epochs: int, batch: int, lr: float):
+        """Minibatch Adam on the GPU, in place on theta; returns the mean
+        loss of each epoch."""
+        out = (C.c_float * epochs)()
+        _check(lib().ftgemm_mlp_train(self._h, X.shape[0], _ptr(X), _ptr(t), int(epochs), int(batch),
+                                      float(lr), _ptr(theta), out))
+        return list(out)
 
     def set_fp8_scales(self, scale_a: float, scale_b: float):
         _check(lib().ftgemm_set_fp8_scales(self._h, float(scale_a), float(scale_b)))

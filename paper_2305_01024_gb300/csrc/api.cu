@@ -34,6 +34,12 @@ cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatc
                            cudaStream_t st);
 cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
                             int* launches, cudaStream_t st);
+int mlp_grad_blocks(long long nb);
+cudaError_t launch_mlp_grad(const float* X, const float* t, long long s0, int nb, const float* theta, float inv_n,
+                            float* part, int nblk, cudaStream_t st);
+cudaError_t launch_mlp_reduce(const float* part, int nblk, float* grad_out, float* theta, float* m, float* v, int step,
+                              float lr, float inv_n, float* loss_out, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* X, long long n, const float* theta, float* y, cudaStream_t st);
 
 // The compiled SIMT tile tuples: the five kernel setups of Table 1, plus the
 // large tile with a 16-wide k-step in two thread layouts (8 x 8 fragments on
@@ -94,6 +100,16 @@ struct ftgemm_ctx {
   double lambda_tc[2] = {32.0, 32.0};  // bf16, e4m3
   float fp8_sa = 1.f, fp8_sb = 1.f;
   float* qscratch = nullptr;  // amax bits + scale of ftgemm_quantize
+  // learned threshold (tensor-core path)
+  float* mlp_theta = nullptr;  // device, FTGEMM_MLP_PARAMS floats
+  bool mlp_on = false;
+  float mlp_scale = 1.f;
+  float* mlp_ws = nullptr;     // training: block partials, Adam moments, step losses
+  size_t mlp_ws_floats = 0;
+  // residual sink (tensor-core path)
+  float* sink_lam = nullptr;
+  float* sink_x = nullptr;
+  int64_t sink_cap = 0;
   // instrumentation
   int64_t launches = 0;
   bool timing = false;
@@ -362,6 +378,8 @@ static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
     P.nB_part = take((size_t)((K + (dt == 0 ? 63 : 127)) / (dt == 0 ? 64 : 128)) * P.N);
     P.froA = take(tm);
     P.froB = take(tn);
+    P.coA = take(tm);
+    P.coB = take(tn);
   }
   return o;
 }
@@ -405,6 +423,8 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   TcProblem& P = b.one;
   tc_set_problem(P, dt, abft, (int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, alpha, beta,
                  dt == 1 ? h->fp8_sa * h->fp8_sb : 1.f, (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24)));
+  P.mlp = h->mlp_on ? h->mlp_theta : nullptr;
+  P.mlp_scale = h->mlp_scale;
   b.table = nullptr;
   b.nprob = 1;
   b.total_tiles = P.tiles_m * P.tiles_n;
@@ -434,7 +454,10 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
     int rc = tc_make_maps(mb.one, P, dt, abft);
     if (rc) return rc;
   }
-  TcRun run{nf > 0 ? h->d_faults : nullptr, nf, h->rep, h->recs};
+  if (h->sink_lam && abft && b.total_tiles > h->sink_cap)
+    FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the call has %d", (long long)h->sink_cap, b.total_tiles);
+  TcRun run{nf > 0 ? h->d_faults : nullptr, nf, h->rep, h->recs, abft ? h->sink_lam : nullptr,
+            abft ? h->sink_x : nullptr};
   const int grid = std::max(1, std::min(b.total_tiles, h->num_sms > 0 ? h->num_sms : 148));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (h->timing) {
@@ -570,6 +593,8 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
     tc_set_problem(P, dt, abft, (int)u.m, (int)u.n, (int)u.k, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.alpha, u.beta,
                    dt == 1 ? u.scale_a * u.scale_b : 1.f, lam_u);
     P.id = order[q];
+    P.mlp = h->mlp_on ? h->mlp_theta : nullptr;
+    P.mlp_scale = h->mlp_scale;
     g->pos[order[q]] = q;
     P.tile_start = (int)tiles;
     tiles += (long long)P.tiles_m * P.tiles_n;
@@ -692,7 +717,10 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   TcMapsBatch mb;
   memset(&mb, 0, sizeof(mb));
   mb.table = g->d_maps;
-  TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, h->rep, h->recs};
+  if (h->sink_lam && g->abft && g->total_tiles > h->sink_cap)
+    FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the group has %d", (long long)h->sink_cap, g->total_tiles);
+  TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, h->rep, h->recs,
+            g->abft ? h->sink_lam : nullptr, g->abft ? h->sink_x : nullptr};
   const int grid = g->ncta;  // the schedule was built for this many CTAs
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(h->stream, &cs));
@@ -795,6 +823,8 @@ int ftgemm_destroy(ftgemm_handle_t h) {
   if (h->h_faults) cudaFreeHost(h->h_faults);
   if (h->faults_free) cudaEventDestroy(h->faults_free);
   if (h->qscratch) cudaFree(h->qscratch);
+  if (h->mlp_theta) cudaFree(h->mlp_theta);
+  if (h->mlp_ws) cudaFree(h->mlp_ws);
   for (auto& e : h->pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   for (auto& e : h->pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   delete h;
@@ -830,9 +860,119 @@ int ftgemm_get_schedule(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, ftge
 
 int ftgemm_set_threshold(ftgemm_handle_t h, int mode, double lambda, const float* w, size_t nw) {
   if (!h) FAIL(FTGEMM_ERR_ARG, "ftgemm_set_threshold: NULL handle");
-  (void)w; (void)nw;
-  if (mode != 0) FAIL(FTGEMM_ERR_UNSUPPORTED, "threshold mode %d is not available", mode);
-  if (lambda > 0) h->lambda = lambda;
+  if (mode == 0) {
+    if (lambda > 0) h->lambda = lambda;
+    h->mlp_on = false;
+    return FTGEMM_OK;
+  }
+  if (mode != 1) FAIL(FTGEMM_ERR_UNSUPPORTED, "threshold mode %d is not available", mode);
+  if (!w || nw != (size_t)FTGEMM_MLP_PARAMS)
+    FAIL(FTGEMM_ERR_ARG, "learned threshold: %d network parameters expected, got %zu", FTGEMM_MLP_PARAMS, nw);
+  if (!(lambda > 0)) FAIL(FTGEMM_ERR_ARG, "learned threshold: the scale must be positive");
+  for (size_t i = 0; i < nw; ++i)
+    if (!std::isfinite(w[i])) FAIL(FTGEMM_ERR_ARG, "learned threshold: parameter %zu is not finite", i);
+  CK(cudaSetDevice(h->device));
+  if (!h->mlp_theta) CK(cudaMalloc(&h->mlp_theta, sizeof(float) * FTGEMM_MLP_PARAMS));
+  CK(cudaStreamSynchronize(h->stream));  // a launch in flight may read the old parameters
+  CK(cudaMemcpy(h->mlp_theta, w, sizeof(float) * FTGEMM_MLP_PARAMS, cudaMemcpyHostToDevice));
+  h->mlp_on = true;
+  h->mlp_scale = (float)lambda;
+  return FTGEMM_OK;
+}
+
+int ftgemm_set_residual_sink(ftgemm_handle_t h, float* lam_needed, float* features, int64_t capacity) {
+  if (!h) FAIL(FTGEMM_ERR_ARG, "ftgemm_set_residual_sink: NULL handle");
+  if (!lam_needed) {
+    h->sink_lam = nullptr;
+    h->sink_x = nullptr;
+    h->sink_cap = 0;
+    return FTGEMM_OK;
+  }
+  if (!features || capacity <= 0) FAIL(FTGEMM_ERR_ARG, "ftgemm_set_residual_sink: bad argument");
+  h->sink_lam = lam_needed;
+  h->sink_x = features;
+  h->sink_cap = capacity;
+  return FTGEMM_OK;
+}
+
+static int ensure_mlp_ws(ftgemm_ctx* h, size_t floats) {
+  if (floats <= h->mlp_ws_floats) return FTGEMM_OK;
+  if (h->mlp_ws) CK(cudaFree(h->mlp_ws));
+  h->mlp_ws = nullptr;
+  h->mlp_ws_floats = 0;
+  CK(cudaMalloc(&h->mlp_ws, floats * sizeof(float)));
+  h->mlp_ws_floats = floats;
+  return FTGEMM_OK;
+}
+
+int ftgemm_mlp_forward(ftgemm_handle_t h, int64_t n, const float* X, const float* theta, float* y) {
+  if (!h || !X || !theta || !y || n <= 0) FAIL(FTGEMM_ERR_ARG, "ftgemm_mlp_forward: bad argument");
+  CK(cudaSetDevice(h->device));
+  CK(launch_mlp_forward(X, n, theta, y, h->stream));
+  ++h->launches;
+  return FTGEMM_OK;
+}
+
+int ftgemm_mlp_grad(ftgemm_handle_t h, int64_t n, const float* X, const float* t, const float* theta, float* grad,
+                    float* loss) {
+  if (!h || !X || !t || !theta || !grad || n <= 0 || n > INT32_MAX)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_mlp_grad: bad argument");
+  CK(cudaSetDevice(h->device));
+  const int nblk = mlp_grad_blocks(n);
+  const size_t slot = FTGEMM_MLP_PARAMS + 1;
+  int rc = ensure_mlp_ws(h, (size_t)nblk * slot + 1);
+  if (rc) return rc;
+  float* part = h->mlp_ws;
+  float* dloss = h->mlp_ws + (size_t)nblk * slot;
+  const float inv_n = (float)(1.0 / (double)n);
+  CK(launch_mlp_grad(X, t, 0, (int)n, theta, inv_n, part, nblk, h->stream));
+  CK(launch_mlp_reduce(part, nblk, grad, nullptr, nullptr, nullptr, 0, 0.f, inv_n, dloss, h->stream));
+  h->launches += 2;
+  if (loss) {
+    CK(cudaMemcpyAsync(loss, dloss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return FTGEMM_OK;
+}
+
+int ftgemm_mlp_train(ftgemm_handle_t h, int64_t n, const float* X, const float* t, int32_t epochs, int32_t batch,
+                     float lr, float* theta, float* losses) {
+  if (!h || !X || !t || !theta || n <= 0 || n > INT32_MAX || epochs <= 0 || batch <= 0 || !(lr > 0.f))
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_mlp_train: bad argument");
+  CK(cudaSetDevice(h->device));
+  const long long steps_per_epoch = (n + batch - 1) / batch;
+  const long long steps = steps_per_epoch * epochs;
+  const int nblk = mlp_grad_blocks(std::min<long long>(batch, n));
+  const size_t slot = FTGEMM_MLP_PARAMS + 1;
+  int rc = ensure_mlp_ws(h, (size_t)nblk * slot + 2 * (size_t)FTGEMM_MLP_PARAMS + (size_t)steps);
+  if (rc) return rc;
+  float* part = h->mlp_ws;
+  float* m = part + (size_t)nblk * slot;
+  float* v = m + FTGEMM_MLP_PARAMS;
+  float* step_loss = v + FTGEMM_MLP_PARAMS;
+  CK(cudaMemsetAsync(m, 0, sizeof(float) * 2 * FTGEMM_MLP_PARAMS, h->stream));
+  long long step = 0;
+  for (int e = 0; e < epochs; ++e) {
+    for (long long s0 = 0; s0 < n; s0 += batch) {
+      const int nb = (int)std::min<long long>(batch, n - s0);
+      const float inv_n = (float)(1.0 / (double)nb);
+      CK(launch_mlp_grad(X, t, s0, nb, theta, inv_n, part, nblk, h->stream));
+      ++step;
+      CK(launch_mlp_reduce(part, nblk, nullptr, theta, m, v, (int)step, lr, inv_n, step_loss + (step - 1),
+                           h->stream));
+    }
+  }
+  h->launches += 2 * steps;
+  if (losses) {
+    std::vector<float> sl((size_t)steps);
+    CK(cudaMemcpyAsync(sl.data(), step_loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int e = 0; e < epochs; ++e) {
+      double acc = 0.0;
+      for (long long q = 0; q < steps_per_epoch; ++q) acc += sl[(size_t)(e * steps_per_epoch + q)];
+      losses[e] = (float)(acc / (double)steps_per_epoch);
+    }
+  }
   return FTGEMM_OK;
 }
 

@@ -121,12 +121,14 @@ struct TcProblem {
   float* nA; float* nB;           // [M] row 2-norms of A, [N] column 2-norms of B
   float* nA_part; float* nB_part; // squared-norm partials per k-chunk: [ceil(K/256)][M], [ceil(K/kc)][N]
   float* froA; float* froB;       // [tiles_m], [tiles_n] Frobenius norms of the blocks
+  float* coA; float* coB;         // [tiles_m], [tiles_n] coherence of the blocks (threshold features)
   float* C; long long ldc;
   int c_vec;                      // C rows 16-byte aligned (float4 stores)
   float alpha, beta;
   float acc_scale;                // fp8: product of the per-tensor scales; bf16: 1
   float lam_u;                    // analytic threshold factor lambda * u
-  const float* lam_tile;          // per-tile lambda * u (learned threshold), or null
+  const float* mlp;               // learned threshold: network parameters (device), or null
+  float mlp_scale;                // lambda of a tile = mlp_scale * 2^network(features)
 };
 
 struct TcBatch {
@@ -156,6 +158,9 @@ struct TcMapsBatch {
 struct TcRun {
   const Fault* faults; int nfaults;  // sorted by global tile (tile_start + local)
   DevReport* rep; ftgemm_fault_record* recs;
+  // residual sink (optional): per global tile, the smallest lambda that
+  // would have flagged nothing, and the tile's 5 threshold features
+  float* sink_lam; float* sink_x;
 };
 
 __device__ __forceinline__ const TcProblem& tc_problem(const TcBatch& b, int pi) {

@@ -35,6 +35,7 @@
 #include <climits>
 
 #include "internal.cuh"
+#include "mlp.cuh"
 #include "ptx.cuh"
 
 namespace ftg {
@@ -84,6 +85,7 @@ struct TcSmemTail {
   unsigned long long bestr, bestc;
   int fix_row[2], fix_col[2];      // per accumulator parity
   double fix_delta[2];
+  unsigned int sink_max;           // residual sink: largest residual / (u * norms) of the tile
   float colpart[4][256];           // per epilogue warp partial column sums (data rows)
   float ccp[TC_CS_SLOTS][256];     // column-checksum pieces, TMEM lanes 120..127
   float crow[128];                 // row checksums
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__(192, 1)
           T.fix_row[ab] = -1;
           T.fix_col[ab] = -1;
           T.fix_delta[ab] = 0.0;
+          T.sink_max = 0u;
         }
         epi_bar();
       }
@@ -356,7 +359,25 @@ __global__ void __launch_bounds__(192, 1)
         }
       } else {
         epi_bar();
-        const float lam_u = P.lam_tile ? P.lam_tile[x.tm * P.tiles_n + x.tn] : P.lam_u;
+        // ----- threshold of this tile -----
+        // analytic: lambda * u; learned: lambda = mlp_scale * 2^f(x) with x
+        // the tile's features (log2 K, block coherences, operand type, tile
+        // size), evaluated on every epilogue warp; the analytic value is the
+        // fallback for a non-finite or non-positive output
+        const int rows = min(DM, P.M - row0), cols = min(DN, P.N - col0);
+        float feat[MLP_IN];
+        feat[0] = log2f((float)P.K) * 0.0625f;
+        feat[1] = P.coA ? P.coA[x.tm] : 0.f;
+        feat[2] = P.coB ? P.coB[x.tn] : 0.f;
+        feat[3] = DT == 0 ? 0.5f : 1.f;
+        feat[4] = log2f((float)rows * (float)cols) * 0.0625f;
+        float lam_u = P.lam_u;
+        if (P.mlp) {
+          MlpAct act;
+          mlp_forward_warp(P.mlp, feat, lane, act);
+          const float lam = P.mlp_scale * exp2f(act.y);
+          if (isfinite(lam) && lam > 0.f) lam_u = lam * 5.9604644775390625e-8f;  // * 2^-24
+        }
         // ----- one pass over the accumulator: fp32 screen sums and the store -----
         // C is written before verification; a confirmed fault is then
         // patched in place (a single element, below).
@@ -412,6 +433,11 @@ __global__ void __launch_bounds__(192, 1)
         T.tr[r] = (data_row && gr < P.M) ? lam_u * P.nA[gr] * P.froB[x.tn] : 0.f;
         int flagged = data_row && fabsf(rs - crow) > T.tr[r];
         T.flag_r[r] = flagged;
+        constexpr float kU = 5.9604644775390625e-8f;  // 2^-24
+        if (run.sink_lam && data_row && gr < P.M) {
+          const float den = kU * P.nA[gr] * P.froB[x.tn];
+          if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(rs - crow) / den));
+        }
         epi_bar();
         for (int c = r; c < BN; c += 128) {
           int fl = 0;
@@ -424,6 +450,10 @@ __global__ void __launch_bounds__(192, 1)
             tcv = gc < P.N ? lam_u * P.froA[x.tm] * P.nB[gc] : 0.f;
             const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
             fl = fabsf(s - cc) > tcv;
+            if (run.sink_lam && gc < P.N) {
+              const float den = kU * P.froA[x.tm] * P.nB[gc];
+              if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(s - cc) / den));
+            }
           }
           T.ccol[c] = cc;
           T.tc[c] = tcv;
@@ -431,7 +461,13 @@ __global__ void __launch_bounds__(192, 1)
           flagged |= fl;
         }
         // barrier + OR over the four epilogue warps: the same answer in all
-        if (bar_red_or(1, 128, flagged)) {
+        const int any_flag = bar_red_or(1, 128, flagged);
+        if (run.sink_lam && r == 0 && ok) {
+          run.sink_lam[my_tile] = __uint_as_float(T.sink_max);
+#pragma unroll
+          for (int q = 0; q < MLP_IN; ++q) run.sink_x[(long long)my_tile * MLP_IN + q] = feat[q];
+        }
+        if (any_flag) {
           // ----- fp64 confirmation of every screened row / column -----
           if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
           for (int c = r; c < BN; c += 128) T.sum_c[c] = 0.0;

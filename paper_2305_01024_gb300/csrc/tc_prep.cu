@@ -166,11 +166,20 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
     }
   }
   if constexpr (ABFT) {
+    // each warp saw KC/8 of the chunk's k rows: sum the warps' column partials
+    __shared__ float sqw[8][NBW];
     if (in_cols) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int n = n0 + lane * 8 + e;
-        if (n < P.N) P.nB_part[(long long)kc * P.N + n] = sq[e];
+      for (int e = 0; e < 8; ++e) sqw[warp][lane * 8 + e] = sq[e];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NBW; c += blockDim.x) {
+      const int n = n0 + c;
+      if (n < P.N) {
+        float q = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) q += sqw[w][c];
+        P.nB_part[(long long)kc * P.N + n] = q;
       }
     }
   }
@@ -203,11 +212,13 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
 }
 
 // Norms from the partials: nA / nB and the Frobenius norm of each row block
-// of A (first tiles_m blocks) and column block of B (next tiles_n).
+// of A (first tiles_m blocks) and column block of B (next tiles_n); also the
+// coherence ||v_I||_2 / (sqrt(|I|) ||A_I||_F) of each block (the same for
+// w_J and B_J), a feature of the learned threshold.
 template <int DT>
 __global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ TcBatch b) {
   TC_BLOCK_OF(P_FIN);
-  __shared__ float red[8];
+  __shared__ float red[8], red2[8];
   constexpr int KC = DT == 0 ? 64 : 128;
   const bool side_a = lb < P.tiles_m;
   const int blk = side_a ? lb : lb - P.tiles_m;
@@ -221,15 +232,31 @@ __global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ T
     for (int c = 0; c < nparts; ++c) s += part[(long long)c * R + r];
     nrm[r] = sqrtf(s);
   }
+  // squared norm of the checksum vector of this block over K
+  const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.K;
+  float c = 0.f;
+  for (int k = t; k < P.K; k += blockDim.x) c = fmaf(S[k], S[k], c);
   float f = s;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-  if ((t & 31) == 0) red[t >> 5] = f;
+  for (int o = 16; o > 0; o >>= 1) {
+    f += __shfl_xor_sync(0xffffffffu, f, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((t & 31) == 0) {
+    red[t >> 5] = f;
+    red2[t >> 5] = c;
+  }
   __syncthreads();
   if (t == 0) {
-    float tot = 0.f;
-    for (int w = 0; w < 8; ++w) tot += red[w];
-    (side_a ? P.froA : P.froB)[blk] = sqrtf(tot);
+    float tot = 0.f, cs = 0.f;
+    for (int w = 0; w < 8; ++w) {
+      tot += red[w];
+      cs += red2[w];
+    }
+    const float fro = sqrtf(tot);
+    (side_a ? P.froA : P.froB)[blk] = fro;
+    const int cnt = min(bs, R - blk * bs);
+    (side_a ? P.coA : P.coB)[blk] = fro > 0.f ? sqrtf(cs) / (sqrtf((float)cnt) * fro) : 0.f;
   }
 }
 
