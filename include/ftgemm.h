@@ -59,8 +59,10 @@ typedef enum {
   FTGEMM_FT_THREAD = 1, /* unit = one thread's m_t x n_t fragment (4.2.1)     */
   FTGEMM_FT_WARP = 2,   /* unit = one warp's m_w x n_w tile (4.2.2)           */
   FTGEMM_FT_BLOCK = 3,  /* unit = the threadblock's m_tb x n_tb tile (4.2.3)  */
-  FTGEMM_FT_TILE = 4    /* unit = the tensor-core CTA tile, verified in the
+  FTGEMM_FT_TILE = 4,   /* unit = the tensor-core CTA tile, verified in the
                            epilogue (bf16 / e4m3 only)                        */
+  FTGEMM_FT_AUTO = 5    /* F32: the level ftgemm_autotune found fastest for
+                           this shape (BLOCK when the shape is not tuned)     */
 } ftgemm_ft_level;
 
 /* Kernel schedule: the 7-parameter tile tuple of Table 1 plus the checksum
@@ -292,6 +294,24 @@ int ftgemm_grouped_gemm(ftgemm_handle_t handle, ftgemm_group_t group);
 
 /* Release a group (synchronises the handle's stream first). */
 int ftgemm_group_destroy(ftgemm_group_t group);
+
+/* Autotuner (F32 SIMT path).  The paper picks kernel parameters per shape
+ * by a code-generation search (Section 3.2); here the compiled tile tuples,
+ * split-K and the verification cadence are timed on the given operands and
+ * the fastest kept: (1) every tuple with the paper's period K_s = 256 and no
+ * split-K, plus the default schedule; (2) split-K 2, 4, ... for the two
+ * fastest while every split keeps >= 8 k-steps; (3) for the fastest,
+ * verification once per split instead of every K_s.  With ft_level =
+ * FTGEMM_FT_AUTO the search also runs at BLOCK, WARP and THREAD and keeps the
+ * fastest level.  Each candidate runs once untimed, then `reps` times
+ * between CUDA events (alpha = 1, beta = 0: C is overwritten).  The result is
+ * cached in the handle for (m, n, k, ft_level) and used by later ftgemm_gemm
+ * and ftgemm_get_schedule calls with that shape and level unless a schedule
+ * is forced with ftgemm_set_schedule.  out / level_out may be NULL. */
+int ftgemm_autotune(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, const float* A,
+                    int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc,
+                    ftgemm_ft_level ft_level, int32_t reps, ftgemm_schedule* out,
+                    ftgemm_ft_level* level_out);
 
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them. */

@@ -18,8 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libftgemm.so")
 
 F32, BF16, E4M3 = 0, 1, 2
-FT_OFF, FT_THREAD, FT_WARP, FT_BLOCK, FT_TILE = 0, 1, 2, 3, 4
-LEVELS = {"off": FT_OFF, "thread": FT_THREAD, "warp": FT_WARP, "block": FT_BLOCK, "tile": FT_TILE}
+FT_OFF, FT_THREAD, FT_WARP, FT_BLOCK, FT_TILE, FT_AUTO = 0, 1, 2, 3, 4, 5
+LEVELS = {"off": FT_OFF, "thread": FT_THREAD, "warp": FT_WARP, "block": FT_BLOCK, "tile": FT_TILE,
+          "auto": FT_AUTO}
 CORRECTED, UNCORRECTABLE, CHECKSUM_ONLY = 0, 1, 2
 OK, ERR_ARG, ERR_UNSUPPORTED, ERR_ALIGN, ERR_CUDA, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 
@@ -123,6 +124,8 @@ def lib():
     L.ftgemm_mlp_forward.argtypes = [vp, i64, vp, vp, vp]
     L.ftgemm_mlp_grad.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(C.c_float)]
     L.ftgemm_mlp_train.argtypes = [vp, i64, vp, vp, i32, i32, C.c_float, vp, C.POINTER(C.c_float)]
+    L.ftgemm_autotune.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_int, i32,
+                                  C.POINTER(Schedule), C.POINTER(C.c_int)]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
@@ -132,7 +135,7 @@ def lib():
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
                "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
-               "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train"):
+               "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -257,6 +260,20 @@ class Handle:
         _check(lib().ftgemm_report_fetch(self._h, C.byref(rep)))
         return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
                         rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def autotune(self, A, B, C_out, level=FT_BLOCK, reps: int = 3):
+        """Time the candidate F32 schedules on these operands (C_out is
+        overwritten) and cache the fastest; returns (Schedule, level)."""
+        if isinstance(level, str):
+            level = LEVELS[level]
+        M, K = A.shape
+        N = B.shape[1]
+        s = Schedule()
+        lv = C.c_int(0)
+        _check(lib().ftgemm_autotune(self._h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                     _ptr(C_out), C_out.stride(0), level, int(reps), C.byref(s),
+                                     C.byref(lv)))
+        return s, lv.value
 
     def set_residual_sink(self, lam_needed=None, features=None):
         """Route every later TILE-level tensor-core call's per-tile residual

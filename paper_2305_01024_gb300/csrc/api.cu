@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
@@ -106,6 +108,8 @@ struct ftgemm_ctx {
   float mlp_scale = 1.f;
   float* mlp_ws = nullptr;     // training: block partials, Adam moments, step losses
   size_t mlp_ws_floats = 0;
+  // autotuned SIMT schedules: (m, n, k, requested level) -> (schedule, level to run)
+  std::map<std::tuple<int64_t, int64_t, int64_t, int>, std::pair<ftgemm_schedule, int>> tuned;
   // residual sink (tensor-core path)
   float* sink_lam = nullptr;
   float* sink_x = nullptr;
@@ -198,6 +202,29 @@ static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
   s->split_k = split;
   return FTGEMM_OK;
 }
+
+// The schedule and level an F32 call runs with: the handle's forced
+// schedule, else an autotuned one for this shape and requested level, else
+// the default.  FTGEMM_FT_AUTO without a tuned entry runs BLOCK.
+static void choose_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, ftgemm_ft_level level,
+                            ftgemm_schedule* s, ftgemm_ft_level* run_level) {
+  *run_level = level == FTGEMM_FT_AUTO ? FTGEMM_FT_BLOCK : level;
+  if (h->has_sched) {
+    *s = h->sched;
+    return;
+  }
+  auto it = h->tuned.find(std::make_tuple(m, n, k, (int)level));
+  if (it != h->tuned.end()) {
+    *s = it->second.first;
+    *run_level = (ftgemm_ft_level)it->second.second;
+    return;
+  }
+  default_schedule(h, m, n, k, (int)*run_level, s);
+}
+
+static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_ft_level level,
+                     const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report);
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -853,9 +880,9 @@ int ftgemm_get_schedule(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, ftge
                         ftgemm_ft_level level, ftgemm_schedule* out) {
   if (!h || !out || m <= 0 || n <= 0 || k <= 0) FAIL(FTGEMM_ERR_ARG, "ftgemm_get_schedule: bad argument");
   if (dtype != FTGEMM_F32) FAIL(FTGEMM_ERR_UNSUPPORTED, "only FTGEMM_F32 has a SIMT schedule");
-  (void)level;
-  if (h->has_sched) { *out = h->sched; return FTGEMM_OK; }
-  return default_schedule(h, m, n, k, (int)level, out);
+  ftgemm_ft_level run_level;
+  choose_schedule(h, m, n, k, level, out, &run_level);
+  return FTGEMM_OK;
 }
 
 int ftgemm_set_threshold(ftgemm_handle_t h, int mode, double lambda, const float* w, size_t nw) {
@@ -1080,13 +1107,24 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   if (dtype == FTGEMM_BF16 || dtype == FTGEMM_E4M3)
     return tc_gemm(h, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, dtype, level, inject, report);
   if (dtype != FTGEMM_F32) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: dtype %d", (int)dtype);
-  if (level < FTGEMM_FT_OFF || level > FTGEMM_FT_BLOCK)
-    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: level %d needs a tensor-core dtype", (int)level);
+  if (level == FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: level TILE needs a tensor-core dtype");
+  if (level < FTGEMM_FT_OFF || level > FTGEMM_FT_AUTO)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: level %d", (int)level);
   CK(cudaSetDevice(h->device));
-
   ftgemm_schedule s;
-  if (h->has_sched) s = h->sched;
-  else default_schedule(h, m, n, k, (int)level, &s);
+  ftgemm_ft_level run_level;
+  choose_schedule(h, m, n, k, level, &s, &run_level);
+  return simt_gemm(h, m, n, k, alpha, (const float*)A, lda, (const float*)B, ldb, beta, C, ldc, run_level, s,
+                   inject, report);
+}
+
+}  // extern "C"
+
+// The SIMT path of ftgemm_gemm with an explicit schedule and level.
+static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_ft_level level,
+                     const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report) {
   const SimtConfig* cfg = find_simt(s);
   if (!cfg) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: schedule is not a compiled kernel");
 
@@ -1098,8 +1136,8 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   const int cadence = s.cadence > 0 ? s.cadence : ks_per_split;
   const int tiles_m = (M + s.m_tb - 1) / s.m_tb, tiles_n = (N + s.n_tb - 1) / s.n_tb;
 
-  const float* Af = (const float*)A;
-  const float* Bf = (const float*)B;
+  const float* Af = A;
+  const float* Bf = B;
   auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
 
   // ---- faults: validate, resolve, sort, upload -----------------------------
@@ -1209,4 +1247,106 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
   return FTGEMM_OK;
 }
 
-}  // extern "C"
+// ---- autotuner (Section 3.2's parameter selection, done by measurement) ----
+
+int ftgemm_autotune(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
+                    const float* B, int64_t ldb, float* C, int64_t ldc, ftgemm_ft_level level, int32_t reps,
+                    ftgemm_schedule* out, ftgemm_ft_level* level_out) {
+  if (!h || !A || !B || !C || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n || ldc < n)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_autotune: bad argument");
+  if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_autotune: size too large");
+  if (level < FTGEMM_FT_OFF || level > FTGEMM_FT_AUTO || level == FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_autotune: level %d (F32 SIMT levels and AUTO only)", (int)level);
+  CK(cudaSetDevice(h->device));
+  reps = std::max(1, reps);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool timing = h->timing;
+  h->timing = false;
+  // time one candidate: a warm-up run, then `reps` runs between two events
+  auto time_it = [&](const ftgemm_schedule& s, ftgemm_ft_level lv, float* ms) -> int {
+    int rc = simt_gemm(h, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, lv, s, nullptr, nullptr);
+    if (rc) return rc;
+    CK(cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < reps; ++r) {
+      rc = simt_gemm(h, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, lv, s, nullptr, nullptr);
+      if (rc) return rc;
+    }
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= reps;
+    return FTGEMM_OK;
+  };
+  std::vector<ftgemm_ft_level> levels;
+  if (level == FTGEMM_FT_AUTO) levels = {FTGEMM_FT_BLOCK, FTGEMM_FT_WARP, FTGEMM_FT_THREAD};
+  else levels = {level};
+  float best_ms = 1e30f;
+  ftgemm_schedule best{};
+  ftgemm_ft_level best_lv = levels[0];
+  int rc = FTGEMM_OK;
+  for (ftgemm_ft_level lv : levels) {
+    // 1. the tile tuple, with the default cadence and no split-K (and the
+    //    default schedule itself)
+    std::vector<std::pair<float, ftgemm_schedule>> tried;
+    ftgemm_schedule d;
+    default_schedule(h, m, n, k, (int)lv, &d);
+    for (int c = -1; c < (int)(sizeof(kSimtConfigs) / sizeof(kSimtConfigs[0])); ++c) {
+      ftgemm_schedule s = d;
+      if (c >= 0) {
+        const SimtConfig& q = kSimtConfigs[c];
+        s = ftgemm_schedule{q.m_tb, q.n_tb, q.k_tb, q.m_w, q.n_w, q.m_t, q.n_t, std::max(1, 256 / q.k_tb), 1};
+        if (s.m_tb == d.m_tb && s.n_tb == d.n_tb && s.k_tb == d.k_tb && s.m_w == d.m_w && s.n_w == d.n_w &&
+            s.m_t == d.m_t && s.n_t == d.n_t && d.split_k == 1)
+          continue;  // the same as the default
+      }
+      float ms;
+      if ((rc = time_it(s, lv, &ms))) break;
+      tried.push_back({ms, s});
+    }
+    if (rc) break;
+    std::sort(tried.begin(), tried.end(), [](const std::pair<float, ftgemm_schedule>& a,
+                                             const std::pair<float, ftgemm_schedule>& b) { return a.first < b.first; });
+    // 2. split-K for the two fastest tuples while each split keeps >= 8 k-steps
+    const size_t top = std::min<size_t>(2, tried.size());
+    for (size_t q = 0; q < top && !rc; ++q) {
+      const ftgemm_schedule base = tried[q].second;
+      const int64_t ksteps = (k + base.k_tb - 1) / base.k_tb;
+      for (int split = 2; split <= 64 && ksteps / split >= 8; split *= 2) {
+        ftgemm_schedule s = base;
+        s.split_k = split;
+        float ms;
+        if ((rc = time_it(s, lv, &ms))) break;
+        tried.push_back({ms, s});
+      }
+    }
+    if (rc) break;
+    std::sort(tried.begin(), tried.end(), [](const std::pair<float, ftgemm_schedule>& a,
+                                             const std::pair<float, ftgemm_schedule>& b) { return a.first < b.first; });
+    // 3. the verification cadence of the fastest: the paper's K_s = 256
+    //    against once per split (checksums still accumulated every k-step)
+    if (lv != FTGEMM_FT_OFF) {
+      ftgemm_schedule s = tried[0].second;
+      s.cadence = 0;  // once, after the last k-step of each split
+      float ms;
+      if ((rc = time_it(s, lv, &ms))) break;
+      tried.push_back({ms, s});
+      std::sort(tried.begin(), tried.end(), [](const std::pair<float, ftgemm_schedule>& a,
+                                               const std::pair<float, ftgemm_schedule>& b) { return a.first < b.first; });
+    }
+    if (tried[0].first < best_ms) {
+      best_ms = tried[0].first;
+      best = tried[0].second;
+      best_lv = lv;
+    }
+  }
+  h->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  h->tuned[std::make_tuple(m, n, k, (int)level)] = {best, (int)best_lv};
+  if (out) *out = best;
+  if (level_out) *level_out = best_lv;
+  return FTGEMM_OK;
+}
