@@ -55,7 +55,37 @@ def parse():
     ap.add_argument("--level", default="block", choices=["block", "warp", "thread"])
     ap.add_argument("--no-extras", action="store_true", help="skip levels/sweep side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
+    ap.add_argument("--case", default=None,
+                    help="run one small kernel case for a profiler and exit: tc-<bf16|e4m3>-<tile|off>-<n>")
     return ap.parse_args()
+
+
+def run_case(case):
+    """A profiler case: three launches of the tensor-core GEMM on n x n x n
+    N(0,1) operands (seeds 11, 12), nothing else timed or printed."""
+    import torch
+    import paper_2305_01024_gb300 as ft
+    import synth
+    kind, dtn, lvn, n = case.split("-")
+    assert kind == "tc", case
+    n = int(n)
+    Af = synth.torch_make("normal", (n, n), 11, "cuda")
+    Bf = synth.torch_make("normal", (n, n), 12, "cuda")
+    h = ft.Handle(0)
+    if dtn == "bf16":
+        dt, A, B = ft.BF16, Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
+    else:
+        dt = ft.E4M3
+        A, sa = h.quantize(Af, ft.E4M3)
+        B, sb = h.quantize(Bf, ft.E4M3)
+        h.set_fp8_scales(sa, sb)
+    C = torch.empty(n, n, device="cuda")
+    for _ in range(3):
+        h.gemm(A, B, C, level=ft.LEVELS[lvn], dtype=dt, report=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": case, "detected": h.report_fetch().detected}))
+    h.close()
+    return 0
 
 
 def workload_config(n, level):
@@ -253,8 +283,248 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# side measurements (configs 4, 5 and 3)
+# ---------------------------------------------------------------------------
+
+TDM, TDN = 120, 248  # tensor-core data tile of C with the checksums in the MMA tile
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _tile_faults(synth, seed, count, M, N, K, kblk, unit=1.0):
+    """`count` faults on distinct 120 x 248 tiles, |delta| log-uniform in
+    [1e-2, 1e3] x the expected tile maximum of an N(0,1) product (4 sqrt K),
+    in accumulator units (`unit` = 1 / (scale_a scale_b) for e4m3 codes)."""
+    tm, tn = -(-M // TDM), -(-N // TDN)
+    nks = -(-K // kblk)
+    pos = synth.fault_positions(seed, count, tm, tn, nks, TDM, TDN, M, N, nks)
+    mags = synth.log_uniform(seed + 1, count, 1e-2, 1e3)
+    sign = synth.unit(seed + 2, count)
+    return [(a, b, ks, r, c, float((1 if sg < 0.5 else -1) * g * 4 * math.sqrt(K) * unit))
+            for (a, b, ks, r, c), g, sg in zip(pos, mags, sign)]
+
+
+def _above_threshold(A, B, i, j, r0, c0, lam=32.0):
+    """|delta| that the analytic threshold (lambda = 32) flags on both the
+    row and the column of element (i, j) of the tile at (r0, c0): the larger
+    of the two thresholds, from the stored operand values."""
+    import torch
+
+    def val(x):
+        return x.view(torch.float8_e4m3fn).float() if x.dtype == torch.uint8 else x.float()
+    M, N = A.shape[0], B.shape[1]
+    AI = val(A[r0:min(M, r0 + TDM)])
+    BJ = val(B[:, c0:min(N, c0 + TDN)])
+    row = val(A[i]).norm() * BJ.norm()
+    col = AI.norm() * val(B[:, j]).norm()
+    return float(lam * 2.0 ** -24 * torch.maximum(row, col))
+
+
+def _count(records, faults, key_of):
+    want = {}
+    for f in faults:
+        want[key_of(f)] = want.get(key_of(f), 0) + 1
+    found = false = 0
+    for r in records:
+        k = (r.get("problem", 0), r["row"], r["col"])
+        if r["kind"] == 0 and want.get(k, 0) > 0:
+            want[k] -= 1
+            found += 1
+        else:
+            false += 1
+    return found, false
+
+
+def tensor_core_extras(ft, h, synth, dev, timed_loop):
+    """Config 4 at its largest size: bf16 and fp8 E4M3 (per-tensor amax
+    scale), fp32 accumulation, tile-level checksums carried through the MMA,
+    16 seeded faults per GEMM; error against an fp64 product on sampled rows."""
+    import torch
+    n = 16384
+    fl = 2.0 * n ** 3
+    Af = synth.torch_make("normal", (n, n), synth.config_seed(4, 0), dev)
+    Bf = synth.torch_make("normal", (n, n), synth.config_seed(4, 1), dev)
+    C = torch.empty(n, n, device=dev)
+    peaks = _peaks()
+    out = {"workload": f"M=N=K={n}, A,B~N(0,1), alpha=1, beta=0, TILE level (120x248 data tile)"}
+    rows = sorted({int(u * n) for u in synth.unit(synth.config_seed(4, 5), 16)})
+    for name, dt in (("bf16", ft.BF16), ("e4m3", ft.E4M3)):
+        if dt == ft.BF16:
+            A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
+            sa = sb = 1.0
+            Aval, Bval = A.double(), B.double()
+        else:
+            A, sa = h.quantize(Af, ft.E4M3)
+            B, sb = h.quantize(Bf, ft.E4M3)
+            h.set_fp8_scales(sa, sb)
+            Aval = A.view(torch.float8_e4m3fn).double() * sa
+            Bval = B.view(torch.float8_e4m3fn).double() * sb
+        r = {}
+        for lvn, lv in (("off", ft.FT_OFF), ("tile", ft.FT_TILE)):
+            h.enable_timing(True)
+            h.stats(reset=True)
+            ms = timed_loop(lambda i: h.gemm(A, B, C, level=lv, dtype=dt, report=False), 5, warm=2)
+            st = h.stats(reset=True)
+            h.enable_timing(False)
+            r[f"{lvn}_tflops"] = fl / (ms / 1e3) / 1e12
+            r[f"{lvn}_kernel_tflops"] = fl / (st["kernel_ms"] / max(1, st["timed_launches"]) / 1e3) / 1e12
+        r["overhead_pct_kernel"] = 100.0 * (r["off_kernel_tflops"] / r["tile_kernel_tflops"] - 1.0)
+        r["overhead_pct"] = 100.0 * (r["off_tflops"] / r["tile_tflops"] - 1.0)
+        h.report_fetch()
+        # 16 seeded faults in one GEMM: corrected at their positions?
+        faults = _tile_faults(synth, synth.config_seed(4, 20 + dt), 16, n, n, n, 64 if dt == ft.BF16 else 128,
+                              unit=1.0 / (sa * sb))
+        rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=dt, inject=faults)
+        found, false = _count(rep.records, faults, lambda f: (0, f[0] * TDM + f[3], f[1] * TDN + f[4]))
+        above = sum(abs(f[5]) > _above_threshold(A, B, f[0] * TDM + f[3], f[1] * TDN + f[4], f[0] * TDM, f[1] * TDN)
+                    for f in faults)
+        r["faults"] = {"injected": len(faults), "above_analytic_threshold": above,
+                       "corrected_at_position": found, "false_alarms": false,
+                       "detect_rate_above_threshold": found / above if above else None}
+        # max relative error of the (corrected) result against fp64 on sampled rows
+        ref = Aval[rows] @ Bval
+        got = C[rows].double()
+        r["max_rel_err_vs_fp64"] = float(((got - ref).abs().max() / ref.abs().max()).item())
+        if dt == ft.BF16:
+            ct = torch.empty(n, n, device=dev, dtype=torch.bfloat16)
+            r["torch_matmul_tflops"] = fl / (timed_loop(lambda i: torch.matmul(A, B, out=ct), 5, warm=2) / 1e3) / 1e12
+            pk = peaks.get("bf16_tflops")
+            r["roofline"] = {"bound": "tensor", "achieved": r["tile_kernel_tflops"], "peak": pk, "unit": "TFLOP/s",
+                             "frac": r["tile_kernel_tflops"] / pk if pk else None, "traffic": None,
+                             "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"}
+            del ct
+        else:
+            try:
+                a8 = A.view(torch.float8_e4m3fn)
+                b8 = B.view(torch.float8_e4m3fn).t().contiguous().t()
+                one = torch.tensor(1.0, device=dev)
+                r["torch_scaled_mm_tflops"] = fl / (timed_loop(
+                    lambda i: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.float32), 5,
+                    warm=2) / 1e3) / 1e12
+                del b8
+            except Exception as exc:
+                r["torch_scaled_mm_tflops"] = f"unavailable: {type(exc).__name__}"
+            pk = peaks.get("bf16_tflops")
+            r["roofline"] = {"bound": "tensor", "achieved": r["tile_kernel_tflops"],
+                             "peak": 2 * pk if pk else None, "unit": "TFLOP/s",
+                             "frac": r["tile_kernel_tflops"] / (2 * pk) if pk else None, "traffic": None,
+                             "peak_basis": "measured bf16 burst x 2 (nominal fp8 / bf16 dense ratio)"}
+        h.report_fetch()
+        out[name] = {k: (float(f"{v:.5g}") if isinstance(v, float) else v) for k, v in r.items()}
+        del A, B, Aval, Bval
+    h.set_fp8_scales(1.0, 1.0)
+    del Af, Bf, C
+    return out
+
+
+def grouped_extras(ft, h, synth, dev, timed_loop):
+    """Config 5: 512 bf16 problems, M, N uniform on 64..4096 and K on
+    64..2048 (multiples of 16), N(0,1); one persistent launch replayed from a
+    CUDA graph; 1% of the tiles get one seeded fault."""
+    import torch
+    nprob = 512
+    u = synth.unit(synth.config_seed(5, 0), 3 * nprob)
+    shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253), 64 + 16 * int(u[3 * q + 2] * 125))
+              for q in range(nprob)]
+    fl = sum(2.0 * M * N * K for M, N, K in shapes)
+    probs = []
+    for q, (M, N, K) in enumerate(shapes):
+        A = synth.torch_make("normal", (M, K), synth.config_seed(5, 100 + 2 * q), dev).to(torch.bfloat16)
+        B = synth.torch_make("normal", (K, N), synth.config_seed(5, 101 + 2 * q), dev).to(torch.bfloat16)
+        probs.append((A, B, torch.empty(M, N, device=dev)))
+    out = {"workload": f"{nprob} problems, M,N~U{{64..4096 step 16}}, K~U{{64..2048 step 16}}, bf16 N(0,1)",
+           "gflop": fl / 1e9}
+    capture = torch.cuda.Stream()
+    main_stream = torch.cuda.current_stream()
+    try:
+        for lvn, lv in (("off", ft.FT_OFF), ("tile", ft.FT_TILE)):
+            g = ft.Group(h, probs, dtype=ft.BF16, level=lv)
+            faults = []
+            if lv == ft.FT_TILE:
+                # the graph captures the fault table: set it first
+                tm, tn = g.tiles()
+                tiles = sum(a * b for a, b in zip(tm, tn))
+                nf = max(1, tiles // 100)
+                pick = synth.unit(synth.config_seed(5, 7), nf)
+                by_prob = {}
+                for f in range(nf):
+                    q = int(pick[f] * nprob)
+                    by_prob[q] = by_prob.get(q, 0) + 1
+                for q, cnt in sorted(by_prob.items()):
+                    M, N, K = shapes[q]
+                    cnt = min(cnt, tm[q] * tn[q])
+                    faults += [(q,) + f for f in _tile_faults(synth, synth.config_seed(5, 1000 + q), cnt, M, N, K, 64)]
+                g.set_faults(faults)
+            graph = torch.cuda.CUDAGraph()
+            h.set_stream(capture)  # captured on a side stream, replayed on the main one
+            with torch.cuda.graph(graph, stream=capture):
+                g.run()
+            h.set_stream(main_stream)
+            h.report_fetch()
+            reps = 13
+            ms = timed_loop(lambda i: graph.replay(), reps - 3, warm=3)
+            out[f"graph_{lvn}_tflops"] = fl / (ms / 1e3) / 1e12
+            if faults:
+                rep = h.report_fetch(capacity=1 << 16)
+                found, false = _count(rep.records, faults * reps,
+                                      lambda f: (f[0], f[1] * TDM + f[4], f[2] * TDN + f[5]))
+                above = sum(abs(f[6]) > _above_threshold(probs[f[0]][0], probs[f[0]][1], f[1] * TDM + f[4],
+                                                          f[2] * TDN + f[5], f[1] * TDM, f[2] * TDN)
+                            for f in faults)
+                out["faults"] = {"tiles": tiles, "injected_per_launch": len(faults), "launches": reps,
+                                 "above_analytic_threshold_per_launch": above,
+                                 "corrected_at_position": found, "false_alarms": false,
+                                 "detect_rate_above_threshold": found / (above * reps) if above else None}
+            g.close()
+        out["overhead_pct"] = 100.0 * (out["graph_off_tflops"] / out["graph_tile_tflops"] - 1.0)
+    finally:
+        h.set_stream(main_stream)
+    ms = timed_loop(lambda i: [torch.matmul(A, B) for A, B, _ in probs], 3, warm=1)
+    out["torch_matmul_loop_tflops"] = fl / (ms / 1e3) / 1e12
+    return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in out.items()}
+
+
+def irregular_extras(ft, h, synth, dev, timed_loop):
+    """Config 3: irregular fp32 shapes, N(0,1), schedule and checksum level
+    picked per shape by the autotuner, one seeded fault per GEMM."""
+    import torch
+    h.set_schedule(None)
+    out = {}
+    for q, (M, N, K) in enumerate([(16384, 16384, 32), (20480, 256, 20480), (256, 256, 65536), (4096, 96, 4096),
+                                   (777, 1531, 2049)]):
+        A = synth.torch_make("normal", (M, K), synth.config_seed(3, 2 * q), dev)
+        B = synth.torch_make("normal", (K, N), synth.config_seed(3, 2 * q + 1), dev)
+        C = torch.empty(M, N, device=dev)
+        s, lv = h.autotune(A, B, C, level=ft.FT_AUTO, reps=2)
+        fl = 2.0 * M * N * K
+        ms = timed_loop(lambda i: h.gemm(A, B, C, level=ft.FT_AUTO, report=False), 5, warm=1)
+        ms_off = timed_loop(lambda i: h.gemm(A, B, C, level=ft.FT_OFF, report=False), 5, warm=1)
+        ct = torch.empty_like(C)
+        ms_t = timed_loop(lambda i: torch.matmul(A, B, out=ct), 5, warm=1)
+        tiles_m, tiles_n = -(-M // s.m_tb), -(-N // s.n_tb)
+        (a, b, ks, r, c), = synth.fault_positions(synth.config_seed(3, 50 + q), 1, tiles_m, tiles_n,
+                                                  -(-K // s.k_tb), s.m_tb, s.n_tb, M, N, max(1, s.cadence))
+        rep = h.gemm(A, B, C, level=ft.FT_AUTO, inject=[(a, b, ks, r, c, 64.0 * math.sqrt(K))])
+        ok = [(x["row"], x["col"], x["kind"]) for x in rep.records] == [(a * s.m_tb + r, b * s.n_tb + c, 0)]
+        out[f"{M}x{N}x{K}"] = {"tflops": round(fl / (ms / 1e3) / 1e12, 3),
+                               "ft_off_default_tflops": round(fl / (ms_off / 1e3) / 1e12, 3),
+                               "torch_fp32_tflops": round(fl / (ms_t / 1e3) / 1e12, 3),
+                               "level": [k for k, v in ft.LEVELS.items() if v == lv][0],
+                               "schedule": s.as_dict(), "fault_corrected": ok}
+        del A, B, C, ct
+    return out
+
+
 def main():
     args = parse()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -409,6 +679,19 @@ def main():
         h.set_schedule(SCHED)
         del a, b, c, ct
 
+    # ---- configs 4, 5, 3: tensor cores, grouped, irregular (side lines) ----
+    side = {}
+    if not args.no_extras and rank == 0:
+        for name, fn in (("tensor_core", tensor_core_extras), ("grouped", grouped_extras),
+                         ("irregular", irregular_extras)):
+            try:
+                side[name] = fn(ft, h, synth, dev, timed_loop)
+            except Exception as exc:  # reported, not hidden: the headline line still prints
+                side[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+        h.set_schedule(SCHED)
+        h.report_fetch()
+
     # ---- end to end through the C ABI from pinned host buffers -------------
     hA = A.cpu().pin_memory()
     hB = B.cpu().pin_memory()
@@ -453,6 +736,7 @@ def main():
     if extras:
         line["other_levels_tflops"] = extras
         line["sweep"] = sweep
+    line.update(side)
     h.close()
     del A, B, C, C0, Ct
     if rank == 0:

@@ -36,6 +36,7 @@ cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatc
                            cudaStream_t st);
 cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
                             int* launches, cudaStream_t st);
+cudaError_t launch_fault_bits(const Fault* f, int n, uint32_t* bits, size_t words, cudaStream_t st);
 int mlp_grad_blocks(long long nb);
 cudaError_t launch_mlp_grad(const float* X, const float* t, long long s0, int nb, const float* theta, float inv_n,
                             float* part, int nblk, cudaStream_t st);
@@ -94,6 +95,8 @@ struct ftgemm_ctx {
   Fault* d_faults = nullptr;
   Fault* h_faults = nullptr;  // pinned staging
   int faults_cap = 0;
+  uint32_t* d_fbits = nullptr;  // tensor-core path: one bit per tile with a fault
+  size_t fbits_words = 0;
   cudaEvent_t faults_free = nullptr;
   // settings
   bool has_sched = false;
@@ -483,7 +486,22 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   }
   if (h->sink_lam && abft && b.total_tiles > h->sink_cap)
     FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the call has %d", (long long)h->sink_cap, b.total_tiles);
-  TcRun run{nf > 0 ? h->d_faults : nullptr, nf, h->rep, h->recs, abft ? h->sink_lam : nullptr,
+  const uint32_t* fbits = nullptr;
+  if (nf > 0) {
+    const size_t words = ((size_t)b.total_tiles + 31) / 32;
+    if (words > h->fbits_words) {
+      CK(cudaStreamSynchronize(h->stream));
+      if (h->d_fbits) CK(cudaFree(h->d_fbits));
+      h->d_fbits = nullptr;
+      h->fbits_words = 0;
+      CK(cudaMalloc(&h->d_fbits, words * sizeof(uint32_t)));
+      h->fbits_words = words;
+    }
+    CK(launch_fault_bits(h->d_faults, nf, h->d_fbits, words, h->stream));
+    ++launches;
+    fbits = h->d_fbits;
+  }
+  TcRun run{nf > 0 ? h->d_faults : nullptr, nf, fbits, h->rep, h->recs, abft ? h->sink_lam : nullptr,
             abft ? h->sink_x : nullptr};
   const int grid = std::max(1, std::min(b.total_tiles, h->num_sms > 0 ? h->num_sms : 148));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -521,6 +539,7 @@ struct ftgemm_group {
   int total[P_KINDS] = {};
   int total_tiles = 0;
   Fault* d_faults = nullptr;
+  uint32_t* d_fbits = nullptr;  // one bit per tile with a fault
   int nfaults = 0;
 };
 
@@ -571,6 +590,7 @@ static void group_free(ftgemm_group* g) {
   if (g->d_cta_start) cudaFree(g->d_cta_start);
   if (g->ws) cudaFree(g->ws);
   if (g->d_faults) cudaFree(g->d_faults);
+  if (g->d_fbits) cudaFree(g->d_fbits);
   delete g;
 }
 
@@ -718,11 +738,17 @@ int ftgemm_group_set_faults(ftgemm_group_t g, const int32_t* problem, const ftge
   CK(cudaSetDevice(g->h->device));
   CK(cudaStreamSynchronize(g->h->stream));  // a launch in flight may read the old table
   if (g->d_faults) cudaFree(g->d_faults);
+  if (g->d_fbits) cudaFree(g->d_fbits);
   g->d_faults = nullptr;
+  g->d_fbits = nullptr;
   g->nfaults = 0;
   if (nf > 0) {
+    std::vector<uint32_t> bits(((size_t)g->total_tiles + 31) / 32, 0u);
+    for (const Fault& f : fv) bits[f.tile >> 5] |= 1u << (f.tile & 31);
     CK(cudaMalloc(&g->d_faults, sizeof(Fault) * nf));
+    CK(cudaMalloc(&g->d_fbits, sizeof(uint32_t) * bits.size()));
     CK(cudaMemcpy(g->d_faults, fv.data(), sizeof(Fault) * nf, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g->d_fbits, bits.data(), sizeof(uint32_t) * bits.size(), cudaMemcpyHostToDevice));
   }
   g->nfaults = nf;
   return FTGEMM_OK;
@@ -746,7 +772,7 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   mb.table = g->d_maps;
   if (h->sink_lam && g->abft && g->total_tiles > h->sink_cap)
     FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the group has %d", (long long)h->sink_cap, g->total_tiles);
-  TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, h->rep, h->recs,
+  TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, g->d_fbits, h->rep, h->recs,
             g->abft ? h->sink_lam : nullptr, g->abft ? h->sink_x : nullptr};
   const int grid = g->ncta;  // the schedule was built for this many CTAs
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -850,6 +876,7 @@ int ftgemm_destroy(ftgemm_handle_t h) {
   if (h->h_faults) cudaFreeHost(h->h_faults);
   if (h->faults_free) cudaEventDestroy(h->faults_free);
   if (h->qscratch) cudaFree(h->qscratch);
+  if (h->d_fbits) cudaFree(h->d_fbits);
   if (h->mlp_theta) cudaFree(h->mlp_theta);
   if (h->mlp_ws) cudaFree(h->mlp_ws);
   for (auto& e : h->pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }

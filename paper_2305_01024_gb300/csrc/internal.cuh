@@ -157,6 +157,7 @@ struct TcMapsBatch {
 
 struct TcRun {
   const Fault* faults; int nfaults;  // sorted by global tile (tile_start + local)
+  const uint32_t* fault_bits;        // bit t set when global tile t has a fault (with faults only)
   DevReport* rep; ftgemm_fault_record* recs;
   // residual sink (optional): per global tile, the smallest lambda that
   // would have flagged nothing, and the tile's 5 threshold features

@@ -320,7 +320,8 @@ __global__ void __launch_bounds__(192, 1)
       // accumulation being additive, an offset is applied to the
       // tensor-memory accumulator here, where the k-step it was scheduled
       // for only changes rounding.
-      if (run.nfaults > 0) {
+      // one bit per tile keeps the table search off the path of fault-free tiles
+      if (run.nfaults > 0 && ((run.fault_bits[my_tile >> 5] >> (my_tile & 31)) & 1u)) {
         for (int f = first_fault(run.faults, run.nfaults, my_tile); f < run.nfaults && run.faults[f].tile == my_tile;
              ++f) {
           const Fault F = run.faults[f];

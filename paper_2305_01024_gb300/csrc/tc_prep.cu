@@ -408,6 +408,19 @@ cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[
   return cudaGetLastError();
 }
 
+// bits[t / 32] |= 1 << (t % 32) for the tile t of every fault (bits zeroed before)
+__global__ void fault_bits_kernel(const Fault* __restrict__ f, int n, uint32_t* __restrict__ bits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicOr(&bits[f[i].tile >> 5], 1u << (f[i].tile & 31));
+}
+
+cudaError_t launch_fault_bits(const Fault* f, int n, uint32_t* bits, size_t words, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bits, 0, words * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  fault_bits_kernel<<<(n + 255) / 256, 256, 0, st>>>(f, n, bits);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
                             int* launches, cudaStream_t st) {
   const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 8);
