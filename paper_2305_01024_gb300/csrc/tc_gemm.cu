@@ -260,6 +260,54 @@ __global__ void __launch_bounds__(192, 1)
       const int ab = lt & 1;
       const int row0 = x.tm * DM, col0 = x.tn * DN, gr = row0 + r;
       const uint32_t tl = tmem + (uint32_t)(ab * BN) + ((uint32_t)(lq * 32) << 16);
+      // Everything this tile needs from global memory, and its threshold,
+      // is fetched and computed before waiting for the accumulator, so the
+      // load latency hides behind the tile's main loop.
+      const int pM = P.M, pN = P.N;
+      const float sc = P.alpha * P.acc_scale;  // fp8: product of the per-tensor scales
+      const float beta = P.beta;
+      const int c_vec = P.c_vec;
+      const long long ldc = P.ldc;
+      float* const Cp = P.C;
+      const int my_tile = P.tile_start + x.tm * P.tiles_n + x.tn;
+      const bool has_fault =
+          run.nfaults > 0 && ((run.fault_bits[my_tile >> 5] >> (my_tile & 31)) & 1u);
+      float nA_r = 0.f, froA_t = 0.f, froB_t = 0.f, nB_c[2] = {0.f, 0.f};
+      float wsc[Cfg::NPIECE], vsc[Cfg::NPIECE];
+      float lam_u = P.lam_u;
+      float feat[MLP_IN];
+      if constexpr (ABFT) {
+        nA_r = (data_row && gr < pM) ? P.nA[gr] : 0.f;
+        froA_t = P.froA[x.tm];
+        froB_t = P.froB[x.tn];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = r + 128 * h, gc = col0 + c;
+          nB_c[h] = (c < DN && gc < pN) ? P.nB[gc] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < Cfg::NPIECE; ++q) {
+          wsc[q] = P.wscale[(size_t)x.tn * CSR + q];
+          vsc[q] = P.vscale[(size_t)x.tm * CSR + q];
+        }
+        // ----- threshold of this tile -----
+        // analytic: lambda * u; learned: lambda = mlp_scale * 2^f(x) with x
+        // the tile's features (log2 K, block coherences, operand type, tile
+        // size), evaluated on every epilogue warp; the analytic value is the
+        // fallback for a non-finite or non-positive output
+        const int rows = min(DM, pM - row0), cols = min(DN, pN - col0);
+        feat[0] = log2f((float)P.K) * 0.0625f;
+        feat[1] = P.coA ? P.coA[x.tm] : 0.f;
+        feat[2] = P.coB ? P.coB[x.tn] : 0.f;
+        feat[3] = DT == 0 ? 0.5f : 1.f;
+        feat[4] = log2f((float)rows * (float)cols) * 0.0625f;
+        if (P.mlp) {
+          MlpAct act;
+          mlp_forward_warp(P.mlp, feat, lane, act);
+          const float lam = P.mlp_scale * exp2f(act.y);
+          if (isfinite(lam) && lam > 0.f) lam_u = lam * 5.9604644775390625e-8f;  // * 2^-24
+        }
+      }
       // after one wait gave up the remaining tiles are walked without waits
       // (and without stores), so the barriers below still line up
       const bool ok = !dead && mbar_wait(&T.acc_full[ab], (lt >> 1) & 1);
@@ -268,11 +316,8 @@ __global__ void __launch_bounds__(192, 1)
         atomicExch(&T.abort, 1);
       }
       tc_fence_after();
-      const float sc = P.alpha * P.acc_scale;  // fp8: product of the per-tensor scales
-      const float beta = P.beta;
-      const int my_tile = P.tile_start + x.tm * P.tiles_n + x.tn;
-      const bool row_ok = ok && data_row && gr < P.M;
-      float* crow_ptr = P.C + (long long)(row_ok ? gr : 0) * P.ldc + col0;
+      const bool row_ok = ok && data_row && gr < pM;
+      float* crow_ptr = Cp + (long long)(row_ok ? gr : 0) * ldc + col0;
       // alpha * acc + beta * C of one 16-column chunk of this row, data
       // columns inside the matrix only
       auto store16 = [&](int ch, const float* v) {
@@ -283,7 +328,7 @@ __global__ void __launch_bounds__(192, 1)
           const int gc = col0 + c;
           float* dst = crow_ptr + c;
           // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
-          if (P.c_vec && c + 3 < DN && gc + 3 < P.N) {
+          if (c_vec && c + 3 < DN && gc + 3 < pN) {
             float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
             if (beta != 0.f) {
               const float4 ci = *reinterpret_cast<const float4*>(dst);
@@ -294,7 +339,7 @@ __global__ void __launch_bounds__(192, 1)
           } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              if (c + e < DN && gc + e < P.N) {
+              if (c + e < DN && gc + e < pN) {
                 const float o = sc * v[q + e];
                 dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
               }
@@ -321,7 +366,7 @@ __global__ void __launch_bounds__(192, 1)
       // tensor-memory accumulator here, where the k-step it was scheduled
       // for only changes rounding.
       // one bit per tile keeps the table search off the path of fault-free tiles
-      if (run.nfaults > 0 && ((run.fault_bits[my_tile >> 5] >> (my_tile & 31)) & 1u)) {
+      if (has_fault) {
         for (int f = first_fault(run.faults, run.nfaults, my_tile); f < run.nfaults && run.faults[f].tile == my_tile;
              ++f) {
           const Fault F = run.faults[f];
@@ -360,25 +405,6 @@ __global__ void __launch_bounds__(192, 1)
         }
       } else {
         epi_bar();
-        // ----- threshold of this tile -----
-        // analytic: lambda * u; learned: lambda = mlp_scale * 2^f(x) with x
-        // the tile's features (log2 K, block coherences, operand type, tile
-        // size), evaluated on every epilogue warp; the analytic value is the
-        // fallback for a non-finite or non-positive output
-        const int rows = min(DM, P.M - row0), cols = min(DN, P.N - col0);
-        float feat[MLP_IN];
-        feat[0] = log2f((float)P.K) * 0.0625f;
-        feat[1] = P.coA ? P.coA[x.tm] : 0.f;
-        feat[2] = P.coB ? P.coB[x.tn] : 0.f;
-        feat[3] = DT == 0 ? 0.5f : 1.f;
-        feat[4] = log2f((float)rows * (float)cols) * 0.0625f;
-        float lam_u = P.lam_u;
-        if (P.mlp) {
-          MlpAct act;
-          mlp_forward_warp(P.mlp, feat, lane, act);
-          const float lam = P.mlp_scale * exp2f(act.y);
-          if (isfinite(lam) && lam > 0.f) lam_u = lam * 5.9604644775390625e-8f;  // * 2^-24
-        }
         // ----- one pass over the accumulator: fp32 screen sums and the store -----
         // C is written before verification; a confirmed fault is then
         // patched in place (a single element, below).
@@ -398,7 +424,9 @@ __global__ void __launch_bounds__(192, 1)
               rc = (tt - rs) - y;
               rs = tt;
             } else if (c - DN < Cfg::NPIECE) {
-              crow = fmaf(v[q], P.wscale[(size_t)x.tn * CSR + (c - DN)], crow);
+#pragma unroll
+              for (int pc = 0; pc < Cfg::NPIECE; ++pc)
+                if (c - DN == pc) crow = fmaf(v[q], wsc[pc], crow);
             }
           }
           // the column checksum pieces sit in lanes DM..DM+NPIECE-1
@@ -431,28 +459,30 @@ __global__ void __launch_bounds__(192, 1)
         }
         crow += T.cradj[r];
         T.crow[r] = crow;
-        T.tr[r] = (data_row && gr < P.M) ? lam_u * P.nA[gr] * P.froB[x.tn] : 0.f;
+        T.tr[r] = (data_row && gr < pM) ? lam_u * nA_r * froB_t : 0.f;
         int flagged = data_row && fabsf(rs - crow) > T.tr[r];
         T.flag_r[r] = flagged;
         constexpr float kU = 5.9604644775390625e-8f;  // 2^-24
-        if (run.sink_lam && data_row && gr < P.M) {
-          const float den = kU * P.nA[gr] * P.froB[x.tn];
+        if (run.sink_lam && data_row && gr < pM) {
+          const float den = kU * nA_r * froB_t;
           if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(rs - crow) / den));
         }
         epi_bar();
-        for (int c = r; c < BN; c += 128) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = r + 128 * h;
           int fl = 0;
           float cc = 0.f, tcv = 0.f;
           if (c < DN) {
 #pragma unroll
-            for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], P.vscale[(size_t)x.tm * CSR + q], cc);
+            for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], vsc[q], cc);
             cc += T.ccadj[c];
             const int gc = col0 + c;
-            tcv = gc < P.N ? lam_u * P.froA[x.tm] * P.nB[gc] : 0.f;
+            tcv = gc < pN ? lam_u * froA_t * nB_c[h] : 0.f;
             const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
             fl = fabsf(s - cc) > tcv;
-            if (run.sink_lam && gc < P.N) {
-              const float den = kU * P.froA[x.tm] * P.nB[gc];
+            if (run.sink_lam && gc < pN) {
+              const float den = kU * froA_t * nB_c[h];
               if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(s - cc) / den));
             }
           }
