@@ -668,12 +668,24 @@ def main():
             fl = 2.0 * sz ** 3
             it = 5
             row = {}
-            for name, lv in (("block", ft.FT_BLOCK), ("off", ft.FT_OFF)):
-                h.set_schedule(None)
-                row[name] = fl / (timed_loop(lambda i: h.gemm(a, b, c, 1.0, 0.5, level=lv, report=False), it, warm=2) / 1e3) / 1e12
+            h.set_schedule(None)
+            for tuned in (False, True):
+                for name, lv in (("block", ft.FT_BLOCK), ("off", ft.FT_OFF)):
+                    if tuned:  # the autotuner's pick for this size and level
+                        h.autotune(a, b, c, level=lv, reps=2)
+                    h.enable_timing(True)
+                    h.stats(reset=True)
+                    t_ = timed_loop(lambda i: h.gemm(a, b, c, 1.0, 0.5, level=lv, report=False), it, warm=2)
+                    st_ = h.stats(reset=True)
+                    h.enable_timing(False)
+                    key = name + ("_tuned" if tuned else "")
+                    row[key] = fl / (t_ / 1e3) / 1e12
+                    row[key + "_kernel"] = fl / (st_["kernel_ms"] / max(1, st_["timed_launches"]) / 1e3) / 1e12
             ct = torch.empty_like(c)
             row["torch_fp32"] = fl / (timed_loop(lambda i: torch.matmul(a, b, out=ct), it, warm=2) / 1e3) / 1e12
             row["overhead_pct"] = 100.0 * (row["off"] / row["block"] - 1.0)
+            row["overhead_pct_tuned"] = 100.0 * (row["off_tuned"] / row["block_tuned"] - 1.0)
+            row["overhead_pct_kernel_tuned"] = 100.0 * (row["off_tuned_kernel"] / row["block_tuned_kernel"] - 1.0)
             sweep[str(sz)] = {k: round(v, 3) for k, v in row.items()}
         h.report_fetch()
         h.set_schedule(SCHED)

@@ -8,6 +8,8 @@
 //   n[l]    = ||X(:, l)||_2                               (column norms)
 // so with X = A^T it yields e^T A per row block of A and ||A(i,:)||, and
 // with X = B it yields B e per column block and ||B(:,j)||.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace ftg {
@@ -42,28 +44,45 @@ __global__ void copy_pad_kernel(const float* __restrict__ X, long long ldx, int 
   Y[(long long)r * ldy + c] = __ldg(X + (long long)r * ldx + c);
 }
 
-constexpr int kEncRows = 64;     // k-rows per CTA
+constexpr int kEncRows = 64;     // most k-rows per CTA
 constexpr int kEncCols = 1024;   // columns per CTA (256 threads x 4)
 
-// One CTA: kEncRows rows x kEncCols columns of a k-major X.  Block sums over
-// groups of n_u columns (n_u a power of two, 2..1024) for every row, and
-// partial column sums of squares over the CTA's rows.
+// k-rows per CTA: enough CTAs to fill the GPU (about 4 per SM on 152 SMs)
+// on small problems, at most kEncRows on large ones; a multiple of 8.
+static int enc_rows(int K, int L) {
+  const int colblocks = (L + kEncCols - 1) / kEncCols;
+  const int want = std::max(1, 608 / colblocks);
+  int rows = (K + want - 1) / want;
+  rows = (rows + 7) / 8 * 8;
+  return std::min(kEncRows, std::max(8, rows));
+}
+
+// One CTA: `rows` k-rows x kEncCols columns of a k-major X (float4 loads
+// when `vec`: 16-byte aligned rows).  Block sums over groups of n_u columns
+// (n_u a power of two, 2..1024) for every row, and partial column sums of
+// squares over the CTA's rows.
 __global__ void __launch_bounds__(256) encode_kmajor_kernel(const float* __restrict__ X, long long ldx,
-                                                            int K, int L, int n_u,
+                                                            int K, int L, int n_u, int rows, int vec,
                                                             float* __restrict__ S, long long lds,
                                                             float* __restrict__ part) {
   __shared__ float wpart[kEncRows][8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c0 = blockIdx.x * kEncCols + tid * 4;
-  const int k0 = blockIdx.y * kEncRows;
-  const int k1 = min(K, k0 + kEncRows);
+  const int k0 = blockIdx.y * rows;
+  const int k1 = min(K, k0 + rows);
   const int g = n_u / 4;  // lanes per block when n_u <= 128
   float sq[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k = k0; k < k1; ++k) {
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {  // unrolled: several rows' loads in flight
     const float* row = X + (long long)k * ldx;
     float v[4];
+    if (vec && c0 + 3 < L) {
+      const float4 q4 = __ldg(reinterpret_cast<const float4*>(row + c0));
+      v[0] = q4.x; v[1] = q4.y; v[2] = q4.z; v[3] = q4.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (c0 + q < L) ? __ldg(row + c0 + q) : 0.f;
+      for (int q = 0; q < 4; ++q) v[q] = (c0 + q < L) ? __ldg(row + c0 + q) : 0.f;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) sq[q] = fmaf(v[q], v[q], sq[q]);
     if (S) {
@@ -146,7 +165,8 @@ cudaError_t launch_copy_pad(const float* X, long long ldx, int R, int Cn, float*
 }
 
 long long kmajor_scratch_floats(int K, int L) {
-  return (long long)((K + kEncRows - 1) / kEncRows) * L;
+  const int rows = enc_rows(K, L);
+  return (long long)((K + rows - 1) / rows) * L;
 }
 
 // S (may be null): [ceil(L/n_u)][lds] block sums; nrm (may be null): [L].
@@ -155,9 +175,11 @@ cudaError_t launch_encode_kmajor(const float* X, long long ldx, int K, int L, in
                                  long long lds, float* nrm, float* scratch, int* launches,
                                  cudaStream_t st) {
   if (n_u < 2 || n_u > kEncCols || (n_u & (n_u - 1))) return cudaErrorInvalidValue;
-  const int chunks = (K + kEncRows - 1) / kEncRows;
+  const int vec = (ldx % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  const int rows = enc_rows(K, L);
+  const int chunks = (K + rows - 1) / rows;
   dim3 g((L + kEncCols - 1) / kEncCols, chunks);
-  encode_kmajor_kernel<<<g, 256, 0, st>>>(X, ldx, K, L, n_u, S, lds, nrm ? scratch : nullptr);
+  encode_kmajor_kernel<<<g, 256, 0, st>>>(X, ldx, K, L, n_u, rows, vec, S, lds, nrm ? scratch : nullptr);
   *launches += 1;
   if (nrm) {
     colnorm_finish_kernel<<<(L + 255) / 256, 256, 0, st>>>(scratch, chunks, L, nrm);

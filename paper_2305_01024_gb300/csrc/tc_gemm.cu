@@ -503,6 +503,10 @@ __global__ void __launch_bounds__(192, 1)
           if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
           for (int c = r; c < BN; c += 128) T.sum_c[c] = 0.0;
           epi_bar();
+          // fp64 sums only where the screen flagged: a flagged row in its own
+          // thread, a flagged column (the same in all lanes) by a warp
+          // shuffle reduction and one shared-memory add per warp
+          const bool my_row_flagged = T.flag_r[r] != 0;
           double sr = 0.0;
           for (int ch = 0; ch < BN / 16; ++ch) {
             float v[16];
@@ -512,8 +516,13 @@ __global__ void __launch_bounds__(192, 1)
             for (int q = 0; q < 16; ++q) {
               const int c = ch * 16 + q;
               if (c < DN) {
-                sr += (double)v[q];
-                if (data_row && T.flag_c[c]) atomicAdd(&T.sum_c[c], (double)v[q]);
+                if (my_row_flagged) sr += (double)v[q];
+                if (T.flag_c[c]) {  // warp-uniform
+                  double xs = data_row ? (double)v[q] : 0.0;
+#pragma unroll
+                  for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
+                  if (lane == 0) atomicAdd(&T.sum_c[c], xs);
+                }
               }
             }
           }
