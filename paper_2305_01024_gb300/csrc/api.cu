@@ -23,6 +23,9 @@ cudaError_t simt_launch_huge(int, const SimtMaps&, const SimtParams&, int, cudaS
 cudaError_t simt_launch_huge16(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_wide(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t launch_transpose(const float*, long long, int, int, float*, long long, cudaStream_t);
+cudaError_t launch_transpose_encode(const float* A, long long lda, int M, int K, float* At, long long ldt, int m_u,
+                                    float* V, long long ldv, float* nrm, float* scratch, int* launches,
+                                    cudaStream_t st);
 cudaError_t launch_copy_pad(const float*, long long, int, int, float*, long long, cudaStream_t);
 long long kmajor_scratch_floats(int K, int L);
 cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*, long long, float*,
@@ -1197,7 +1200,9 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   const size_t nV = need_vw ? (size_t)nvb * ldv : 0;
   const size_t nW = need_vw ? (size_t)nwb * ldv : 0;
   const size_t nNa = abft ? (size_t)M : 0, nNb = abft ? (size_t)N : 0;
-  const size_t nScr = abft ? (size_t)std::max(kmajor_scratch_floats(K, M), kmajor_scratch_floats(K, N)) : 0;
+  const size_t nScr = abft ? (size_t)std::max<long long>((long long)((K + 31) / 32) * M,
+                                                         kmajor_scratch_floats(K, N))
+                           : 0;
   const size_t nPart = split > 1 ? (size_t)split * M * N : 0;
   const size_t oAt = 0, oBp = align64(oAt + nAt), oV = align64(oBp + nBp), oW = align64(oV + nV),
                oNa = align64(oW + nW), oNb = align64(oNa + nNa), oScr = align64(oNb + nNb),
@@ -1208,8 +1213,9 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   }
   float* ws = h->ws;
   int launches = 0;
-  CK(launch_transpose(Af, lda, M, K, ws + oAt, ldt, h->stream));
-  ++launches;
+  // A^T, with the A side of the encoding (block sums, row norms) in the same pass
+  CK(launch_transpose_encode(Af, lda, M, K, ws + oAt, ldt, m_u, need_vw ? ws + oV : nullptr, ldv,
+                             abft ? ws + oNa : nullptr, ws + oScr, &launches, h->stream));
   const float* Bk = Bf;
   if (!b_ok) {
     CK(launch_copy_pad(Bf, ldb, K, N, ws + oBp, ldbp, h->stream));
@@ -1217,8 +1223,6 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
     Bk = ws + oBp;
   }
   if (abft) {
-    CK(launch_encode_kmajor(ws + oAt, ldt, K, M, need_vw ? m_u : 2, need_vw ? ws + oV : nullptr, ldv,
-                            ws + oNa, ws + oScr, &launches, h->stream));
     CK(launch_encode_kmajor(Bk, ldbp, K, N, need_vw ? n_u : 2, need_vw ? ws + oW : nullptr, ldv,
                             ws + oNb, ws + oScr, &launches, h->stream));
   }

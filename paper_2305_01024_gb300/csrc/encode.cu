@@ -36,6 +36,76 @@ __global__ void transpose_kernel(const float* __restrict__ A, long long lda, int
 
 // Row-padded copy X (R x C, ldx) -> Y (R x ldy), for operands whose stride
 // or base address does not meet the 16-byte rule of TMA.
+// A (M x K, row-major) -> A^T (K x ldt), fused with the A side of the
+// encoding (Eq. 1): V[b][k] = sum of the m_u rows of block b of column k
+// (m_u a power of two, 2..128; 0 = no block sums) and the partial squared
+// row norms of the 32 columns of this CTA's k-tile, part[k-tile][M].
+// CTA tile: 128 rows x 32 columns through shared memory; A is read once.
+__global__ void __launch_bounds__(256) transpose_encode_kernel(const float* __restrict__ A, long long lda, int M,
+                                                               int K, float* __restrict__ At, long long ldt,
+                                                               int m_u, float* __restrict__ V, long long ldv,
+                                                               float* __restrict__ part) {
+  __shared__ float tile[128][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 128;
+  // load: warp w takes rows w, w + 8, ...; lane = column.  All 16 loads of
+  // a thread are issued before any is used (bytes in flight hide latency).
+  float vals[16];
+  const int k = k0 + lane;
+#pragma unroll
+  for (int it = 0; it < 16; ++it) {
+    const int gi = m0 + warp + 8 * it;
+    vals[it] = (gi < M && k < K) ? A[(long long)gi * lda + k] : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < 16; ++it) {
+    const int i = warp + 8 * it, gi = m0 + i;
+    tile[i][lane] = vals[it];
+    if (part) {
+      float sq = vals[it] * vals[it];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0 && gi < M) part[(long long)blockIdx.x * M + gi] = sq;
+    }
+  }
+  __syncthreads();
+  // store: warp w writes A^T rows k0 + w, + 8, ...; lane covers rows
+  // m = lane + 32 j of A (coalesced 128-byte segments)
+  for (int kk = warp; kk < 32; kk += 8) {
+    const int k = k0 + kk;
+    if (k >= K) break;  // warp-uniform
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = tile[lane + 32 * j][kk];
+      const int m = m0 + lane + 32 * j;
+      if (m < M) At[(long long)k * ldt + m] = v[j];
+    }
+    if (V && m_u >= 2) {
+      if (m_u <= 32) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float sv = v[j];
+          for (int o = 1; o < m_u; o <<= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+          const int m = m0 + lane + 32 * j;
+          if ((lane & (m_u - 1)) == 0 && m < M) V[(long long)(m / m_u) * ldv + k] = sv;
+        }
+      } else {
+        // 64: j-pairs form a block; 128: all four
+        const int per = m_u / 32;
+        for (int jb = 0; jb < 4; jb += per) {
+          float sv = 0.f;
+          for (int j = jb; j < jb + per; ++j) sv += v[j];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+          const int m = m0 + 32 * jb;
+          if (lane == 0 && m < M) V[(long long)(m / m_u) * ldv + k] = sv;
+        }
+      }
+    }
+  }
+}
+
 __global__ void copy_pad_kernel(const float* __restrict__ X, long long ldx, int R, int Cn,
                                 float* __restrict__ Y, long long ldy) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,17 +142,26 @@ __global__ void __launch_bounds__(256) encode_kmajor_kernel(const float* __restr
   const int k1 = min(K, k0 + rows);
   const int g = n_u / 4;  // lanes per block when n_u <= 128
   float sq[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-  for (int k = k0; k < k1; ++k) {  // unrolled: several rows' loads in flight
+  // rows are fetched four at a time, all four loads issued before use
+  constexpr int AHEAD = 4;
+  float4 buf[AHEAD];
+  auto fetch = [&](int k) -> float4 {
+    if (k >= k1) return make_float4(0.f, 0.f, 0.f, 0.f);
     const float* row = X + (long long)k * ldx;
-    float v[4];
-    if (vec && c0 + 3 < L) {
-      const float4 q4 = __ldg(reinterpret_cast<const float4*>(row + c0));
-      v[0] = q4.x; v[1] = q4.y; v[2] = q4.z; v[3] = q4.w;
-    } else {
+    if (vec && c0 + 3 < L) return __ldg(reinterpret_cast<const float4*>(row + c0));
+    float t[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = (c0 + q < L) ? __ldg(row + c0 + q) : 0.f;
-    }
+    for (int q = 0; q < 4; ++q) t[q] = (c0 + q < L) ? __ldg(row + c0 + q) : 0.f;
+    return make_float4(t[0], t[1], t[2], t[3]);
+  };
+  for (int kb = k0; kb < k1; kb += AHEAD) {
+#pragma unroll
+    for (int a = 0; a < AHEAD; ++a) buf[a] = fetch(kb + a);
+#pragma unroll
+  for (int a = 0; a < AHEAD; ++a) {
+    const int k = kb + a;
+    if (k >= k1) break;  // uniform over the CTA
+    float v[4] = {buf[a].x, buf[a].y, buf[a].z, buf[a].w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) sq[q] = fmaf(v[q], v[q], sq[q]);
     if (S) {
@@ -103,6 +182,7 @@ __global__ void __launch_bounds__(256) encode_kmajor_kernel(const float* __restr
         if (lane == 0) wpart[k - k0][warp] = s;
       }
     }
+  }
   }
   if (S && n_u > 128) {
     __syncthreads();
@@ -125,13 +205,27 @@ __global__ void __launch_bounds__(256) encode_kmajor_kernel(const float* __restr
   }
 }
 
-__global__ void colnorm_finish_kernel(const float* __restrict__ part, int chunks, int L,
-                                      float* __restrict__ nrm) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= L) return;
+// nrm[j] = sqrt(sum over chunks of part[c][j]): a CTA finishes 32 columns,
+// warp w summing chunks w, w + 8, ... (lane = column), then the 8 warps'
+// sums in a fixed order.
+__global__ void __launch_bounds__(256) colnorm_finish_kernel(const float* __restrict__ part, int chunks, int L,
+                                                             float* __restrict__ nrm) {
+  __shared__ float red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int c = 0; c < chunks; ++c) s += part[(long long)c * L + j];
-  nrm[j] = sqrtf(s);
+  if (j < L) {
+#pragma unroll 4
+    for (int c = warp; c < chunks; c += 8) s += part[(long long)c * L + j];
+  }
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && j < L) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    nrm[j] = sqrtf(t);
+  }
 }
 
 // C = alpha * sum_s partial[s] + beta * C   (split-K; the sum is unprotected)
@@ -154,6 +248,22 @@ cudaError_t launch_transpose(const float* A, long long lda, int M, int K, float*
                              cudaStream_t st) {
   dim3 g((K + 31) / 32, (M + 31) / 32);
   transpose_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, M, K, At, ldt);
+  return cudaGetLastError();
+}
+
+// A^T plus, when V / nrm are given, the A-side block sums and row norms;
+// scratch: ceil(K/32) * M floats when nrm is requested.
+cudaError_t launch_transpose_encode(const float* A, long long lda, int M, int K, float* At, long long ldt, int m_u,
+                                    float* V, long long ldv, float* nrm, float* scratch, int* launches,
+                                    cudaStream_t st) {
+  if (V && (m_u < 2 || m_u > 128 || (m_u & (m_u - 1)))) return cudaErrorInvalidValue;
+  dim3 g((K + 31) / 32, (M + 127) / 128);
+  transpose_encode_kernel<<<g, 256, 0, st>>>(A, lda, M, K, At, ldt, V ? m_u : 0, V, ldv, nrm ? scratch : nullptr);
+  ++*launches;
+  if (nrm) {
+    colnorm_finish_kernel<<<(M + 31) / 32, 256, 0, st>>>(scratch, (K + 31) / 32, M, nrm);
+    ++*launches;
+  }
   return cudaGetLastError();
 }
 
@@ -182,7 +292,7 @@ cudaError_t launch_encode_kmajor(const float* X, long long ldx, int K, int L, in
   encode_kmajor_kernel<<<g, 256, 0, st>>>(X, ldx, K, L, n_u, rows, vec, S, lds, nrm ? scratch : nullptr);
   *launches += 1;
   if (nrm) {
-    colnorm_finish_kernel<<<(L + 255) / 256, 256, 0, st>>>(scratch, chunks, L, nrm);
+    colnorm_finish_kernel<<<(L + 31) / 32, 256, 0, st>>>(scratch, chunks, L, nrm);
     *launches += 1;
   }
   return cudaGetLastError();
