@@ -313,6 +313,16 @@ int ftgemm_autotune(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, con
                     ftgemm_ft_level ft_level, int32_t reps, ftgemm_schedule* out,
                     ftgemm_ft_level* level_out);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).
+ * Every mbarrier wait of the GEMM kernels gives up after about 2^31 SM
+ * cycles, counts the give-up in the handle's report and lets the kernel
+ * return, so that a lost copy or MMA completion ends in FTGEMM_ERR_TIMEOUT
+ * rather than a hung GPU.  This call launches one CTA that waits on a
+ * barrier nothing arrives on, with a limit of `limit_cycles` (1 .. 2^34),
+ * then fetches the report: it returns FTGEMM_ERR_TIMEOUT when the path
+ * works, and the handle stays usable.  Synchronises the handle's stream. */
+int ftgemm_selftest_wait(ftgemm_handle_t handle, int64_t limit_cycles);
+
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them. */
 int ftgemm_report_fetch(ftgemm_handle_t handle, ftgemm_report* report);

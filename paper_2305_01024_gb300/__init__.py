@@ -126,6 +126,7 @@ def lib():
     L.ftgemm_mlp_train.argtypes = [vp, i64, vp, vp, i32, i32, C.c_float, vp, C.POINTER(C.c_float)]
     L.ftgemm_autotune.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_int, i32,
                                   C.POINTER(Schedule), C.POINTER(C.c_int)]
+    L.ftgemm_selftest_wait.argtypes = [vp, i64]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
@@ -135,7 +136,8 @@ def lib():
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
                "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
-               "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune"):
+               "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune",
+               "ftgemm_selftest_wait"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L

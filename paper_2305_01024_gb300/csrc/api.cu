@@ -40,6 +40,7 @@ cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatc
 cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
                             int* launches, cudaStream_t st);
 cudaError_t launch_fault_bits(const Fault* f, int n, uint32_t* bits, size_t words, cudaStream_t st);
+cudaError_t launch_wait_selftest(DevReport* rep, long long limit_cycles, cudaStream_t st);
 int mlp_grad_blocks(long long nb);
 cudaError_t launch_mlp_grad(const float* X, const float* t, long long s0, int nb, const float* theta, float inv_n,
                             float* part, int nblk, cudaStream_t st);
@@ -1380,4 +1381,17 @@ int ftgemm_autotune(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const fl
   if (out) *out = best;
   if (level_out) *level_out = best_lv;
   return FTGEMM_OK;
+}
+
+int ftgemm_selftest_wait(ftgemm_handle_t h, int64_t limit_cycles) {
+  if (!h || limit_cycles <= 0 || limit_cycles > (1ll << 34))
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_selftest_wait: bad argument");
+  CK(cudaSetDevice(h->device));
+  int rc = clear_report(h);
+  if (rc) return rc;
+  CK(launch_wait_selftest(h->rep, limit_cycles, h->stream));
+  ++h->launches;
+  ftgemm_report r;
+  memset(&r, 0, sizeof(r));
+  return ftgemm_report_fetch(h, &r);  // FTGEMM_ERR_TIMEOUT when the wait gave up
 }

@@ -57,4 +57,5 @@ def test_host_side_argument_checks(libpath):
     assert L.ftgemm_group_set_faults(None, None, None) == -1
     assert L.ftgemm_group_tiles(None, None, None) == -1
     assert L.ftgemm_group_destroy(None) == 0
+    assert L.ftgemm_selftest_wait(None, 1000) == -1
     assert b"NULL" in L.ftgemm_last_error() or len(L.ftgemm_last_error()) > 0
