@@ -756,6 +756,10 @@ def main():
         else:
             false_alarms += 1
 
+    # the one exchange of the multi-GPU path: whole-job fault counters
+    from paper_2305_01024_gb300 import dist as fdist
+    tot = fdist.sum_counts({"injected": injected, "found": found, "false_alarms": false_alarms,
+                            "uncorrectable": int(rep.uncorrectable), "checksum_only": int(rep.checksum_only)})
     kern_ms = st["kernel_ms"] / max(1, st["timed_launches"])
     achieved = flops / (kern_ms / 1e3) / 1e12
     peak_spec = fp32_peak_tflops(sms, 2070.0)
@@ -898,10 +902,11 @@ def main():
         "best_ft_off_schedule": dict(SCHED_OFF_BEST),
         "torch_matmul_fp32_tflops": flops * world / (ms_torch / 1e3) / 1e12,
         "vs_torch_matmul": ms_torch / ms,
-        "faults": {"injected": injected, "corrected_at_injected_position": found,
-                   "false_alarms": false_alarms, "detect_rate": (found / injected) if injected else None,
-                   "uncorrectable": rep.uncorrectable, "checksum_only": rep.checksum_only,
-                   "poisson_per_min": FAULTS_PER_MIN, "t_kernel_s": t_est},
+        "faults": {"injected": tot["injected"], "corrected_at_injected_position": tot["found"],
+                   "false_alarms": tot["false_alarms"],
+                   "detect_rate": (tot["found"] / tot["injected"]) if tot["injected"] else None,
+                   "uncorrectable": tot["uncorrectable"], "checksum_only": tot["checksum_only"],
+                   "poisson_per_min": FAULTS_PER_MIN, "t_kernel_s": t_est, "ranks": world},
         "roofline": roofline,
         "e2e": e2e,
         "clocks": clk,
