@@ -323,6 +323,23 @@ int ftgemm_autotune(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, con
  * works, and the handle stays usable.  Synchronises the handle's stream. */
 int ftgemm_selftest_wait(ftgemm_handle_t handle, int64_t limit_cycles);
 
+/* Non-fused ABFT baseline (the comparison scheme of Section 5.3, after Ding
+ * et al.), for measurement: F32 only.  C is accumulated as a sequence of
+ * rank-K_s updates C_acc += A(:, s) B(s, :) (K_s = ks, a multiple of 16;
+ * <= 0 gives 256), each a separate GEMM launch; the checksums (e^T A) B and
+ * A (B e) of every 128 x 128 tile are updated by separate GEMM launches
+ * (Eq. 4); after each step faults scheduled inside it are applied and a
+ * separate kernel verifies every tile, locates, corrects and reports, with
+ * the threshold of ftgemm_set_threshold mode 0.  Finally C = alpha * C_acc +
+ * beta * C.  inject: tile_m / tile_n on the 128 x 128 grid, kstep in units
+ * of 16 of K (the fault lands at the end of the step holding it), as for
+ * ftgemm_gemm at BLOCK level with cadence K_s / 16.  Uses a second handle
+ * workspace (allocated on first use).  Errors as ftgemm_gemm. */
+int ftgemm_gemm_nonfused(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, double alpha,
+                         const float* A, int64_t lda, const float* B, int64_t ldb, double beta,
+                         float* C, int64_t ldc, int32_t ks, const ftgemm_inject_spec* inject,
+                         ftgemm_report* report);
+
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them. */
 int ftgemm_report_fetch(ftgemm_handle_t handle, ftgemm_report* report);

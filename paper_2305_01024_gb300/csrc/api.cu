@@ -41,6 +41,14 @@ cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsign
                             int* launches, cudaStream_t st);
 cudaError_t launch_fault_bits(const Fault* f, int n, uint32_t* bits, size_t words, cudaStream_t st);
 cudaError_t launch_wait_selftest(DevReport* rep, long long limit_cycles, cudaStream_t st);
+cudaError_t launch_nonfused_inject(const Fault* f, int nf, int ks_lo, int ks_hi, int tiles_n, float* acc,
+                                   long long ldacc, float* Cc, long long ldcc, float* CrT, long long ldcr,
+                                   cudaStream_t st);
+cudaError_t launch_nonfused_verify(float* acc, long long ldacc, int M, int N, float* Cc, long long ldcc,
+                                   float* CrT, long long ldcr, const float* nA, const float* nB, float lam_u,
+                                   int kstep, DevReport* rep, ftgemm_fault_record* recs, cudaStream_t st);
+cudaError_t launch_nonfused_epilogue(const float* acc, long long ldacc, int M, int N, float alpha, float beta,
+                                     float* C, long long ldc, cudaStream_t st);
 int mlp_grad_blocks(long long nb);
 cudaError_t launch_mlp_grad(const float* X, const float* t, long long s0, int nb, const float* theta, float inv_n,
                             float* part, int nblk, cudaStream_t st);
@@ -117,6 +125,9 @@ struct ftgemm_ctx {
   size_t mlp_ws_floats = 0;
   // autotuned SIMT schedules: (m, n, k, requested level) -> (schedule, level to run)
   std::map<std::tuple<int64_t, int64_t, int64_t, int>, std::pair<ftgemm_schedule, int>> tuned;
+  // second workspace (non-fused baseline: its buffers live across the GEMM calls it makes)
+  float* ws2 = nullptr;
+  size_t ws2_floats = 0;
   // residual sink (tensor-core path)
   float* sink_lam = nullptr;
   float* sink_x = nullptr;
@@ -231,7 +242,8 @@ static void choose_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
 
 static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
                      const float* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_ft_level level,
-                     const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report);
+                     const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report,
+                     const float* At_given = nullptr, int64_t ldat = 0);
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -881,6 +893,7 @@ int ftgemm_destroy(ftgemm_handle_t h) {
   if (h->faults_free) cudaEventDestroy(h->faults_free);
   if (h->qscratch) cudaFree(h->qscratch);
   if (h->d_fbits) cudaFree(h->d_fbits);
+  if (h->ws2) cudaFree(h->ws2);
   if (h->mlp_theta) cudaFree(h->mlp_theta);
   if (h->mlp_ws) cudaFree(h->mlp_ws);
   for (auto& e : h->pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -1153,9 +1166,13 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
 }  // extern "C"
 
 // The SIMT path of ftgemm_gemm with an explicit schedule and level.
+// At_given (OFF only): A already k-major (K x M, row stride ldat, 16-byte
+// aligned rows); the transpose pass is skipped.
 static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
                      const float* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_ft_level level,
-                     const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report) {
+                     const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report,
+                     const float* At_given, int64_t ldat) {
+  if (At_given && level != FTGEMM_FT_OFF) FAIL(FTGEMM_ERR_ARG, "internal: k-major A needs level OFF");
   const SimtConfig* cfg = find_simt(s);
   if (!cfg) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: schedule is not a compiled kernel");
 
@@ -1191,12 +1208,12 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   if (level == FTGEMM_FT_BLOCK) { m_u = s.m_tb; n_u = s.n_tb; need_vw = true; }
   const int NV = level == FTGEMM_FT_WARP ? s.m_tb / s.m_w : 1;
   const int NW = level == FTGEMM_FT_WARP ? s.n_tb / s.n_w : 1;
-  const long long ldt = (M + 3) / 4 * 4;  // A^T row stride (16-byte multiple)
+  const long long ldt = At_given ? ldat : (M + 3) / 4 * 4;  // A^T row stride (16-byte multiple)
   const long long ldv = (K + 3) / 4 * 4;  // encoded-vector row stride
   const bool b_ok = (ldb % 4 == 0) && al16(B);
   const long long ldbp = b_ok ? ldb : (N + 3) / 4 * 4;
   const int nvb = (M + m_u - 1) / m_u, nwb = (N + n_u - 1) / n_u;
-  const size_t nAt = (size_t)K * ldt;
+  const size_t nAt = At_given ? 0 : (size_t)K * ldt;
   const size_t nBp = b_ok ? 0 : (size_t)K * ldbp;
   const size_t nV = need_vw ? (size_t)nvb * ldv : 0;
   const size_t nW = need_vw ? (size_t)nwb * ldv : 0;
@@ -1215,8 +1232,10 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   float* ws = h->ws;
   int launches = 0;
   // A^T, with the A side of the encoding (block sums, row norms) in the same pass
-  CK(launch_transpose_encode(Af, lda, M, K, ws + oAt, ldt, m_u, need_vw ? ws + oV : nullptr, ldv,
-                             abft ? ws + oNa : nullptr, ws + oScr, &launches, h->stream));
+  const float* At = At_given ? At_given : ws + oAt;
+  if (!At_given)
+    CK(launch_transpose_encode(Af, lda, M, K, ws + oAt, ldt, m_u, need_vw ? ws + oV : nullptr, ldv,
+                               abft ? ws + oNa : nullptr, ws + oScr, &launches, h->stream));
   const float* Bk = Bf;
   if (!b_ok) {
     CK(launch_copy_pad(Bf, ldb, K, N, ws + oBp, ldbp, h->stream));
@@ -1230,7 +1249,7 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
 
   SimtMaps maps;
   {
-    int rc = make_map_2d(&maps.A, ws + oAt, M, K, ldt, s.m_tb, s.k_tb);
+    int rc = make_map_2d(&maps.A, At, M, K, ldt, s.m_tb, s.k_tb);
     if (!rc) rc = make_map_2d(&maps.B, Bk, N, K, ldbp, s.n_tb, s.k_tb);
     if (!rc && need_vw) rc = make_map_2d(&maps.V, ws + oV, K, nvb, ldv, s.k_tb, NV);
     if (!rc && need_vw) rc = make_map_2d(&maps.W, ws + oW, K, nwb, ldv, s.k_tb, NW);
@@ -1394,4 +1413,93 @@ int ftgemm_selftest_wait(ftgemm_handle_t h, int64_t limit_cycles) {
   ftgemm_report r;
   memset(&r, 0, sizeof(r));
   return ftgemm_report_fetch(h, &r);  // FTGEMM_ERR_TIMEOUT when the wait gave up
+}
+
+// ---- non-fused ABFT baseline (Section 5.3's comparison scheme) --------------
+
+int ftgemm_gemm_nonfused(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha, const float* A,
+                         int64_t lda, const float* B, int64_t ldb, double beta, float* C, int64_t ldc, int32_t ks,
+                         const ftgemm_inject_spec* inject, ftgemm_report* report) {
+  if (!h || !A || !B || !C || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n || ldc < n)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_nonfused: bad argument");
+  if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_nonfused: size too large");
+  if (ks <= 0) ks = 256;
+  if (ks % 16) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_nonfused: the step K_s must be a multiple of 16");
+  CK(cudaSetDevice(h->device));
+  const int M = (int)m, N = (int)n, K = (int)k, T = 128;
+  const int tiles_m = (M + T - 1) / T, tiles_n = (N + T - 1) / T, ksteps = (K + 15) / 16;
+  const ftgemm_schedule unit{T, T, 16, 64, 64, 16, 8, ks / 16, 1};  // the tiling faults refer to
+  int nf = 0;
+  {
+    int rc = upload_faults(h, inject, unit, M, N, ksteps, tiles_m, tiles_n, FTGEMM_FT_BLOCK, &nf);
+    if (rc) return rc;
+  }
+  if (report) {
+    int rc = clear_report(h);
+    if (rc) return rc;
+  }
+  // workspace (its own buffer: the GEMM calls below use the handle's)
+  auto r4 = [](long long x) { return (x + 3) / 4 * 4; };
+  const long long ldt = r4(M), ldv = r4(K), ldvt = r4(tiles_m), ldwt = r4(tiles_n), ldacc = r4(N);
+  size_t o = 0;
+  auto take = [&](size_t floats) { const size_t at = o; o = align64(o + floats); return at; };
+  const size_t oAt = take((size_t)K * ldt), oV = take((size_t)tiles_m * ldv), oW = take((size_t)tiles_n * ldv),
+               oVt = take((size_t)K * ldvt), oWt = take((size_t)K * ldwt), oNa = take(M), oNb = take(N),
+               oScr = take((size_t)std::max<long long>((long long)((K + 31) / 32) * M, kmajor_scratch_floats(K, N))),
+               oAcc = take((size_t)M * ldacc), oCc = take((size_t)tiles_m * ldacc), oCr = take((size_t)tiles_n * ldt);
+  if (o > h->ws2_floats) {
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->ws2) CK(cudaFree(h->ws2));
+    h->ws2 = nullptr;
+    h->ws2_floats = 0;
+    CK(cudaMalloc(&h->ws2, o * sizeof(float)));
+    h->ws2_floats = o;
+  }
+  float* w = h->ws2;
+  float *At = w + oAt, *V = w + oV, *W = w + oW, *Vt = w + oVt, *Wt = w + oWt, *nA = w + oNa, *nB = w + oNb,
+        *Acc = w + oAcc, *Cc = w + oCc, *CrT = w + oCr;
+  int launches = 0;
+  // encode (Eq. 1-2): A^T with e^T A per 128-row block and row norms; B e per
+  // 128-column block and column norms; the checksum vectors k-major
+  CK(launch_transpose_encode(A, lda, M, K, At, ldt, T, V, ldv, nA, w + oScr, &launches, h->stream));
+  CK(launch_encode_kmajor(B, ldb, K, N, T, W, ldv, nB, w + oScr, &launches, h->stream));
+  CK(launch_transpose(V, ldv, tiles_m, K, Vt, ldvt, h->stream));
+  CK(launch_transpose(W, ldv, tiles_n, K, Wt, ldwt, h->stream));
+  launches += 2;
+  const float lam_u = (float)(h->lambda * std::ldexp(1.0, -24));
+  const bool timing = h->timing;
+  h->timing = false;
+  int rc = FTGEMM_OK;
+  for (int k0 = 0; k0 < K && !rc; k0 += ks) {
+    const int kl = std::min(ks, K - k0);
+    const double b0 = k0 == 0 ? 0.0 : 1.0;
+    ftgemm_schedule sa, sb, sc;
+    default_schedule(h, M, N, kl, FTGEMM_FT_OFF, &sa);
+    default_schedule(h, tiles_m, N, kl, FTGEMM_FT_OFF, &sb);
+    default_schedule(h, tiles_n, M, kl, FTGEMM_FT_OFF, &sc);
+    // the step's product and the updates of the two checksums (Eq. 4)
+    rc = simt_gemm(h, M, N, kl, 1.0, nullptr, 0, B + (long long)k0 * ldb, ldb, b0, Acc, ldacc, FTGEMM_FT_OFF, sa,
+                   nullptr, nullptr, At + (long long)k0 * ldt, ldt);
+    if (!rc)
+      rc = simt_gemm(h, tiles_m, N, kl, 1.0, nullptr, 0, B + (long long)k0 * ldb, ldb, b0, Cc, ldacc, FTGEMM_FT_OFF,
+                     sb, nullptr, nullptr, Vt + (long long)k0 * ldvt, ldvt);
+    if (!rc)
+      rc = simt_gemm(h, tiles_n, M, kl, 1.0, nullptr, 0, At + (long long)k0 * ldt, ldt, b0, CrT, ldt, FTGEMM_FT_OFF,
+                     sc, nullptr, nullptr, Wt + (long long)k0 * ldwt, ldwt);
+    if (rc) break;
+    // faults scheduled inside this step, then the verification after it
+    const int ks_lo = k0 / 16, ks_hi = (k0 + kl + 15) / 16;
+    CK(launch_nonfused_inject(nf > 0 ? h->d_faults : nullptr, nf, ks_lo, ks_hi, tiles_n, Acc, ldacc, Cc, ldacc, CrT,
+                              ldt, h->stream));
+    CK(launch_nonfused_verify(Acc, ldacc, M, N, Cc, ldacc, CrT, ldt, nA, nB, lam_u, ks_hi - 1, h->rep, h->recs,
+                              h->stream));
+    launches += (nf > 0 ? 1 : 0) + 1;
+  }
+  h->timing = timing;
+  if (rc) return rc;
+  CK(launch_nonfused_epilogue(Acc, ldacc, M, N, (float)alpha, (float)beta, C, ldc, h->stream));
+  ++launches;
+  h->launches += launches;
+  if (report) return ftgemm_report_fetch(h, report);
+  return FTGEMM_OK;
 }
