@@ -663,6 +663,58 @@ def nonfused_extras(ft, h, synth, dev, timed_loop):
     return out
 
 
+def offline_extras(ft, h, synth, dev, timed_loop):
+    """Online vs offline ABFT (Section 5.5) at a per-tile error rate gamma0 =
+    1/256: every attempt draws a fault in each tile with probability gamma0;
+    offline detects and recomputes until an attempt is clean, online corrects
+    in one pass.  Reports mean attempts and the cost of offline in units of
+    online, beside the paper's model (1 - gamma) / (1 - 2 gamma)."""
+    import torch
+    gamma0, trials, max_runs = 1.0 / 256, 24, 32
+    out = {"gamma0": gamma0, "trials": trials}
+    for n in (512, 1024, 1536):
+        tiles_1d = -(-n // 128)
+        tiles = tiles_1d * tiles_1d
+        gamma = 1 - (1 - gamma0) ** tiles
+        A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 40), dev)
+        B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 41), dev)
+        Cm = torch.empty(n, n, device=dev)
+        delta = 64 * 4 * math.sqrt(n / 9)
+
+        def draw(trial, attempt):
+            u = synth.unit(synth.config_seed(2, 100000 + 1000 * n + 64 * trial + attempt), 4 * tiles)
+            fl = []
+            for t in range(tiles):
+                if u[t] < gamma0:
+                    fl.append((t // tiles_1d, t % tiles_1d, int(u[tiles + t] * (n // 16)),
+                               int(u[2 * tiles + t] * 128), int(u[3 * tiles + t] * 128), delta))
+            return fl
+
+        plans = [[draw(tr, a) for a in range(max_runs)] for tr in range(trials)]
+        h.set_schedule(None)
+        attempts = []
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for tr in range(trials):
+            st, runs, _ = h.gemm_offline(A, B, Cm, injects=plans[tr], max_runs=max_runs)
+            attempts.append(runs if st == ft.OK else max_runs)
+        torch.cuda.synchronize()
+        t_off = time.time() - t0
+        h.set_schedule(SCHED)
+        t0 = time.time()
+        for tr in range(trials):
+            h.gemm(A, B, Cm, level=ft.FT_BLOCK, inject=plans[tr][0] or None, report=False)
+        torch.cuda.synchronize()
+        t_on = time.time() - t0
+        h.report_fetch(capacity=1 << 14)
+        model = (1 - gamma) / (1 - 2 * gamma) if gamma < 0.5 else None
+        out[str(n)] = {"tiles": tiles, "gamma": round(gamma, 4), "mean_attempts": sum(attempts) / trials,
+                       "geometric_expectation": round(1 / (1 - gamma), 4), "paper_model": model,
+                       "offline_cost_vs_online": round(t_off / t_on, 3)}
+        del A, B, Cm
+    return out
+
+
 def irregular_extras(ft, h, synth, dev, timed_loop):
     """Config 3: irregular fp32 shapes, N(0,1), schedule and checksum level
     picked per shape by the autotuner, one seeded fault per GEMM."""
@@ -873,7 +925,7 @@ def main():
     if not args.no_extras and rank == 0:
         for name, fn in (("tensor_core", tensor_core_extras), ("grouped", grouped_extras),
                          ("learned_threshold", learned_extras), ("nonfused", nonfused_extras),
-                         ("irregular", irregular_extras)):
+                         ("offline", offline_extras), ("irregular", irregular_extras)):
             try:
                 side[name] = fn(ft, h, synth, dev, timed_loop)
             except Exception as exc:  # reported, not hidden: the headline line still prints

@@ -43,6 +43,7 @@ extern "C" {
 #define FTGEMM_ERR_ALIGN (-3)       /* pointer or stride alignment for TMA   */
 #define FTGEMM_ERR_CUDA (-4)        /* a CUDA runtime call failed            */
 #define FTGEMM_ERR_TIMEOUT (-5)     /* a bounded device wait gave up         */
+#define FTGEMM_ERR_UNRECOVERED (-6) /* offline ABFT: every attempt was hit   */
 
 typedef struct ftgemm_ctx* ftgemm_handle_t;
 
@@ -339,6 +340,23 @@ int ftgemm_gemm_nonfused(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k
                          const float* A, int64_t lda, const float* B, int64_t ldb, double beta,
                          float* C, int64_t ldc, int32_t ks, const ftgemm_inject_spec* inject,
                          ftgemm_report* report);
+
+/* Offline ABFT (Section 5.5): detect-only verification with recompute.
+ * F32.  Attempt r computes C = alpha * A * B + beta * C_in with the
+ * block-level checksums of the 128 x 128 x 16 tile verified once, after the
+ * last k-step, and the faults of injects[r] (NULL entry or injects NULL: no
+ * faults; positions as for ftgemm_gemm on that tiling); if anything is
+ * detected the attempt is discarded and the next one starts from C_in.
+ * *runs_out (may be NULL) receives the attempts made.  Returns
+ * FTGEMM_ERR_UNRECOVERED when all max_runs attempts were hit (C then holds
+ * the last attempt).  report (may be NULL): the events of all attempts.
+ * The online scheme (ftgemm_gemm) corrects in place instead; the paper's
+ * expected attempt count under a per-tile error rate gamma0 is
+ * (1 - gamma) / (1 - 2 gamma), gamma = 1 - (1 - gamma0)^tiles. */
+int ftgemm_gemm_offline(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, double alpha,
+                        const float* A, int64_t lda, const float* B, int64_t ldb, double beta,
+                        float* C, int64_t ldc, const ftgemm_inject_spec* const* injects,
+                        int32_t max_runs, int32_t* runs_out, ftgemm_report* report);
 
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them. */

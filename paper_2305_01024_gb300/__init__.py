@@ -22,7 +22,7 @@ FT_OFF, FT_THREAD, FT_WARP, FT_BLOCK, FT_TILE, FT_AUTO = 0, 1, 2, 3, 4, 5
 LEVELS = {"off": FT_OFF, "thread": FT_THREAD, "warp": FT_WARP, "block": FT_BLOCK, "tile": FT_TILE,
           "auto": FT_AUTO}
 CORRECTED, UNCORRECTABLE, CHECKSUM_ONLY = 0, 1, 2
-OK, ERR_ARG, ERR_UNSUPPORTED, ERR_ALIGN, ERR_CUDA, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+OK, ERR_ARG, ERR_UNSUPPORTED, ERR_ALIGN, ERR_CUDA, ERR_TIMEOUT, ERR_UNRECOVERED = 0, -1, -2, -3, -4, -5, -6
 
 
 class FtgemmError(RuntimeError):
@@ -127,6 +127,10 @@ def lib():
     L.ftgemm_autotune.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_int, i32,
                                   C.POINTER(Schedule), C.POINTER(C.c_int)]
     L.ftgemm_selftest_wait.argtypes = [vp, i64]
+    L.ftgemm_gemm_offline.argtypes = [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64,
+                                      C.POINTER(C.POINTER(InjectSpec)), i32, C.POINTER(i32), C.POINTER(Report)]
+    L.ftgemm_gemm_nonfused.argtypes = [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32,
+                                       C.POINTER(InjectSpec), C.POINTER(Report)]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
@@ -137,7 +141,7 @@ def lib():
                "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
                "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune",
-               "ftgemm_selftest_wait"):
+               "ftgemm_selftest_wait", "ftgemm_gemm_offline", "ftgemm_gemm_nonfused"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -276,6 +280,28 @@ class Handle:
                                      _ptr(C_out), C_out.stride(0), level, int(reps), C.byref(s),
                                      C.byref(lv)))
         return s, lv.value
+
+    def gemm_offline(self, A, B, C_out, alpha=1.0, beta=0.0, injects=None, max_runs: int = 8,
+                     capacity: int = 4096):
+        """Offline (detect-only) ABFT: attempts until one is fault-free.
+        injects: one fault list per attempt (or None).  Returns (status,
+        attempts, PyReport); status is OK or ERR_UNRECOVERED."""
+        M, K = A.shape
+        N = B.shape[1]
+        specs = [make_inject(f) if f else None for f in (injects or [])]
+        specs += [None] * (max_runs - len(specs))
+        arr = (C.POINTER(InjectSpec) * max_runs)(*[C.pointer(sp) if sp else C.POINTER(InjectSpec)()
+                                                   for sp in specs[:max_runs]])
+        runs = C.c_int32(0)
+        recs = (FaultRecord * capacity)()
+        rep = Report(capacity=capacity, records=recs)
+        st = lib().ftgemm_gemm_offline(self._h, M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B),
+                                       B.stride(0), float(beta), _ptr(C_out), C_out.stride(0), arr, max_runs,
+                                       C.byref(runs), C.byref(rep))
+        if st not in (OK, ERR_UNRECOVERED):
+            _check(st)
+        return st, runs.value, PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
+                                        rep.n_records, bool(rep.overflow), _records(rep, capacity))
 
     def set_residual_sink(self, lam_needed=None, features=None):
         """Route every later TILE-level tensor-core call's per-tile residual

@@ -849,6 +849,7 @@ const char* ftgemm_status_string(int status) {
     case FTGEMM_ERR_ALIGN: return "misaligned pointer or stride";
     case FTGEMM_ERR_CUDA: return "CUDA error";
     case FTGEMM_ERR_TIMEOUT: return "device wait timed out";
+    case FTGEMM_ERR_UNRECOVERED: return "every offline attempt detected a fault";
     default: return "unknown status";
   }
 }
@@ -1502,4 +1503,62 @@ int ftgemm_gemm_nonfused(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, dou
   h->launches += launches;
   if (report) return ftgemm_report_fetch(h, report);
   return FTGEMM_OK;
+}
+
+// ---- offline (detect-only, recompute) ABFT (Section 5.5) --------------------
+
+int ftgemm_gemm_offline(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha, const float* A,
+                        int64_t lda, const float* B, int64_t ldb, double beta, float* C, int64_t ldc,
+                        const ftgemm_inject_spec* const* injects, int32_t max_runs, int32_t* runs_out,
+                        ftgemm_report* report) {
+  if (runs_out) *runs_out = 0;
+  if (!h || !A || !B || !C || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n || ldc < n || max_runs <= 0)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_offline: bad argument");
+  if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_offline: size too large");
+  CK(cudaSetDevice(h->device));
+  // detector: block-level checksums of the 128 x 128 x 16 tile, one
+  // verification after the last k-step (cadence 0)
+  const ftgemm_schedule det{128, 128, 16, 64, 64, 16, 8, 0, 1};
+  // C_in is kept for the recomputation when beta reads it
+  float* cin = nullptr;
+  const size_t cin_floats = (size_t)m * (size_t)n;
+  if (beta != 0.0) {
+    if (cin_floats > h->ws2_floats) {
+      CK(cudaStreamSynchronize(h->stream));
+      if (h->ws2) CK(cudaFree(h->ws2));
+      h->ws2 = nullptr;
+      h->ws2_floats = 0;
+      CK(cudaMalloc(&h->ws2, cin_floats * sizeof(float)));
+      h->ws2_floats = cin_floats;
+    }
+    cin = h->ws2;
+    CK(cudaMemcpy2DAsync(cin, n * sizeof(float), C, ldc * sizeof(float), n * sizeof(float), m,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  }
+  int rc = clear_report(h);
+  if (rc) return rc;
+  unsigned long long before = 0;
+  for (int r = 0; r < max_runs; ++r) {
+    if (cin && r > 0)
+      CK(cudaMemcpy2DAsync(C, ldc * sizeof(float), cin, n * sizeof(float), n * sizeof(float), m,
+                           cudaMemcpyDeviceToDevice, h->stream));
+    rc = simt_gemm(h, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, FTGEMM_FT_BLOCK, det,
+                   injects ? injects[r] : nullptr, nullptr);
+    if (rc) return rc;
+    // the detection count so far (the report accumulates over attempts)
+    unsigned long long det_now = 0;
+    CK(cudaMemcpyAsync(&det_now, &h->rep->detected, sizeof(det_now), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (runs_out) *runs_out = r + 1;
+    if (det_now == before) {
+      if (report) return ftgemm_report_fetch(h, report);
+      return FTGEMM_OK;
+    }
+    before = det_now;
+  }
+  if (report) {
+    rc = ftgemm_report_fetch(h, report);
+    if (rc) return rc;
+  }
+  FAIL(FTGEMM_ERR_UNRECOVERED, "ftgemm_gemm_offline: all %d attempts detected a fault", max_runs);
 }
