@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(192, 1)
       // load latency hides behind the tile's main loop.
       const int pM = P.M, pN = P.N;
       const float sc = P.alpha * P.acc_scale;  // fp8: product of the per-tensor scales
+      const bool unit_sc = sc == 1.f;           // skip the scaling multiplies
       const float beta = P.beta;
       const int c_vec = P.c_vec;
       const long long ldc = P.ldc;
@@ -329,7 +330,8 @@ __global__ void __launch_bounds__(192, 1)
           float* dst = crow_ptr + c;
           // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
           if (c_vec && c + 3 < DN && gc + 3 < pN) {
-            float4 o = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
+            float4 o = unit_sc ? make_float4(v[q], v[q + 1], v[q + 2], v[q + 3])
+                               : make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
             if (beta != 0.f) {
               const float4 ci = *reinterpret_cast<const float4*>(dst);
               o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
@@ -413,21 +415,38 @@ __global__ void __launch_bounds__(192, 1)
           float v[16];
           tmem_ld16(tl + ch * 16, v);
           tmem_wait_ld();
-          // row sum over the data columns (two-term fp32 summation); the row
-          // checksum pieces sit in columns DN..DN+NPIECE-1
+          // row sum over the data columns: a pairwise tree over the chunk,
+          // then a compensated (two-term) add of the chunk's sum; the row
+          // checksum pieces sit in columns DN..DN+NPIECE-1 of the last chunk
+          constexpr int FULL = DN / 16, REM = DN % 16;
+          static_assert(REM + Cfg::NPIECE <= 16, "pieces inside the last chunk");
+          float part;
+          if (ch < FULL) {
+            float t[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int c = ch * 16 + q;
-            if (c < DN) {
-              const float y = v[q] - rc;
-              const float tt = rs + y;
-              rc = (tt - rs) - y;
-              rs = tt;
-            } else if (c - DN < Cfg::NPIECE) {
+            for (int q = 0; q < 16; ++q) t[q] = v[q];
 #pragma unroll
-              for (int pc = 0; pc < Cfg::NPIECE; ++pc)
-                if (c - DN == pc) crow = fmaf(v[q], wsc[pc], crow);
-            }
+            for (int st = 8; st > 0; st >>= 1)
+#pragma unroll
+              for (int q = 0; q < st; ++q) t[q] += t[q + st];
+            part = t[0];
+          } else {
+            float t[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) t[q] = q < REM ? v[q] : 0.f;
+#pragma unroll
+            for (int st = 8; st > 0; st >>= 1)
+#pragma unroll
+              for (int q = 0; q < st; ++q) t[q] += t[q + st];
+            part = t[0];
+#pragma unroll
+            for (int pc = 0; pc < Cfg::NPIECE; ++pc) crow = fmaf(v[REM + pc], wsc[pc], crow);
+          }
+          {
+            const float y = part - rc;
+            const float tt = rs + y;
+            rc = (tt - rs) - y;
+            rs = tt;
           }
           // the column checksum pieces sit in lanes DM..DM+NPIECE-1
           if (r >= DM && r - DM < Cfg::NPIECE) {
