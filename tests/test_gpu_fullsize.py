@@ -1,0 +1,143 @@
+"""Parity at the workloads' full sizes, in the launch configurations bench.py
+times, on outputs the oracle computes one by one: sampled rows of C (every
+row holding a fault among them), and every fault located and corrected.
+
+* config 2: 16384^3 fp32, block-level checksums on the 128 x 128 x 16 tile
+  (16 x 8 fragments), verification every 256 of K, alpha 1, beta 0.5;
+* config 4: 16384^3 bf16, tile-level checksums through the tensor cores;
+* config 5: the 512-problem bf16 group, one persistent launch, 1% of tiles
+  faulted; sampled problems compared in full.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ft():
+    import torch
+    import paper_2305_01024_gb300 as ft
+    assert torch.cuda.is_available()
+    ft.lib()
+    return ft
+
+
+def _rows(seed, M, extra):
+    return sorted(set(int(u * M) for u in synth.unit(seed, 12)) | set(extra))
+
+
+def test_config2_full_size_sampled_rows(ft, orc):
+    import torch
+    n = 16384
+    sched = dict(m_tb=128, n_tb=128, k_tb=16, m_w=64, n_w=64, m_t=16, n_t=8, cadence=16, split_k=1)
+    A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 0), "cuda")
+    B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 1), "cuda")
+    C0 = synth.torch_make("uniform", (n, n), synth.config_seed(2, 2), "cuda")
+    tiles, ksteps = n // 128, n // 16
+    pos = synth.fault_positions(synth.config_seed(2, 70), 6, tiles, tiles, ksteps, 128, 128, n, n, 16)
+    mags = synth.log_uniform(synth.config_seed(2, 71), 6, 1e-1, 1e3)
+    faults = [(tm, tn, ks, r, c, float(g * 4 * math.sqrt(n / 9))) for (tm, tn, ks, r, c), g in zip(pos, mags)]
+    h = ft.Handle(0)
+    h.set_schedule(sched)
+    C = C0.clone()
+    rep = h.gemm(A, B, C, alpha=1.0, beta=0.5, level=ft.FT_BLOCK, inject=faults)
+    torch.cuda.synchronize()
+    where = [(tm * 128 + r, tn * 128 + c) for (tm, tn, ks, r, c, d) in faults]
+    assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
+    rows = _rows(synth.config_seed(2, 72), n, [i for i, _ in where])
+    Ar, Bh, Cr = A[rows].cpu().numpy(), B.cpu().numpy(), C0[rows].cpu().numpy()
+    ref = orc.gemm_ref(Ar, Bh, 1.0, 0.5, Cr)
+    got = C[rows].cpu().numpy().astype(np.float64)
+    bound = 2 * n * U32 * (np.abs(Ar.astype(np.float64)) @ np.abs(Bh.astype(np.float64)) + 0.5 * np.abs(Cr))
+    slack = np.zeros_like(got)
+    for x in rep.records:
+        slack[rows.index(x["row"]), x["col"]] = x["tau"]
+    assert np.all(np.abs(got - ref) <= bound + slack)
+    h.close()
+
+
+def test_config4_full_size_bf16_sampled_rows(ft, orc):
+    import torch
+    n = 16384
+    Af = synth.torch_make("normal", (n, n), synth.config_seed(4, 0), "cuda")
+    Bf = synth.torch_make("normal", (n, n), synth.config_seed(4, 1), "cuda")
+    A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
+    del Af, Bf
+    tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 64
+    pos = synth.fault_positions(synth.config_seed(4, 80), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    faults = [(a, b, ks, r, c, float(64 * math.sqrt(n))) for (a, b, ks, r, c) in pos]
+    h = ft.Handle(0)
+    C = torch.empty(n, n, device="cuda")
+    rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=ft.BF16, inject=faults)
+    torch.cuda.synchronize()
+    where = [(a * 120 + r, b * 248 + c) for (a, b, ks, r, c, d) in faults]
+    assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
+    rows = _rows(synth.config_seed(4, 81), n, [i for i, _ in where])
+    Ar = A[rows].float().cpu().numpy()
+    Bh = B.float().cpu().numpy()
+    ref = orc.gemm_ref(Ar, Bh)
+    got = C[rows].cpu().numpy().astype(np.float64)
+    bound = 2 * n * U32 * (np.abs(Ar.astype(np.float64)) @ np.abs(Bh.astype(np.float64)))
+    slack = np.zeros_like(got)
+    for x in rep.records:
+        slack[rows.index(x["row"]), x["col"]] = x["tau"]
+    assert np.all(np.abs(got - ref) <= bound + slack)
+    h.close()
+
+
+def test_config5_full_group_sampled_problems(ft, orc):
+    import torch
+    nprob = 512
+    u = synth.unit(synth.config_seed(5, 0), 3 * nprob)
+    shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253), 64 + 16 * int(u[3 * q + 2] * 125))
+              for q in range(nprob)]
+    probs = []
+    for q, (M, N, K) in enumerate(shapes):
+        A = synth.torch_make("normal", (M, K), synth.config_seed(5, 100 + 2 * q), "cuda").to(torch.bfloat16)
+        B = synth.torch_make("normal", (K, N), synth.config_seed(5, 101 + 2 * q), "cuda").to(torch.bfloat16)
+        probs.append((A, B, torch.empty(M, N, device="cuda")))
+    h = ft.Handle(0)
+    g = ft.Group(h, probs, dtype=ft.BF16, level=ft.FT_TILE)
+    tm, tn = g.tiles()
+    tiles = sum(a * b for a, b in zip(tm, tn))
+    nf = tiles // 100
+    pick = synth.unit(synth.config_seed(5, 7), nf)
+    by_prob = {}
+    for f in range(nf):
+        q = int(pick[f] * nprob)
+        by_prob[q] = by_prob.get(q, 0) + 1
+    faults = []
+    for q, cnt in sorted(by_prob.items()):
+        M, N, K = shapes[q]
+        cnt = min(cnt, tm[q] * tn[q])
+        for (a, b, ks, r, c) in synth.fault_positions(synth.config_seed(5, 1000 + q), cnt, tm[q], tn[q],
+                                                      -(-K // 64), 120, 248, M, N, -(-K // 64)):
+            faults.append((q, a, b, ks, r, c, float(64 * math.sqrt(K))))
+    g.set_faults(faults)
+    g.run()
+    torch.cuda.synchronize()
+    rep = h.report_fetch(capacity=1 << 15)
+    want = sorted((f[0], f[1] * 120 + f[4], f[2] * 248 + f[5], 0) for f in faults)
+    assert sorted((x["problem"], x["row"], x["col"], x["kind"]) for x in rep.records) == want
+    # sampled problems in full, and every faulted problem among them
+    sample = sorted(set(int(x * nprob) for x in synth.unit(synth.config_seed(5, 8), 6)) | {faults[0][0]})
+    for q in sample:
+        A, B, Cq = probs[q]
+        Ah, Bh = A.float().cpu().numpy(), B.float().cpu().numpy()
+        ref = orc.gemm_ref(Ah, Bh)
+        got = Cq.cpu().numpy().astype(np.float64)
+        K = Ah.shape[1]
+        bound = 2 * K * U32 * (np.abs(Ah.astype(np.float64)) @ np.abs(Bh.astype(np.float64)))
+        slack = np.zeros_like(got)
+        for x in rep.records:
+            if x["problem"] == q:
+                slack[x["row"], x["col"]] = x["tau"]
+        assert np.all(np.abs(got - ref) <= bound + slack)
+    g.close()
+    h.close()
