@@ -33,6 +33,7 @@ cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*,
 cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, float*, long long,
                                  cudaStream_t);
 void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]);
+int tc_nb_parts(int dt, long long K);
 cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
                            cudaStream_t st);
 cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
@@ -421,7 +422,7 @@ static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
     P.nA = take(P.M);
     P.nB = take(P.N);
     P.nA_part = take((size_t)((K + 255) / 256) * P.M);
-    P.nB_part = take((size_t)((K + (dt == 0 ? 63 : 127)) / (dt == 0 ? 64 : 128)) * P.N);
+    P.nB_part = take((size_t)tc_nb_parts(dt, K) * P.N);
     P.froA = take(tm);
     P.froB = take(tn);
     P.coA = take(tm);

@@ -83,6 +83,35 @@ __device__ __forceinline__ void ld8(const void* base, long long ld, long long ro
   }
 }
 
+// Raw codes of eight consecutive elements (one 16-byte load for bf16, one
+// 8-byte load for e4m3, in .x/.y); the caller guarantees alignment and
+// bounds.  Kept apart from the conversion so that a thread can issue several
+// loads before it consumes any.
+template <int DT>
+__device__ __forceinline__ uint4 ldraw8(const void* base, long long ld, long long row, int c0) {
+  if constexpr (DT == 0) {
+    return __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const uint16_t*>(base) + row * ld + c0));
+  } else {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint8_t*>(base) + row * ld + c0));
+    return make_uint4(q.x, q.y, 0u, 0u);
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void cvt8(const uint4 q, float* v) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if constexpr (DT == 0) {
+      v[i] = __uint_as_float(i & 1 ? w[i >> 1] & 0xFFFF0000u : w[i >> 1] << 16);  // exact
+    } else {
+      __nv_fp8_e4m3 e;
+      e.__x = (__nv_fp8_storage_t)((w[i >> 2] >> (8 * (i & 3))) & 0xFF);
+      v[i] = float(e);
+    }
+  }
+}
+
 // A: block sums over TC_DM-row blocks (-> Vf) and squared row-norm partials
 // over 256-wide k-chunks (-> nA_part), one pass.  Block = (row block, chunk);
 // warp w takes rows w, w+8, ..., lane l the 8 columns 8l..8l+7 of the chunk.
@@ -97,12 +126,7 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
   const int elem = DT == 0 ? 2 : 1;
   const bool vec_ok = ((uintptr_t)P.A % (8 * elem) == 0) && ((P.lda * elem) % (8 * elem) == 0);
   float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int rr = warp; rr < TC_DM; rr += 8) {
-    const int r = r0 + rr;
-    if (r >= P.M) break;  // warp-uniform
-    float v[8];
-    uint16_t raw[8];
-    ld8<DT>(P.A, P.lda, r, k0 + lane * 8, P.K, vec_ok, v, raw);
+  auto take = [&](const float* v, int r) {
     float sq = 0.f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -112,6 +136,36 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if (lane == 0) P.nA_part[(long long)kx * P.M + r] = sq;
+  };
+  if (__all_sync(0xffffffffu, vec_ok && k0 + lane * 8 + 8 <= P.K)) {
+    // whole chunk aligned and inside K: the warp's 15 rows in groups of 5,
+    // five raw loads in flight (rows past M read row M - 1, then skipped)
+    constexpr int RPW = TC_DM / 8, GRP = 5;
+    static_assert(RPW % GRP == 0, "row groups");
+    for (int g0 = 0; g0 < RPW; g0 += GRP) {
+      uint4 q[GRP];
+#pragma unroll
+      for (int gi = 0; gi < GRP; ++gi)
+        q[gi] = ldraw8<DT>(P.A, P.lda, min(r0 + warp + 8 * (g0 + gi), P.M - 1), k0 + lane * 8);
+#pragma unroll
+      for (int gi = 0; gi < GRP; ++gi) {
+        const int r = r0 + warp + 8 * (g0 + gi);
+        if (r < P.M) {
+          float v[8];
+          cvt8<DT>(q[gi], v);
+          take(v, r);
+        }
+      }
+    }
+  } else {
+    for (int rr = warp; rr < TC_DM; rr += 8) {
+      const int r = r0 + rr;
+      if (r >= P.M) break;  // warp-uniform
+      float v[8];
+      uint16_t raw[8];
+      ld8<DT>(P.A, P.lda, r, k0 + lane * 8, P.K, vec_ok, v, raw);
+      take(v, r);
+    }
   }
 #pragma unroll
   for (int e = 0; e < 8; ++e) part[warp][lane * 8 + e] = cs[e];
@@ -126,9 +180,13 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
 }
 
 // B (K x N, N contiguous): B^T (N x ldk, K contiguous) in KC x NBW tiles
-// through shared memory; with checksums also the block sums over NBW-column
-// blocks (-> Wf) and squared column-norm partials per k-chunk (-> nB_part).
-// KC is one 128-byte k-block of the operand type.
+// through shared memory, TC_ENC_B_SUB consecutive tiles along K per block;
+// with checksums also the block sums over NBW-column blocks (-> Wf) and
+// squared column-norm partials per block (-> nB_part, one per
+// TC_ENC_B_SUB * KC rows of K).  KC is one 128-byte k-block of the operand
+// type.
+constexpr int TC_ENC_B_SUB = 4;
+
 template <int DT, bool ABFT>
 __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant__ TcBatch b) {
   TC_BLOCK_OF(P_ENC_B);
@@ -138,21 +196,14 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
   constexpr int PITCH = NBW + (DT == 0 ? 10 : 20);  // elements; staggers the banks
   __shared__ __align__(16) E tile[KC][PITCH];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkc = (P.K + KC - 1) / KC;
-  const int kc = lb % nkc, nb = lb / nkc;
-  const int k0 = kc * KC, n0 = nb * NBW;
+  const int nkc = (P.K + KC - 1) / KC, nkg = (nkc + TC_ENC_B_SUB - 1) / TC_ENC_B_SUB;
+  const int kg = lb % nkg, nb = lb / nkg;
+  const int n0 = nb * NBW;
   const bool vec_ok = ((uintptr_t)P.B % (8 * sizeof(E)) == 0) && ((P.ldb * (long long)sizeof(E)) % (8 * sizeof(E)) == 0);
   const bool in_cols = lane * 8 < NBW;  // 31 of 32 lanes for 248 columns
+  const bool fast = __all_sync(0xffffffffu, vec_ok && (!in_cols || n0 + lane * 8 + 8 <= P.N));
   float sq[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int kk = warp; kk < KC; kk += 8) {
-    const int k = k0 + kk;
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    uint16_t raw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (k < P.K && in_cols) ld8<DT>(P.B, P.ldb, k, n0 + lane * 8, P.N, vec_ok, v, raw);
-    if (in_cols) {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) tile[kk][lane * 8 + e] = (E)raw[e];
-    }
+  auto take = [&](const float* v, int k) {
     if constexpr (ABFT) {
       float rs = 0.f;
 #pragma unroll
@@ -164,9 +215,85 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
       for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
       if (lane == 0 && k < P.K) P.Wf[(long long)nb * P.K + k] = rs;
     }
+  };
+  E* Bt = reinterpret_cast<E*>(P.Bt);
+  constexpr int EPV = 16 / (int)sizeof(E);  // elements per 16-byte vector
+  for (int sub = 0; sub < TC_ENC_B_SUB; ++sub) {
+    const int kc = kg * TC_ENC_B_SUB + sub;
+    if (kc >= nkc) break;  // block-uniform
+    const int k0 = kc * KC;
+    if (fast) {
+      // columns aligned and inside N: the warp's KC/8 k-rows in groups of
+      // 4, four raw loads in flight (rows past K read row K - 1, then count
+      // as zeros)
+      constexpr int RPW = KC / 8, GRP = 4;
+      static_assert(RPW % GRP == 0, "row groups");
+      for (int g0 = 0; g0 < RPW; g0 += GRP) {
+        uint4 q[GRP];
+#pragma unroll
+        for (int gi = 0; gi < GRP; ++gi)
+          q[gi] = in_cols ? ldraw8<DT>(P.B, P.ldb, min(k0 + warp + 8 * (g0 + gi), P.K - 1), n0 + lane * 8)
+                          : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int gi = 0; gi < GRP; ++gi) {
+          const int kk = warp + 8 * (g0 + gi), k = k0 + kk;
+          const uint4 w = k < P.K ? q[gi] : make_uint4(0u, 0u, 0u, 0u);
+          if (in_cols) {
+            // row pitch and column offset are multiples of 4 bytes
+            uint32_t* t = reinterpret_cast<uint32_t*>(&tile[kk][lane * 8]);
+            t[0] = w.x;
+            t[1] = w.y;
+            if constexpr (DT == 0) {
+              t[2] = w.z;
+              t[3] = w.w;
+            }
+          }
+          float v[8];
+          cvt8<DT>(w, v);
+          take(v, k);
+        }
+      }
+    } else {
+      for (int kk = warp; kk < KC; kk += 8) {
+        const int k = k0 + kk;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint16_t raw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (k < P.K && in_cols) ld8<DT>(P.B, P.ldb, k, n0 + lane * 8, P.N, vec_ok, v, raw);
+        if (in_cols) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) tile[kk][lane * 8 + e] = (E)raw[e];
+        }
+        take(v, k);
+      }
+    }
+    __syncthreads();
+    // B^T rows n0..n0+NBW-1, k0..k0+KC-1: 8 threads write one 128-byte row
+    // segment (the k-range past K is zero, inside the padded row)
+    for (int i = threadIdx.x; i < NBW * 8; i += 256) {
+      const int nn = i >> 3, vq = i & 7;
+      const int n = n0 + nn;
+      if (n >= P.N) continue;
+      E o[EPV];
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) o[e] = tile[vq * EPV + e][nn];
+      uint4 w;
+      if constexpr (DT == 0) {
+        w.x = (uint32_t)o[0] | ((uint32_t)o[1] << 16); w.y = (uint32_t)o[2] | ((uint32_t)o[3] << 16);
+        w.z = (uint32_t)o[4] | ((uint32_t)o[5] << 16); w.w = (uint32_t)o[6] | ((uint32_t)o[7] << 16);
+      } else {
+        uint32_t q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          q[j] = (uint32_t)o[4 * j] | ((uint32_t)o[4 * j + 1] << 8) | ((uint32_t)o[4 * j + 2] << 16) |
+                 ((uint32_t)o[4 * j + 3] << 24);
+        w = make_uint4(q[0], q[1], q[2], q[3]);
+      }
+      *reinterpret_cast<uint4*>(Bt + (long long)n * P.ldk + k0 + vq * EPV) = w;
+    }
+    __syncthreads();  // the tile is refilled by the next chunk
   }
   if constexpr (ABFT) {
-    // each warp saw KC/8 of the chunk's k rows: sum the warps' column partials
+    // each warp saw 1/8 of the block's k rows: sum the warps' column partials
     __shared__ float sqw[8][NBW];
     if (in_cols) {
 #pragma unroll
@@ -179,35 +306,9 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
         float q = 0.f;
 #pragma unroll
         for (int w = 0; w < 8; ++w) q += sqw[w][c];
-        P.nB_part[(long long)kc * P.N + n] = q;
+        P.nB_part[(long long)kg * P.N + n] = q;
       }
     }
-  }
-  __syncthreads();
-  // B^T rows n0..n0+NBW-1, k0..k0+KC-1: 8 threads write one 128-byte row
-  // segment (the k-range past K is zero, inside the padded row)
-  E* Bt = reinterpret_cast<E*>(P.Bt);
-  constexpr int EPV = 16 / (int)sizeof(E);  // elements per 16-byte vector
-  for (int i = threadIdx.x; i < NBW * 8; i += 256) {
-    const int nn = i >> 3, vq = i & 7;
-    const int n = n0 + nn;
-    if (n >= P.N) continue;
-    E o[EPV];
-#pragma unroll
-    for (int e = 0; e < EPV; ++e) o[e] = tile[vq * EPV + e][nn];
-    uint4 w;
-    if constexpr (DT == 0) {
-      w.x = (uint32_t)o[0] | ((uint32_t)o[1] << 16); w.y = (uint32_t)o[2] | ((uint32_t)o[3] << 16);
-      w.z = (uint32_t)o[4] | ((uint32_t)o[5] << 16); w.w = (uint32_t)o[6] | ((uint32_t)o[7] << 16);
-    } else {
-      uint32_t q[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        q[j] = (uint32_t)o[4 * j] | ((uint32_t)o[4 * j + 1] << 8) | ((uint32_t)o[4 * j + 2] << 16) |
-               ((uint32_t)o[4 * j + 3] << 24);
-      w = make_uint4(q[0], q[1], q[2], q[3]);
-    }
-    *reinterpret_cast<uint4*>(Bt + (long long)n * P.ldk + k0 + vq * EPV) = w;
   }
 }
 
@@ -219,22 +320,40 @@ template <int DT>
 __global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ TcBatch b) {
   TC_BLOCK_OF(P_FIN);
   __shared__ float red[8], red2[8];
+  __shared__ float sred[8][256];
   constexpr int KC = DT == 0 ? 64 : 128;
+  static_assert(TC_DM <= 256 && TC_DN <= 256, "one thread per row of a block");
   const bool side_a = lb < P.tiles_m;
   const int blk = side_a ? lb : lb - P.tiles_m;
   const int R = side_a ? P.M : P.N, bs = side_a ? TC_DM : TC_DN;
-  const int nparts = side_a ? (P.K + 255) / 256 : (P.K + KC - 1) / KC;
+  const int nparts = side_a ? (P.K + 255) / 256 : (P.K + KC * TC_ENC_B_SUB - 1) / (KC * TC_ENC_B_SUB);
   const float* part = side_a ? P.nA_part : P.nB_part;
   float* nrm = side_a ? P.nA : P.nB;
-  const int t = threadIdx.x, r = blk * bs + t;
+  const int t = threadIdx.x, r = blk * bs + t, warp = t >> 5, lane = t & 31;
+  // warp w sums partials w, w + 8, ... of rows blk*bs + lane + 32 j, all
+  // j at once (8 independent loads per partial); then thread t adds the
+  // 8 warps' sums of row t in warp order
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+  for (int c = warp; c < nparts; c += 8) {
+    const float* pc = part + (long long)c * R;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)  // rows outside the block read a valid row; their sums are never used
+      acc[j] += pc[min(blk * bs + min(lane + 32 * j, bs - 1), R - 1)];
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) sred[warp][lane + 32 * j] = acc[j];
+  __syncthreads();
   float s = 0.f;
   if (t < bs && r < R) {
-    for (int c = 0; c < nparts; ++c) s += part[(long long)c * R + r];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += sred[w][t];
     nrm[r] = sqrtf(s);
   }
   // squared norm of the checksum vector of this block over K
   const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.K;
   float c = 0.f;
+#pragma unroll 8
   for (int k = t; k < P.K; k += blockDim.x) c = fmaf(S[k], S[k], c);
   float f = s;
 #pragma unroll
@@ -370,11 +489,17 @@ __global__ void cast_e4m3_kernel(const float* __restrict__ x, long long n, const
 
 // ---------------------------------------------------------------------------
 
+// Column-norm partials of B per column: one per encode_b block along K.
+int tc_nb_parts(int dt, long long K) {
+  const long long kr = (dt == 0 ? 64 : 128) * TC_ENC_B_SUB;
+  return (int)((K + kr - 1) / kr);
+}
+
 // Blocks each batched encode launch gives one problem.
 void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]) {
   const int nkx = (P.K + 255) / 256, kc = dt == 0 ? 64 : 128;
   out[P_ENC_A] = nkx * P.tiles_m;
-  out[P_ENC_B] = ((P.K + kc - 1) / kc) * P.tiles_n;
+  out[P_ENC_B] = ((P.K + kc * TC_ENC_B_SUB - 1) / (kc * TC_ENC_B_SUB)) * P.tiles_n;
   out[P_FIN] = P.tiles_m + P.tiles_n;
   out[P_SCALE] = P.tiles_m + P.tiles_n;
   out[P_PIECES] = nkx * (P.tiles_m + P.tiles_n);
