@@ -11,6 +11,8 @@ Functions (each cites the paper passage it follows):
   encode        e^T A per row block, B e per column block (Eq. 1-2) and norms
   gemm_ft       the online ABFT algorithm: Eq. 4 checksums, periodic
                 verification, location and correction (Sections 2.2, 4.2)
+  dgemm_schedule  the fp64 (DGEMM) tiling: gemm_ft with u = 2^-53 (Section 6)
+  zgemm_ref / zgemm_ft  the same on complex values (Section 6: ZGEMM)
   round_bf16    RNE rounding to bfloat16
   quant_e4m3    per-tensor amax scaling + RNE/saturating E4M3 (OCP FP8)
   offline_expected_runs  online vs offline ABFT cost model (Section 5.5)
@@ -58,6 +60,14 @@ class _Fault(C.Structure):
                 ("delta", C.c_double)]
 
 
+class _ZRec(C.Structure):
+    _fields_ = [("tile_m", C.c_int32), ("tile_n", C.c_int32), ("kstep", C.c_int32),
+                ("row", C.c_int32), ("col", C.c_int32), ("kind", C.c_int32),
+                ("delta_re", C.c_double), ("delta_im", C.c_double),
+                ("res_r_re", C.c_double), ("res_r_im", C.c_double),
+                ("res_c_re", C.c_double), ("res_c_im", C.c_double), ("tau", C.c_double)]
+
+
 class _Rec(C.Structure):
     _fields_ = [("tile_m", C.c_int32), ("tile_n", C.c_int32), ("kstep", C.c_int32),
                 ("row", C.c_int32), ("col", C.c_int32), ("kind", C.c_int32),
@@ -81,6 +91,12 @@ def lib():
                                      i32, C.POINTER(_Rec), i32, C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int32)]
         _lib.orc_gemm_ft.restype = C.c_int
+        _lib.orc_zgemm_ref.argtypes = [i64, i64, i64, d, d, i64, d, i64, d, d, i64, d, i64]
+        _lib.orc_zgemm_ft.argtypes = [i64, i64, i64, d, d, i64, d, i64, d, d, i64, d, i64,
+                                      i32, i32, i32, i32, i32, C.c_double, C.c_double,
+                                      C.POINTER(_Fault), i32, C.POINTER(_ZRec), i32,
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        _lib.orc_zgemm_ft.restype = C.c_int
         _lib.orc_round_bf16.argtypes = [C.POINTER(C.c_float), i64, d]
         _lib.orc_quant_e4m3.argtypes = [C.POINTER(C.c_float), i64, d, d]
         _lib.orc_quant_e4m3.restype = C.c_double
@@ -198,6 +214,83 @@ def gemm_ft(A, B, sched: Schedule, faults=(), alpha=1.0, beta=0.0, Cin=None,
         raise ValueError(f"orc_gemm_ft rejected its arguments (rc={rc})")
     rl = [Record(r.tile_m, r.tile_n, r.kstep, r.row, r.col, r.kind, r.delta,
                  r.residual_r, r.residual_c, r.tau) for r in recs[: min(nrec.value, cap)]]
+    return Result(out, cnt[0], cnt[1], cnt[2], cnt[3], rl)
+
+
+U64 = 2.0 ** -53
+T_IMAG = 4  # fault target flag of the complex GEMM: the offset is delta * i
+
+
+def dgemm_schedule(cadence: int, lam: float = 32.0, level: int = BLOCK) -> Schedule:
+    """The double-precision GEMM's tiling for gemm_ft: 128 x 128 output
+    tiles, k-steps of 8, one verification unit per tile, u = 2^-53."""
+    return Schedule(m_tb=128, n_tb=128, k_tb=8, m_w=128, n_w=128, m_t=8, n_t=8, cadence=cadence,
+                    split_k=1, level=level, lam=lam, u=U64)
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def zgemm_ref(A, B, alpha=1.0, beta=0.0, Cin=None) -> np.ndarray:
+    """C = alpha*A*B + beta*C_in in complex double precision."""
+    A, B = _c128(A), _c128(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    Ci = _c128(Cin) if (Cin is not None and beta != 0) else np.zeros((1, 1), np.complex128)
+    out = np.empty((M, N), dtype=np.complex128)
+    al = np.array([complex(alpha).real, complex(alpha).imag])
+    be = np.array([complex(beta).real, complex(beta).imag])
+    lib().orc_zgemm_ref(M, N, K, _dp(al), _dp(A), K, _dp(B), N, _dp(be), _dp(Ci), Ci.shape[1], _dp(out), N)
+    return out
+
+
+@dataclass
+class ZRecord:
+    tile_m: int
+    tile_n: int
+    kstep: int
+    row: int
+    col: int
+    kind: int
+    delta: complex
+    residual_r: complex
+    residual_c: complex
+    tau: float
+
+
+def zgemm_ft(A, B, tile: int = 64, k_tb: int = 8, cadence: int = 1, faults=(), alpha=1.0, beta=0.0,
+             Cin=None, lam: float = 32.0, u: float = U64, verify: bool = True,
+             cap: int = 1 << 16) -> Result:
+    """The online ABFT GEMM on complex operands at block level: tile x tile
+    output tiles, k-steps of k_tb, verification every `cadence` k-steps.
+    ``faults``: (tile_m, tile_n, kstep, row, col, delta[, target]) with a real
+    delta; target | T_IMAG puts the offset on the imaginary part."""
+    A, B = _c128(A), _c128(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    Ci = _c128(Cin) if (Cin is not None and beta != 0) else np.zeros((1, 1), np.complex128)
+    out = np.empty((M, N), dtype=np.complex128)
+    al = np.array([complex(alpha).real, complex(alpha).imag])
+    be = np.array([complex(beta).real, complex(beta).imag])
+    nf = len(faults)
+    fa = (_Fault * max(1, nf))()
+    for q, f in enumerate(faults):
+        tgt = f[6] if len(f) > 6 else T_ACC
+        fa[q] = _Fault(int(f[0]), int(f[1]), int(f[2]), int(f[3]), int(f[4]), int(tgt), float(f[5]))
+    recs = (_ZRec * cap)()
+    cnt = (C.c_int64 * 4)()
+    nrec = C.c_int32(0)
+    rc = lib().orc_zgemm_ft(M, N, K, _dp(al), _dp(A), K, _dp(B), N, _dp(be), _dp(Ci), Ci.shape[1],
+                            _dp(out), N, tile, tile, k_tb, cadence, 1 if verify else 0, lam, u,
+                            fa, nf, recs, cap, cnt, C.byref(nrec))
+    if rc != 0:
+        raise ValueError(f"orc_zgemm_ft rejected its arguments (rc={rc})")
+    rl = [ZRecord(r.tile_m, r.tile_n, r.kstep, r.row, r.col, r.kind, complex(r.delta_re, r.delta_im),
+                  complex(r.res_r_re, r.res_r_im), complex(r.res_c_re, r.res_c_im), r.tau)
+          for r in recs[: min(nrec.value, cap)]]
     return Result(out, cnt[0], cnt[1], cnt[2], cnt[3], rl)
 
 

@@ -36,8 +36,14 @@
  *   - the verification unit is the thread fragment, warp tile or block tile of
  *     the chosen level, with the fragment layout given by unit_row()/unit_col();
  *   - with split-K each split verifies its own partial sum; the sum of the
- *     splits and the alpha/beta epilogue are not protected.
+ *     splits and the alpha/beta epilogue are not protected;
+ *   - double precision (DGEMM, the extension named in Section 6) is (2) with
+ *     u = 2^-53; double complex (ZGEMM) is (3): the same steps on complex
+ *     values, one unit per output tile, |d| compared with a threshold built
+ *     from the norms sqrt(sum |a|^2) and sqrt(sum |b|^2); a fault is a real
+ *     or an imaginary offset.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -430,6 +436,247 @@ int orc_gemm_ft(int64_t M, int64_t N, int64_t K, double alpha,
   *nrec = all.n;
   for (int q = 0; q < 4; ++q) counters[q] = cnt[q];
   free(all.r);
+  free(nA);
+  free(nB);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* (3) Double-complex GEMM (ZGEMM), block-level units (Section 6 names DGEMM */
+/* and ZGEMM as the extension of the scheme).  Matrices are interleaved      */
+/* (re, im) pairs; leading dimensions count complex elements.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t tile_m, tile_n, kstep, row, col, kind; /* row/col global, -1 if none */
+  double delta_re, delta_im;                     /* amount subtracted / checksum offset */
+  double res_r_re, res_r_im, res_c_re, res_c_im; /* residuals of the flagged row / column */
+  double tau;
+} orc_zrecord;
+
+static double complex zat(const double* p, int64_t idx) { return p[2 * idx] + p[2 * idx + 1] * I; }
+
+/* C = alpha * A B + beta * C_in, complex double precision. */
+void orc_zgemm_ref(int64_t M, int64_t N, int64_t K, const double* alpha,
+                   const double* A, int64_t lda, const double* B, int64_t ldb,
+                   const double* beta, const double* Cin, int64_t ldc, double* C,
+                   int64_t ldo) {
+  const double complex al = alpha[0] + alpha[1] * I, be = beta[0] + beta[1] * I;
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      double complex s = 0.0;
+      for (int64_t k = 0; k < K; ++k) s += zat(A, i * lda + k) * zat(B, k * ldb + j);
+      double complex c = al * s;
+      if (be != 0.0) c += be * zat(Cin, i * ldc + j);
+      C[2 * (i * ldo + j)] = creal(c);
+      C[2 * (i * ldo + j) + 1] = cimag(c);
+    }
+  }
+}
+
+static int zrec_cmp(const void* a, const void* b) {
+  const orc_zrecord* x = (const orc_zrecord*)a;
+  const orc_zrecord* y = (const orc_zrecord*)b;
+  if (x->tile_m != y->tile_m) return x->tile_m < y->tile_m ? -1 : 1;
+  if (x->tile_n != y->tile_n) return x->tile_n < y->tile_n ? -1 : 1;
+  if (x->kstep != y->kstep) return x->kstep < y->kstep ? -1 : 1;
+  if (x->row != y->row) return x->row < y->row ? -1 : 1;
+  if (x->col != y->col) return x->col < y->col ? -1 : 1;
+  return x->kind - y->kind;
+}
+
+/* The online ABFT GEMM on complex values: tiles mt x nt, k-steps of kt,
+ * verification every `cadence` k-steps and after the last (when verify).
+ * Fault targets: low two bits as in (2); bit 2 set = the offset is imaginary
+ * (delta * i).  Output and counters as in orc_gemm_ft. */
+int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb,
+                 const double* beta, const double* Cin, int64_t ldc, double* Cout,
+                 int64_t ldo, int32_t mt, int32_t nt, int32_t kt, int32_t cadence,
+                 int32_t verify, double lambda, double u, const orc_fault* faults,
+                 int32_t nfaults, orc_zrecord* recs, int32_t cap, int64_t* counters,
+                 int32_t* nrec) {
+  if (M <= 0 || N <= 0 || K <= 0 || mt <= 0 || nt <= 0 || kt <= 0 || cadence <= 0) return -1;
+  const double complex al = alpha[0] + alpha[1] * I, be = beta[0] + beta[1] * I;
+  const int64_t tiles_m = (M + mt - 1) / mt, tiles_n = (N + nt - 1) / nt;
+  const int64_t nks = (K + kt - 1) / kt;
+
+  /* norms over the full K: sqrt(sum |a|^2), sqrt(sum |b|^2) */
+  double* nA = (double*)calloc((size_t)M, sizeof(double));
+  double* nB = (double*)calloc((size_t)N, sizeof(double));
+  for (int64_t i = 0; i < M; ++i) {
+    double s = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+      double complex a = zat(A, i * lda + k);
+      s += creal(a) * creal(a) + cimag(a) * cimag(a);
+    }
+    nA[i] = sqrt(s);
+  }
+  for (int64_t j = 0; j < N; ++j) {
+    double s = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+      double complex b = zat(B, k * ldb + j);
+      s += creal(b) * creal(b) + cimag(b) * cimag(b);
+    }
+    nB[j] = sqrt(s);
+  }
+
+  int64_t cnt[4] = {0, 0, 0, 0};
+  orc_zrecord* all = NULL;
+  int32_t nall = 0, capall = 0;
+
+  int64_t t;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (t = 0; t < tiles_m * tiles_n; ++t) {
+    const int64_t ti = t / tiles_n, tj = t % tiles_n;
+    const int64_t i0 = ti * mt, j0 = tj * nt;
+    const int rows = (int)(M - i0 < mt ? M - i0 : mt);
+    const int cols = (int)(N - j0 < nt ? N - j0 : nt);
+    double complex* acc = (double complex*)calloc((size_t)mt * nt, sizeof(double complex));
+    double complex* cr = (double complex*)calloc((size_t)mt, sizeof(double complex));
+    double complex* cc = (double complex*)calloc((size_t)nt, sizeof(double complex));
+    double complex* dr = (double complex*)calloc((size_t)mt, sizeof(double complex));
+    double complex* dc = (double complex*)calloc((size_t)nt, sizeof(double complex));
+    double* tr = (double*)calloc((size_t)mt, sizeof(double));
+    double* tc = (double*)calloc((size_t)nt, sizeof(double));
+    orc_zrecord* L = NULL;
+    int32_t nL = 0, capL = 0;
+    int64_t lc[4] = {0, 0, 0, 0};
+
+    /* thresholds: lambda*u*||A(i,:)||*||B(:,J)||_F and lambda*u*||A(I,:)||_F*||B(:,j)|| */
+    double fa = 0.0, fb = 0.0;
+    for (int r = 0; r < rows; ++r) fa += nA[i0 + r] * nA[i0 + r];
+    for (int c = 0; c < cols; ++c) fb += nB[j0 + c] * nB[j0 + c];
+    for (int r = 0; r < rows; ++r) tr[r] = lambda * u * nA[i0 + r] * sqrt(fb);
+    for (int c = 0; c < cols; ++c) tc[c] = lambda * u * sqrt(fa) * nB[j0 + c];
+
+    for (int64_t s = 0; s < nks; ++s) {
+      const int64_t k0 = s * kt, k1 = (k0 + kt < K) ? k0 + kt : K;
+      /* acc_IJ += A_I(:,s) B_J(s,:) */
+      for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) {
+          double complex a = 0.0;
+          for (int64_t k = k0; k < k1; ++k) a += zat(A, (i0 + r) * lda + k) * zat(B, k * ldb + j0 + c);
+          acc[r * nt + c] += a;
+        }
+      if (verify) {
+        for (int64_t k = k0; k < k1; ++k) {
+          /* row checksum c^r += A_I(:,k) (B_J(k,:) e);  column checksum c^c += (e^T A_I(:,k)) B_J(k,:) */
+          double complex w = 0.0, v = 0.0;
+          for (int c = 0; c < cols; ++c) w += zat(B, k * ldb + j0 + c);
+          for (int r = 0; r < rows; ++r) v += zat(A, (i0 + r) * lda + k);
+          for (int r = 0; r < rows; ++r) cr[r] += zat(A, (i0 + r) * lda + k) * w;
+          for (int c = 0; c < cols; ++c) cc[c] += v * zat(B, k * ldb + j0 + c);
+        }
+      }
+      for (int f = 0; f < nfaults; ++f) {
+        const orc_fault* F = &faults[f];
+        int64_t fk = F->kstep < 0 ? nks - 1 : F->kstep;
+        if (F->tile_m != ti || F->tile_n != tj || fk != s) continue;
+        if (F->row < 0 || F->row >= rows || F->col < 0 || F->col >= cols) continue;
+        const double complex off = (F->target & 4) ? F->delta * I : F->delta + 0.0 * I;
+        switch (F->target & 3) {
+          case ORC_T_ROWSUM: cr[F->row] += off; break;
+          case ORC_T_COLSUM: cc[F->col] += off; break;
+          default: acc[F->row * nt + F->col] += off; break;
+        }
+      }
+      if (!verify || !(((s + 1) % cadence) == 0 || s == nks - 1)) continue;
+      int nr = 0, nc = 0, ib = -1, jb = -1;
+      double sbr = -1.0, sbc = -1.0;
+      for (int r = 0; r < rows; ++r) {
+        double complex S = 0.0;
+        for (int c = 0; c < cols; ++c) S += acc[r * nt + c];
+        dr[r] = S - cr[r];
+        if (cabs(dr[r]) > tr[r]) {
+          ++nr;
+          double sc = score(cabs(dr[r]), tr[r]);
+          if (sc > sbr) { sbr = sc; ib = r; }
+        }
+      }
+      for (int c = 0; c < cols; ++c) {
+        double complex S = 0.0;
+        for (int r = 0; r < rows; ++r) S += acc[r * nt + c];
+        dc[c] = S - cc[c];
+        if (cabs(dc[c]) > tc[c]) {
+          ++nc;
+          double sc = score(cabs(dc[c]), tc[c]);
+          if (sc > sbc) { sbc = sc; jb = c; }
+        }
+      }
+      if (nr == 0 && nc == 0) continue;
+      ++lc[0];
+      orc_zrecord rec;
+      memset(&rec, 0, sizeof(rec));
+      rec.tile_m = (int32_t)ti; rec.tile_n = (int32_t)tj; rec.kstep = (int32_t)s;
+      rec.row = ib >= 0 ? (int32_t)(i0 + ib) : -1;
+      rec.col = jb >= 0 ? (int32_t)(j0 + jb) : -1;
+      if (ib >= 0) { rec.res_r_re = creal(dr[ib]); rec.res_r_im = cimag(dr[ib]); }
+      if (jb >= 0) { rec.res_c_re = creal(dc[jb]); rec.res_c_im = cimag(dc[jb]); }
+      rec.tau = (ib >= 0 ? tr[ib] : 0.0) + (jb >= 0 ? tc[jb] : 0.0);
+      double complex delta = 0.0;
+      if (nr == 1 && nc == 1) {
+        if (cabs(dr[ib] - dc[jb]) <= tr[ib] + tc[jb]) {
+          acc[ib * nt + jb] -= dr[ib]; /* subtract the offset (Section 4.2.1) */
+          delta = dr[ib];
+          rec.kind = ORC_CORRECTED; ++lc[1];
+        } else {
+          rec.kind = ORC_UNCORRECTABLE; ++lc[2];
+        }
+      } else if ((nr == 1 && nc == 0) || (nr == 0 && nc == 1)) {
+        /* a checksum was hit: reset it from the data, keep C */
+        if (nr == 1) {
+          double complex S = 0.0;
+          for (int c = 0; c < cols; ++c) S += acc[ib * nt + c];
+          delta = cr[ib] - S;
+          cr[ib] = S;
+        } else {
+          double complex S = 0.0;
+          for (int r = 0; r < rows; ++r) S += acc[r * nt + jb];
+          delta = cc[jb] - S;
+          cc[jb] = S;
+        }
+        rec.kind = ORC_CHECKSUM_ONLY; ++lc[3];
+      } else {
+        rec.kind = ORC_UNCORRECTABLE; ++lc[2];
+      }
+      rec.delta_re = creal(delta);
+      rec.delta_im = cimag(delta);
+      if (nL == capL) {
+        capL = capL ? 2 * capL : 16;
+        L = (orc_zrecord*)realloc(L, sizeof(orc_zrecord) * (size_t)capL);
+      }
+      L[nL++] = rec;
+    }
+    /* epilogue: C = alpha*acc + beta*C_in (unprotected) */
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) {
+        double complex v = al * acc[r * nt + c];
+        if (be != 0.0) v += be * zat(Cin, (i0 + r) * ldc + j0 + c);
+        Cout[2 * ((i0 + r) * ldo + j0 + c)] = creal(v);
+        Cout[2 * ((i0 + r) * ldo + j0 + c) + 1] = cimag(v);
+      }
+#pragma omp critical
+    {
+      for (int q = 0; q < 4; ++q) cnt[q] += lc[q];
+      for (int q = 0; q < nL; ++q) {
+        if (nall == capall) {
+          capall = capall ? 2 * capall : 16;
+          all = (orc_zrecord*)realloc(all, sizeof(orc_zrecord) * (size_t)capall);
+        }
+        all[nall++] = L[q];
+      }
+    }
+    free(L);
+    free(acc); free(cr); free(cc); free(dr); free(dc); free(tr); free(tc);
+  }
+
+  if (nall > 1) qsort(all, (size_t)nall, sizeof(orc_zrecord), zrec_cmp);
+  for (int q = 0; q < nall && q < cap; ++q) recs[q] = all[q];
+  *nrec = nall;
+  for (int q = 0; q < 4; ++q) counters[q] = cnt[q];
+  free(all);
   free(nA);
   free(nB);
   return 0;
