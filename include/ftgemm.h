@@ -358,6 +358,48 @@ int ftgemm_gemm_offline(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                         float* C, int64_t ldc, const ftgemm_inject_spec* const* injects,
                         int32_t max_runs, int32_t* runs_out, ftgemm_report* report);
 
+/* ---- double and double complex (Section 6: DGEMM / ZGEMM extension) ---- */
+
+#define FTGEMM_DGEMM_TILE 128 /* output tile (and checksum unit) of ftgemm_dgemm */
+#define FTGEMM_ZGEMM_TILE 64  /* output tile (and checksum unit) of ftgemm_zgemm */
+#define FTGEMM_F64_KSTEP 8    /* k-step of both: the unit of inject kstep and cadence */
+#define FTGEMM_TARGET_IMAG 4  /* ftgemm_zgemm inject target flag: offset on the imaginary part */
+
+/* C = alpha * A * B + beta * C in double precision on the CUDA cores, with
+ * the online ABFT of the paper at block level: e^T A per 128-row block and
+ * B e per 128-column block (Eq. 1-2) accumulate beside each 128 x 128
+ * output tile during the K loop (Eq. 4); every `cadence` k-steps of 8
+ * (cadence <= 0: once, after the last k-step) the tile's row and column
+ * sums are compared with them against lambda * 2^-53 * ||A(i,:)|| *
+ * ||B(:,J)||_F and lambda * 2^-53 * ||A(I,:)||_F * ||B(:,j)|| (lambda of
+ * ftgemm_set_threshold mode 0), and one corrupted element is located and
+ * corrected or a corrupted checksum reset (Section 4.2.1); records as for
+ * ftgemm_gemm.  Device pointers, row-major, leading dimensions in elements
+ * (lda >= k, ldb >= n, ldc >= n); beta == 0: C is not read.  ft_level:
+ * FTGEMM_FT_OFF or FTGEMM_FT_BLOCK (FTGEMM_FT_AUTO runs BLOCK); others give
+ * FTGEMM_ERR_UNSUPPORTED.  inject: tile_m / tile_n on the 128 x 128 grid,
+ * kstep in units of 8 of K, target 0 / 1 / 2 as for ftgemm_gemm; the offset
+ * is delta.  report may be NULL.  Enqueued on the handle's stream;
+ * synchronises only when report is given. */
+int ftgemm_dgemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, double alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                 double* C, int64_t ldc, ftgemm_ft_level ft_level, int32_t cadence,
+                 const ftgemm_inject_spec* inject, ftgemm_report* report);
+
+/* The same for double complex on 64 x 64 tiles: matrices of interleaved
+ * (re, im) doubles (C99 double complex layout), 16-byte aligned, leading
+ * dimensions in complex elements; alpha and beta are HOST arrays {re, im}.
+ * Norms are sqrt(sum |a|^2); a residual d is flagged when |d| exceeds its
+ * threshold; the largest |d| / tau is located.  inject targets may carry
+ * FTGEMM_TARGET_IMAG: the offset is then delta * i.  Records hold the real
+ * parts of delta, residual_r and residual_c; when `imag` (HOST, 3 doubles
+ * per record slot of the report, may be NULL) is given it receives their
+ * imaginary parts in the same order as report->records. */
+int ftgemm_zgemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, const double* alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta,
+                 double* C, int64_t ldc, ftgemm_ft_level ft_level, int32_t cadence,
+                 const ftgemm_inject_spec* inject, ftgemm_report* report, double* imag);
+
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them. */
 int ftgemm_report_fetch(ftgemm_handle_t handle, ftgemm_report* report);

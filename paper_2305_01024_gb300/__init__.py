@@ -33,6 +33,8 @@ class FtgemmError(RuntimeError):
 
 MLP_INPUTS = 5
 MLP_PARAMS = 1281
+DGEMM_TILE, ZGEMM_TILE, F64_KSTEP = 128, 64, 8
+TARGET_IMAG = 4  # zgemm inject target flag: the offset is delta * i
 
 
 class Schedule(C.Structure):
@@ -131,6 +133,10 @@ def lib():
                                       C.POINTER(C.POINTER(InjectSpec)), i32, C.POINTER(i32), C.POINTER(Report)]
     L.ftgemm_gemm_nonfused.argtypes = [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32,
                                        C.POINTER(InjectSpec), C.POINTER(Report)]
+    L.ftgemm_dgemm.argtypes = [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, C.c_int, i32,
+                               C.POINTER(InjectSpec), C.POINTER(Report)]
+    L.ftgemm_zgemm.argtypes = [vp, i64, i64, i64, C.POINTER(dbl), vp, i64, vp, i64, C.POINTER(dbl), vp, i64,
+                               C.c_int, i32, C.POINTER(InjectSpec), C.POINTER(Report), C.POINTER(dbl)]
     L.ftgemm_status_string.argtypes = [C.c_int]
     L.ftgemm_status_string.restype = C.c_char_p
     L.ftgemm_last_error.restype = C.c_char_p
@@ -141,7 +147,8 @@ def lib():
                "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
                "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune",
-               "ftgemm_selftest_wait", "ftgemm_gemm_offline", "ftgemm_gemm_nonfused"):
+               "ftgemm_selftest_wait", "ftgemm_gemm_offline", "ftgemm_gemm_nonfused", "ftgemm_dgemm",
+               "ftgemm_zgemm"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -302,6 +309,60 @@ class Handle:
             _check(st)
         return st, runs.value, PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
                                         rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def dgemm(self, A, B, C_out, alpha=1.0, beta=0.0, level=FT_BLOCK, cadence: int = 16, inject=None,
+              report=True, capacity: int = 4096):
+        """C_out = alpha*A@B + beta*C_out in float64 through ftgemm_dgemm
+        (block-level ABFT on 128 x 128 tiles, verification every `cadence`
+        k-steps of 8).  Returns a PyReport if `report`, else None."""
+        if isinstance(level, str):
+            level = LEVELS[level]
+        M, K = A.shape
+        N = B.shape[1]
+        assert B.shape[0] == K and tuple(C_out.shape) == (M, N)
+        spec = make_inject(inject) if inject else None
+        rep, recs = None, None
+        if report:
+            recs = (FaultRecord * capacity)()
+            rep = Report(capacity=capacity, records=recs)
+        _check(lib().ftgemm_dgemm(self._h, M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                  float(beta), _ptr(C_out), C_out.stride(0), level, int(cadence),
+                                  C.byref(spec) if spec else None, C.byref(rep) if rep else None))
+        if not report:
+            return None
+        return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
+                        rep.n_records, bool(rep.overflow), _records(rep, capacity))
+
+    def zgemm(self, A, B, C_out, alpha=1.0, beta=0.0, level=FT_BLOCK, cadence: int = 16, inject=None,
+              report=True, capacity: int = 4096):
+        """The complex128 counterpart through ftgemm_zgemm (64 x 64 tiles).
+        Record fields delta / residual_r / residual_c come back as Python
+        complex numbers."""
+        if isinstance(level, str):
+            level = LEVELS[level]
+        M, K = A.shape
+        N = B.shape[1]
+        assert B.shape[0] == K and tuple(C_out.shape) == (M, N)
+        spec = make_inject(inject) if inject else None
+        al = (C.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (C.c_double * 2)(complex(beta).real, complex(beta).imag)
+        rep, recs, im = None, None, None
+        if report:
+            recs = (FaultRecord * capacity)()
+            rep = Report(capacity=capacity, records=recs)
+            im = (C.c_double * (3 * capacity))()
+        _check(lib().ftgemm_zgemm(self._h, M, N, K, al, _ptr(A), A.stride(0), _ptr(B), B.stride(0), be,
+                                  _ptr(C_out), C_out.stride(0), level, int(cadence),
+                                  C.byref(spec) if spec else None, C.byref(rep) if rep else None, im))
+        if not report:
+            return None
+        rl = _records(rep, capacity)
+        for q, r in enumerate(rl):
+            r["delta"] = complex(r["delta"], im[3 * q])
+            r["residual_r"] = complex(r["residual_r"], im[3 * q + 1])
+            r["residual_c"] = complex(r["residual_c"], im[3 * q + 2])
+        return PyReport(rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only,
+                        rep.n_records, bool(rep.overflow), rl)
 
     def set_residual_sink(self, lam_needed=None, features=None):
         """Route every later TILE-level tensor-core call's per-tile residual

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "fp64.cuh"
 
 namespace ftg {
 using SimtLaunch = cudaError_t (*)(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
@@ -129,6 +130,8 @@ struct ftgemm_ctx {
   // second workspace (non-fused baseline: its buffers live across the GEMM calls it makes)
   float* ws2 = nullptr;
   size_t ws2_floats = 0;
+  // fp64 complex path: Im of (delta, residual_r, residual_c) per record slot
+  double* zimag = nullptr;
   // residual sink (tensor-core path)
   float* sink_lam = nullptr;
   float* sink_x = nullptr;
@@ -286,7 +289,8 @@ static int make_map_2d(CUtensorMap* m, const float* base, uint64_t inner, uint64
 // Validate an injection spec against the tiling, resolve k-step -1, sort by
 // (tile, k-step) and upload it; *nf receives the number of faults.
 static int upload_faults(ftgemm_ctx* h, const ftgemm_inject_spec* inject, const ftgemm_schedule& s, int M,
-                         int N, int ksteps, int tiles_m, int tiles_n, ftgemm_ft_level level, int* nf_out) {
+                         int N, int ksteps, int tiles_m, int tiles_n, ftgemm_ft_level level, int* nf_out,
+                         bool imag_targets = false) {
   int nf = inject ? inject->n : 0;
   *nf_out = 0;
   if (nf < 0) FAIL(FTGEMM_ERR_ARG, "inject->n < 0");
@@ -309,8 +313,9 @@ static int upload_faults(ftgemm_ctx* h, const ftgemm_inject_spec* inject, const 
     const int rows = std::min(s.m_tb, M - tm * s.m_tb), cols = std::min(s.n_tb, N - tn * s.n_tb);
     if (r < 0 || r >= rows || c < 0 || c >= cols)
       FAIL(FTGEMM_ERR_ARG, "inject[%d]: element (%d,%d) outside tile (%d x %d)", i, r, c, rows, cols);
-    if (tg < 0 || tg > 2) FAIL(FTGEMM_ERR_ARG, "inject[%d]: target %d", i, tg);
-    if (level == FTGEMM_FT_OFF && tg != 0) FAIL(FTGEMM_ERR_ARG, "inject[%d]: no checksums at level OFF", i);
+    const int tb = imag_targets ? (tg & ~FTGEMM_TARGET_IMAG) : tg;
+    if (tg < 0 || tb > 2) FAIL(FTGEMM_ERR_ARG, "inject[%d]: target %d", i, tg);
+    if (level == FTGEMM_FT_OFF && tb != 0) FAIL(FTGEMM_ERR_ARG, "inject[%d]: no checksums at level OFF", i);
     fv[i] = Fault{tm * tiles_n + tn, ks, r, c, tg, inject->delta[i]};
   }
   std::stable_sort(fv.begin(), fv.end(), [](const Fault& a, const Fault& b) {
@@ -890,6 +895,7 @@ int ftgemm_destroy(ftgemm_handle_t h) {
   if (h->ws) cudaFree(h->ws);
   if (h->rep) cudaFree(h->rep);
   if (h->recs) cudaFree(h->recs);
+  if (h->zimag) cudaFree(h->zimag);
   if (h->d_faults) cudaFree(h->d_faults);
   if (h->h_faults) cudaFreeHost(h->h_faults);
   if (h->faults_free) cudaEventDestroy(h->faults_free);
@@ -1562,4 +1568,111 @@ int ftgemm_gemm_offline(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, doub
     if (rc) return rc;
   }
   FAIL(FTGEMM_ERR_UNRECOVERED, "ftgemm_gemm_offline: all %d attempts detected a fault", max_runs);
+}
+
+// ---- double and double complex (Section 6: DGEMM / ZGEMM) -------------------
+
+static int f64_gemm(ftgemm_ctx* h, bool cplx, int64_t m, int64_t n, int64_t k, const double* alpha,
+                    const void* A, int64_t lda, const void* B, int64_t ldb, const double* beta, void* C,
+                    int64_t ldc, ftgemm_ft_level level, int32_t cadence, const ftgemm_inject_spec* inject,
+                    ftgemm_report* report, double* imag) {
+  const char* who = cplx ? "ftgemm_zgemm" : "ftgemm_dgemm";
+  if (!h || !A || !B || !C || !alpha || !beta || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n || ldc < n)
+    FAIL(FTGEMM_ERR_ARG, "%s: bad argument", who);
+  if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "%s: size too large", who);
+  if (level == FTGEMM_FT_AUTO) level = FTGEMM_FT_BLOCK;
+  if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_BLOCK)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "%s: checksum level %d (OFF or BLOCK only)", who, (int)level);
+  const size_t esz = cplx ? 16 : 8;
+  if ((uintptr_t)A % esz || (uintptr_t)B % esz || (uintptr_t)C % esz)
+    FAIL(FTGEMM_ERR_ALIGN, "%s: operands must be aligned to their element size (%zu bytes)", who, esz);
+  CK(cudaSetDevice(h->device));
+  const int M = (int)m, N = (int)n, K = (int)k, T = f64_tile(cplx);
+  const int tiles_m = (M + T - 1) / T, tiles_n = (N + T - 1) / T, ksteps = (K + FTGEMM_F64_KSTEP - 1) / FTGEMM_F64_KSTEP;
+  if (tiles_m > 65535) FAIL(FTGEMM_ERR_ARG, "%s: m too large for the tile grid", who);
+  const bool abft = level == FTGEMM_FT_BLOCK;
+  const ftgemm_schedule unit{T, T, FTGEMM_F64_KSTEP, T, T, T / 16, T / 16, 1, 1};  // the tiling faults refer to
+  int nf = 0;
+  {
+    int rc = upload_faults(h, inject, unit, M, N, ksteps, tiles_m, tiles_n, level, &nf, cplx);
+    if (rc) return rc;
+  }
+  if (report) {
+    int rc = clear_report(h);
+    if (rc) return rc;
+  }
+  if (cplx && !h->zimag) CK(cudaMalloc(&h->zimag, sizeof(double) * 3 * (size_t)h->rep_cap));
+  int launches = 0;
+  // workspace: V[tiles_m][K], W[tiles_n][K] (operand type), nA[M], nB[N]
+  const size_t ev = esz / 4;  // floats per element
+  size_t o = 0;
+  auto take = [&](size_t floats) { const size_t at = o; o = align64(o + floats); return at; };
+  const size_t oV = take(ev * (size_t)tiles_m * K), oW = take(ev * (size_t)tiles_n * K), oNa = take(2 * (size_t)M),
+               oNb = take(2 * (size_t)N);
+  if (abft) {
+    int rc = ensure_ws(h, o);
+    if (rc) return rc;
+    CK(launch_f64_encode(cplx, A, lda, B, ldb, M, N, K, h->ws + oV, h->ws + oW, (double*)(h->ws + oNa),
+                         (double*)(h->ws + oNb), &launches, h->stream));
+  }
+  F64Params p{};
+  p.M = M; p.N = N; p.K = K;
+  p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
+  p.alpha_re = alpha[0]; p.alpha_im = cplx ? alpha[1] : 0.0;
+  p.beta_re = beta[0]; p.beta_im = cplx ? beta[1] : 0.0;
+  p.beta_zero = p.beta_re == 0.0 && p.beta_im == 0.0;
+  if (abft) {
+    p.V = h->ws + oV; p.W = h->ws + oW;
+    p.nA = (const double*)(h->ws + oNa); p.nB = (const double*)(h->ws + oNb);
+  }
+  p.lam_u = h->lambda * std::ldexp(1.0, -53);
+  p.cadence = cadence > 0 ? cadence : ksteps;
+  p.faults = nf > 0 ? h->d_faults : nullptr;
+  p.nfaults = nf;
+  p.rep = h->rep;
+  p.recs = h->recs;
+  p.imag = cplx ? h->zimag : nullptr;
+  std::pair<cudaEvent_t, cudaEvent_t> ev2;
+  if (h->timing) {
+    int rc = take_events(h, &ev2);
+    if (rc) return rc;
+    CK(cudaEventRecord(ev2.first, h->stream));
+  }
+  CK(launch_f64_gemm(cplx, abft, p, h->stream));
+  ++launches;
+  if (h->timing) {
+    CK(cudaEventRecord(ev2.second, h->stream));
+    h->pending.push_back(ev2);
+  }
+  h->launches += launches;
+  if (!report) return FTGEMM_OK;
+  int rc = ftgemm_report_fetch(h, report);
+  if (rc) return rc;
+  // pair each returned record with its imaginary parts through its slot
+  const int w = std::min(std::max(0, report->capacity), std::min(report->n_records, h->rep_cap));
+  if (cplx && imag && w > 0 && report->records) {
+    const int slots = std::min(report->n_records, h->rep_cap);
+    std::vector<double> im(3 * (size_t)slots);
+    CK(cudaMemcpy(im.data(), h->zimag, sizeof(double) * im.size(), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < w; ++q) {
+      const int sl = report->records[q].reserved;
+      for (int e = 0; e < 3; ++e) imag[3 * q + e] = (sl >= 0 && sl < slots) ? im[3 * (size_t)sl + e] : 0.0;
+    }
+  }
+  for (int q = 0; q < w && report->records; ++q) report->records[q].reserved = 0;
+  return FTGEMM_OK;
+}
+
+int ftgemm_dgemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double beta, double* C, int64_t ldc, ftgemm_ft_level ft_level,
+                 int32_t cadence, const ftgemm_inject_spec* inject, ftgemm_report* report) {
+  const double al[2] = {alpha, 0.0}, be[2] = {beta, 0.0};
+  return f64_gemm(h, false, m, n, k, al, A, lda, B, ldb, be, C, ldc, ft_level, cadence, inject, report, nullptr);
+}
+
+int ftgemm_zgemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const double* alpha, const double* A,
+                 int64_t lda, const double* B, int64_t ldb, const double* beta, double* C, int64_t ldc,
+                 ftgemm_ft_level ft_level, int32_t cadence, const ftgemm_inject_spec* inject, ftgemm_report* report,
+                 double* imag) {
+  return f64_gemm(h, true, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ft_level, cadence, inject, report, imag);
 }

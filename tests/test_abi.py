@@ -60,5 +60,9 @@ def test_host_side_argument_checks(libpath):
     assert L.ftgemm_selftest_wait(None, 1000) == -1
     assert L.ftgemm_gemm_offline(None, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, 1, None, None) == -1
     assert L.ftgemm_gemm_nonfused(None, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 256, None, None) == -1
+    assert L.ftgemm_dgemm(None, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, ft.FT_BLOCK, 1, None, None) == -1
+    one = (ctypes.c_double * 2)(1.0, 0.0)
+    assert L.ftgemm_zgemm(None, 4, 4, 4, one, None, 4, None, 4, one, None, 4, ft.FT_BLOCK, 1, None, None,
+                          None) == -1
     assert L.ftgemm_status_string(ft.ERR_UNRECOVERED) == b"every offline attempt detected a fault"
     assert b"NULL" in L.ftgemm_last_error() or len(L.ftgemm_last_error()) > 0
