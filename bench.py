@@ -757,6 +757,51 @@ def small_shapes_extras(ft, h, synth, dev, timed_loop):
             "note": "ratio = torch time / our time per call (launch overheads included)"}
 
 
+def fp64_extras(ft, h, synth, dev, timed_loop):
+    """Section 6's extension: DGEMM (4096^3) and ZGEMM (2048^3) with online
+    block-level ABFT (verification every 16 k-steps of 8), N(0,1) operands,
+    four seeded faults per call; against the same kernel with checksums off
+    and against torch.matmul (cuBLAS) in float64 / complex128.  These kernels
+    run on the FP64 units (no fast FP64 tensor path on this part), whose
+    nominal rate is the roofline."""
+    import torch
+    fp64_nominal = 1.25  # TFLOP/s, GB300 FP64
+    out = {"fp64_nominal_tflops": fp64_nominal}
+    for kind, n, tile, flop_per in (("dgemm", 4096, ft.DGEMM_TILE, 2.0), ("zgemm", 2048, ft.ZGEMM_TILE, 8.0)):
+        if kind == "dgemm":
+            A = synth.torch_make("normal", (n, n), synth.config_seed(6, 0), dev, torch.float64)
+            B = synth.torch_make("normal", (n, n), synth.config_seed(6, 1), dev, torch.float64)
+            call = h.dgemm
+        else:
+            A = torch.complex(synth.torch_make("normal", (n, n), synth.config_seed(7, 0), dev, torch.float64),
+                              synth.torch_make("normal", (n, n), synth.config_seed(7, 1), dev, torch.float64))
+            B = torch.complex(synth.torch_make("normal", (n, n), synth.config_seed(7, 2), dev, torch.float64),
+                              synth.torch_make("normal", (n, n), synth.config_seed(7, 3), dev, torch.float64))
+            call = h.zgemm
+        Cm = torch.empty_like(A)
+        tiles, ks = n // tile, n // ft.F64_KSTEP
+        pos = synth.fault_positions(synth.config_seed(6 if kind == "dgemm" else 7, 9), 4, tiles, tiles, ks,
+                                    tile, tile, n, n, 16)
+        faults = [(a, b, k, r, c, 1e-8 * math.sqrt(n)) for (a, b, k, r, c) in pos]
+        ms_off = timed_loop(lambda i: call(A, B, Cm, level=ft.FT_OFF, report=False), 3, warm=1)
+        h.report_fetch()
+        ms_ft = timed_loop(lambda i: call(A, B, Cm, level=ft.FT_BLOCK, cadence=16, inject=faults, report=False),
+                           3, warm=1)
+        rep = h.report_fetch()
+        ct = torch.empty_like(A)
+        ms_t = timed_loop(lambda i: torch.matmul(A, B, out=ct), 3, warm=1)
+        fl = flop_per * n ** 3
+        tf = lambda ms: fl / (ms / 1e3) / 1e12  # noqa: E731
+        out[kind] = {"n": n, "tile": tile, "tflops_block": round(tf(ms_ft), 4), "tflops_off": round(tf(ms_off), 4),
+                     "overhead_pct": round(100 * (ms_ft / ms_off - 1), 2),
+                     "torch_tflops": round(tf(ms_t), 4), "speed_vs_torch": round(ms_t / ms_ft, 3),
+                     "frac_of_nominal_fp64": round(tf(ms_ft) / fp64_nominal, 3),
+                     "faults_per_call": len(faults), "calls": 4,
+                     "corrected": rep.corrected, "detected": rep.detected}
+        del A, B, Cm, ct
+    return out
+
+
 def irregular_extras(ft, h, synth, dev, timed_loop):
     """Config 3: irregular fp32 shapes, N(0,1), schedule and checksum level
     picked per shape by the autotuner, one seeded fault per GEMM."""
@@ -968,7 +1013,7 @@ def main():
         for name, fn in (("tensor_core", tensor_core_extras), ("grouped", grouped_extras),
                          ("learned_threshold", learned_extras), ("nonfused", nonfused_extras),
                          ("offline", offline_extras), ("small_shapes", small_shapes_extras),
-                         ("irregular", irregular_extras)):
+                         ("irregular", irregular_extras), ("fp64", fp64_extras)):
             try:
                 side[name] = fn(ft, h, synth, dev, timed_loop)
             except Exception as exc:  # reported, not hidden: the headline line still prints
