@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip levels/sweep side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
     ap.add_argument("--case", default=None,
-                    help="run one small kernel case for a profiler and exit: tc-<bf16|e4m3>-<tile|off>-<n>")
+                    help="run one small kernel case for a profiler and exit: tc-<bf16|e4m3>-<tile|off>-<n>, "
+                         "tcgroup-bf16-<tile|off>-<problems>, f64-<d|z>-<block|off>-<n>")
     return ap.parse_args()
 
 
@@ -67,8 +68,22 @@ def run_case(case):
     import paper_2305_01024_gb300 as ft
     import synth
     kind, dtn, lvn, n = case.split("-")
-    assert kind in ("tc", "tcgroup"), case
+    assert kind in ("tc", "tcgroup", "f64"), case
     n = int(n)
+    if kind == "f64":  # f64-<d|z>-<off|block>-<n>: DGEMM / ZGEMM on N(0,1) operands, cadence 16
+        h = ft.Handle(0)
+        mk = lambda s: synth.torch_make("normal", (n, n), s, "cuda", torch.float64)  # noqa: E731
+        if dtn == "d":
+            A, B, call = mk(11), mk(12), h.dgemm
+        else:
+            A, B, call = torch.complex(mk(11), mk(13)), torch.complex(mk(12), mk(14)), h.zgemm
+        Cm = torch.empty_like(A)
+        for _ in range(3):
+            call(A, B, Cm, level=ft.LEVELS[lvn], cadence=16, report=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "detected": h.report_fetch().detected}))
+        h.close()
+        return 0
     if kind == "tcgroup":  # n problems of config 5's shape distribution, bf16
         u = synth.unit(synth.config_seed(5, 0), 3 * n)
         shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253),
