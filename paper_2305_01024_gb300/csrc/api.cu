@@ -395,6 +395,9 @@ static void tc_set_problem(TcProblem& P, int dt, bool abft, int M, int N, int K,
   P.nkb = (K + kblk - 1) / kblk;
   P.A = A; P.lda = lda; P.B = B; P.ldb = ldb;
   P.ldk = (K + 127) / 128 * 128;  // elements; a 16-byte multiple for both types
+  // without checksums a bf16 B is read in place by the MMA (MN-major) when
+  // TMA can address it: 256-column tiles keep its boxes on 128-byte lines
+  P.b_mn = !abft && dt == 0 && ((uintptr_t)B & 15) == 0 && (ldb * 2) % 16 == 0;
   P.C = C; P.ldc = ldc;
   P.c_vec = (ldc % 4 == 0) && (((uintptr_t)C & 15) == 0);
   P.alpha = (float)alpha; P.beta = (float)beta;
@@ -414,10 +417,10 @@ static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
     o = align64(o + floats);
     return ws ? ws + at : nullptr;
   };
-  P.Bt = take(fl(eb * (size_t)P.N * P.ldk));
+  P.Bt = P.b_mn ? nullptr : take(fl(eb * (size_t)P.N * P.ldk));
   if (abft) {
-    P.Vf = take(tm * K);
-    P.Wf = take(tn * K);
+    P.Vf = take(tm * P.ldk);
+    P.Wf = take(tn * P.ldk);
     P.Vt = take(fl(eb * tm * ns * P.ldk));
     P.Wt = take(fl(eb * tn * ns * P.ldk));
     P.vscale = take(tm * ns);
@@ -442,7 +445,10 @@ static int tc_make_maps(TcProbMaps& mp, const TcProblem& P, int dt, bool abft) {
   const uint32_t ns = TC_CS_SLOTS;
   memset(&mp, 0, sizeof(mp));
   int rc = make_map_sw128(&mp.A, P.A, elem, P.K, P.M, P.lda, BK, dm);
-  if (!rc) rc = make_map_sw128(&mp.B, P.Bt, elem, P.K, P.N, P.ldk, BK, dn);
+  if (!rc) {
+    if (P.b_mn) rc = make_map_sw128(&mp.B, P.B, elem, P.N, P.K, P.ldb, 64, BK);  // 64-column boxes
+    else rc = make_map_sw128(&mp.B, P.Bt, elem, P.K, P.N, P.ldk, BK, dn);
+  }
   if (!rc && abft) rc = make_map_sw128(&mp.W, P.Wt, elem, P.K, (uint64_t)P.tiles_n * ns, P.ldk, BK, ns);
   if (!rc && abft) rc = make_map_sw128(&mp.V, P.Vt, elem, P.K, (uint64_t)P.tiles_m * ns, P.ldk, BK, ns);
   if (rc) return rc;

@@ -114,7 +114,9 @@ struct TcProblem {
   const void* A; long long lda;   // M x K, operand type, K contiguous
   const void* B; long long ldb;   // K x N, operand type, N contiguous
   void* Bt; long long ldk;        // B^T (N x ldk); ldk also the row stride of Vt / Wt
-  float* Vf; float* Wf;           // fp32 e^T A [tiles_m][K], B e [tiles_n][K]
+  int b_mn;                       // checksums off, bf16, B 16-byte aligned: the MMA reads B
+                                  // in place as an MN-major operand (no B^T, no encode pass)
+  float* Vf; float* Wf;           // fp32 e^T A [tiles_m][ldk], B e [tiles_n][ldk] (first K used)
   void* Vt; void* Wt;             // pieces [tiles * TC_CS_SLOTS][ldk], operand type
   float* vscale; float* wscale;   // [tiles * TC_CS_SLOTS] multiplier of each piece
   float* s0v; float* s0w;         // [tiles] fp8 piece base scales
@@ -145,7 +147,7 @@ struct TcBatch {
 
 struct alignas(128) TcProbMaps {
   CUtensorMap A;  // A:   dims {K, M}, box {k-block, data rows}, 128-byte swizzle
-  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, data columns}
+  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, data columns}; b_mn: B, dims {N, K}, box {64, k-block}
   CUtensorMap W;  // pieces of B e:   dims {K, 8 * tiles_n}, box {k-block, 8}
   CUtensorMap V;  // pieces of e^T A: dims {K, 8 * tiles_m}, box {k-block, 8}
 };

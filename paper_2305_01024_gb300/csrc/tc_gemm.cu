@@ -29,6 +29,14 @@
 // accumulator (each warp the 32 lanes its index allows), verify, correct and
 // store -- so the epilogue of one tile overlaps the main loop of the next.
 // k-block = one 128-byte swizzle row (64 bf16 or 128 fp8 elements).
+//
+// B operand.  Without checksums, for bf16 with a 16-byte aligned B, the MMA
+// reads B where it lies, as an MN-major operand: four TMA boxes of 64
+// columns x 64 k-rows per stage, each k-row a whole 128-byte line of B (the
+// tiles are 256 columns wide), so no encode pass runs at all.  With
+// checksums the data tile is 248 columns wide, its boxes would start off
+// the 128-byte lines of B, and the kernel reads B^T (written by the encode
+// pass) K-major instead, as for e4m3 and unaligned B.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -53,6 +61,7 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * 128;            // 32 KB
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int THREADS = 192;
+  static constexpr int MN_BOX = 64 * 128;  // bytes of one 64-column x 64-row box of an MN-major B
   static constexpr uint32_t TMEM_COLS = 2 * BN;       // two fp32 accumulators
   static constexpr int NPIECE = DT == 0 ? 3 : 5;      // checksum pieces in use
   static_assert(!ABFT || NPIECE <= CSR, "pieces must fit the checksum slots");
@@ -66,6 +75,23 @@ __host__ __device__ constexpr uint32_t tc_idesc(int dt, int m, int n) {
          | ((dt == 0 ? 1u : 0u) << 7)                // A format: bf16 (kind::f16) / e4m3
          | ((dt == 0 ? 1u : 0u) << 10)               // B format
          | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+constexpr uint32_t TC_IDESC_B_MN = 1u << 16;  // instruction descriptor: B is MN-major
+
+// Shared-memory descriptor of an MN-major operand stored as 128-byte swizzled
+// boxes of 64 MN elements x 64 k-rows: within a box the 8-row groups along K
+// are 1024 bytes apart (stride byte offset), and the 64-element groups along
+// MN are whole boxes apart (leading byte offset).
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(const void* tile, uint32_t box_bytes) {
+  const uint64_t addr = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (addr & 0x3FFFFull) >> 4;             // start address
+  d |= (uint64_t)((box_bytes >> 4) & 0x3FFF) << 16;  // leading byte offset: next 64 MN elements
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8 k-rows
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
 }
 
 template <int DT>
@@ -128,7 +154,7 @@ __device__ __forceinline__ TcTile tc_my_tile(const TcBatch& b, int my0, int j) {
 }
 
 template <int DT, bool ABFT>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcBatch b, const __grid_constant__ TcMapsBatch mb, const TcRun run) {
   using Cfg = TcCfg<DT, ABFT>;
   constexpr int BM = Cfg::BM, BN = Cfg::BN, DM = Cfg::DM, DN = Cfg::DN, BK = Cfg::BK, UK = Cfg::UK;
@@ -187,15 +213,23 @@ __global__ void __launch_bounds__(192, 1)
         last_pi = x.pi;
       }
       const int row0 = x.tm * DM, col0 = x.tn * DN;
+      const bool mn = !ABFT && DT == 0 && tc_problem(b, x.pi).b_mn;
       for (int kb = 0; kb < x.nkb; ++kb, ++it) {
         const int s = it % S;
         if (it >= S && !mbar_wait(&T.empty[s], ((it / S) & 1u) ^ 1u)) {
           dead = true;
           break;
         }
+        // the same byte count either way: an MN-major B is 4 boxes of 8 KB
         mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
         tma_load_2d(sA(s), &mp->A, &T.full[s], kb * BK, row0);
-        tma_load_2d(sB(s), &mp->B, &T.full[s], kb * BK, col0);
+        if (mn) {
+#pragma unroll
+          for (int g = 0; g < BN / 64; ++g)
+            tma_load_2d(sB(s) + g * Cfg::MN_BOX, &mp->B, &T.full[s], col0 + 64 * g, kb * BK);
+        } else {
+          tma_load_2d(sB(s), &mp->B, &T.full[s], kb * BK, col0);
+        }
         if constexpr (ABFT) {
           tma_load_2d(sA(s) + DM * 128, &mp->V, &T.full[s], kb * BK, x.tm * CSR);
           tma_load_2d(sB(s) + DN * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
@@ -217,6 +251,8 @@ __global__ void __launch_bounds__(192, 1)
     TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
     for (; lt < n_my && !dead; ++lt) {
       const int nkb = nx.nkb;
+      const bool mn = !ABFT && DT == 0 && tc_problem(b, nx.pi).b_mn;
+      const uint32_t id_t = mn ? (idesc | TC_IDESC_B_MN) : idesc;
       const int ab = lt & 1;
       if (lt >= 2 && !mbar_wait(&T.acc_empty[ab], ((lt >> 1) - 1) & 1)) {
         dead = true;
@@ -231,11 +267,15 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc_fence_after();
-        const uint64_t da = smem_desc_sw128(sA(s)), db = smem_desc_sw128(sB(s));
+        const uint64_t da = smem_desc_sw128(sA(s));
+        const uint64_t db = mn ? smem_desc_mn_sw128(sB(s), Cfg::MN_BOX) : smem_desc_sw128(sB(s));
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk) {
-          const uint64_t step = (uint64_t)(kk * 32) >> 4;  // 32 bytes per instruction
-          tc_mma<DT>(d, da + step, db + step, idesc, (kb | kk) != 0);
+          // K-major: 32 bytes along the swizzled row per instruction;
+          // MN-major: UK k-rows of 128 bytes
+          const uint64_t step_a = (uint64_t)(kk * 32) >> 4;
+          const uint64_t step_b = mn ? (uint64_t)(kk * UK * 128) >> 4 : step_a;
+          tc_mma<DT>(d, da + step_a, db + step_b, id_t, (kb | kk) != 0);
         }
         tc_commit(&T.empty[s]);  // the stage is free once these MMAs completed
         if (kb == 0 && lt + 1 < n_my) nx = tc_my_tile(b, my0, lt + 1);

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
     float s = 0.f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s += part[w][t];
-    P.Vf[(long long)blk * P.K + k0 + t] = s;
+    P.Vf[(long long)blk * P.ldk + k0 + t] = s;
   }
 }
 
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-      if (lane == 0 && k < P.K) P.Wf[(long long)nb * P.K + k] = rs;
+      if (lane == 0 && k < P.K) P.Wf[(long long)nb * P.ldk + k] = rs;
     }
   };
   E* Bt = reinterpret_cast<E*>(P.Bt);
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ T
     nrm[r] = sqrtf(s);
   }
   // squared norm of the checksum vector of this block over K
-  const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.K;
+  const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.ldk;
   float c = 0.f;
 #pragma unroll 8
   for (int k = t; k < P.K; k += blockDim.x) c = fmaf(S[k], S[k], c);
@@ -385,7 +385,7 @@ __global__ void tc_blockscale_kernel(const __grid_constant__ TcBatch b) {
   __shared__ float red[32];
   const bool side_a = lb < P.tiles_m;
   const int blk = side_a ? lb : lb - P.tiles_m;
-  const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.K;
+  const float* S = (side_a ? P.Vf : P.Wf) + (long long)blk * P.ldk;
   float m = 0.f;
   for (int k = threadIdx.x; k < P.K; k += blockDim.x) m = fmaxf(m, fabsf(S[k]));
 #pragma unroll
@@ -433,7 +433,7 @@ __global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b) {
     scale[blk * NS + c] = m;
   }
   if (k >= P.K) return;
-  float x = S[(long long)blk * P.K + k];
+  float x = S[(long long)blk * P.ldk + k];
   if constexpr (DT == 0) {
     __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Pc);
     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
@@ -496,10 +496,11 @@ int tc_nb_parts(int dt, long long K) {
 }
 
 // Blocks each batched encode launch gives one problem.
+// An MN-major B (checksums off) needs no encode blocks at all.
 void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]) {
   const int nkx = (P.K + 255) / 256, kc = dt == 0 ? 64 : 128;
   out[P_ENC_A] = nkx * P.tiles_m;
-  out[P_ENC_B] = ((P.K + kc * TC_ENC_B_SUB - 1) / (kc * TC_ENC_B_SUB)) * P.tiles_n;
+  out[P_ENC_B] = P.b_mn ? 0 : ((P.K + kc * TC_ENC_B_SUB - 1) / (kc * TC_ENC_B_SUB)) * P.tiles_n;
   out[P_FIN] = P.tiles_m + P.tiles_n;
   out[P_SCALE] = P.tiles_m + P.tiles_n;
   out[P_PIECES] = nkx * (P.tiles_m + P.tiles_n);
@@ -511,6 +512,7 @@ void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]) {
 cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
                            cudaStream_t st) {
   if (!abft) {
+    if (total[P_ENC_B] == 0) return cudaSuccess;  // every B is read in place
     if (dt == 0) tc_encode_b_kernel<0, false><<<total[P_ENC_B], 256, 0, st>>>(b);
     else tc_encode_b_kernel<1, false><<<total[P_ENC_B], 256, 0, st>>>(b);
     ++*launches;

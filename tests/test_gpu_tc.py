@@ -61,7 +61,10 @@ def _bound(A, B, Cin, alpha, beta, K):
 
 
 @pytest.mark.parametrize("level", ["off", "tile"])
-@pytest.mark.parametrize("shape", [(256, 512, 320), (200, 300, 136), (128, 256, 64), (130, 260, 72)])
+# N a multiple of 8: B is read in place (MN-major), including ragged last tiles (264, 504);
+# N = 300, 260: B goes through the transposed copy
+@pytest.mark.parametrize("shape", [(256, 512, 320), (200, 300, 136), (128, 256, 64), (130, 260, 72),
+                                   (200, 264, 136), (136, 504, 200)])
 def test_tc_bf16_integers_exact(ft, handle, orc, level, shape):
     M, N, K = shape
     A, B = _bf16_inputs(orc, "int", M, N, K, 500 + M)
