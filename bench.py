@@ -1036,7 +1036,7 @@ def main():
     copy = torch.cuda.Stream(device=dev)
     e2e_steps = args.steps
 
-    def e2e_run(steps):
+    def e2e_run(steps, gemm_ev=None):
         up = [torch.cuda.Event() for _ in range(2)]
         done = [torch.cuda.Event() for _ in range(2)]
         free = [torch.cuda.Event() for _ in range(2)]  # result read back: buffer reusable
@@ -1057,7 +1057,11 @@ def main():
             if i + 1 < steps:
                 upload(i + 1)
             stream.wait_event(up[i % 2])
+            if gemm_ev is not None:
+                gemm_ev[i][0].record(stream)
             h.gemm(a, b, c, alpha=1.0, beta=0.5, level=level, report=False)
+            if gemm_ev is not None:
+                gemm_ev[i][1].record(stream)
             done[i % 2].record(stream)
             with torch.cuda.stream(copy):
                 copy.wait_event(done[i % 2])
@@ -1068,17 +1072,25 @@ def main():
     e2e_run(1)  # warm-up
     torch.cuda.synchronize()
     barrier()
+    gemm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(e2e_steps)]
+    e2e_clocks = ClockSampler(clocks.gpu)
+    e2e_clocks.start()
     s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s_.record(stream)
-    e2e_run(e2e_steps)
+    e2e_run(e2e_steps, gemm_ev)
     e_.record(stream)
     torch.cuda.synchronize()
+    e2e_clk = e2e_clocks.stop()
     barrier()
     ms_e2e = max_over_ranks(s_.elapsed_time(e_) / e2e_steps)
+    gemm_ms = [a.elapsed_time(b) for a, b in gemm_ev]
     h.report_fetch()
     e2e = {"value": flops * world / (ms_e2e / 1e3) / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
-           "ms_per_step": ms_e2e, "pipelining": "inputs double-buffered on a copy stream"}
+           "ms_per_step": ms_e2e, "pipelining": "inputs double-buffered on a copy stream",
+           "gemm_ms_mean": sum(gemm_ms) / len(gemm_ms), "gemm_ms_max": max(gemm_ms),
+           "clocks": e2e_clk}
     del bufs
 
     # ---- configs 4, 5, 3: tensor cores, grouped, irregular (side lines) ----
