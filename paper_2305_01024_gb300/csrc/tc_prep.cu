@@ -11,7 +11,8 @@
 //   e4m3: x = sum_c q_c / s_c with s_c = s_0 * 16^c, q_c = e4m3(residual * s_c)
 //         and s_0 a power of two putting the block's largest |x| near 448.
 // Norms of the rows of A and of the columns of B scale the detection
-// threshold.  B is also transposed to the K-major layout the MMA reads.
+// threshold.  B is also transposed to the K-major layout the MMA reads,
+// except a bf16 B without checksums, which the MMA reads in place.
 // Each operand is read once: one kernel reads A for its block sums and row
 // norms, one reads B for B^T, its block sums and column norms (partial
 // norms per k-chunk, finished without atomics so results are reproducible).
@@ -506,7 +507,7 @@ void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]) {
   out[P_PIECES] = nkx * (P.tiles_m + P.tiles_n);
 }
 
-// The encode pass of a batch: B^T for every problem; with checksums also
+// The encode pass of a batch: B^T for every problem that needs it; with checksums also
 // the block sums, norms, Frobenius norms and pieces.  total[kind] = blocks
 // of each launch over the batch.
 cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,

@@ -216,3 +216,26 @@ def test_zgemm_alignment_is_checked(ft):
     st = L.ftgemm_zgemm(h._h, 8, 8, 8, one, p, 8, p, 8, one, p, 8, ft.FT_BLOCK, 1, None, None, None)
     assert st == ft.ERR_ALIGN
     h.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 300, 7), (129, 1, 9), (65, 70, 13)])
+def test_fp64_degenerate_and_ragged_shapes(ft, orc, shape):
+    """One element, one row or column, K not a multiple of the k-step: both
+    kernels against the oracle, bit-exact on integers, with a fault each."""
+    M, N, K = shape
+    A, B = _ints((M, K), 301 + M), _ints((K, N), 302 + N)
+    fd = [(0, 0, 0, M - 1, N - 1, 8.0)]
+    h = ft.Handle(0)
+    dC = _cuda(np.zeros((M, N)))
+    rep = h.dgemm(_cuda(A), _cuda(B), dC, cadence=1, inject=fd)
+    res = orc.gemm_ft(A, B, orc.dgemm_schedule(cadence=1), faults=fd)
+    assert np.array_equal(dC.cpu().numpy(), res.C)
+    assert sorted(map(_key, rep.records)) == sorted(map(_key, res.records))
+    Z, W = A + 1j * _ints((M, K), 303), B - 1j * _ints((K, N), 304)
+    fz = [(0, 0, 0, M - 1, N - 1, 8.0, ft.TARGET_IMAG)]
+    dZ = _cuda(np.zeros((M, N), np.complex128))
+    rz = h.zgemm(_cuda(Z), _cuda(W), dZ, cadence=1, inject=fz)
+    oz = orc.zgemm_ft(Z, W, tile=64, k_tb=8, cadence=1, faults=fz)
+    assert np.array_equal(dZ.cpu().numpy(), oz.C)
+    assert sorted(map(_key, rz.records)) == sorted(map(_zkey_res, oz.records))
+    h.close()
