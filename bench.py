@@ -43,6 +43,7 @@ SCHED = dict(m_tb=128, n_tb=128, k_tb=16, m_w=64, n_w=64, m_t=16, n_t=8, cadence
 SCHED_OFF_BEST = dict(m_tb=128, n_tb=128, k_tb=16, m_w=32, n_w=64, m_t=8, n_t=8, cadence=16, split_k=1)
 FAULTS_PER_MIN = 200.0
 KERNEL_SOURCES = ["simt_ftgemm.cuh", "simt_wide.cu", "internal.cuh", "ptx.cuh"]
+TC_KERNEL_SOURCES = ["tc_gemm.cu", "internal.cuh", "ptx.cuh", "mlp.cuh"]
 
 
 def parse():
@@ -186,24 +187,24 @@ class ClockSampler:
 # helpers
 # ---------------------------------------------------------------------------
 
-def kernel_source_sha():
+def kernel_source_sha(files=KERNEL_SOURCES):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2305_01024_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def committed_traffic(kernel_key):
+def committed_traffic(kernel_key, files=KERNEL_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current sources of the kernel (`files`); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         return None
     ent = data.get(kernel_key)
-    if not ent or ent.get("source_sha256") != kernel_source_sha():
+    if not ent or ent.get("source_sha256") != kernel_source_sha(files):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -425,7 +426,8 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
             r["torch_matmul_tflops"] = fl / (timed_loop(lambda i: torch.matmul(A, B, out=ct), 5, warm=2) / 1e3) / 1e12
             pk = peaks.get("bf16_tflops")
             r["roofline"] = {"bound": "tensor", "achieved": r["tile_kernel_tflops"], "peak": pk, "unit": "TFLOP/s",
-                             "frac": r["tile_kernel_tflops"] / pk if pk else None, "traffic": None,
+                             "frac": r["tile_kernel_tflops"] / pk if pk else None,
+                             "traffic": committed_traffic("tc_gemm_bf16_tile_16384", TC_KERNEL_SOURCES),
                              "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"}
             del ct
         else:
@@ -442,7 +444,8 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
             pk = peaks.get("bf16_tflops")
             r["roofline"] = {"bound": "tensor", "achieved": r["tile_kernel_tflops"],
                              "peak": 2 * pk if pk else None, "unit": "TFLOP/s",
-                             "frac": r["tile_kernel_tflops"] / (2 * pk) if pk else None, "traffic": None,
+                             "frac": r["tile_kernel_tflops"] / (2 * pk) if pk else None,
+                             "traffic": committed_traffic("tc_gemm_e4m3_tile_16384", TC_KERNEL_SOURCES),
                              "peak_basis": "measured bf16 burst x 2 (nominal fp8 / bf16 dense ratio)"}
         h.report_fetch()
         out[name] = {k: (float(f"{v:.5g}") if isinstance(v, float) else v) for k, v in r.items()}
