@@ -35,8 +35,8 @@ cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, floa
                                  cudaStream_t);
 void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]);
 int tc_nb_parts(int dt, long long K);
-cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
-                           cudaStream_t st);
+cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS],
+                           const int* const* bmap, int* launches, cudaStream_t st);
 cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
                            cudaStream_t st);
 cudaError_t launch_quantize(int dt, const float* x, long long n, void* y, unsigned int* amax_bits, float* scale,
@@ -505,7 +505,7 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   int total[P_KINDS];
   tc_prep_blocks(P, dt, total);
   int launches = 0;
-  CK(launch_tc_prep(dt, abft, b, total, &launches, h->stream));
+  CK(launch_tc_prep(dt, abft, b, total, nullptr, &launches, h->stream));
   TcMapsBatch mb;
   memset(&mb, 0, sizeof(mb));
   {
@@ -562,6 +562,8 @@ struct ftgemm_group {
   TcProbMaps* d_maps = nullptr;
   int4* d_tiles = nullptr;      // the schedule: per-CTA tile lists, concatenated
   int* d_cta_start = nullptr;   // [ncta + 1]
+  int* d_bmap = nullptr;        // encode launches: the problem of every block, kinds concatenated
+  const int* bmap[P_KINDS] = {};
   int ncta = 0;
   float* ws = nullptr;
   int total[P_KINDS] = {};
@@ -616,6 +618,7 @@ static void group_free(ftgemm_group* g) {
   if (g->d_maps) cudaFree(g->d_maps);
   if (g->d_tiles) cudaFree(g->d_tiles);
   if (g->d_cta_start) cudaFree(g->d_cta_start);
+  if (g->d_bmap) cudaFree(g->d_bmap);
   if (g->ws) cudaFree(g->ws);
   if (g->d_faults) cudaFree(g->d_faults);
   if (g->d_fbits) cudaFree(g->d_fbits);
@@ -714,10 +717,25 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
   if (e == cudaSuccess) e = cudaMemcpy(g->d_tiles, sched.data(), sizeof(int4) * sched.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(g->d_cta_start, cta_start.data(), sizeof(int) * cta_start.size(), cudaMemcpyHostToDevice);
+  // the problem of every block of each encode launch (no search on the device)
+  std::vector<int> bmap;
+  size_t at[P_KINDS];
+  for (int kd = 0; kd < P_KINDS; ++kd) {
+    at[kd] = bmap.size();
+    for (int q = 0; q < count; ++q) {
+      int nb[P_KINDS];
+      tc_prep_blocks(g->probs[q], dt, nb);
+      bmap.insert(bmap.end(), (size_t)nb[kd], q);
+    }
+  }
+  if (e == cudaSuccess && !bmap.empty()) e = cudaMalloc(&g->d_bmap, sizeof(int) * bmap.size());
+  if (e == cudaSuccess && !bmap.empty())
+    e = cudaMemcpy(g->d_bmap, bmap.data(), sizeof(int) * bmap.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     group_free(g);
     FAIL(FTGEMM_ERR_CUDA, "ftgemm_group_create: %s", cudaGetErrorString(e));
   }
+  for (int kd = 0; kd < P_KINDS; ++kd) g->bmap[kd] = g->d_bmap ? g->d_bmap + at[kd] : nullptr;
   *out = g;
   return FTGEMM_OK;
 }
@@ -794,7 +812,7 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   b.nprob = g->count;
   b.total_tiles = g->total_tiles;
   int launches = 0;
-  CK(launch_tc_prep(g->dt, g->abft, b, g->total, &launches, h->stream));
+  CK(launch_tc_prep(g->dt, g->abft, b, g->total, g->bmap, &launches, h->stream));
   TcMapsBatch mb;
   memset(&mb, 0, sizeof(mb));
   mb.table = g->d_maps;

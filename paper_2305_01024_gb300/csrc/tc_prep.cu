@@ -41,10 +41,12 @@ __device__ __forceinline__ float ld_elem(const void* base, long long idx) {
 }
 
 // Every encode kernel runs over a batch of problems (TcBatch): a problem's
-// blocks of launch `kind` start at blk_start[kind], found by binary search.
-#define TC_BLOCK_OF(KIND)                                  \
-  const int pi = tc_find_block(b, KIND, blockIdx.x);       \
-  const TcProblem& P = tc_problem(b, pi);                  \
+// blocks of launch `kind` start at blk_start[kind].  A group passes `bmap`,
+// the problem of every block of the launch (built once, at group creation);
+// otherwise the problem is found by binary search.
+#define TC_BLOCK_OF(KIND)                                                  \
+  const int pi = bmap ? bmap[blockIdx.x] : tc_find_block(b, KIND, blockIdx.x); \
+  const TcProblem& P = tc_problem(b, pi);                                  \
   const int lb = (int)blockIdx.x - P.blk_start[KIND]
 
 // Eight consecutive elements of row `row` (columns c0..c0+7, zero past
@@ -117,7 +119,7 @@ __device__ __forceinline__ void cvt8(const uint4 q, float* v) {
 // over 256-wide k-chunks (-> nA_part), one pass.  Block = (row block, chunk);
 // warp w takes rows w, w+8, ..., lane l the 8 columns 8l..8l+7 of the chunk.
 template <int DT>
-__global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant__ TcBatch b) {
+__global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_ENC_A);
   __shared__ float part[8][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
 constexpr int TC_ENC_B_SUB = 4;
 
 template <int DT, bool ABFT>
-__global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant__ TcBatch b) {
+__global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_ENC_B);
   using E = typename std::conditional<DT == 0, uint16_t, uint8_t>::type;
   constexpr int KC = 128 / (int)sizeof(E);
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
 // coherence ||v_I||_2 / (sqrt(|I|) ||A_I||_F) of each block (the same for
 // w_J and B_J), a feature of the learned threshold.
 template <int DT>
-__global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ TcBatch b) {
+__global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_FIN);
   __shared__ float red[8], red2[8];
   __shared__ float sred[8][256];
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ T
 }
 
 // s0[blk]: power of two with max_k |S[blk][k]| * s0 in (224, 448]  (fp8 only)
-__global__ void tc_blockscale_kernel(const __grid_constant__ TcBatch b) {
+__global__ void tc_blockscale_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_SCALE);
   __shared__ float red[32];
   const bool side_a = lb < P.tiles_m;
@@ -410,11 +412,11 @@ __global__ void tc_blockscale_kernel(const __grid_constant__ TcBatch b) {
 // and their multipliers scale[blk*TC_CS_SLOTS + c]; row blocks of A first,
 // then column blocks of B.
 template <int DT>
-__global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b) {
+__global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_PIECES);
-  constexpr int NS = TC_CS_SLOTS;
-  const int nkx = (P.K + 255) / 256;
-  const int k = (lb % nkx) * 256 + threadIdx.x, bi = lb / nkx;
+  constexpr int NS = TC_CS_SLOTS, KPT = 8;  // k per thread: one 16-byte (bf16) / 8-byte (fp8) store per slot
+  const int nkx = (P.K + 256 * KPT - 1) / (256 * KPT);
+  const int k0 = (lb % nkx) * 256 * KPT + threadIdx.x * KPT, bi = lb / nkx;
   const bool side_a = bi < P.tiles_m;
   const int blk = side_a ? bi : bi - P.tiles_m;
   const float* S = side_a ? P.Vf : P.Wf;
@@ -433,33 +435,60 @@ __global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b) {
     }
     scale[blk * NS + c] = m;
   }
-  if (k >= P.K) return;
-  float x = S[(long long)blk * P.ldk + k];
+  if (k0 >= P.K) return;
+  // rows are ldk long (a multiple of 128), so k0 .. k0+7 stay inside the row;
+  // values past K are zero (the GEMM's TMA never reads them)
+  float x[KPT];
+  {
+    const float4* src = reinterpret_cast<const float4*>(S + (long long)blk * P.ldk + k0);
+    const float4 u = src[0], v = src[1];
+    const float t[KPT] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) x[j] = k0 + j < P.K ? t[j] : 0.f;
+  }
   if constexpr (DT == 0) {
-    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Pc);
-    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(hi);
-    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(mid);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
+    uint16_t q[3][KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
+      const float r1 = x[j] - __bfloat162float(hi);
+      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      q[0][j] = __bfloat16_as_ushort(hi);
+      q[1][j] = __bfloat16_as_ushort(mid);
+      q[2][j] = __bfloat16_as_ushort(lo);
+    }
+    uint16_t* out = reinterpret_cast<uint16_t*>(Pc);
+#pragma unroll
     for (int c = 0; c < NS; ++c) {
-      const __nv_bfloat16 v = c == 0 ? hi : c == 1 ? mid : c == 2 ? lo : __float2bfloat16_rn(0.f);
-      out[(long long)(blk * NS + c) * P.ldk + k] = v;
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      if (c < 3)
+        w = make_uint4((uint32_t)q[c][0] | ((uint32_t)q[c][1] << 16), (uint32_t)q[c][2] | ((uint32_t)q[c][3] << 16),
+                       (uint32_t)q[c][4] | ((uint32_t)q[c][5] << 16), (uint32_t)q[c][6] | ((uint32_t)q[c][7] << 16));
+      *reinterpret_cast<uint4*>(out + (long long)(blk * NS + c) * P.ldk + k0) = w;
     }
   } else {
     __nv_fp8_storage_t* out = reinterpret_cast<__nv_fp8_storage_t*>(Pc);
-    float sc = s0[blk];
-    for (int c = 0; c < NS; ++c) {
-      __nv_fp8_storage_t q = 0;
-      if (c < 5) {
-        q = __nv_cvt_float_to_fp8(x * sc, __NV_SATFINITE, __NV_E4M3);
+    uint32_t lo4[NS], hi4[NS];
+#pragma unroll
+    for (int c = 0; c < NS; ++c) { lo4[c] = 0u; hi4[c] = 0u; }
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      float sc = s0[blk], r = x[j];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const __nv_fp8_storage_t qv = __nv_cvt_float_to_fp8(r * sc, __NV_SATFINITE, __NV_E4M3);
         __nv_fp8_e4m3 qq;
-        qq.__x = q;
-        x -= float(qq) / sc;
+        qq.__x = qv;
+        r -= float(qq) / sc;
         sc *= 16.f;
+        if (j < 4) lo4[c] |= (uint32_t)qv << (8 * j);
+        else hi4[c] |= (uint32_t)qv << (8 * (j - 4));
       }
-      out[(long long)(blk * NS + c) * P.ldk + k] = q;
     }
+#pragma unroll
+    for (int c = 0; c < NS; ++c)
+      *reinterpret_cast<uint2*>(out + (long long)(blk * NS + c) * P.ldk + k0) = make_uint2(lo4[c], hi4[c]);
   }
 }
 
@@ -504,34 +533,36 @@ void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]) {
   out[P_ENC_B] = P.b_mn ? 0 : ((P.K + kc * TC_ENC_B_SUB - 1) / (kc * TC_ENC_B_SUB)) * P.tiles_n;
   out[P_FIN] = P.tiles_m + P.tiles_n;
   out[P_SCALE] = P.tiles_m + P.tiles_n;
-  out[P_PIECES] = nkx * (P.tiles_m + P.tiles_n);
+  out[P_PIECES] = ((P.K + 2047) / 2048) * (P.tiles_m + P.tiles_n);  // 8 k per thread
 }
 
 // The encode pass of a batch: B^T for every problem that needs it; with checksums also
 // the block sums, norms, Frobenius norms and pieces.  total[kind] = blocks
 // of each launch over the batch.
-cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS], int* launches,
-                           cudaStream_t st) {
+// bmap: null, or per launch kind the problem of each of its blocks.
+cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS],
+                           const int* const* bmap, int* launches, cudaStream_t st) {
+  auto mp = [&](int kind) -> const int* { return bmap ? bmap[kind] : nullptr; };
   if (!abft) {
     if (total[P_ENC_B] == 0) return cudaSuccess;  // every B is read in place
-    if (dt == 0) tc_encode_b_kernel<0, false><<<total[P_ENC_B], 256, 0, st>>>(b);
-    else tc_encode_b_kernel<1, false><<<total[P_ENC_B], 256, 0, st>>>(b);
+    if (dt == 0) tc_encode_b_kernel<0, false><<<total[P_ENC_B], 256, 0, st>>>(b, mp(P_ENC_B));
+    else tc_encode_b_kernel<1, false><<<total[P_ENC_B], 256, 0, st>>>(b, mp(P_ENC_B));
     ++*launches;
     return cudaGetLastError();
   }
   if (dt == 0) {
-    tc_encode_b_kernel<0, true><<<total[P_ENC_B], 256, 0, st>>>(b);
-    tc_encode_a_kernel<0><<<total[P_ENC_A], 256, 0, st>>>(b);
-    tc_norms_kernel<0><<<total[P_FIN], 256, 0, st>>>(b);
+    tc_encode_b_kernel<0, true><<<total[P_ENC_B], 256, 0, st>>>(b, mp(P_ENC_B));
+    tc_encode_a_kernel<0><<<total[P_ENC_A], 256, 0, st>>>(b, mp(P_ENC_A));
+    tc_norms_kernel<0><<<total[P_FIN], 256, 0, st>>>(b, mp(P_FIN));
   } else {
-    tc_encode_b_kernel<1, true><<<total[P_ENC_B], 256, 0, st>>>(b);
-    tc_encode_a_kernel<1><<<total[P_ENC_A], 256, 0, st>>>(b);
-    tc_norms_kernel<1><<<total[P_FIN], 256, 0, st>>>(b);
-    tc_blockscale_kernel<<<total[P_SCALE], 256, 0, st>>>(b);
+    tc_encode_b_kernel<1, true><<<total[P_ENC_B], 256, 0, st>>>(b, mp(P_ENC_B));
+    tc_encode_a_kernel<1><<<total[P_ENC_A], 256, 0, st>>>(b, mp(P_ENC_A));
+    tc_norms_kernel<1><<<total[P_FIN], 256, 0, st>>>(b, mp(P_FIN));
+    tc_blockscale_kernel<<<total[P_SCALE], 256, 0, st>>>(b, mp(P_SCALE));
     ++*launches;
   }
-  if (dt == 0) tc_pieces_kernel<0><<<total[P_PIECES], 256, 0, st>>>(b);
-  else tc_pieces_kernel<1><<<total[P_PIECES], 256, 0, st>>>(b);
+  if (dt == 0) tc_pieces_kernel<0><<<total[P_PIECES], 256, 0, st>>>(b, mp(P_PIECES));
+  else tc_pieces_kernel<1><<<total[P_PIECES], 256, 0, st>>>(b, mp(P_PIECES));
   *launches += 4;
   return cudaGetLastError();
 }
