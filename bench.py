@@ -978,6 +978,25 @@ def main():
                 "frac_at_measured_clock": achieved / peak_meas if peak_meas else None,
                 "kernel_ms": kern_ms}
 
+    # ---- the encoding pass (Eq. 1-2): e^T A per 128-row block, B e per
+    # 128-column block, row and column norms.  Algorithmic bytes: read A and
+    # B, write the checksum vectors and norms.  Timed on its own through
+    # ftgemm_encode, and inside the GEMM call as call time minus kernel time
+    # (there it also writes A^T for the k-major TMA stream).
+    tm_, tn_ = -(-n // 128), -(-n // 128)
+    Venc = torch.empty(tm_, n, device=dev)
+    Wenc = torch.empty(tn_, n, device=dev)
+    nAe, nBe = torch.empty(n, device=dev), torch.empty(n, device=dev)
+    ms_enc = max_over_ranks(timed_loop(lambda i: h.encode(A, B, 128, 128, Venc, Wenc, nAe, nBe), 5, warm=2))
+    enc_bytes = 4 * (2 * n * n + (tm_ + tn_) * n + 2 * n)
+    hbm = _peaks().get("hbm_gbs")
+    encode_pass = {"algorithmic_bytes": enc_bytes, "standalone_ms": ms_enc,
+                   "standalone_gbs": enc_bytes / (ms_enc / 1e3) / 1e9,
+                   "in_gemm_ms": ms - kern_ms, "in_gemm_gbs": enc_bytes / ((ms - kern_ms) / 1e3) / 1e9,
+                   "peak_gbs": hbm, "standalone_frac": (enc_bytes / (ms_enc / 1e3) / 1e9) / hbm if hbm else None,
+                   "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+    del Venc, Wenc, nAe, nBe
+
     # ---- the same kernel with ABFT off, and torch.matmul ------------------
     ms_off = max_over_ranks(timed_loop(lambda i: step(ft.FT_OFF), args.steps, warm=args.warmup))
     h.set_schedule(SCHED_OFF_BEST)
@@ -1129,6 +1148,7 @@ def main():
                    "uncorrectable": tot["uncorrectable"], "checksum_only": tot["checksum_only"],
                    "poisson_per_min": FAULTS_PER_MIN, "t_kernel_s": t_est, "ranks": world},
         "roofline": roofline,
+        "encode_pass": encode_pass,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": st["launches"],
