@@ -224,7 +224,11 @@ def test_fp64_degenerate_and_ragged_shapes(ft, orc, shape):
     kernels against the oracle, bit-exact on integers, with a fault each."""
     M, N, K = shape
     A, B = _ints((M, K), 301 + M), _ints((K, N), 302 + N)
-    fd = [(0, 0, 0, M - 1, N - 1, 8.0)]
+
+    def last(T, target):  # a fault on the last element, in tile coordinates of tile size T
+        return [((M - 1) // T, (N - 1) // T, 0, (M - 1) % T, (N - 1) % T, 8.0, target)]
+
+    fd = last(ft.DGEMM_TILE, 0)
     h = ft.Handle(0)
     dC = _cuda(np.zeros((M, N)))
     rep = h.dgemm(_cuda(A), _cuda(B), dC, cadence=1, inject=fd)
@@ -232,7 +236,7 @@ def test_fp64_degenerate_and_ragged_shapes(ft, orc, shape):
     assert np.array_equal(dC.cpu().numpy(), res.C)
     assert sorted(map(_key, rep.records)) == sorted(map(_key, res.records))
     Z, W = A + 1j * _ints((M, K), 303), B - 1j * _ints((K, N), 304)
-    fz = [(0, 0, 0, M - 1, N - 1, 8.0, ft.TARGET_IMAG)]
+    fz = last(ft.ZGEMM_TILE, ft.TARGET_IMAG)
     dZ = _cuda(np.zeros((M, N), np.complex128))
     rz = h.zgemm(_cuda(Z), _cuda(W), dZ, cadence=1, inject=fz)
     oz = orc.zgemm_ft(Z, W, tile=64, k_tb=8, cadence=1, faults=fz)
