@@ -1094,6 +1094,15 @@ def main():
     e2e_run(1)  # warm-up
     torch.cuda.synchronize()
     barrier()
+    # the host link on this machine: one upload of A and one download of C (pinned)
+    def copy_gbs(dst, src):
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        dst.copy_(src, non_blocking=True)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        return src.numel() * src.element_size() / (a_.elapsed_time(b_) / 1e3) / 1e9
+    link = {"h2d_gbs": copy_gbs(bufs[1][0], hA), "d2h_gbs": copy_gbs(hOut[0], C)}
     gemm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(e2e_steps)]
     e2e_clocks = ClockSampler(clocks.gpu)
@@ -1112,7 +1121,7 @@ def main():
            "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
            "ms_per_step": ms_e2e, "pipelining": "inputs double-buffered on a copy stream",
            "gemm_ms_mean": sum(gemm_ms) / len(gemm_ms), "gemm_ms_max": max(gemm_ms),
-           "clocks": e2e_clk}
+           "host_link": link, "clocks": e2e_clk}
     del bufs
 
     # ---- configs 4, 5, 3: tensor cores, grouped, irregular (side lines) ----

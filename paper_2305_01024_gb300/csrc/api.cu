@@ -29,6 +29,8 @@ cudaError_t launch_transpose_encode(const float* A, long long lda, int M, int K,
                                     cudaStream_t st);
 cudaError_t launch_copy_pad(const float*, long long, int, int, float*, long long, cudaStream_t);
 long long kmajor_scratch_floats(int K, int L);
+cudaError_t launch_encode_rowmajor(const float* A, long long lda, int M, int K, int m_u, float* V, long long ldv,
+                                   float* nA, float* scratch, int* launches, cudaStream_t st);
 cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*, long long, float*,
                                  float*, int*, cudaStream_t);
 cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, float*, long long,
@@ -1154,19 +1156,14 @@ int ftgemm_encode(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const floa
     FAIL(FTGEMM_ERR_ARG, "ftgemm_encode: bad argument (block sizes must be powers of two in [2,1024])");
   CK(cudaSetDevice(h->device));
   const int M = (int)m, N = (int)n, K = (int)k;
-  const long long ldt = (M + 3) / 4 * 4;
-  const size_t oAt = 0, oScr = align64(oAt + (size_t)K * ldt);
-  const size_t nScr = (size_t)std::max(kmajor_scratch_floats(K, M), kmajor_scratch_floats(K, N));
-  int rc = ensure_ws(h, align64(oScr + nScr));
+  // A is read once in place (no transpose); B is k-major already
+  const size_t nScr = (size_t)std::max<long long>((long long)((K + 255) / 256) * M, kmajor_scratch_floats(K, N));
+  int rc = ensure_ws(h, align64(nScr));
   if (rc) return rc;
   int launches = 0;
-  if (V || nA) {
-    CK(launch_transpose(A, lda, M, K, h->ws + oAt, ldt, h->stream));
-    ++launches;
-    CK(launch_encode_kmajor(h->ws + oAt, ldt, K, M, m_u, V, K, nA, h->ws + oScr, &launches, h->stream));
-  }
+  if (V || nA) CK(launch_encode_rowmajor(A, lda, M, K, m_u, V, K, nA, h->ws, &launches, h->stream));
   if (W || nB)
-    CK(launch_encode_kmajor(B, ldb, K, N, n_u, W, K, nB, h->ws + oScr, &launches, h->stream));
+    CK(launch_encode_kmajor(B, ldb, K, N, n_u, W, K, nB, h->ws, &launches, h->stream));
   h->launches += launches;
   return FTGEMM_OK;
 }

@@ -228,6 +228,67 @@ __global__ void __launch_bounds__(256) colnorm_finish_kernel(const float* __rest
   }
 }
 
+// Row-major A (M x K) read once: V[blk][k] = sum of A[i][k] over the m_u
+// rows of block blk (e^T A per row block, Eq. 1) and squared row-norm
+// partials per 256-column chunk (part[chunk][i], finished by
+// colnorm_finish_kernel).  Block = (chunk, row block); warp w takes rows
+// w, w+8, ..., four rows' loads issued before any is used; lane l the 8
+// columns 8l..8l+7 of the chunk.  Column sums combine over the warps in
+// warp order, so results are reproducible.
+__global__ void __launch_bounds__(256) encode_rowmajor_kernel(const float* __restrict__ A, long long lda, int M,
+                                                              int K, int m_u, int vec, float* __restrict__ V,
+                                                              long long ldv, float* __restrict__ part) {
+  __shared__ float colp[8][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k0 = blockIdx.x * 256 + lane * 8, r0 = blockIdx.y * m_u, r1 = min(M, r0 + m_u);
+  const bool fast = vec && k0 + 8 <= K;
+  float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  auto row8 = [&](int r, float* v) {
+    const float* p = A + (long long)r * lda + k0;
+    if (fast) {
+      const float4 u = __ldg(reinterpret_cast<const float4*>(p)), w = __ldg(reinterpret_cast<const float4*>(p) + 1);
+      v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = k0 + e < K ? p[e] : 0.f;
+    }
+  };
+  auto take = [&](int r, const float* v) {
+    float sq = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      cs[e] += v[e];
+      sq = fmaf(v[e], v[e], sq);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (part && lane == 0) part[(long long)blockIdx.x * M + r] = sq;
+  };
+  int r = r0 + warp;
+  for (; r + 24 < r1; r += 32) {  // four rows of this warp, loads first
+    float v[4][8];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) row8(r + 8 * g, v[g]);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) take(r + 8 * g, v[g]);
+  }
+  for (; r < r1; r += 8) {
+    float v[8];
+    row8(r, v);
+    take(r, v);
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) colp[warp][lane * 8 + e] = cs[e];
+  __syncthreads();
+  const int k = blockIdx.x * 256 + threadIdx.x;
+  if (V && k < K) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += colp[w][threadIdx.x];
+    V[(long long)blockIdx.y * ldv + k] = s;
+  }
+}
+
 // C = alpha * sum_s partial[s] + beta * C   (split-K; the sum is unprotected)
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, int M, int N,
                                      float alpha, float beta, float* C, long long ldc) {
@@ -271,6 +332,23 @@ cudaError_t launch_copy_pad(const float* X, long long ldx, int R, int Cn, float*
                             cudaStream_t st) {
   const long long total = (long long)R * Cn;
   copy_pad_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, ldx, R, Cn, Y, ldy);
+  return cudaGetLastError();
+}
+
+// e^T A per m_u-row block (V, [ceil(M/m_u)][ldv]) and row norms of a
+// row-major A (nA, [M]) reading A once; scratch: ceil(K/256) * M floats
+// when nA is requested.
+cudaError_t launch_encode_rowmajor(const float* A, long long lda, int M, int K, int m_u, float* V, long long ldv,
+                                   float* nA, float* scratch, int* launches, cudaStream_t st) {
+  const int vec = (lda % 4 == 0) && (((uintptr_t)A & 15) == 0);
+  const int chunks = (K + 255) / 256;
+  dim3 g(chunks, (M + m_u - 1) / m_u);
+  encode_rowmajor_kernel<<<g, 256, 0, st>>>(A, lda, M, K, m_u, vec, V, ldv, nA ? scratch : nullptr);
+  *launches += 1;
+  if (nA) {
+    colnorm_finish_kernel<<<(M + 31) / 32, 256, 0, st>>>(scratch, chunks, M, nA);
+    *launches += 1;
+  }
   return cudaGetLastError();
 }
 
