@@ -842,7 +842,16 @@ def irregular_extras(ft, h, synth, dev, timed_loop):
                                                   -(-K // s.k_tb), s.m_tb, s.n_tb, M, N, max(1, s.cadence))
         rep = h.gemm(A, B, C, level=ft.FT_AUTO, inject=[(a, b, ks, r, c, 64.0 * math.sqrt(K))])
         ok = [(x["row"], x["col"], x["kind"]) for x in rep.records] == [(a * s.m_tb + r, b * s.n_tb + c, 0)]
+        # roofline of the shape: the slower of streaming A, B, C once through
+        # HBM (measured copy rate) and the fp32 ALU peak
+        hbm = _peaks().get("hbm_gbs") or 0.0
+        t_hbm = 4.0 * (M * K + K * N + M * N) / (hbm * 1e9) if hbm else 0.0
+        t_alu = fl / (fp32_peak_tflops(152, 2070.0) * 1e12)
+        attain = fl / max(t_hbm, t_alu) / 1e12
         out[f"{M}x{N}x{K}"] = {"tflops": round(fl / (ms / 1e3) / 1e12, 3),
+                               "bound": "hbm" if t_hbm > t_alu else "alu",
+                               "attainable_tflops": round(attain, 3),
+                               "frac_of_attainable": round(fl / (ms / 1e3) / 1e12 / attain, 3),
                                "ft_off_default_tflops": round(fl / (ms_off / 1e3) / 1e12, 3),
                                "torch_fp32_tflops": round(fl / (ms_t / 1e3) / 1e12, 3),
                                "level": [k for k, v in ft.LEVELS.items() if v == lv][0],
