@@ -1388,12 +1388,19 @@ int ftgemm_autotune(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const fl
     if (rc) break;
     std::sort(tried.begin(), tried.end(), [](const std::pair<float, ftgemm_schedule>& a,
                                              const std::pair<float, ftgemm_schedule>& b) { return a.first < b.first; });
-    // 2. split-K for the two fastest tuples while each split keeps >= 8 k-steps
-    const size_t top = std::min<size_t>(2, tried.size());
+    // 2. split-K for every tuple (a large tile with few tiles can be the
+    //    fastest once split) while each split keeps >= 8 k-steps and the
+    //    CTAs stay within 16 per SM; not only powers of two, so that
+    //    tiles x splits can fill the SMs without a nearly empty last wave
+    static const int kSplits[] = {2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 48, 64, 96, 128};
+    const size_t top = tried.size();
+    const int64_t max_ctas = 16LL * (h->num_sms > 0 ? h->num_sms : 148);
     for (size_t q = 0; q < top && !rc; ++q) {
       const ftgemm_schedule base = tried[q].second;
       const int64_t ksteps = (k + base.k_tb - 1) / base.k_tb;
-      for (int split = 2; split <= 64 && ksteps / split >= 8; split *= 2) {
+      const int64_t tiles = ((m + base.m_tb - 1) / base.m_tb) * ((n + base.n_tb - 1) / base.n_tb);
+      for (int split : kSplits) {
+        if (ksteps / split < 8 || tiles * split > max_ctas) break;
         ftgemm_schedule s = base;
         s.split_k = split;
         float ms;

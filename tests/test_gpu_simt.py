@@ -195,6 +195,24 @@ def test_split_k_exact(ft, handle, orc):
     assert rep.corrected == 3
 
 
+@pytest.mark.parametrize("split", [3, 5, 6])
+def test_split_k_not_a_power_of_two(ft, handle, orc, split):
+    """Split counts the autotuner may pick to fill the SMs' CTA slots, on a
+    ragged K: every split verifies its own partial, faults near split edges."""
+    M, N = 200, 130
+    K = 16 * 301 + 7  # 302 k-steps of 16, the last one short
+    A = synth.integers((M, K), 95 + split)
+    B = synth.integers((K, N), 96 + split)
+    s = _sched("wide", cadence=8, split_k=split)
+    per = -(-302 // split)
+    faults = [(0, 0, per - 1, 3, 4, 256.0), (1, 1, per, 70, 1, -512.0), (0, 1, 301, 127, 1, 1024.0)]
+    C, rep = _run(ft, handle, A, B, np.zeros((M, N), np.float32), 1.0, 0.0, 3, s, faults)
+    res = orc.gemm_ft(A, B, _oracle_sched(orc, s, 3), faults=faults)
+    assert np.array_equal(C, A.astype(np.int64) @ B.astype(np.int64))
+    _compare_exact(rep, res)
+    assert rep.corrected == 3
+
+
 def test_degenerate_shapes(ft, handle, orc):
     for (M, N, K) in [(1, 1, 1), (1, 5, 3), (7, 1, 2), (3, 3, 17)]:
         A = synth.integers((M, K), 100 + M)
