@@ -120,7 +120,14 @@ struct TcSmemTail {
   float tr[128], tc[256];          // thresholds
   int flag_r[128], flag_c[256];
   double sum_r[128], sum_c[256];   // fp64 confirmation sums
+  // per epilogue warp: its 32 rows x 16 columns of one accumulator chunk,
+  // rows 80 bytes apart (16-byte writes of 8 consecutive rows hit distinct
+  // banks), read back row-segment-wise so that C is written in 64-byte runs
+  alignas(16) float stg[4][32][20];
 };
+
+static_assert(1024 + TC_STAGES * TcCfg<0, true>::STAGE_BYTES + sizeof(TcSmemTail) <= 227 * 1024,
+              "dynamic shared memory within the 227 KB a CTA may use");
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -359,19 +366,27 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       tc_fence_after();
       const bool row_ok = ok && data_row && gr < pM;
       float* crow_ptr = Cp + (long long)(row_ok ? gr : 0) * ldc + col0;
-      // alpha * acc + beta * C of one 16-column chunk of this row, data
-      // columns inside the matrix only
-      auto store16 = [&](int ch, const float* v) {
+      // alpha * acc + beta * C of one 16-column chunk of the warp's 32 rows,
+      // rows and columns inside the matrix only.  The chunk goes through the
+      // warp's staging tile: lane l then writes 16 bytes of row 8s + l/4
+      // (s = 0..3), so each store instruction covers 8 rows x 64 bytes
+      // instead of 32 rows x 16 bytes.  All lanes call it.
+      auto store16w = [&](int ch, const float* v) {
+        float(*S)[20] = T.stg[lq];
 #pragma unroll
-        for (int q = 0; q < 16; q += 4) {
-          const int c = ch * 16 + q;  // tile column of this group of 4
-          if (c >= DN) break;
-          const int gc = col0 + c;
-          float* dst = crow_ptr + c;
-          // col0 and c are multiples of 4: a 16-byte aligned row gives an aligned float4
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<float4*>(&S[lane][4 * q]) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int sgrp = 0; sgrp < 4; ++sgrp) {
+          const int rr = 8 * sgrp + (lane >> 2), cq = lane & 3;
+          const int tr_ = lq * 32 + rr, gr_ = row0 + tr_;  // tile row, matrix row
+          const float4 x = *reinterpret_cast<const float4*>(&S[rr][4 * cq]);
+          const int c = ch * 16 + 4 * cq, gc = col0 + c;
+          if (!ok || tr_ >= DM || gr_ >= pM || c >= DN) continue;
+          float* dst = Cp + (long long)gr_ * ldc + gc;
           if (c_vec && c + 3 < DN && gc + 3 < pN) {
-            float4 o = unit_sc ? make_float4(v[q], v[q + 1], v[q + 2], v[q + 3])
-                               : make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
+            float4 o = unit_sc ? x : make_float4(sc * x.x, sc * x.y, sc * x.z, sc * x.w);
             if (beta != 0.f) {
               const float4 ci = *reinterpret_cast<const float4*>(dst);
               o.x = fmaf(beta, ci.x, o.x); o.y = fmaf(beta, ci.y, o.y);
@@ -379,15 +394,17 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
             }
             *reinterpret_cast<float4*>(dst) = o;
           } else {
+            const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               if (c + e < DN && gc + e < pN) {
-                const float o = sc * v[q + e];
+                const float o = sc * xs[e];
                 dst[e] = beta != 0.f ? fmaf(beta, dst[e], o) : o;
               }
             }
           }
         }
+        __syncwarp();  // the tile is refilled by the next chunk
       };
 
       if constexpr (ABFT) {
@@ -443,7 +460,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           float v[16];
           tmem_ld16(tl + ch * 16, v);
           tmem_wait_ld();
-          if (row_ok) store16(ch, v);
+          store16w(ch, v);
         }
       } else {
         epi_bar();
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
 #pragma unroll
             for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
           }
-          if (row_ok) store16(ch, v);
+          store16w(ch, v);
           // warp partial column sums over the data rows: a reduce-scatter
           // over the lanes leaves lanes 2q and 2q+1 with column idx(q)
           float w[16];
