@@ -41,6 +41,7 @@
 #include <cuda_fp8.h>
 
 #include <climits>
+#include <cstddef>
 
 #include "internal.cuh"
 #include "mlp.cuh"
@@ -112,7 +113,7 @@ struct TcSmemTail {
   int fix_row[2], fix_col[2];      // per accumulator parity
   double fix_delta[2];
   unsigned int sink_max;           // residual sink: largest residual / (u * norms) of the tile
-  float colpart[4][256];           // per epilogue warp partial column sums (data rows)
+  alignas(16) float colpart[4][256];  // per epilogue warp partial column sums (data rows); float4 stores
   float ccp[TC_CS_SLOTS][256];     // column-checksum pieces, TMEM lanes 120..127
   float crow[128];                 // row checksums
   float ccol[256];                 // column checksums
@@ -126,6 +127,8 @@ struct TcSmemTail {
   alignas(16) float stg[4][32][20];
 };
 
+static_assert(offsetof(TcSmemTail, colpart) % 16 == 0 && offsetof(TcSmemTail, stg) % 16 == 0,
+              "vector stores into the epilogue's shared arrays");
 static_assert(1024 + TC_STAGES * TcCfg<0, true>::STAGE_BYTES + sizeof(TcSmemTail) <= 227 * 1024,
               "dynamic shared memory within the 227 KB a CTA may use");
 
@@ -371,17 +374,27 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       // warp's staging tile: lane l then writes 16 bytes of row 8s + l/4
       // (s = 0..3), so each store instruction covers 8 rows x 64 bytes
       // instead of 32 rows x 16 bytes.  All lanes call it.
+      // With checksums it also leaves, in T.colpart[lq], the sums of the
+      // chunk's 16 columns over the warp's data rows: each lane adds its 4
+      // rows of 4 columns, then an xor tree over the 8 lanes of a column
+      // group.
       auto store16w = [&](int ch, const float* v) {
         float(*S)[20] = T.stg[lq];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           *reinterpret_cast<float4*>(&S[lane][4 * q]) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         __syncwarp();
+        float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int sgrp = 0; sgrp < 4; ++sgrp) {
           const int rr = 8 * sgrp + (lane >> 2), cq = lane & 3;
           const int tr_ = lq * 32 + rr, gr_ = row0 + tr_;  // tile row, matrix row
           const float4 x = *reinterpret_cast<const float4*>(&S[rr][4 * cq]);
+          if constexpr (ABFT) {
+            if (tr_ < DM) {
+              cs.x += x.x; cs.y += x.y; cs.z += x.z; cs.w += x.w;
+            }
+          }
           const int c = ch * 16 + 4 * cq, gc = col0 + c;
           if (!ok || tr_ >= DM || gr_ >= pM || c >= DN) continue;
           float* dst = Cp + (long long)gr_ * ldc + gc;
@@ -403,6 +416,16 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
               }
             }
           }
+        }
+        if constexpr (ABFT) {
+#pragma unroll
+          for (int o = 4; o < 32; o <<= 1) {
+            cs.x += __shfl_xor_sync(0xffffffffu, cs.x, o);
+            cs.y += __shfl_xor_sync(0xffffffffu, cs.y, o);
+            cs.z += __shfl_xor_sync(0xffffffffu, cs.z, o);
+            cs.w += __shfl_xor_sync(0xffffffffu, cs.w, o);
+          }
+          if (lane < 4) *reinterpret_cast<float4*>(&T.colpart[lq][ch * 16 + 4 * lane]) = cs;
         }
         __syncwarp();  // the tile is refilled by the next chunk
       };
@@ -510,28 +533,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
 #pragma unroll
             for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
           }
-          store16w(ch, v);
-          // warp partial column sums over the data rows: a reduce-scatter
-          // over the lanes leaves lanes 2q and 2q+1 with column idx(q)
-          float w[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) w[q] = data_row ? v[q] : 0.f;
-#pragma unroll
-          for (int lev = 16, half = 8; lev >= 2; lev >>= 1, half >>= 1) {
-            const bool up = (lane & lev) != 0;
-#pragma unroll
-            for (int q = 0; q < half; ++q) {
-              const float snd = up ? w[q] : w[q + half];
-              const float kp = up ? w[q + half] : w[q];
-              w[q] = kp + __shfl_xor_sync(0xffffffffu, snd, lev);
-            }
-          }
-          w[0] += __shfl_xor_sync(0xffffffffu, w[0], 1);
-          if ((lane & 1) == 0) {
-            const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                            ((lane >> 1) & 1);
-            T.colpart[lq][ch * 16 + idx] = w[0];
-          }
+          store16w(ch, v);  // also the warp's column partial sums of the chunk
         }
         crow += T.cradj[r];
         T.crow[r] = crow;
