@@ -236,7 +236,10 @@ int ftgemm_quantize(ftgemm_handle_t handle, int64_t n, const float* x, void* y,
  * of the tile are verified once, after its last k-step, from tensor memory;
  * injected faults are applied to the tensor-memory accumulator at that
  * point (the accumulation being additive, the k-step of a fault changes
- * only rounding); E4M3 results are scaled by ftgemm_set_fp8_scales. */
+ * only rounding); E4M3 results are scaled by ftgemm_set_fp8_scales.  B may
+ * have any alignment: at level OFF a BF16 B with a 16-byte aligned base and
+ * row stride is read in place, otherwise the call first writes a transposed
+ * copy into the handle's workspace. */
 int ftgemm_gemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                 double alpha, const void* A, int64_t lda, const void* B,
                 int64_t ldb, double beta, float* C, int64_t ldc,
