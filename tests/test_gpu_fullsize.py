@@ -4,7 +4,8 @@ row holding a fault among them), and every fault located and corrected.
 
 * config 2: 16384^3 fp32, block-level checksums on the 128 x 128 x 16 tile
   (16 x 8 fragments), verification every 256 of K, alpha 1, beta 0.5;
-* config 4: 16384^3 bf16, tile-level checksums through the tensor cores;
+* config 4: 16384^3 bf16 and e4m3, tile-level checksums through the tensor
+  cores (e4m3: the quantizer against the oracle's on sampled rows);
 * config 5: the 512-problem bf16 group, one persistent launch, 1% of tiles
   faulted; sampled problems compared in full.
 """
@@ -140,4 +141,53 @@ def test_config5_full_group_sampled_problems(ft, orc):
                 slack[x["row"], x["col"]] = x["tau"]
         assert np.all(np.abs(got - ref) <= bound + slack)
     g.close()
+    h.close()
+
+
+def test_config4_full_size_e4m3_sampled_rows(ft, orc):
+    """Config 4 in fp8: 16384^3 N(0,1) quantized to E4M3 with per-tensor
+    scales, checksums through the MMA, 16 faults.  The quantizer matches the
+    oracle's on sampled rows (the sample carries the tensor's largest
+    element, so the per-tensor scale is the same); every fault is located
+    and corrected; sampled rows of C match the oracle's product of the
+    oracle-quantized operands."""
+    import torch
+    n = 16384
+    tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 128
+    pos = synth.fault_positions(synth.config_seed(4, 23), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    where = [(a * 120 + r, b * 248 + c) for (a, b, ks, r, c) in pos]
+    rows = _rows(synth.config_seed(4, 22), n, [i for i, _ in where])
+    Af = synth.torch_make("normal", (n, n), synth.config_seed(4, 20), "cuda")
+    Bf = synth.torch_make("normal", (n, n), synth.config_seed(4, 21), "cuda")
+    h = ft.Handle(0)
+    A8, sa = h.quantize(Af, ft.E4M3)
+    B8, sb = h.quantize(Bf, ft.E4M3)
+    h.set_fp8_scales(sa, sb)
+    # the oracle quantizes the sampled rows of A together with A's largest
+    # element (so its per-tensor scale is A's), and all of B
+    amax_idx = int(torch.argmax(Af.abs()).item())
+    sample = np.concatenate([Af[rows].cpu().numpy().ravel(), Af.view(-1)[amax_idx:amax_idx + 1].cpu().numpy()])
+    Bh = Bf.cpu().numpy()
+    del Af, Bf
+    _, q_s, sa_orc = orc.quant_e4m3(sample)
+    _, Bq, sb_orc = orc.quant_e4m3(Bh)
+    assert np.float32(sa) == np.float32(sa_orc) and np.float32(sb) == np.float32(sb_orc)
+    Aq = q_s[:-1].reshape(len(rows), n)
+    got_codes = A8[rows].cpu().view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(got_codes, Aq)
+    # offsets of 64 sqrt(K) in value units, i.e. / (sa sb) in units of the
+    # accumulated code products
+    faults = [(a, b, ks, r, c, float(64 * math.sqrt(n) / (sa * sb))) for (a, b, ks, r, c) in pos]
+    C = torch.empty(n, n, device="cuda")
+    rep = h.gemm(A8, B8, C, level=ft.FT_TILE, dtype=ft.E4M3, inject=faults)
+    torch.cuda.synchronize()
+    assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
+    scale = np.float64(np.float32(sa)) * np.float64(np.float32(sb))
+    ref = orc.gemm_ref(Aq, Bq) * scale
+    got = C[rows].cpu().numpy().astype(np.float64)
+    bound = (2 * n * U32 * (np.abs(Aq) @ np.abs(Bq))) * scale + 4 * U32 * np.abs(ref)
+    slack = np.zeros_like(got)
+    for x in rep.records:
+        slack[rows.index(x["row"]), x["col"]] = x["tau"] * scale
+    assert np.all(np.abs(got - ref) <= bound + slack)
     h.close()
