@@ -23,6 +23,7 @@ cudaError_t simt_launch_tall(int, const SimtMaps&, const SimtParams&, int, cudaS
 cudaError_t simt_launch_huge(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_huge16(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_wide(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_wide32(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t launch_transpose(const float*, long long, int, int, float*, long long, cudaStream_t);
 cudaError_t launch_transpose_encode(const float* A, long long lda, int M, int K, float* At, long long ldt, int m_u,
                                     float* V, long long ldv, float* nrm, float* scratch, int* launches,
@@ -71,6 +72,7 @@ struct SimtConfig {
 };
 static const SimtConfig kSimtConfigs[] = {
     {"wide", 128, 128, 16, 64, 64, 16, 8, simt_launch_wide},
+    {"wide32", 128, 128, 32, 64, 64, 16, 8, simt_launch_wide32},
     {"huge16", 128, 128, 16, 32, 64, 8, 8, simt_launch_huge16},
     {"huge", 128, 128, 8, 32, 64, 8, 8, simt_launch_huge},
     {"large", 64, 64, 8, 32, 64, 8, 8, simt_launch_large},
@@ -196,7 +198,9 @@ static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
   const int sms = h->num_sms > 0 ? h->num_sms : 152;
   const SimtConfig* pick = nullptr;
   for (const auto& c : kSimtConfigs) {
-    if (c.launch == simt_launch_huge) continue;  // the k_tb=8 variant only on request
+    // the k_tb=8 variant and the two-stage k_tb=32 one only on request (or
+    // through the autotuner): the latter wins only for long K at block level
+    if (c.launch == simt_launch_huge || c.launch == simt_launch_wide32) continue;
     // on the 128 x 128 tile, 16 x 8 fragments win with checksums (fewer
     // shared-memory wavefronts per FMA leave room for the checksum loads),
     // 8 x 8 fragments without

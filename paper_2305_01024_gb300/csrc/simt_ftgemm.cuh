@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   // BLOCK on the 128 x 128 tile: checksums kept in shared memory (see below)
   constexpr int NSIDE = T::NWARP / 2;  // warps per checksum side
   constexpr bool kSCS = LEVEL == L_BLOCK && MT == 128 && NT == 128 && (NSIDE == 2 || NSIDE == 4) &&
-                        KT % NSIDE == 0 && (KT / NSIDE == 2 || KT / NSIDE == 4 || KT / NSIDE == 8);
+                        KT % NSIDE == 0 && (KT / NSIDE == 2 || KT / NSIDE == 4 || KT / NSIDE == 8 || KT / NSIDE == 16);
   constexpr int KQ = kSCS ? KT / NSIDE : 1;
   float cr[LEVEL == L_THREAD ? TM : 1], cc[LEVEL == L_THREAD ? TN : 1];
   float wr[LEVEL == L_WARP ? RPL : 1], wc[LEVEL == L_WARP ? CPL : 1];

@@ -10,7 +10,7 @@ import synth
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 SHAPES = [(16384, 16384, 32), (20480, 256, 20480), (256, 256, 65536), (4096, 96, 4096), (777, 1531, 2049)]
-TUPLES = {(128, 128, 16, 64, 64, 16, 8), (128, 128, 16, 32, 64, 8, 8), (128, 128, 8, 32, 64, 8, 8),
+TUPLES = {(128, 128, 16, 64, 64, 16, 8), (128, 128, 32, 64, 64, 16, 8), (128, 128, 16, 32, 64, 8, 8), (128, 128, 8, 32, 64, 8, 8),
           (64, 64, 8, 32, 64, 8, 8), (32, 128, 8, 16, 64, 4, 8), (32, 32, 8, 16, 32, 4, 4),
           (16, 16, 16, 8, 16, 2, 2)}
 

@@ -2,8 +2,9 @@
 times, on outputs the oracle computes one by one: sampled rows of C (every
 row holding a fault among them), and every fault located and corrected.
 
-* config 2: 16384^3 fp32, block-level checksums on the 128 x 128 x 16 tile
-  (16 x 8 fragments), verification every 256 of K, alpha 1, beta 0.5;
+* config 2: 16384^3 fp32, block-level checksums on the 128 x 128 tile with
+  16 x 8 fragments and k-steps of 32, verification every 256 of K, alpha 1,
+  beta 0.5;
 * config 4: 16384^3 bf16 and e4m3, tile-level checksums through the tensor
   cores (e4m3: the quantizer against the oracle's on sampled rows);
 * config 5: the 512-problem bf16 group, one persistent launch, 1% of tiles
@@ -36,12 +37,12 @@ def _rows(seed, M, extra):
 def test_config2_full_size_sampled_rows(ft, orc):
     import torch
     n = 16384
-    sched = dict(m_tb=128, n_tb=128, k_tb=16, m_w=64, n_w=64, m_t=16, n_t=8, cadence=16, split_k=1)
+    sched = dict(m_tb=128, n_tb=128, k_tb=32, m_w=64, n_w=64, m_t=16, n_t=8, cadence=8, split_k=1)
     A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 0), "cuda")
     B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 1), "cuda")
     C0 = synth.torch_make("uniform", (n, n), synth.config_seed(2, 2), "cuda")
-    tiles, ksteps = n // 128, n // 16
-    pos = synth.fault_positions(synth.config_seed(2, 70), 6, tiles, tiles, ksteps, 128, 128, n, n, 16)
+    tiles, ksteps = n // 128, n // 32
+    pos = synth.fault_positions(synth.config_seed(2, 70), 6, tiles, tiles, ksteps, 128, 128, n, n, 8)
     mags = synth.log_uniform(synth.config_seed(2, 71), 6, 1e-1, 1e3)
     faults = [(tm, tn, ks, r, c, float(g * 4 * math.sqrt(n / 9))) for (tm, tn, ks, r, c), g in zip(pos, mags)]
     h = ft.Handle(0)

@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 
 TUPLES = {
     "wide": (128, 128, 16, 64, 64, 16, 8),
+    "wide32": (128, 128, 32, 64, 64, 16, 8),
     "huge16": (128, 128, 16, 32, 64, 8, 8),
     "huge": (128, 128, 8, 32, 64, 8, 8),
     "large": (64, 64, 8, 32, 64, 8, 8),
