@@ -984,7 +984,7 @@ def main():
     peak_meas = fp32_peak_tflops(sms, clk["sm_mhz"]) if clk.get("sm_mhz") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_spec, "unit": "TFLOP/s",
                 "frac": achieved / peak_spec, "traffic": committed_traffic("simt_ftgemm_block_wide_16384"),
-                "kernel": "simt_ftgemm_kernel<128x128x32 (m_t=16, n_t=8, 2 stages), BLOCK>",
+                "kernel": "simt_ftgemm_kernel<128x128x32 (m_t=16, n_t=8, 3 stages), BLOCK>",
                 "peak_basis": f"fp32 CUDA cores: {sms} SMs x 128 x 2 flop x 2070 MHz (max SM clock)",
                 "peak_at_measured_clock": peak_meas,
                 "frac_at_measured_clock": achieved / peak_meas if peak_meas else None,

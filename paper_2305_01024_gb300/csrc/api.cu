@@ -198,7 +198,7 @@ static int default_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
   const int sms = h->num_sms > 0 ? h->num_sms : 152;
   const SimtConfig* pick = nullptr;
   for (const auto& c : kSimtConfigs) {
-    // the k_tb=8 variant and the two-stage k_tb=32 one only on request (or
+    // the k_tb=8 variant and the k_tb=32 one only on request (or
     // through the autotuner): the latter wins only for long K at block level
     if (c.launch == simt_launch_huge || c.launch == simt_launch_wide32) continue;
     // on the 128 x 128 tile, 16 x 8 fragments win with checksums (fewer
