@@ -15,6 +15,9 @@
  * Conventions used by every entry point
  *   - All matrices are row-major.  A is M x K (leading dimension lda >= K),
  *     B is K x N (ldb >= N), C is M x N (ldc >= N), in elements.
+ *   - Sizes are at least 1 and at most INT32_MAX.  An empty product (M, N
+ *     or K equal to 0) is rejected with FTGEMM_ERR_ARG before any work is
+ *     enqueued, not run as a no-op; the handle stays usable.
  *   - Matrix pointers are DEVICE pointers owned by the caller.  Host pointers
  *     (schedules, injection arrays, reports) are read or written during the
  *     call only.

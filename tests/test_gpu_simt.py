@@ -245,6 +245,25 @@ def test_argument_errors(ft, handle):
     assert e.value.status == ft.ERR_UNSUPPORTED
 
 
+def test_empty_operands_rejected(ft, handle):
+    # an empty product is an argument error (M, N or K of 0), raised before
+    # any work is enqueued; the handle computes normally afterwards
+    import torch
+    for M, N, K in ((0, 8, 8), (8, 0, 8), (8, 8, 0)):
+        A = torch.zeros(M, K, device="cuda")
+        B = torch.zeros(K, N, device="cuda")
+        C = torch.zeros(M, N, device="cuda")
+        with pytest.raises(ft.FtgemmError) as e:
+            handle.gemm(A, B, C)
+        assert e.value.status == ft.ERR_ARG
+    A = synth.integers((40, 24), 900)
+    B = synth.integers((24, 56), 901)
+    C = torch.zeros(40, 56, device="cuda")
+    rep = handle.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C)
+    assert rep.detected == 0
+    assert np.array_equal(C.cpu().numpy(), A.astype(np.int64) @ B.astype(np.int64))
+
+
 # ---------------------------------------------------------------------------
 # floating-point inputs
 # ---------------------------------------------------------------------------
