@@ -184,7 +184,8 @@ static int ensure_faults(ftgemm_ctx* h, int n) {
   if (h->h_faults) CK(cudaFreeHost(h->h_faults));
   h->d_faults = nullptr;
   h->h_faults = nullptr;
-  int cap = std::max(n, 2 * h->faults_cap);
+  const int cap = std::max(n, 2 * h->faults_cap);
+  h->faults_cap = 0;  // nothing usable until both buffers exist
   CK(cudaMalloc(&h->d_faults, sizeof(Fault) * cap));
   CK(cudaHostAlloc(&h->h_faults, sizeof(Fault) * cap, cudaHostAllocDefault));
   h->faults_cap = cap;
@@ -904,16 +905,16 @@ int ftgemm_create(ftgemm_handle_t* handle, int device, void* cuda_stream) {
   h->stream = (cudaStream_t)cuda_stream;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) h->num_sms = prop.multiProcessorCount;
-  if (cudaMalloc(&h->rep, sizeof(DevReport)) != cudaSuccess ||
-      cudaMalloc(&h->recs, sizeof(ftgemm_fault_record) * h->rep_cap) != cudaSuccess ||
-      cudaMemset(h->rep, 0, sizeof(DevReport)) != cudaSuccess) {
-    delete h;
-    FAIL(FTGEMM_ERR_CUDA, "ftgemm_create: cannot allocate the report ring");
-  }
   DevReport r{};
   r.capacity = h->rep_cap;
-  CK(cudaMemcpy(h->rep, &r, sizeof(r), cudaMemcpyHostToDevice));
-  CK(cudaEventCreateWithFlags(&h->faults_free, cudaEventDisableTiming));
+  cudaError_t e = cudaMalloc(&h->rep, sizeof(DevReport));
+  if (e == cudaSuccess) e = cudaMalloc(&h->recs, sizeof(ftgemm_fault_record) * h->rep_cap);
+  if (e == cudaSuccess) e = cudaMemcpy(h->rep, &r, sizeof(r), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->faults_free, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    ftgemm_destroy(h);  // releases whatever was allocated
+    FAIL(FTGEMM_ERR_CUDA, "ftgemm_create: cannot set up the report ring: %s", cudaGetErrorString(e));
+  }
   *handle = h;
   return FTGEMM_OK;
 }
@@ -1006,6 +1007,7 @@ int ftgemm_set_residual_sink(ftgemm_handle_t h, float* lam_needed, float* featur
 
 static int ensure_mlp_ws(ftgemm_ctx* h, size_t floats) {
   if (floats <= h->mlp_ws_floats) return FTGEMM_OK;
+  CK(cudaStreamSynchronize(h->stream));  // earlier launches may still read it
   if (h->mlp_ws) CK(cudaFree(h->mlp_ws));
   h->mlp_ws = nullptr;
   h->mlp_ws_floats = 0;
