@@ -321,6 +321,65 @@ def test_e4m3_quantization_matches_torch(orc):
     assert np.abs(q).max() == 448.0
 
 
+def test_bf16_hand_worked_values(orc):
+    # bf16: 8 exponent bits (as fp32), 7 stored mantissa bits, round to
+    # nearest with ties to the even mantissa.  Spacing is 2^-7 on [1, 2),
+    # 2 on [256, 512) and 2^-133 among the subnormals.
+    cases = [
+        (1.0 + 2.0 ** -8, 1.0),                      # tie: mantissa 0 (even) wins
+        (1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -6),      # tie between 1 (odd) and 2 (even)
+        (1.0 + 2.0 ** -8 + 2.0 ** -16, 1.0 + 2.0 ** -7),  # just above the tie
+        (256.5, 256.0),
+        (257.0, 256.0),                              # tie between 256 and 258
+        (259.0, 260.0),                              # tie between 258 and 260
+        (-3.0, -3.0),
+        (2.0 ** -130, 2.0 ** -130),                  # subnormal, representable
+        (1.5 * 2.0 ** -133, 2.0 ** -132),            # subnormal tie to even
+        ((2.0 - 2.0 ** -7) * 2.0 ** 127, (2.0 - 2.0 ** -7) * 2.0 ** 127),  # largest finite
+        (0.0, 0.0),
+    ]
+    x = np.array([c[0] for c in cases], dtype=np.float32)
+    assert np.array_equal(x.astype(np.float64), [c[0] for c in cases])  # inputs exact in fp32
+    assert list(orc.round_bf16(x)) == [c[1] for c in cases]
+    # 0.1f = 1.6000000238 * 2^-4: 204.80000305 / 128 rounds to 205 / 128
+    assert orc.round_bf16(np.array([0.1], np.float32))[0] == 205 / 128 * 2.0 ** -4
+
+
+def test_e4m3_hand_worked_values(orc):
+    # OCP FP8 E4M3: bias 7, 3 mantissa bits, largest finite 1.75 * 2^8 = 448,
+    # smallest normal 2^-6, subnormal spacing 2^-9; round to nearest even,
+    # saturating.  448 is in the input, so the per-tensor scale
+    # amax / 448 is exactly 1 and q holds the codes' values directly.
+    cases = [
+        (448.0, 448.0),
+        (1.0625, 1.0),                  # tie between 1.0 (even) and 1.125
+        (1.1875, 1.25),                 # tie between 1.125 (odd) and 1.25
+        (17.0, 16.0),                   # spacing 2 on [16, 32): tie to 16
+        (19.0, 20.0),
+        (240.0, 240.0),                 # 1.875 * 2^7, exact
+        (248.0, 256.0),                 # tie between 240 (odd) and 256 (even)
+        (440.0, 448.0),                 # above the 432 midpoint
+        (0.3, 0.3125),                  # spacing 2^-5 on [0.25, 0.5): 9.6 -> 10
+        (2.0 ** -9, 2.0 ** -9),         # smallest subnormal
+        (2.0 ** -10, 0.0),              # tie between 0 (even) and 2^-9
+        (3 * 2.0 ** -10, 2.0 ** -8),    # tie between 1 and 2 subnormal steps
+        (7 * 2.0 ** -9, 7 * 2.0 ** -9),  # largest subnormal
+        (7.5 * 2.0 ** -9, 2.0 ** -6),   # tie into the smallest normal
+        (-1.0625, -1.0),
+        (0.0, 0.0),
+    ]
+    x = np.array([c[0] for c in cases], dtype=np.float32)
+    deq, q, scale = orc.quant_e4m3(x)
+    assert scale == 1.0
+    assert list(q) == [c[1] for c in cases]
+    assert np.array_equal(deq, q)
+    # a scale of 2: amax 896 maps to 448, and the codes are those of x / 2
+    # (-150: spacing 16 on [128, 256), 9.375 -> 9; 50: spacing 4, 12.5 -> 12)
+    y = np.array([896.0, -300.0, 100.0], np.float32)
+    _, qy, sy = orc.quant_e4m3(y)
+    assert sy == 2.0 and list(qy) == [448.0, -144.0, 48.0]
+
+
 # --------------------------------------------------------------------------
 # Section 5.5 cost model vs a Monte-Carlo simulation of the restart process
 # --------------------------------------------------------------------------
