@@ -281,6 +281,25 @@ typedef struct ftgemm_group* ftgemm_group_t;
 int ftgemm_group_create(ftgemm_handle_t handle, int32_t count, const ftgemm_problem* problems,
                         ftgemm_dtype dtype, ftgemm_ft_level ft_level, ftgemm_group_t* out);
 
+/* The static schedule ftgemm_group_create builds, computed on the host
+ * alone: no handle, no device work (no counterpart in the paper).  m, n, k:
+ * host arrays of `count` problem sizes; dtype and ft_level as for
+ * ftgemm_group_create; ncta: the persistent CTAs (ftgemm_group_create uses
+ * min(total tiles, SM count)).  Problems are taken longest-K first (stable),
+ * each problem's tiles in the kernel's raster (groups of 16 tile rows,
+ * column by column inside a group), and each tile goes to the CTA with the
+ * least work so far, a tile costing max(k-blocks, 6)
+ * (longest-processing-time greedy).  Output: *total_tiles; if `tiles` is not
+ * NULL, 4 * total_tiles int32 {problem (the caller's index), tile_m, tile_n,
+ * k-blocks} listed CTA by CTA, each CTA's tiles in the order it runs them;
+ * if `cta_start` is not NULL, ncta + 1 offsets: CTA c runs entries
+ * cta_start[c] .. cta_start[c+1] - 1.  Both NULL: a size query.  Errors:
+ * FTGEMM_ERR_ARG (NULL, sizes, ncta < 1, more than INT32_MAX tiles),
+ * FTGEMM_ERR_UNSUPPORTED (dtype, level). */
+int ftgemm_group_plan(int32_t count, const int64_t* m, const int64_t* n, const int64_t* k,
+                      ftgemm_dtype dtype, ftgemm_ft_level ft_level, int32_t ncta, int32_t* tiles,
+                      int32_t* cta_start, int32_t* total_tiles);
+
 /* Tile grid of each problem (caller arrays of `count`): 120 x 248 tiles of C
  * at level TILE, 128 x 256 at OFF. */
 int ftgemm_group_tiles(ftgemm_group_t group, int32_t* tiles_m, int32_t* tiles_n);

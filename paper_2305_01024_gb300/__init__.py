@@ -119,6 +119,8 @@ def lib():
     L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.ftgemm_group_create.argtypes = [vp, i32, C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(vp)]
     L.ftgemm_group_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.ftgemm_group_plan.argtypes = [i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.c_int, C.c_int, i32,
+                                    C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.ftgemm_group_set_faults.argtypes = [vp, C.POINTER(i32), C.POINTER(InjectSpec)]
     L.ftgemm_grouped_gemm.argtypes = [vp, vp]
     L.ftgemm_group_destroy.argtypes = [vp]
@@ -144,7 +146,7 @@ def lib():
                "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
-               "ftgemm_group_create", "ftgemm_group_tiles", "ftgemm_group_set_faults",
+               "ftgemm_group_create", "ftgemm_group_plan", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
                "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune",
                "ftgemm_selftest_wait", "ftgemm_gemm_offline", "ftgemm_gemm_nonfused", "ftgemm_dgemm",
@@ -425,6 +427,25 @@ class Handle:
         _, N = B.shape
         _check(lib().ftgemm_encode(self._h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
                                    m_u, n_u, _ptr(V), _ptr(W), _ptr(nA), _ptr(nB)))
+
+
+def group_plan(shapes, dtype=BF16, level=FT_TILE, ncta: int = 152):
+    """The static tile schedule ftgemm_group_create would build for problems
+    of sizes shapes = [(m, n, k), ...] over `ncta` persistent CTAs, computed
+    on the host (ftgemm_group_plan).  Returns (tiles, cta_start): tiles is a
+    list of (problem, tile_m, tile_n, k_blocks) listed CTA by CTA, and CTA c
+    runs tiles[cta_start[c]:cta_start[c + 1]]."""
+    count = len(shapes)
+    m = (C.c_int64 * max(1, count))(*[s[0] for s in shapes])
+    n = (C.c_int64 * max(1, count))(*[s[1] for s in shapes])
+    k = (C.c_int64 * max(1, count))(*[s[2] for s in shapes])
+    total = C.c_int32(0)
+    _check(lib().ftgemm_group_plan(count, m, n, k, dtype, level, ncta, None, None, C.byref(total)))
+    tiles = (C.c_int32 * (4 * max(1, total.value)))()
+    start = (C.c_int32 * (ncta + 1))()
+    _check(lib().ftgemm_group_plan(count, m, n, k, dtype, level, ncta, tiles, start, C.byref(total)))
+    flat = list(tiles)[:4 * total.value]
+    return [tuple(flat[i:i + 4]) for i in range(0, len(flat), 4)], list(start)
 
 
 class Group:

@@ -619,6 +619,16 @@ static void tc_schedule(const std::vector<TcProblem>& probs, int ncta, std::vect
   cta_start[ncta] = (int)tiles.size();
 }
 
+// The order in which a group's problems are laid out and scheduled: longer
+// K first (stable), so each CTA's static tile list ends on the cheap tiles.
+template <class KOf>
+static std::vector<int> longest_k_first(int count, KOf k_of) {
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return k_of(a) > k_of(c); });
+  return order;
+}
+
 static void group_free(ftgemm_group* g) {
   if (!g) return;
   if (g->d_probs) cudaFree(g->d_probs);
@@ -661,11 +671,7 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
   CK(cudaSetDevice(h->device));
   ftgemm_group* g = new ftgemm_group;
   g->h = h; g->dt = dt; g->abft = abft; g->count = count;
-  // schedule order: longer K first, so each CTA's static tile list ends on
-  // the cheap tiles
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pr[a].k > pr[c].k; });
+  const std::vector<int> order = longest_k_first(count, [&](int i) { return pr[i].k; });
   g->probs.resize(count);
   g->pos.resize(count);
   const float lam_u = (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24));
@@ -744,6 +750,49 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
   }
   for (int kd = 0; kd < P_KINDS; ++kd) g->bmap[kd] = g->d_bmap ? g->d_bmap + at[kd] : nullptr;
   *out = g;
+  return FTGEMM_OK;
+}
+
+int ftgemm_group_plan(int32_t count, const int64_t* m, const int64_t* n, const int64_t* k, ftgemm_dtype dtype,
+                      ftgemm_ft_level level, int32_t ncta, int32_t* tiles, int32_t* cta_start,
+                      int32_t* total_tiles) {
+  if (count <= 0 || !m || !n || !k || ncta <= 0 || !total_tiles)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_group_plan: bad argument");
+  if (dtype != FTGEMM_BF16 && dtype != FTGEMM_E4M3)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_group_plan: bf16 or e4m3 operands only");
+  if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_group_plan: level OFF or TILE, not %d", (int)level);
+  for (int i = 0; i < count; ++i)
+    if (m[i] <= 0 || n[i] <= 0 || k[i] <= 0 || m[i] > INT32_MAX || n[i] > INT32_MAX || k[i] > INT32_MAX)
+      FAIL(FTGEMM_ERR_ARG, "problem %d: sizes %lld x %lld x %lld", i, (long long)m[i], (long long)n[i],
+           (long long)k[i]);
+  const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
+  const bool abft = level == FTGEMM_FT_TILE;
+  // the same problem order, tile grid and schedule as ftgemm_group_create
+  const std::vector<int> order = longest_k_first(count, [&](int i) { return k[i]; });
+  std::vector<TcProblem> probs(count);
+  long long total = 0;
+  for (int q = 0; q < count; ++q) {
+    const int i = order[q];
+    tc_set_problem(probs[q], dt, abft, (int)m[i], (int)n[i], (int)k[i], nullptr, k[i], nullptr, n[i], nullptr,
+                   n[i], 1.0, 0.0, 1.f, 0.f);
+    total += (long long)probs[q].tiles_m * probs[q].tiles_n;
+    if (total > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_plan: too many tiles");
+  }
+  *total_tiles = (int32_t)total;
+  if (!tiles && !cta_start) return FTGEMM_OK;  // size query
+  std::vector<int4> sched;
+  std::vector<int> start;
+  tc_schedule(probs, ncta, sched, start);
+  if (tiles)
+    for (size_t j = 0; j < sched.size(); ++j) {
+      tiles[4 * j + 0] = order[sched[j].x];  // the caller's problem index
+      tiles[4 * j + 1] = sched[j].y;
+      tiles[4 * j + 2] = sched[j].z;
+      tiles[4 * j + 3] = sched[j].w;
+    }
+  if (cta_start)
+    for (int c = 0; c <= ncta; ++c) cta_start[c] = start[c];
   return FTGEMM_OK;
 }
 
