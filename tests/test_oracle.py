@@ -406,3 +406,15 @@ def test_offline_expected_runs_monte_carlo(orc):
     assert abs(est - orc.offline_expected_runs(gamma0, tiles)) < 0.01
     assert orc.offline_expected_runs(gamma0, tiles) > 1.0
     assert orc.offline_expected_runs(0.3, 4) == float("inf")
+
+
+def test_offline_expected_runs_closed_forms(orc):
+    # gamma = 1 - (1 - gamma0)^tiles, runs = (1 - gamma) / (1 - 2 gamma), by hand:
+    assert orc.offline_expected_runs(0.0, 64) == 1.0              # no errors: one run
+    assert abs(orc.offline_expected_runs(0.25, 1) - 1.5) < 1e-15  # (3/4) / (1/2)
+    assert abs(orc.offline_expected_runs(1 / 256, 1) - 255 / 254) < 1e-15
+    # two tiles at 1/2: gamma = 3/4 >= 1/2, the restart series diverges
+    assert orc.offline_expected_runs(0.5, 2) == float("inf")
+    # more tiles, more exposure: the expectation grows with the tile count
+    r = [orc.offline_expected_runs(1 / 256, t) for t in (16, 64, 144)]
+    assert 1.0 < r[0] < r[1] < r[2]
