@@ -237,6 +237,30 @@ def test_thread_units_separate_faults_one_block_period(orc):
         assert _thread_unit(0, 0) == _thread_unit(16, 32)
 
 
+def test_warp_units_follow_the_warp_tile(orc):
+    """Same tile and period (Section 4.2.2): faults in different m_w x n_w warp
+    tiles are both corrected at the WARP level, while the BLOCK level sees two
+    flagged rows or columns; two faults inside one warp tile defeat WARP too.
+    The tuple's warp tile is 32 x 64."""
+    M = N = K = 128
+    A = synth.integers((M, K), 41)
+    B = synth.integers((K, N), 42)
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    below = [(0, 0, 2, 0, 0, 16.0), (0, 0, 2, 32, 0, 16.0)]    # warp rows 0 and 1, column 0
+    beside = [(0, 0, 2, 5, 3, 16.0), (0, 0, 2, 5, 64, -16.0)]  # warp columns 0 and 1, row 5
+    inside = [(0, 0, 2, 0, 0, 16.0), (0, 0, 2, 31, 63, 16.0)]  # both in warp tile (0, 0)
+    for faults, lvl, ok in [(below, orc.WARP, True), (below, orc.BLOCK, False),
+                            (beside, orc.WARP, True), (beside, orc.BLOCK, False),
+                            (inside, orc.WARP, False)]:
+        res = orc.gemm_ft(A, B, orc.Schedule(**HUGE, cadence=16, level=lvl), faults=faults)
+        assert np.array_equal(res.C, ref) == ok, (faults, lvl)
+        if ok:
+            assert res.corrected == 2 and res.uncorrectable == 0
+            assert sorted((r.row, r.col) for r in res.records) == sorted((f[3], f[4]) for f in faults)
+        else:
+            assert res.uncorrectable >= 1
+
+
 @pytest.mark.parametrize("target,kind_row", [(1, True), (2, False)])
 def test_checksum_hit_is_reported_and_c_untouched(orc, target, kind_row):
     M = N = K = 64
