@@ -66,3 +66,42 @@ def test_host_side_argument_checks(libpath):
                           None) == -1
     assert L.ftgemm_status_string(ft.ERR_UNRECOVERED) == b"every offline attempt detected a fault"
     assert b"NULL" in L.ftgemm_last_error() or len(L.ftgemm_last_error()) > 0
+
+
+def test_every_handle_entry_point_rejects_null_before_device_work(libpath):
+    # each call fails its argument check (NULL handle or NULL operands) and
+    # returns FTGEMM_ERR_ARG with a message, without touching a device
+    import paper_2305_01024_gb300 as ft
+    L = ft.lib()
+    sched = ft.Schedule()
+    stats = ft.Stats()
+    lv = ctypes.c_int(0)
+    f = ctypes.c_float(0.0)
+    calls = {
+        "ftgemm_set_stream": lambda: L.ftgemm_set_stream(None, None),
+        "ftgemm_get_schedule": lambda: L.ftgemm_get_schedule(None, 64, 64, 64, ft.F32, ft.FT_BLOCK,
+                                                             ctypes.byref(sched)),
+        "ftgemm_set_threshold": lambda: L.ftgemm_set_threshold(None, 0, 32.0, None, 0),
+        "ftgemm_set_residual_sink": lambda: L.ftgemm_set_residual_sink(None, None, None, 0),
+        "ftgemm_mlp_forward": lambda: L.ftgemm_mlp_forward(None, 8, None, None, None),
+        "ftgemm_mlp_grad": lambda: L.ftgemm_mlp_grad(None, 8, None, None, None, None, ctypes.byref(f)),
+        "ftgemm_mlp_train": lambda: L.ftgemm_mlp_train(None, 8, None, None, 1, 8, 1e-3, None, None),
+        "ftgemm_set_fp8_scales": lambda: L.ftgemm_set_fp8_scales(None, 1.0, 1.0),
+        "ftgemm_quantize": lambda: L.ftgemm_quantize(None, 8, None, None, ft.BF16, None),
+        "ftgemm_autotune": lambda: L.ftgemm_autotune(None, 64, 64, 64, None, 64, None, 64, None, 64,
+                                                     ft.FT_BLOCK, 1, ctypes.byref(sched), ctypes.byref(lv)),
+        "ftgemm_encode": lambda: L.ftgemm_encode(None, 64, 64, 64, None, 64, None, 64, 16, 16,
+                                                 None, None, None, None),
+        "ftgemm_enable_timing": lambda: L.ftgemm_enable_timing(None, 1),
+        "ftgemm_get_stats": lambda: L.ftgemm_get_stats(None, ctypes.byref(stats), 0),
+    }
+    for name, call in calls.items():
+        assert call() == ft.ERR_ARG, name
+        assert L.ftgemm_last_error(), name
+    i64, vp = ctypes.c_int64, ctypes.c_void_p
+    noalloc = L.ftgemm_gemm_noalloc
+    noalloc.argtypes = [i64, i64, i64, ctypes.c_double, vp, i64, vp, i64, ctypes.c_double, vp, i64,
+                        ctypes.c_int, vp, vp]
+    noalloc.restype = ctypes.c_int
+    assert noalloc(64, 64, 64, 1.0, None, 64, None, 64, 0.0, None, 64, ft.FT_BLOCK, None, None) == ft.ERR_ARG
+    assert b"ftgemm_gemm_noalloc" in L.ftgemm_last_error()
