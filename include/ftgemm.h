@@ -140,11 +140,14 @@ typedef struct {
 
 /* Create a handle bound to CUDA device `device` and stream `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  Makes `device`
- * current on the calling thread. */
+ * current on the calling thread.  (Runtime plumbing, no counterpart in the
+ * paper.) */
 int ftgemm_create(ftgemm_handle_t* handle, int device, void* cuda_stream);
-/* Release the handle and its workspaces (synchronises its stream). */
+/* Release the handle and its workspaces (synchronises its stream).
+ * (Runtime plumbing, no counterpart in the paper.) */
 int ftgemm_destroy(ftgemm_handle_t handle);
-/* Change the stream later calls enqueue on. */
+/* Change the stream later calls enqueue on.  (Runtime plumbing, no
+ * counterpart in the paper.) */
 int ftgemm_set_stream(ftgemm_handle_t handle, void* cuda_stream);
 
 /* Fix the schedule of later fp32 calls (NULL = choose per shape, see
@@ -152,7 +155,9 @@ int ftgemm_set_stream(ftgemm_handle_t handle, void* cuda_stream);
  * of the compiled kernels (Table 1's five tuples); cadence must be >= 0 and
  * split_k >= 1. */
 int ftgemm_set_schedule(ftgemm_handle_t handle, const ftgemm_schedule* schedule);
-/* The schedule ftgemm_gemm would use for this problem. */
+/* The schedule ftgemm_gemm would use for this problem: a tile tuple of
+ * Table 1 (the kernel parameters of Section 3.2.2), the verification
+ * cadence (default K_s = 256 of Section 5.3) and split-K. */
 int ftgemm_get_schedule(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                         ftgemm_dtype dtype, ftgemm_ft_level ft_level,
                         ftgemm_schedule* out);
@@ -209,7 +214,8 @@ int ftgemm_mlp_train(ftgemm_handle_t handle, int64_t n, const float* X, const fl
                      int32_t epochs, int32_t batch, float lr, float* theta, float* losses);
 
 /* Per-tensor scales of E4M3 operands: the product is scale_a * scale_b *
- * (A_q B_q) with A_q, B_q the stored codes (see ftgemm_quantize). */
+ * (A_q B_q) with A_q, B_q the stored codes (see ftgemm_quantize).  (No
+ * counterpart in the paper, whose kernels are fp32.) */
 int ftgemm_set_fp8_scales(ftgemm_handle_t handle, float scale_a, float scale_b);
 
 /* ---- compute ------------------------------------------------------------ */
@@ -223,7 +229,11 @@ int ftgemm_set_fp8_scales(ftgemm_handle_t handle, float scale_a, float scale_b);
 int ftgemm_quantize(ftgemm_handle_t handle, int64_t n, const float* x, void* y,
                     ftgemm_dtype dtype, float* scale_out);
 
-/* C = alpha * A * B + beta * C with online ABFT at `ft_level`.
+/* C = alpha * A * B + beta * C with online ABFT at `ft_level`: the checksums
+ * of Eq. 1-2 carried through the K loop in the outer-product form of Eq. 4,
+ * verified at the unit of Section 4.2.1 / 4.2.2 / 4.2.3 (or the tensor-core
+ * tile), errors located and corrected as in Section 4.2.1 under the fault
+ * model of Section 4.1; `inject` follows Section 5.3.
  * A, B: device pointers of `dtype` elements; C: device fp32.  With beta == 0
  * C is not read.  inject: NULL for none.  report: NULL = do not wait (events
  * accumulate in the handle until ftgemm_report_fetch); non-NULL = the
@@ -301,24 +311,28 @@ int ftgemm_group_plan(int32_t count, const int64_t* m, const int64_t* n, const i
                       int32_t* cta_start, int32_t* total_tiles);
 
 /* Tile grid of each problem (caller arrays of `count`): 120 x 248 tiles of C
- * at level TILE, 128 x 256 at OFF. */
+ * at level TILE, 128 x 256 at OFF.  (No counterpart in the paper.) */
 int ftgemm_group_tiles(ftgemm_group_t group, int32_t* tiles_m, int32_t* tiles_n);
 
-/* Faults applied by every later ftgemm_grouped_gemm of the group: problem[i]
- * is the problem of fault i, the other fields as in ftgemm_gemm's inject
+/* Faults applied by every later ftgemm_grouped_gemm of the group (the
+ * injection of Section 5.3, per problem): problem[i] is the problem of
+ * fault i, the other fields as in ftgemm_gemm's inject
  * (tile indices and in-tile offsets on that problem's grid).  NULL or n = 0
  * clears them.  Synchronises the handle's stream; not for use while a
  * stream capture is in progress. */
 int ftgemm_group_set_faults(ftgemm_group_t group, const int32_t* problem, const ftgemm_inject_spec* inject);
 
-/* Enqueue the group on the handle's stream: the batched encode pass and one
- * persistent tensor-core launch over every tile of every problem.  No host
+/* Enqueue the group on the handle's stream: the batched encode pass (Eq. 1-2)
+ * and one persistent tensor-core launch over every tile of every problem,
+ * each tile verified as in ftgemm_gemm (no counterpart in the paper, which
+ * runs one GEMM at a time).  No host
  * synchronisation and no allocation, so the call can be captured into a CUDA
  * graph and replayed; each replay recomputes every C.  Fault events
  * accumulate in the handle; read them with ftgemm_report_fetch. */
 int ftgemm_grouped_gemm(ftgemm_handle_t handle, ftgemm_group_t group);
 
-/* Release a group (synchronises the handle's stream first). */
+/* Release a group (synchronises the handle's stream first).  (No
+ * counterpart in the paper.) */
 int ftgemm_group_destroy(ftgemm_group_t group);
 
 /* Autotuner (F32 SIMT path).  The paper picks kernel parameters per shape
@@ -411,7 +425,8 @@ int ftgemm_dgemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, double
                  double* C, int64_t ldc, ftgemm_ft_level ft_level, int32_t cadence,
                  const ftgemm_inject_spec* inject, ftgemm_report* report);
 
-/* The same for double complex on 64 x 64 tiles: matrices of interleaved
+/* The same for double complex on 64 x 64 tiles (ZGEMM, the other extension
+ * Section 6 names): matrices of interleaved
  * (re, im) doubles (C99 double complex layout), 16-byte aligned, leading
  * dimensions in complex elements; alpha and beta are HOST arrays {re, im}.
  * Norms are sqrt(sum |a|^2); a residual d is flagged when |d| exceeds its
@@ -426,7 +441,8 @@ int ftgemm_zgemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, const 
                  const ftgemm_inject_spec* inject, ftgemm_report* report, double* imag);
 
 /* Synchronise the handle's stream, copy out the events accumulated since the
- * last fetch (or the last call that returned a report) and clear them. */
+ * last fetch (or the last call that returned a report) and clear them: the
+ * located and corrected errors of Section 4.2.1, one record each. */
 int ftgemm_report_fetch(ftgemm_handle_t handle, ftgemm_report* report);
 
 /* Checksum encoding on its own (Eq. 1-2), fp32:
@@ -451,10 +467,11 @@ typedef struct {
   double kernel_ms;
 } ftgemm_stats;
 
-/* Enable (1) or disable (0) the events around the main GEMM kernel. */
+/* Enable (1) or disable (0) the events around the main GEMM kernel.
+ * (Measurement plumbing, no counterpart in the paper.) */
 int ftgemm_enable_timing(ftgemm_handle_t handle, int enable);
 /* Synchronise the handle's stream and read the counters; reset != 0 zeroes
- * them afterwards. */
+ * them afterwards.  (Measurement plumbing, no counterpart in the paper.) */
 int ftgemm_get_stats(ftgemm_handle_t handle, ftgemm_stats* out, int reset);
 
 /* ---- allocation-free entry point --------------------------------------- */
@@ -465,9 +482,10 @@ int ftgemm_get_stats(ftgemm_handle_t handle, ftgemm_stats* out, int reset);
  * until the process exits. */
 #define FTGEMM_NOALLOC_SCRATCH_BYTES (16u << 20)
 
-/* C = alpha * A * B + beta * C (fp32, the 128 x 128 x 16 tile, verification
- * every 256 of K, no split-K, no fault injection) without allocating any
- * device memory and without a handle.  It is for callers that may not call
+/* C = alpha * A * B + beta * C (fp32, the 128 x 128 x 16 tile, the checksum
+ * levels of Section 4.2, verification every 256 of K, no split-K, no fault
+ * injection) without allocating any device memory and without a handle (no
+ * counterpart in the paper).  It is for callers that may not call
  * cudaMalloc when they need the GEMM: a framework whose memory pool owns the
  * device, code that must not cause the device-wide synchronisation that
  * cudaMalloc / cudaFree can, or recovery code after an out-of-memory error.
@@ -489,9 +507,10 @@ int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha, const flo
                         int64_t ldc, ftgemm_ft_level ft_level, void* cuda_stream,
                         ftgemm_report* report);
 
-/* Text of a status code. */
+/* Text of a status code.  (No counterpart in the paper.) */
 const char* ftgemm_status_string(int status);
-/* Text of the last error raised on the calling thread ("" if none). */
+/* Text of the last error raised on the calling thread ("" if none).  (No
+ * counterpart in the paper.) */
 const char* ftgemm_last_error(void);
 
 #ifdef __cplusplus
