@@ -80,7 +80,8 @@ typedef struct {
 } orc_record;
 
 /* ------------------------------------------------------------------------ */
-/* (1) Plain definition: C = alpha * A B + beta * C_in, double precision.    */
+/* (1) Plain definition: C = alpha * A B + beta * C_in, double precision     */
+/*     (the problem of Section 3.1, with the scalars alpha and beta).        */
 /* ------------------------------------------------------------------------ */
 void orc_gemm_ref(int64_t M, int64_t N, int64_t K, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb,
@@ -205,7 +206,10 @@ static double score(double d, double tau) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* (2) The ABFT algorithm.                                                   */
+/* (2) The ABFT algorithm: Eq. 1-2 per unit, the per-k-step update of Eq. 4, */
+/*     verification and correction as in Section 4.2.1 at the unit of the   */
+/*     level (Sections 4.2.1-4.2.3), faults as in Section 5.3, one fault    */
+/*     per unit and period correctable (Section 4.1).                       */
 /*   Cout[i*ldo+j] receives alpha*acc + beta*Cin.                            */
 /*   counters[0..3] = detected, corrected, uncorrectable, checksum_only.     */
 /*   Records are written sorted (tile_m, tile_n, kstep, row, col, kind);     */
@@ -455,7 +459,8 @@ typedef struct {
 
 static double complex zat(const double* p, int64_t idx) { return p[2 * idx] + p[2 * idx + 1] * I; }
 
-/* C = alpha * A B + beta * C_in, complex double precision. */
+/* C = alpha * A B + beta * C_in, complex double precision (the plain        */
+/* definition behind the ZGEMM extension of Section 6).                     */
 void orc_zgemm_ref(int64_t M, int64_t N, int64_t K, const double* alpha,
                    const double* A, int64_t lda, const double* B, int64_t ldb,
                    const double* beta, const double* Cin, int64_t ldc, double* C,
@@ -684,6 +689,8 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
 
 /* ------------------------------------------------------------------------ */
 /* Low-precision inputs.  The ABFT checks run on the quantized values.       */
+/* (No counterpart in the paper, whose kernels are fp32: these follow the   */
+/* published bf16 and OCP FP8 formats.)                                     */
 /* ------------------------------------------------------------------------ */
 
 /* bfloat16: the top 16 bits of a binary32, rounded to nearest, ties to even */
