@@ -160,7 +160,8 @@ class Result:
 
 
 def gemm_ref(A, B, alpha=1.0, beta=0.0, Cin=None) -> np.ndarray:
-    """C = alpha*A*B + beta*C_in, every product and sum in double precision."""
+    """C = alpha*A*B + beta*C_in, every product and sum in double precision
+    (the problem of Section 3.1)."""
     A, B = _f64(A), _f64(B)
     M, K = A.shape
     K2, N = B.shape
@@ -173,7 +174,7 @@ def gemm_ref(A, B, alpha=1.0, beta=0.0, Cin=None) -> np.ndarray:
 
 
 def encode(A, B, m_u: int, n_u: int):
-    """Return V (row-block sums of A, [blocks][K]), W (column-block sums of B,
+    """Eq. 1-2 per block: return V (row-block sums of A, [blocks][K]), W (column-block sums of B,
     [blocks][K]), nA (row 2-norms of A), nB (column 2-norms of B)."""
     A, B = _f64(A), _f64(B)
     M, K = A.shape
@@ -222,8 +223,9 @@ T_IMAG = 4  # fault target flag of the complex GEMM: the offset is delta * i
 
 
 def dgemm_schedule(cadence: int, lam: float = 32.0, level: int = BLOCK) -> Schedule:
-    """The double-precision GEMM's tiling for gemm_ft: 128 x 128 output
-    tiles, k-steps of 8, one verification unit per tile, u = 2^-53."""
+    """The double-precision GEMM's tiling for gemm_ft (DGEMM, the extension
+    Section 6 names): 128 x 128 output tiles, k-steps of 8, one verification
+    unit per tile, u = 2^-53."""
     return Schedule(m_tb=128, n_tb=128, k_tb=8, m_w=128, n_w=128, m_t=8, n_t=8, cadence=cadence,
                     split_k=1, level=level, lam=lam, u=U64)
 
@@ -233,7 +235,8 @@ def _c128(a) -> np.ndarray:
 
 
 def zgemm_ref(A, B, alpha=1.0, beta=0.0, Cin=None) -> np.ndarray:
-    """C = alpha*A*B + beta*C_in in complex double precision."""
+    """C = alpha*A*B + beta*C_in in complex double precision (the plain
+    definition behind Section 6's ZGEMM)."""
     A, B = _c128(A), _c128(B)
     M, K = A.shape
     K2, N = B.shape
@@ -263,7 +266,8 @@ class ZRecord:
 def zgemm_ft(A, B, tile: int = 64, k_tb: int = 8, cadence: int = 1, faults=(), alpha=1.0, beta=0.0,
              Cin=None, lam: float = 32.0, u: float = U64, verify: bool = True,
              cap: int = 1 << 16) -> Result:
-    """The online ABFT GEMM on complex operands at block level: tile x tile
+    """The online ABFT GEMM on complex operands at block level (ZGEMM, the
+    extension Section 6 names; the steps of gemm_ft on complex values): tile x tile
     output tiles, k-steps of k_tb, verification every `cadence` k-steps.
     ``faults``: (tile_m, tile_n, kstep, row, col, delta[, target]) with a real
     delta; target | T_IMAG puts the offset on the imaginary part."""
@@ -295,6 +299,8 @@ def zgemm_ft(A, B, tile: int = 64, k_tb: int = 8, cadence: int = 1, faults=(), a
 
 
 def round_bf16(x) -> np.ndarray:
+    """Round fp32 values to bfloat16, nearest with ties to even (the bf16
+    format; no counterpart in the paper, whose kernels are fp32)."""
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
     out = np.empty(x.shape, dtype=np.float64)
     lib().orc_round_bf16(x.ctypes.data_as(C.POINTER(C.c_float)), x.size, _dp(out))
@@ -302,7 +308,9 @@ def round_bf16(x) -> np.ndarray:
 
 
 def quant_e4m3(x):
-    """Return (dequantized values, raw E4M3 values, scale)."""
+    """Per-tensor amax scaling and saturating round-to-nearest-even to OCP FP8
+    E4M3 (no counterpart in the paper, whose kernels are fp32).  Return
+    (dequantized values, raw E4M3 values, scale)."""
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
     out = np.empty(x.shape, dtype=np.float64)
     q = np.empty(x.shape, dtype=np.float64)
@@ -311,4 +319,7 @@ def quant_e4m3(x):
 
 
 def offline_expected_runs(gamma0: float, tiles: float) -> float:
+    """Expected runs of offline (detect-and-restart) ABFT, Section 5.5:
+    (1 - gamma) / (1 - 2 gamma) with gamma = 1 - (1 - gamma0)^tiles; infinite
+    for gamma >= 1/2."""
     return float(lib().orc_offline_expected_runs(gamma0, tiles))
