@@ -1,5 +1,8 @@
 // api.cu -- the C ABI of libftgemm (include/ftgemm.h): handle, argument
 // checks, schedule choice, fault table, workspaces, dispatch and report.
+// Each entry point implements the passage its declaration in ftgemm.h cites
+// (Eq. 1-4 and Sections 4.1-4.2 for the GEMMs, Section 5.3 for injection,
+// Section 5.5 for the offline scheme, Section 6 for DGEMM / ZGEMM).
 #include <cuda_runtime.h>
 
 #include <algorithm>

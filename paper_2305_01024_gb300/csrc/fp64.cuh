@@ -1,5 +1,6 @@
 // fp64.cuh -- launch parameters of the double / double-complex ABFT GEMM
-// (fp64.cu), shared with the host entry points.
+// (fp64.cu), shared with the host entry points: the DGEMM / ZGEMM
+// extension Section 6 names.
 #pragma once
 #include "internal.cuh"
 

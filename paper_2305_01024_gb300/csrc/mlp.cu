@@ -1,5 +1,7 @@
 // mlp.cu -- training and standalone inference of the threshold network
-// (mlp.cuh): forward, mean-squared-error gradient by backprop, Adam.
+// (mlp.cuh): forward, mean-squared-error gradient by backprop, Adam.  The
+// paper leaves the detection threshold open (Section 2.2); this network has
+// no counterpart there.
 //
 // Gradient: each warp runs samples one at a time with lane j holding unit j
 // (forward, then the chain rule back through both ReLU layers), keeping its

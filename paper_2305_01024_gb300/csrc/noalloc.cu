@@ -1,5 +1,6 @@
 // noalloc.cu -- ftgemm_gemm_noalloc: the fp32 fused-ABFT GEMM without any
-// device allocation, for callers that may not call cudaMalloc.
+// device allocation, for callers that may not call cudaMalloc (no
+// counterpart in the paper; the checksum levels are those of Section 4.2).
 //
 // Some callers cannot allocate device memory at the moment they need a GEMM:
 // a framework whose caching allocator already owns the whole device, code

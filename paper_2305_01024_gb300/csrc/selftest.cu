@@ -1,4 +1,5 @@
-// selftest.cu -- self-test of the bounded device waits.
+// selftest.cu -- self-test of the bounded device waits (no counterpart in
+// the paper).
 //
 // Every wait of the GEMM kernels on an mbarrier gives up after a time limit,
 // records the give-up in the report and lets the kernel return, so that a

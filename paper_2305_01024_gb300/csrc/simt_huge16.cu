@@ -1,5 +1,7 @@
 // simt_huge16.cu -- instantiates the fused-ABFT SGEMM for the tile tuple
-// m_tb=128, n_tb=128, k_tb=16, m_w=32, n_w=64, m_t=8, n_t=8 at every checksum level.
+// m_tb=128, n_tb=128, k_tb=16, m_w=32, n_w=64, m_t=8, n_t=8 at every checksum level;
+// the "huge" tuple of Table 1 with k-steps of 16 instead of 8, a variant the
+// table does not list.
 #include "simt_ftgemm.cuh"
 
 namespace ftg {

@@ -1,5 +1,6 @@
 // simt_medium.cu -- instantiates the fused-ABFT SGEMM for the tile tuple
-// m_tb=32, n_tb=32, k_tb=8, m_w=16, n_w=32, m_t=4, n_t=4 at every checksum level.
+// m_tb=32, n_tb=32, k_tb=8, m_w=16, n_w=32, m_t=4, n_t=4 at every checksum level;
+// Table 1's "medium" tuple.
 #include "simt_ftgemm.cuh"
 
 namespace ftg {

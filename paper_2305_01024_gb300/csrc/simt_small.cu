@@ -1,5 +1,6 @@
 // simt_small.cu -- instantiates the fused-ABFT SGEMM for the tile tuple
-// m_tb=16, n_tb=16, k_tb=16, m_w=8, n_w=16, m_t=2, n_t=2 at every checksum level.
+// m_tb=16, n_tb=16, k_tb=16, m_w=8, n_w=16, m_t=2, n_t=2 at every checksum level;
+// Table 1's "small" tuple.
 #include "simt_ftgemm.cuh"
 
 namespace ftg {

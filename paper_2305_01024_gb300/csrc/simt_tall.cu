@@ -1,5 +1,6 @@
 // simt_tall.cu -- instantiates the fused-ABFT SGEMM for the tile tuple
-// m_tb=32, n_tb=128, k_tb=8, m_w=16, n_w=64, m_t=4, n_t=8 at every checksum level.
+// m_tb=32, n_tb=128, k_tb=8, m_w=16, n_w=64, m_t=4, n_t=8 at every checksum level;
+// Table 1's "tall and skinny" tuple.
 #include "simt_ftgemm.cuh"
 
 namespace ftg {

@@ -1,6 +1,7 @@
 // simt_wide.cu -- instantiates the fused-ABFT SGEMM for the tile tuple
 // m_tb=128, n_tb=128, k_tb=16, m_w=64, n_w=64, m_t=16, n_t=8 (128 threads,
-// 16 x 8 fragments) at every checksum level.
+// 16 x 8 fragments) at every checksum level; not one of Table 1's tuples:
+// its larger fragments leave room for the block checksum loads.
 #include "simt_ftgemm.cuh"
 
 namespace ftg {
