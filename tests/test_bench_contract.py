@@ -1,7 +1,9 @@
 """bench.py's reference arm: the CPU oracle timed on a bounded sample of the
 headline workload.  Its one JSON line carries the keys, metric, unit and
 workload of the GPU arm, and under torchrun the ranks other than 0 exit
-without work.  Runs on the CPU."""
+without work.  Also the host side of the headline's fault injection (the
+Poisson draws, sites and magnitudes bench.py passes to the kernels).  Runs on
+the CPU."""
 import importlib.util
 import json
 import os
@@ -59,3 +61,33 @@ def test_reference_arm_other_ranks_do_no_work():
     p = _reference({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_headline_fault_draws():
+    # the bench's faults: a Poisson count at 200 per minute of kernel time,
+    # sites inside the headline tiling (at most one per tile and period), and
+    # magnitudes log-uniform in [1e-2, 1e3] x the expected tile maximum
+    import math
+    import numpy as np
+    b = _bench_module()
+    n, t_kernel = 16384, 0.14
+    ksteps = n // b.SCHED["k_tb"]
+    tiles = n // b.SCHED["m_tb"]
+    tile_max = 4.0 * math.sqrt(n / 9.0)
+    counts, deltas = [], []
+    for s in range(3000):
+        f = b.make_faults(1000 + 17 * s, t_kernel, n, ksteps)
+        counts.append(len(f))
+        units = set()
+        for tm, tn, ks, r, c, d in f:
+            assert 0 <= tm < tiles and 0 <= tn < tiles and 0 <= ks < ksteps
+            assert 0 <= r < b.SCHED["m_tb"] and 0 <= c < b.SCHED["n_tb"]
+            units.add((tm, tn, ks // b.SCHED["cadence"]))
+            deltas.append(d)
+        assert len(units) == len(f)
+    lam = b.FAULTS_PER_MIN / 60.0 * t_kernel
+    assert abs(np.mean(counts) - lam) < 5 * math.sqrt(lam / len(counts))
+    mags = np.abs(np.array(deltas)) / tile_max
+    assert mags.min() >= 1e-2 * (1 - 1e-6) and mags.max() <= 1e3 * (1 + 1e-6)
+    assert 0.4 < np.mean(np.array(deltas) > 0) < 0.6
+    assert b.make_faults(4242, t_kernel, n, ksteps) == b.make_faults(4242, t_kernel, n, ksteps)
