@@ -19,6 +19,26 @@ import synth
 
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
+# Statistical float tolerance: an fp32 dot product of length K rounds with an
+# error whose typical size is u*sqrt(K)*|a||b| or below (random rounding
+# errors add like a random walk); a corrected element adds the rounding noise
+# of its row residual, far smaller.  A dropped k-slice of 32 terms moves an
+# element by about sqrt(32) |a||b|/K, i.e. 40 or more of these units at
+# K = 16384, so the check below catches it where the worst-case 2Ku bound
+# (about 10^4 times looser) does not.
+STAT_C = 8.0
+
+
+def _stat_check(got, ref, Ar, Bh, K, cin_abs=None, scale=1.0):
+    """max |C - C_ref| / (u sqrt(K) ||a_i|| ||b_j|| * scale + 2u |C_ref|) <= STAT_C."""
+    na = np.sqrt((np.asarray(Ar, np.float64) ** 2).sum(1))
+    nb = np.sqrt((np.asarray(Bh, np.float64) ** 2).sum(0))
+    unit = U32 * math.sqrt(K) * np.outer(na, nb) * scale + 2 * U32 * np.abs(ref)
+    if cin_abs is not None:
+        unit = unit + 2 * U32 * cin_abs
+    ratio = np.abs(got - ref) / unit
+    assert ratio.max() <= STAT_C, f"max error {ratio.max():.3g} units of u sqrt(K)|a||b|"
+    return float(ratio.max())
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +81,7 @@ def test_config2_full_size_sampled_rows(ft, orc):
     for x in rep.records:
         slack[rows.index(x["row"]), x["col"]] = x["tau"]
     assert np.all(np.abs(got - ref) <= bound + slack)
+    _stat_check(got, ref, Ar, Bh, n, cin_abs=0.5 * np.abs(Cr))
     h.close()
 
 
@@ -90,6 +111,7 @@ def test_config4_full_size_bf16_sampled_rows(ft, orc):
     for x in rep.records:
         slack[rows.index(x["row"]), x["col"]] = x["tau"]
     assert np.all(np.abs(got - ref) <= bound + slack)
+    _stat_check(got, ref, Ar, Bh, n)
     h.close()
 
 
@@ -141,6 +163,7 @@ def test_config5_full_group_sampled_problems(ft, orc):
             if x["problem"] == q:
                 slack[x["row"], x["col"]] = x["tau"]
         assert np.all(np.abs(got - ref) <= bound + slack)
+        _stat_check(got, ref, Ah, Bh, K)
     g.close()
     h.close()
 
@@ -191,4 +214,5 @@ def test_config4_full_size_e4m3_sampled_rows(ft, orc):
     for x in rep.records:
         slack[rows.index(x["row"]), x["col"]] = x["tau"] * scale
     assert np.all(np.abs(got - ref) <= bound + slack)
+    _stat_check(got, ref, Aq, Bq, n, scale=scale)
     h.close()

@@ -237,6 +237,37 @@ def test_thread_units_separate_faults_one_block_period(orc):
         assert _thread_unit(0, 0) == _thread_unit(16, 32)
 
 
+WIDE32 = dict(m_tb=128, n_tb=128, k_tb=32, m_w=64, n_w=64, m_t=16, n_t=8)
+
+
+def test_thread_units_of_the_16x8_fragment(orc):
+    """The headline tuple's thread fragments (64 x 64 warp tile, 4 x 8 lanes,
+    16 x 8 per lane): a lane's 16 rows come as 4 chunks of 4 consecutive rows,
+    16 apart, and its 8 columns as 2 chunks of 4, 32 apart.  Rows 0 and 8
+    belong to different lanes (a contiguous 16-row fragment would merge them),
+    rows 0 and 16 to the same lane (chunk 0 and 1 of lane row 0), columns 0
+    and 32 to the same lane, columns 0 and 16 to different ones; rows 0 and 64
+    lie in different warp tiles.  Two faults in one period are both corrected
+    at the THREAD level exactly when they fall in different fragments."""
+    M = N = K = 128
+    A = synth.integers((M, K), 33)
+    B = synth.integers((K, N), 34)
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    unit = lambda r, c: _thread_unit(r, c, m_w=64, n_w=64, m_t=16, n_t=8)
+    cases = [((0, 0), (8, 0), True), ((0, 0), (16, 0), False), ((0, 0), (0, 32), False),
+             ((0, 0), (0, 16), True), ((3, 3), (51, 35), False), ((0, 0), (64, 0), True),
+             ((0, 0), (4, 4), True)]
+    for (r0, c0), (r1, c1), sep in cases:
+        assert (unit(r0, c0) != unit(r1, c1)) == sep, ((r0, c0), (r1, c1))
+        faults = [(0, 0, 1, r0, c0, 8.0), (0, 0, 1, r1, c1, -16.0)]
+        res = orc.gemm_ft(A, B, orc.Schedule(**WIDE32, cadence=2, level=orc.THREAD), faults=faults)
+        assert np.array_equal(res.C, ref) == sep, ((r0, c0), (r1, c1))
+        if sep:
+            assert res.corrected == 2 and res.uncorrectable == 0
+        else:
+            assert res.uncorrectable >= 1
+
+
 def test_warp_units_follow_the_warp_tile(orc):
     """Same tile and period (Section 4.2.2): faults in different m_w x n_w warp
     tiles are both corrected at the WARP level, while the BLOCK level sees two
