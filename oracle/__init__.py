@@ -30,7 +30,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ftgemm_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "libftgemm_oracle.so")
 
-OFF, THREAD, WARP, BLOCK, TILE = 0, 1, 2, 3, 4
+OFF, THREAD, WARP, BLOCK, TILE, DETECT = 0, 1, 2, 3, 4, 5
+# threshold scales: lambda for the norm term, mu for the checksum-growth term
+LAM = 32.0
+MU = 8.0
 CORRECTED, UNCORRECTABLE, CHECKSUM_ONLY = 0, 1, 2
 T_ACC, T_ROWSUM, T_COLSUM = 0, 1, 2
 
@@ -51,7 +54,7 @@ class _Sched(C.Structure):
     _fields_ = [("m_tb", C.c_int32), ("n_tb", C.c_int32), ("k_tb", C.c_int32),
                 ("m_w", C.c_int32), ("n_w", C.c_int32), ("m_t", C.c_int32), ("n_t", C.c_int32),
                 ("cadence", C.c_int32), ("split_k", C.c_int32), ("level", C.c_int32),
-                ("lam", C.c_double), ("u", C.c_double)]
+                ("lam", C.c_double), ("u", C.c_double), ("mu", C.c_double)]
 
 
 class _Fault(C.Structure):
@@ -93,7 +96,7 @@ def lib():
         _lib.orc_gemm_ft.restype = C.c_int
         _lib.orc_zgemm_ref.argtypes = [i64, i64, i64, d, d, i64, d, i64, d, d, i64, d, i64]
         _lib.orc_zgemm_ft.argtypes = [i64, i64, i64, d, d, i64, d, i64, d, d, i64, d, i64,
-                                      i32, i32, i32, i32, i32, C.c_double, C.c_double,
+                                      i32, i32, i32, i32, i32, C.c_double, C.c_double, C.c_double,
                                       C.POINTER(_Fault), i32, C.POINTER(_ZRec), i32,
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         _lib.orc_zgemm_ft.restype = C.c_int
@@ -131,8 +134,9 @@ class Schedule:
     cadence: int = 32
     split_k: int = 1
     level: int = BLOCK
-    lam: float = 32.0
+    lam: float = LAM
     u: float = 2.0 ** -24
+    mu: float = MU
 
 
 @dataclass
@@ -199,7 +203,7 @@ def gemm_ft(A, B, sched: Schedule, faults=(), alpha=1.0, beta=0.0, Cin=None,
     Ci = _f64(Cin) if (Cin is not None and beta != 0.0) else np.zeros((1, 1))
     out = np.empty((M, N), dtype=np.float64)
     s = _Sched(sched.m_tb, sched.n_tb, sched.k_tb, sched.m_w, sched.n_w, sched.m_t,
-               sched.n_t, sched.cadence, sched.split_k, sched.level, sched.lam, sched.u)
+               sched.n_t, sched.cadence, sched.split_k, sched.level, sched.lam, sched.u, sched.mu)
     nf = len(faults)
     fa = (_Fault * max(1, nf))()
     for q, f in enumerate(faults):
@@ -222,12 +226,12 @@ U64 = 2.0 ** -53
 T_IMAG = 4  # fault target flag of the complex GEMM: the offset is delta * i
 
 
-def dgemm_schedule(cadence: int, lam: float = 32.0, level: int = BLOCK) -> Schedule:
+def dgemm_schedule(cadence: int, lam: float = LAM, level: int = BLOCK, mu: float = MU) -> Schedule:
     """The double-precision GEMM's tiling for gemm_ft (DGEMM, the extension
     Section 6 names): 128 x 128 output tiles, k-steps of 8, one verification
     unit per tile, u = 2^-53."""
     return Schedule(m_tb=128, n_tb=128, k_tb=8, m_w=128, n_w=128, m_t=8, n_t=8, cadence=cadence,
-                    split_k=1, level=level, lam=lam, u=U64)
+                    split_k=1, level=level, lam=lam, u=U64, mu=mu)
 
 
 def _c128(a) -> np.ndarray:
@@ -264,7 +268,7 @@ class ZRecord:
 
 
 def zgemm_ft(A, B, tile: int = 64, k_tb: int = 8, cadence: int = 1, faults=(), alpha=1.0, beta=0.0,
-             Cin=None, lam: float = 32.0, u: float = U64, verify: bool = True,
+             Cin=None, lam: float = LAM, u: float = U64, verify: bool = True, mu: float = MU,
              cap: int = 1 << 16) -> Result:
     """The online ABFT GEMM on complex operands at block level (ZGEMM, the
     extension Section 6 names; the steps of gemm_ft on complex values): tile x tile
@@ -288,7 +292,7 @@ def zgemm_ft(A, B, tile: int = 64, k_tb: int = 8, cadence: int = 1, faults=(), a
     cnt = (C.c_int64 * 4)()
     nrec = C.c_int32(0)
     rc = lib().orc_zgemm_ft(M, N, K, _dp(al), _dp(A), K, _dp(B), N, _dp(be), _dp(Ci), Ci.shape[1],
-                            _dp(out), N, tile, tile, k_tb, cadence, 1 if verify else 0, lam, u,
+                            _dp(out), N, tile, tile, k_tb, cadence, 1 if verify else 0, lam, u, mu,
                             fa, nf, recs, cap, cnt, C.byref(nrec))
     if rc != 0:
         raise ValueError(f"orc_zgemm_ft rejected its arguments (rc={rc})")

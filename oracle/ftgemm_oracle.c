@@ -24,9 +24,14 @@
  *       - single-event-upset model: one fault per unit and period (Section 4.1).
  *
  * Readings taken where the paper is silent (all listed in the design notes):
- *   - threshold  tau^r_i = lambda*u*||A(i,:)||_2*||B(:,J_U)||_F and
- *                tau^c_j = lambda*u*||A(I_U,:)||_F*||B(:,j)||_2
- *     (norms over the full K; J_U/I_U are the columns/rows of the unit);
+ *   - threshold, at a verification after k elements of K (of this split):
+ *       tau^r_i = lambda*u*||A(i,:)||_2*||B(:,J_U)||_F + mu*u*sqrt(k)*|c^r_i|
+ *       tau^c_j = lambda*u*||A(I_U,:)||_F*||B(:,j)||_2 + mu*u*sqrt(k)*|c^c_j|
+ *     (norms over the full K; J_U/I_U are the columns/rows of the unit;
+ *     c^r_i, c^c_j the checksums as they stand at the verification).  The
+ *     first term is the size of the random-walk rounding error of zero-mean
+ *     data; the second follows the growth of the partial sums of same-sign
+ *     data, whose rounding error grows like u*sqrt(k) times the sum itself;
  *   - i* / j* = argmax |d|/tau, ties to the smallest index;
  *   - correction value = row residual d^r_{i*};  the pair is consistent only if
  *     |d^r_{i*} - d^c_{j*}| <= tau^r_{i*} + tau^c_{j*};
@@ -37,6 +42,11 @@
  *     the chosen level, with the fragment layout given by unit_row()/unit_col();
  *   - with split-K each split verifies its own partial sum; the sum of the
  *     splits and the alpha/beta epilogue are not protected;
+ *   - detect-only (the offline scheme of Section 5.5): the unit is the whole
+ *     tile and only its column checksums e^T C are compared, once per split
+ *     (the schedule's cadence covers the split); a flagged column is reported
+ *     as a detection (kind uncorrectable, no row) and nothing is corrected:
+ *     the offline scheme recomputes the whole GEMM instead;
  *   - double precision (DGEMM, the extension named in Section 6) is (2) with
  *     u = 2^-53; double complex (ZGEMM) is (3): the same steps on complex
  *     values, one unit per output tile, |d| compared with a threshold built
@@ -53,7 +63,7 @@
 #endif
 
 /* levels of the checksum unit (Section 4.2) */
-enum { ORC_OFF = 0, ORC_THREAD = 1, ORC_WARP = 2, ORC_BLOCK = 3, ORC_TILE = 4 };
+enum { ORC_OFF = 0, ORC_THREAD = 1, ORC_WARP = 2, ORC_BLOCK = 3, ORC_TILE = 4, ORC_DETECT = 5 };
 /* record kinds */
 enum { ORC_CORRECTED = 0, ORC_UNCORRECTABLE = 1, ORC_CHECKSUM_ONLY = 2 };
 /* fault targets */
@@ -65,8 +75,9 @@ typedef struct {
   int32_t cadence;            /* k-steps per verification period (>=1) */
   int32_t split_k;            /* number of K splits (>=1) */
   int32_t level;              /* ORC_* */
-  double lambda;              /* threshold scale */
+  double lambda;              /* threshold scale of the norm term */
   double u;                   /* unit roundoff of the accumulator */
+  double mu;                  /* threshold scale of the checksum-growth term */
 } orc_schedule;
 
 typedef struct {
@@ -268,6 +279,8 @@ int orc_gemm_ft(int64_t M, int64_t N, int64_t K, double alpha,
     double* dc = (double*)calloc((size_t)nt * ngr, sizeof(double));
     double* tr = (double*)calloc((size_t)mt * ngc, sizeof(double));
     double* tc = (double*)calloc((size_t)nt * ngr, sizeof(double));
+    double* er = (double*)calloc((size_t)mt * ngc, sizeof(double)); /* tau at this verification */
+    double* ec = (double*)calloc((size_t)nt * ngr, sizeof(double));
     int64_t lc[4] = {0, 0, 0, 0};
     reclist L = {0, 0, 0};
 
@@ -340,18 +353,25 @@ int orc_gemm_ft(int64_t M, int64_t N, int64_t K, double alpha,
         /* verification at the end of every period and at the split's end */
         const int64_t l = s - s0;
         if (!verify || !(((l + 1) % sch->cadence) == 0 || s == s1 - 1)) continue;
+        /* thresholds at this verification: the norm term plus the growth term
+           mu*u*sqrt(k)*|checksum|, k the elements of K accumulated so far */
+        const double grow = sch->mu * sch->u * sqrt((double)(k1 - s0 * kt));
+        for (int r = 0; r < rows; ++r)
+          for (int g = 0; g < ngc; ++g) er[r * ngc + g] = tr[r * ngc + g] + grow * fabs(cr[r * ngc + g]);
+        for (int c = 0; c < cols; ++c)
+          for (int g = 0; g < ngr; ++g) ec[c * ngr + g] = tc[c * ngr + g] + grow * fabs(cc[c * ngr + g]);
         for (int gr = 0; gr < ngr; ++gr)
           for (int gc = 0; gc < ngc; ++gc) {
             int nr = 0, nc = 0, ib = -1, jb = -1;
             double sbr = -1.0, sbc = -1.0;
-            for (int r = 0; r < rows; ++r) {
+            for (int r = 0; r < rows && sch->level != ORC_DETECT; ++r) {
               if (unit_row(sch, r) != gr) continue;
               double S = 0.0;
               for (int c = 0; c < cols; ++c)
                 if (unit_col(sch, c) == gc) S += acc[r * nt + c];
               double d = S - cr[r * ngc + gc];
               dr[r * ngc + gc] = d;
-              double tau = tr[r * ngc + gc];
+              double tau = er[r * ngc + gc];
               if (fabs(d) > tau) {
                 ++nr;
                 double sc = score(d, tau);
@@ -365,7 +385,7 @@ int orc_gemm_ft(int64_t M, int64_t N, int64_t K, double alpha,
                 if (unit_row(sch, r) == gr) S += acc[r * nt + c];
               double d = S - cc[c * ngr + gr];
               dc[c * ngr + gr] = d;
-              double tau = tc[c * ngr + gr];
+              double tau = ec[c * ngr + gr];
               if (fabs(d) > tau) {
                 ++nc;
                 double sc = score(d, tau);
@@ -374,17 +394,31 @@ int orc_gemm_ft(int64_t M, int64_t N, int64_t K, double alpha,
             }
             if (nr == 0 && nc == 0) continue;
             ++lc[0];
+            if (sch->level == ORC_DETECT) {
+              /* detect-only: report the most flagged column, correct nothing */
+              orc_record rec;
+              rec.tile_m = (int32_t)ti; rec.tile_n = (int32_t)tj; rec.kstep = (int32_t)s;
+              rec.row = -1;
+              rec.col = (int32_t)(j0 + jb);
+              rec.residual_r = 0.0;
+              rec.residual_c = dc[jb * ngr + gr];
+              rec.tau = ec[jb * ngr + gr];
+              rec.delta = 0.0;
+              rec.kind = ORC_UNCORRECTABLE; ++lc[2];
+              rec_push(&L, rec);
+              continue;
+            }
             orc_record rec;
             rec.tile_m = (int32_t)ti; rec.tile_n = (int32_t)tj; rec.kstep = (int32_t)s;
             rec.row = ib >= 0 ? (int32_t)(i0 + ib) : -1;
             rec.col = jb >= 0 ? (int32_t)(j0 + jb) : -1;
             rec.residual_r = ib >= 0 ? dr[ib * ngc + gc] : 0.0;
             rec.residual_c = jb >= 0 ? dc[jb * ngr + gr] : 0.0;
-            rec.tau = (ib >= 0 ? tr[ib * ngc + gc] : 0.0) + (jb >= 0 ? tc[jb * ngr + gr] : 0.0);
+            rec.tau = (ib >= 0 ? er[ib * ngc + gc] : 0.0) + (jb >= 0 ? ec[jb * ngr + gr] : 0.0);
             rec.delta = 0.0;
             if (nr == 1 && nc == 1) {
               double drr = dr[ib * ngc + gc], dcc = dc[jb * ngr + gr];
-              if (fabs(drr - dcc) <= tr[ib * ngc + gc] + tc[jb * ngr + gr]) {
+              if (fabs(drr - dcc) <= er[ib * ngc + gc] + ec[jb * ngr + gr]) {
                 acc[ib * nt + jb] -= drr; /* subtract the offset (Section 4.2.1) */
                 rec.kind = ORC_CORRECTED; rec.delta = drr; ++lc[1];
               } else {
@@ -432,7 +466,7 @@ int orc_gemm_ft(int64_t M, int64_t N, int64_t K, double alpha,
       for (int q = 0; q < L.n; ++q) rec_push(&all, L.r[q]);
     }
     free(L.r);
-    free(acc); free(cr); free(cc); free(dr); free(dc); free(tr); free(tc);
+    free(acc); free(cr); free(cc); free(dr); free(dc); free(tr); free(tc); free(er); free(ec);
   }
 
   if (all.n > 1) qsort(all.r, (size_t)all.n, sizeof(orc_record), rec_cmp);
@@ -499,7 +533,7 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb,
                  const double* beta, const double* Cin, int64_t ldc, double* Cout,
                  int64_t ldo, int32_t mt, int32_t nt, int32_t kt, int32_t cadence,
-                 int32_t verify, double lambda, double u, const orc_fault* faults,
+                 int32_t verify, double lambda, double u, double mu, const orc_fault* faults,
                  int32_t nfaults, orc_zrecord* recs, int32_t cap, int64_t* counters,
                  int32_t* nrec) {
   if (M <= 0 || N <= 0 || K <= 0 || mt <= 0 || nt <= 0 || kt <= 0 || cadence <= 0) return -1;
@@ -545,6 +579,8 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
     double complex* dc = (double complex*)calloc((size_t)nt, sizeof(double complex));
     double* tr = (double*)calloc((size_t)mt, sizeof(double));
     double* tc = (double*)calloc((size_t)nt, sizeof(double));
+    double* er = (double*)calloc((size_t)mt, sizeof(double)); /* tau at this verification */
+    double* ec = (double*)calloc((size_t)nt, sizeof(double));
     orc_zrecord* L = NULL;
     int32_t nL = 0, capL = 0;
     int64_t lc[4] = {0, 0, 0, 0};
@@ -588,15 +624,20 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
         }
       }
       if (!verify || !(((s + 1) % cadence) == 0 || s == nks - 1)) continue;
+      /* thresholds at this verification: the norm term plus the growth term
+         mu*u*sqrt(k)*|checksum| after k elements of K */
+      const double grow = mu * u * sqrt((double)k1);
+      for (int r = 0; r < rows; ++r) er[r] = tr[r] + grow * cabs(cr[r]);
+      for (int c = 0; c < cols; ++c) ec[c] = tc[c] + grow * cabs(cc[c]);
       int nr = 0, nc = 0, ib = -1, jb = -1;
       double sbr = -1.0, sbc = -1.0;
       for (int r = 0; r < rows; ++r) {
         double complex S = 0.0;
         for (int c = 0; c < cols; ++c) S += acc[r * nt + c];
         dr[r] = S - cr[r];
-        if (cabs(dr[r]) > tr[r]) {
+        if (cabs(dr[r]) > er[r]) {
           ++nr;
-          double sc = score(cabs(dr[r]), tr[r]);
+          double sc = score(cabs(dr[r]), er[r]);
           if (sc > sbr) { sbr = sc; ib = r; }
         }
       }
@@ -604,9 +645,9 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
         double complex S = 0.0;
         for (int r = 0; r < rows; ++r) S += acc[r * nt + c];
         dc[c] = S - cc[c];
-        if (cabs(dc[c]) > tc[c]) {
+        if (cabs(dc[c]) > ec[c]) {
           ++nc;
-          double sc = score(cabs(dc[c]), tc[c]);
+          double sc = score(cabs(dc[c]), ec[c]);
           if (sc > sbc) { sbc = sc; jb = c; }
         }
       }
@@ -619,10 +660,10 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
       rec.col = jb >= 0 ? (int32_t)(j0 + jb) : -1;
       if (ib >= 0) { rec.res_r_re = creal(dr[ib]); rec.res_r_im = cimag(dr[ib]); }
       if (jb >= 0) { rec.res_c_re = creal(dc[jb]); rec.res_c_im = cimag(dc[jb]); }
-      rec.tau = (ib >= 0 ? tr[ib] : 0.0) + (jb >= 0 ? tc[jb] : 0.0);
+      rec.tau = (ib >= 0 ? er[ib] : 0.0) + (jb >= 0 ? ec[jb] : 0.0);
       double complex delta = 0.0;
       if (nr == 1 && nc == 1) {
-        if (cabs(dr[ib] - dc[jb]) <= tr[ib] + tc[jb]) {
+        if (cabs(dr[ib] - dc[jb]) <= er[ib] + ec[jb]) {
           acc[ib * nt + jb] -= dr[ib]; /* subtract the offset (Section 4.2.1) */
           delta = dr[ib];
           rec.kind = ORC_CORRECTED; ++lc[1];
@@ -674,7 +715,7 @@ int orc_zgemm_ft(int64_t M, int64_t N, int64_t K, const double* alpha,
       }
     }
     free(L);
-    free(acc); free(cr); free(cc); free(dr); free(dc); free(tr); free(tc);
+    free(acc); free(cr); free(cc); free(dr); free(dc); free(tr); free(tc); free(er); free(ec);
   }
 
   if (nall > 1) qsort(all, (size_t)nall, sizeof(orc_zrecord), zrec_cmp);

@@ -473,3 +473,61 @@ def test_offline_expected_runs_closed_forms(orc):
     # more tiles, more exposure: the expectation grows with the tile count
     r = [orc.offline_expected_runs(1 / 256, t) for t in (16, 64, 144)]
     assert 1.0 < r[0] < r[1] < r[2]
+
+
+# --------------------------------------------------------------------------
+# Detect-only (the offline scheme of Section 5.5)
+# --------------------------------------------------------------------------
+
+DET = dict(m_tb=128, n_tb=128, k_tb=32, m_w=64, n_w=64, m_t=16, n_t=8)
+
+
+def test_detect_only_reports_the_column_and_corrects_nothing(orc):
+    """Integer inputs, one offset per tile: each tile reports one detection
+    at the split's end, at the faulted column with residual exactly the
+    offset, no row; C keeps every offset (the offline scheme recomputes)."""
+    M, N, K = 256, 256, 512
+    A = synth.integers((M, K), 81)
+    B = synth.integers((K, N), 82)
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    faults = [(0, 0, 3, 5, 9, 64.0), (1, 1, 10, 100, 17, -32.0), (0, 1, 15, 0, 127, 8.0)]
+    s = orc.Schedule(**DET, cadence=K // 32, level=orc.DETECT)
+    res = orc.gemm_ft(A, B, s, faults=faults)
+    assert (res.detected, res.corrected, res.uncorrectable, res.checksum_only) == (3, 0, 3, 0)
+    got = sorted((r.tile_m, r.tile_n, r.kstep, r.row, r.col, r.kind, r.residual_c) for r in res.records)
+    want = sorted((tm, tn, K // 32 - 1, -1, tn * 128 + c, orc.UNCORRECTABLE, d) for (tm, tn, ks, r, c, d) in faults)
+    assert got == want
+    diff = res.C - ref
+    assert np.count_nonzero(diff) == 3
+    for (tm, tn, ks, r, c, d) in faults:
+        assert diff[tm * 128 + r, tn * 128 + c] == d
+
+
+def test_detect_only_checks_columns_only(orc):
+    """A hit on a row checksum goes unseen (the detector keeps none); a hit
+    on a column checksum is a detection; two offsets in one tile give one
+    record, at the column with the larger |residual| / tau."""
+    M, N, K = 128, 128, 256
+    A = synth.integers((M, K), 83)
+    B = synth.integers((K, N), 84)
+    s = orc.Schedule(**DET, cadence=K // 32, level=orc.DETECT)
+    row_hit = orc.gemm_ft(A, B, s, faults=[(0, 0, 2, 5, 9, 64.0, orc.T_ROWSUM)])
+    assert row_hit.detected == 0
+    col_hit = orc.gemm_ft(A, B, s, faults=[(0, 0, 2, 5, 9, 64.0, orc.T_COLSUM)])
+    assert col_hit.detected == 1 and col_hit.records[0].col == 9 and col_hit.records[0].residual_c == -64.0
+    two = orc.gemm_ft(A, B, s, faults=[(0, 0, 2, 5, 9, 64.0), (0, 0, 3, 70, 40, -128.0)])
+    assert two.detected == 1 and two.records[0].col == 40
+
+
+def test_detect_only_split_k_and_float_inputs(orc):
+    """With split-K each split reports at its own end; fault-free float
+    inputs raise nothing."""
+    M, N, K = 128, 256, 1024
+    A = synth.integers((M, K), 85)
+    B = synth.integers((K, N), 86)
+    s = orc.Schedule(**DET, cadence=K // 64, split_k=2, level=orc.DETECT)
+    res = orc.gemm_ft(A, B, s, faults=[(0, 1, 3, 1, 2, 16.0), (0, 0, 20, 7, 8, 16.0)])
+    assert sorted((r.tile_n, r.kstep) for r in res.records) == [(0, 31), (1, 15)]
+    Af = synth.uniform((M, K), 87)
+    Bf = synth.uniform((K, N), 88)
+    assert orc.gemm_ft(Af, Bf, orc.Schedule(**DET, cadence=K // 32, level=orc.DETECT)).detected == 0

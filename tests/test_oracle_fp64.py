@@ -168,21 +168,55 @@ def test_zgemm_rotation_by_i():
     assert abs(b.delta - 1j * a.delta) <= 1e-20 + 1e-9 * abs(a.delta)
 
 
-def test_zgemm_threshold_boundary_from_known_norms():
+@pytest.mark.parametrize("kstep", [0, 2])
+def test_zgemm_threshold_boundary_from_known_norms(kstep):
     """All entries 1 + i: |a|^2 = 2, so ||A(i,:)|| = sqrt(2K) and the block
-    norms are sqrt(rows * 2K); with integer data the residual is exactly the
-    offset, flagged exactly when it exceeds lambda * u * norms."""
+    norms are sqrt(rows * 2K); after k = 8 (kstep + 1) elements of K a row
+    checksum is k * (1 + i) * N (1 + i) = 2i k N, of modulus 2 k N.  With
+    integer data the residual is exactly the offset, flagged exactly when it
+    exceeds lambda * u * norms + mu * u * sqrt(k) * 2 k N."""
     M = N = 64
     K = 32
     A = np.full((M, K), 1 + 1j)
     B = np.full((K, N), 1 + 1j)
-    lam, u = 4.0, 2.0 ** -10
-    tau_r = lam * u * np.sqrt(2 * K) * np.sqrt(N * 2 * K)
+    lam, u, mu = 4.0, 2.0 ** -10, 3.0
+    k = 8 * (kstep + 1)
+    tau_r = lam * u * np.sqrt(2 * K) * np.sqrt(N * 2 * K) + mu * u * np.sqrt(k) * 2 * k * N
     for scale, flagged in ((0.99, False), (1.01, True)):
-        res = orc.zgemm_ft(A, B, cadence=1, lam=lam, u=u, faults=[(0, 0, 0, 5, 6, scale * tau_r)])
+        res = orc.zgemm_ft(A, B, cadence=1, lam=lam, u=u, mu=mu, faults=[(0, 0, kstep, 5, 6, scale * tau_r)])
         assert (len(res.records) > 0) == flagged
         if flagged:
+            assert res.records[0].kstep == kstep
             assert res.records[0].tau == pytest.approx(2 * tau_r, rel=1e-14)
+
+
+@pytest.mark.parametrize("kstep,split", [(0, 1), (5, 1), (5, 2)])
+def test_threshold_growth_term_from_known_checksums(kstep, split):
+    """All-ones A and B (same-sign data, the case the growth term is for):
+    after k elements of K in its split a tile's row checksum is k * n_tb and
+    its column checksum k * m_tb, the norms are ||A(i,:)|| = sqrt(K) and
+    ||B(:,J)||_F = sqrt(n_tb K).  So the row threshold is lambda * u * sqrt(K)
+    * sqrt(n_tb K) + mu * u * sqrt(k) * k n_tb, and an offset on the
+    accumulator is flagged exactly when it exceeds it (k-steps of 4; with two
+    splits the second starts at k-step 4, so k counts from there)."""
+    M = N = 16
+    K = 32
+    A = np.ones((M, K))
+    B = np.ones((K, N))
+    lam, u, mu = 2.0, 2.0 ** -12, 5.0
+    s = orc.Schedule(m_tb=16, n_tb=16, k_tb=4, m_w=16, n_w=16, m_t=4, n_t=4, cadence=1, split_k=split,
+                     level=orc.BLOCK, lam=lam, u=u, mu=mu)
+    start = 0 if (split == 1 or kstep < 4) else 4
+    k = 4 * (kstep + 1 - start)
+    tau = lam * u * np.sqrt(K) * np.sqrt(16 * K) + mu * u * np.sqrt(k) * k * 16
+    for scale, flagged in ((0.99, False), (1.01, True)):
+        res = orc.gemm_ft(A, B, s, faults=[(0, 0, kstep, 3, 7, scale * tau)])
+        assert (len(res.records) > 0) == flagged, (scale, tau)
+        if flagged:
+            r = res.records[0]
+            assert (r.kstep, r.row, r.col, r.kind) == (kstep, 3, 7, orc.CORRECTED)
+            assert r.tau == pytest.approx(2 * tau, rel=1e-12)
+            assert np.max(np.abs(res.C - A @ B)) < 1e-12  # the offset came back out
 
 
 def test_zgemm_no_false_alarm_and_close_to_numpy():
