@@ -343,20 +343,26 @@ def _tile_faults(synth, seed, count, M, N, K, kblk, unit=1.0):
             for (a, b, ks, r, c), g, sg in zip(pos, mags, sign)]
 
 
-def _above_threshold(A, B, i, j, r0, c0, lam=32.0):
-    """|delta| that the analytic threshold (lambda = 32) flags on both the
-    row and the column of element (i, j) of the tile at (r0, c0): the larger
-    of the two thresholds, from the stored operand values."""
+def _above_threshold(A, B, i, j, r0, c0, lam=32.0, mu=8.0):
+    """|delta| that the analytic threshold flags on both the row and the
+    column of element (i, j) of the tile at (r0, c0), verified once after the
+    whole K: the larger of lam*u*norms + mu*u*sqrt(K)*|checksum| over the two
+    sides, from the stored operand values (checksums in float64)."""
     import torch
 
     def val(x):
-        return x.view(torch.float8_e4m3fn).float() if x.dtype == torch.uint8 else x.float()
+        return (x.view(torch.float8_e4m3fn) if x.dtype == torch.uint8 else x).double()
     M, N = A.shape[0], B.shape[1]
+    K = A.shape[1]
     AI = val(A[r0:min(M, r0 + TDM)])
     BJ = val(B[:, c0:min(N, c0 + TDN)])
-    row = val(A[i]).norm() * BJ.norm()
-    col = AI.norm() * val(B[:, j]).norm()
-    return float(lam * 2.0 ** -24 * torch.maximum(row, col))
+    ai, bj = val(A[i]), val(B[:, j])
+    c_r = (ai @ BJ.sum(1)).abs()
+    c_c = (AI.sum(0) @ bj).abs()
+    u = 2.0 ** -24
+    row = lam * u * ai.norm() * BJ.norm() + mu * u * math.sqrt(K) * c_r
+    col = lam * u * AI.norm() * bj.norm() + mu * u * math.sqrt(K) * c_c
+    return float(torch.maximum(row, col))
 
 
 def _count(records, faults, key_of):

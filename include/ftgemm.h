@@ -163,21 +163,29 @@ int ftgemm_get_schedule(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
                         ftgemm_schedule* out);
 
 /* Detection threshold (Section 2.2 leaves its value open).
- * mode 0, analytic:  tau_row(i) = lambda * u * ||A(i,:)||_2 * ||B(:,J)||_F and
- *                    tau_col(j) = lambda * u * ||A(I,:)||_F * ||B(:,j)||_2,
- *   J (I) the columns (rows) of the verification unit, u = 2^-24.  lambda <= 0
+ * mode 0, analytic: at a verification after k elements of K,
+ *     tau_row(i) = lambda * u * ||A(i,:)||_2 * ||B(:,J)||_F + mu * u * sqrt(k) * |c_row(i)|
+ *     tau_col(j) = lambda * u * ||A(I,:)||_F * ||B(:,j)||_2 + mu * u * sqrt(k) * |c_col(j)|,
+ *   J (I) the columns (rows) of the verification unit, c the row / column
+ *   checksum as it stands, u = 2^-24 (2^-53 for ftgemm_dgemm / _zgemm),
+ *   mu = 8.  The first term covers the rounding error of zero-mean data, the
+ *   second the growth of the partial sums of same-sign data.  lambda <= 0
  *   keeps the current value (default 32).  Turns the learned threshold off.
- * mode 1, learned (tensor-core path, level TILE; no counterpart in the
- *   paper): each tile uses lambda_t = lambda * 2^f(x_t) in the same formulas,
+ *   Every path screens residuals in fp32 against tau / 2 and confirms the
+ *   screened ones in fp64 against tau.
+ * mode 1, learned (no counterpart in the paper; the tensor-core path at
+ *   level TILE and the fp32 path at level BLOCK): each tile uses
+ *   lambda_t = lambda * 2^f(x_t) in the norm term, with no growth term,
  *   f the 5 -> 32 -> 32 -> 1 ReLU network whose FTGEMM_MLP_PARAMS parameters
  *   mlp_weights holds (host array, copied; layout W1[32][5], b1[32],
  *   W2[32][32], b2[32], W3[32], b3), x_t the tile's features: log2(K)/16,
  *   the coherence ||e^T A_I||_2 / (sqrt|I| ||A_I||_F) of its row block, the
  *   same ||B_J e||_2 / (sqrt|J| ||B_J||_F) of its column block, the operand
- *   type (0.5 bf16, 1 e4m3) and log2(|I| |J|)/16.  f is evaluated in the GEMM
- *   epilogue; a non-finite or non-positive lambda_t falls back to the
- *   analytic one.  lambda (the calibration scale) must be > 0.  The SIMT
- *   path keeps the analytic threshold.  Synchronises the handle's stream.
+ *   type (0 fp32, 0.5 bf16, 1 e4m3) and log2(|I| |J|)/16.  f is evaluated
+ *   once per tile inside the GEMM kernel; a non-finite or non-positive
+ *   lambda_t falls back to the analytic threshold.  lambda (the calibration
+ *   scale) must be > 0.  The fp32 levels THREAD and WARP keep the analytic
+ *   threshold.  Synchronises the handle's stream.
  * Other modes: FTGEMM_ERR_UNSUPPORTED. */
 #define FTGEMM_MLP_INPUTS 5
 #define FTGEMM_MLP_PARAMS 1281
@@ -185,14 +193,15 @@ int ftgemm_set_threshold(ftgemm_handle_t handle, int mode, double lambda,
                          const float* mlp_weights, size_t n_weights);
 
 /* Residual sink for training the learned threshold (no counterpart in the
- * paper): while set, every tensor-core call at level TILE writes, for each
- * of its tiles t (t = tile_m * tiles_n + tile_n; in a group, offset by the
- * tiles of the problems scheduled before it), lam_needed[t] = the largest
- * |residual| / (u * norm product) over the tile's rows and columns -- the
- * smallest analytic lambda that flags nothing there -- and its 5 features
- * into features[5t .. 5t+4] (device arrays of `capacity` tiles, owned by the
- * caller).  lam_needed = NULL removes the sink.  A call with more tiles than
- * `capacity` fails with FTGEMM_ERR_ARG. */
+ * paper): while set, every tensor-core call at level TILE and every fp32
+ * call at level BLOCK writes, for each of its tiles t (t = tile_m * tiles_n
+ * + tile_n; in a group, offset by the tiles of the problems scheduled before
+ * it), lam_needed[t] = the largest |residual| / (u * norm product) over the
+ * tile's rows, columns and (fp32) verification periods -- the smallest
+ * lambda of the norm term alone that flags nothing there -- and its 5
+ * features into features[5t .. 5t+4] (device arrays of `capacity` tiles,
+ * owned by the caller).  lam_needed = NULL removes the sink.  A call with
+ * more tiles than `capacity` fails with FTGEMM_ERR_ARG. */
 int ftgemm_set_residual_sink(ftgemm_handle_t handle, float* lam_needed, float* features,
                              int64_t capacity);
 
@@ -409,9 +418,10 @@ int ftgemm_gemm_offline(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
  * B e per 128-column block (Eq. 1-2) accumulate beside each 128 x 128
  * output tile during the K loop (Eq. 4); every `cadence` k-steps of 8
  * (cadence <= 0: once, after the last k-step) the tile's row and column
- * sums are compared with them against lambda * 2^-53 * ||A(i,:)|| *
- * ||B(:,J)||_F and lambda * 2^-53 * ||A(I,:)||_F * ||B(:,j)|| (lambda of
- * ftgemm_set_threshold mode 0), and one corrupted element is located and
+ * sums are compared with them against the analytic threshold of
+ * ftgemm_set_threshold mode 0 with u = 2^-53 (lambda * u * ||A(i,:)|| *
+ * ||B(:,J)||_F + mu * u * sqrt(k) * |checksum| and its column form; the
+ * comparison is in double, no screen), and one corrupted element is located and
  * corrected or a corrupted checksum reset (Section 4.2.1); records as for
  * ftgemm_gemm.  Device pointers, row-major, leading dimensions in elements
  * (lda >= k, ldb >= n, ldc >= n); beta == 0: C is not read.  ft_level:
@@ -496,12 +506,20 @@ int ftgemm_get_stats(ftgemm_handle_t handle, ftgemm_stats* out, int reset);
  * The array is shared by every call and keeps the last call's contents; each
  * call clears the report counters it relies on.  Calls that overlap on the
  * GPU (different streams, concurrent host threads) race on the array:
- * serialise them.  The first call on a device looks up the array's address
- * with that device current; make that first call before any stream capture.
+ * serialise them.  The first call on a device sets that device up while it
+ * is current: it looks up the array's address and loads every kernel a call
+ * can launch.  With lazy module loading (CUDA's default) that set-up can
+ * itself allocate device memory, so the promise holds from the second call
+ * on: make one call (any size, any level) at start-up, before relying on it
+ * and before any stream capture.
  * A, B, C: device pointers on the current device; cuda_stream: a
  * cudaStream_t (NULL = legacy default stream); level: FTGEMM_FT_OFF..BLOCK;
- * report: NULL, or as for ftgemm_gemm (at most 256 records per call; the
- * call then synchronises the stream). */
+ * report: NULL, or as for ftgemm_gemm: at most 256 records are kept per
+ * call, sorted as ftgemm_report_fetch sorts them before the first
+ * `capacity` are copied; the call then synchronises the stream.  Bounded
+ * device waits that gave up stay counted in the array until a call with a
+ * report reads the count: that call returns FTGEMM_ERR_TIMEOUT and clears
+ * it, so a give-up in an earlier call without a report is reported there. */
 int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha, const float* A,
                         int64_t lda, const float* B, int64_t ldb, double beta, float* C,
                         int64_t ldc, ftgemm_ft_level ft_level, void* cuda_stream,

@@ -367,8 +367,9 @@ class Handle:
                         rep.n_records, bool(rep.overflow), rl)
 
     def set_residual_sink(self, lam_needed=None, features=None):
-        """Route every later TILE-level tensor-core call's per-tile residual
-        ratios and features into the given CUDA tensors (None removes it)."""
+        """Route every later TILE-level tensor-core call's and BLOCK-level
+        fp32 call's per-tile residual ratios and features into the given CUDA
+        tensors (None removes it)."""
         if lam_needed is None:
             _check(lib().ftgemm_set_residual_sink(self._h, None, None, 0))
             return

@@ -52,9 +52,13 @@ cudaError_t launch_wait_selftest(DevReport* rep, long long limit_cycles, cudaStr
 cudaError_t launch_nonfused_inject(const Fault* f, int nf, int ks_lo, int ks_hi, int tiles_n, float* acc,
                                    long long ldacc, float* Cc, long long ldcc, float* CrT, long long ldcr,
                                    cudaStream_t st);
+cudaError_t launch_block_coherence(const float* V, const float* W, long long ldv, int K, const float* nA,
+                                   const float* nB, int M, int N, int m_u, int n_u, float* coA, float* coB,
+                                   cudaStream_t st);
 cudaError_t launch_nonfused_verify(float* acc, long long ldacc, int M, int N, float* Cc, long long ldcc,
                                    float* CrT, long long ldcr, const float* nA, const float* nB, float lam_u,
-                                   int kstep, DevReport* rep, ftgemm_fault_record* recs, cudaStream_t st);
+                                   float grow, int kstep, DevReport* rep, ftgemm_fault_record* recs,
+                                   cudaStream_t st);
 cudaError_t launch_nonfused_epilogue(const float* acc, long long ldacc, int M, int N, float alpha, float beta,
                                      float* C, long long ldc, cudaStream_t st);
 int mlp_grad_blocks(long long nb);
@@ -101,6 +105,11 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 
 using namespace ftg;
 
+// Scale of the threshold's checksum-growth term mu * u * sqrt(k) * |c| (the
+// analytic reading of the "predetermined threshold" of Section 2.2), on the
+// CUDA cores and on the tensor cores alike.
+constexpr double kMu = 8.0;
+
 struct ftgemm_ctx {
   int device = 0;
   int num_sms = 0;
@@ -124,6 +133,8 @@ struct ftgemm_ctx {
   ftgemm_schedule sched{};
   double lambda = 32.0;
   double lambda_tc[2] = {32.0, 32.0};  // bf16, e4m3
+  // checksum-growth term of the analytic threshold, mu * u * sqrt(k) * |c|
+  double mu = kMu;
   float fp8_sa = 1.f, fp8_sb = 1.f;
   float* qscratch = nullptr;  // amax bits + scale of ftgemm_quantize
   // learned threshold (tensor-core path)
@@ -395,8 +406,10 @@ extern "C" int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out);
 // Shape, tiling and epilogue fields of a tensor-core problem.
 static void tc_set_problem(TcProblem& P, int dt, bool abft, int M, int N, int K, const void* A, int64_t lda,
                            const void* B, int64_t ldb, float* C, int64_t ldc, double alpha, double beta,
-                           float acc_scale, float lam_u) {
+                           float acc_scale, float lam_u, double mu) {
   memset(&P, 0, sizeof(P));
+  // checksum-growth term of the analytic threshold at the one verification, k = K
+  P.grow = (float)(mu * std::ldexp(1.0, -24) * std::sqrt((double)K));
   const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
   const int kblk = dt == 0 ? 64 : 128;
   P.M = M; P.N = N; P.K = K;
@@ -490,7 +503,8 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   memset(&b, 0, sizeof(b));
   TcProblem& P = b.one;
   tc_set_problem(P, dt, abft, (int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, alpha, beta,
-                 dt == 1 ? h->fp8_sa * h->fp8_sb : 1.f, (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24)));
+                 dt == 1 ? h->fp8_sa * h->fp8_sb : 1.f, (float)(h->lambda_tc[dt] * std::ldexp(1.0, -24)),
+                 h->mu);
   P.mlp = h->mlp_on ? h->mlp_theta : nullptr;
   P.mlp_scale = h->mlp_scale;
   b.table = nullptr;
@@ -685,7 +699,7 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
     const ftgemm_problem& u = pr[order[q]];
     TcProblem& P = g->probs[q];
     tc_set_problem(P, dt, abft, (int)u.m, (int)u.n, (int)u.k, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.alpha, u.beta,
-                   dt == 1 ? u.scale_a * u.scale_b : 1.f, lam_u);
+                   dt == 1 ? u.scale_a * u.scale_b : 1.f, lam_u, h->mu);
     P.id = order[q];
     P.mlp = h->mlp_on ? h->mlp_theta : nullptr;
     P.mlp_scale = h->mlp_scale;
@@ -778,7 +792,7 @@ int ftgemm_group_plan(int32_t count, const int64_t* m, const int64_t* n, const i
   for (int q = 0; q < count; ++q) {
     const int i = order[q];
     tc_set_problem(probs[q], dt, abft, (int)m[i], (int)n[i], (int)k[i], nullptr, k[i], nullptr, n[i], nullptr,
-                   n[i], 1.0, 0.0, 1.f, 0.f);
+                   n[i], 1.0, 0.0, 1.f, 0.f, 0.0);
     total += (long long)probs[q].tiles_m * probs[q].tiles_n;
     if (total > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_plan: too many tiles");
   }
@@ -1309,9 +1323,16 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
                                                          kmajor_scratch_floats(K, N))
                            : 0;
   const size_t nPart = split > 1 ? (size_t)split * M * N : 0;
+  // learned threshold and residual sink (block level): block coherences
+  const bool learned = level == FTGEMM_FT_BLOCK && h->mlp_on;
+  const bool sink = level == FTGEMM_FT_BLOCK && h->sink_lam != nullptr;
+  if (sink && (long long)tiles_m * tiles_n > h->sink_cap)
+    FAIL(FTGEMM_ERR_ARG, "residual sink: %lld tiles, capacity %lld", (long long)tiles_m * tiles_n,
+         (long long)h->sink_cap);
+  const size_t nCo = (learned || sink) ? (size_t)(tiles_m + tiles_n) : 0;
   const size_t oAt = 0, oBp = align64(oAt + nAt), oV = align64(oBp + nBp), oW = align64(oV + nV),
                oNa = align64(oW + nW), oNb = align64(oNa + nNa), oScr = align64(oNb + nNb),
-               oPart = align64(oScr + nScr), total = align64(oPart + nPart);
+               oPart = align64(oScr + nScr), oCo = align64(oPart + nPart), total = align64(oCo + nCo);
   {
     int rc = ensure_ws(h, total);
     if (rc) return rc;
@@ -1333,6 +1354,12 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
     CK(launch_encode_kmajor(Bk, ldbp, K, N, need_vw ? n_u : 2, need_vw ? ws + oW : nullptr, ldv,
                             ws + oNb, ws + oScr, &launches, h->stream));
   }
+  if (learned || sink) {
+    CK(launch_block_coherence(ws + oV, ws + oW, ldv, K, ws + oNa, ws + oNb, M, N, m_u, n_u, ws + oCo,
+                              ws + oCo + tiles_m, h->stream));
+    ++launches;
+  }
+  if (sink) CK(cudaMemsetAsync(h->sink_lam, 0, sizeof(float) * (size_t)tiles_m * tiles_n, h->stream));
 
   SimtMaps maps;
   {
@@ -1352,6 +1379,7 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   p.nA = abft ? ws + oNa : nullptr;
   p.nB = abft ? ws + oNb : nullptr;
   p.lam_u = (float)(h->lambda * std::ldexp(1.0, -24));
+  p.mu_u = (float)(h->mu * std::ldexp(1.0, -24));
   p.cadence = std::max(1, cadence);
   p.ksteps = ksteps;
   p.ks_per_split = ks_per_split;
@@ -1363,6 +1391,12 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   p.tiles_m = tiles_m;
   p.tiles_n = tiles_n;
   p.group_m = std::min(tiles_m, 16);
+  p.mlp = learned ? h->mlp_theta : nullptr;
+  p.mlp_scale = h->mlp_scale;
+  p.coA = (learned || sink) ? ws + oCo : nullptr;
+  p.coB = (learned || sink) ? ws + oCo + tiles_m : nullptr;
+  p.sink_lam = sink ? h->sink_lam : nullptr;
+  p.sink_x = sink ? h->sink_x : nullptr;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (h->timing) {
     int rc = take_events(h, &ev);
@@ -1585,8 +1619,10 @@ int ftgemm_gemm_nonfused(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, dou
     const int ks_lo = k0 / 16, ks_hi = (k0 + kl + 15) / 16;
     CK(launch_nonfused_inject(nf > 0 ? h->d_faults : nullptr, nf, ks_lo, ks_hi, tiles_n, Acc, ldacc, Cc, ldacc, CrT,
                               ldt, h->stream));
-    CK(launch_nonfused_verify(Acc, ldacc, M, N, Cc, ldacc, CrT, ldt, nA, nB, lam_u, ks_hi - 1, h->rep, h->recs,
-                              h->stream));
+    // growth term after the k0 + kl elements of K accumulated so far
+    const float grow = (float)(h->mu * std::ldexp(1.0, -24) * std::sqrt((double)(k0 + kl)));
+    CK(launch_nonfused_verify(Acc, ldacc, M, N, Cc, ldacc, CrT, ldt, nA, nB, lam_u, grow, ks_hi - 1, h->rep,
+                              h->recs, h->stream));
     launches += (nf > 0 ? 1 : 0) + 1;
   }
   h->timing = timing;
@@ -1712,6 +1748,7 @@ static int f64_gemm(ftgemm_ctx* h, bool cplx, int64_t m, int64_t n, int64_t k, c
     p.nA = (const double*)(h->ws + oNa); p.nB = (const double*)(h->ws + oNb);
   }
   p.lam_u = h->lambda * std::ldexp(1.0, -53);
+  p.mu_u = h->mu * std::ldexp(1.0, -53);
   p.cadence = cadence > 0 ? cadence : ksteps;
   p.faults = nf > 0 ? h->d_faults : nullptr;
   p.nfaults = nf;

@@ -376,6 +376,69 @@ cudaError_t launch_encode_kmajor(const float* X, long long ldx, int K, int L, in
   return cudaGetLastError();
 }
 
+// Coherence of every block, one CTA each: blocks 0..nb_a-1 of A (rows of
+// m_u), then nb_b blocks of B (columns of n_u).  For block b of X with block
+// sums S[b][0..K) and line norms nrm: ||S_b||_2 / (sqrt(count) *
+// sqrt(sum of nrm^2 over the block)), in [0, 1]; 0 for an all-zero block.
+// A feature of the learned threshold (1 when every line of the block is the
+// same, about count^-1/2 for independent zero-mean lines).  Fixed-order
+// reductions, so the value is reproducible.
+__global__ void __launch_bounds__(256) block_coherence_kernel(const float* __restrict__ Sa, const float* __restrict__ Sb,
+                                                              long long lds, int K, const float* __restrict__ nA,
+                                                              const float* __restrict__ nB, int M, int N, int m_u,
+                                                              int n_u, int nb_a, float* __restrict__ coA,
+                                                              float* __restrict__ coB) {
+  __shared__ float red[2][8];
+  const bool side_a = (int)blockIdx.x < nb_a;
+  const int b = side_a ? blockIdx.x : blockIdx.x - nb_a;
+  const float* S = (side_a ? Sa : Sb) + (long long)b * lds;
+  const float* nrm = side_a ? nA : nB;
+  const int l0 = b * (side_a ? m_u : n_u), l1 = min(side_a ? M : N, l0 + (side_a ? m_u : n_u));
+  float cs = 0.f, fr = 0.f;
+  for (int k = threadIdx.x; k < K; k += 256) cs = fmaf(S[k], S[k], cs);
+  for (int l = l0 + threadIdx.x; l < l1; l += 256) fr = fmaf(nrm[l], nrm[l], fr);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    fr += __shfl_xor_sync(0xffffffffu, fr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = cs;
+    red[1][threadIdx.x >> 5] = fr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float c = 0.f, f = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      c += red[0][w];
+      f += red[1][w];
+    }
+    const float fro = sqrtf(f);
+    (side_a ? coA : coB)[b] = fro > 0.f ? sqrtf(c) / (sqrtf((float)(l1 - l0)) * fro) : 0.f;
+  }
+}
+
+cudaError_t launch_block_coherence(const float* V, const float* W, long long ldv, int K, const float* nA,
+                                   const float* nB, int M, int N, int m_u, int n_u, float* coA, float* coB,
+                                   cudaStream_t st) {
+  const int nb_a = (M + m_u - 1) / m_u, nb_b = (N + n_u - 1) / n_u;
+  block_coherence_kernel<<<nb_a + nb_b, 256, 0, st>>>(V, W, ldv, K, nA, nB, M, N, m_u, n_u, nb_a, coA, coB);
+  return cudaGetLastError();
+}
+
+// Load the k-major layout and encoding kernels into the current device's
+// context now (with lazy module loading a kernel is otherwise loaded, which
+// allocates device memory, at its first launch).
+cudaError_t preload_kmajor_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, transpose_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, copy_pad_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, encode_kmajor_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, colnorm_finish_kernel);
+  return e;
+}
+
 cudaError_t launch_splitk_reduce(const float* part, int splits, int M, int N, float alpha,
                                  float beta, float* C, long long ldc, cudaStream_t st) {
   const long long total = (long long)M * N;

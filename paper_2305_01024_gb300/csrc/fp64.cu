@@ -351,18 +351,23 @@ __global__ void __launch_bounds__(256, 1) f64_gemm_kernel(const F64Params p) {
         __syncthreads();
         T d = f64_zero(T{});
         bool flag = false;
+        // this verification's threshold: the norm term plus the growth term
+        // mu * u * sqrt(k) * |checksum| after k elements of K
+        const double tau_now = tau_own + p.mu_u * sqrt((double)min((s + 1) * BK, p.K)) * f64_abs(csum);
         if (own_c) {
           T c = colpart[0][tid];
 #pragma unroll
           for (int w = 1; w < 8; ++w) c = f64_add(c, colpart[w][tid]);
           colpart[0][tid] = c;  // the column sum, kept for a checksum reset
           d = f64_sub(c, csum);
-          flag = tid < cols && f64_abs(d) > tau_own;
+          flag = tid < cols && f64_abs(d) > tau_now;
           dres_c[tid] = d;
+          tau_c[tid] = tid < cols ? tau_now : 0.0;
         } else if (own_r) {
           d = f64_sub(rowsum[tid - BN], csum);
-          flag = tid - BN < rows && f64_abs(d) > tau_own;
+          flag = tid - BN < rows && f64_abs(d) > tau_now;
           dres_r[tid - BN] = d;
+          tau_r[tid - BN] = tid - BN < rows ? tau_now : 0.0;
         }
         if (__syncthreads_or(flag)) {
           // rare path: count, then the largest |d|/tau (exact in double;
@@ -370,7 +375,7 @@ __global__ void __launch_bounds__(256, 1) f64_gemm_kernel(const F64Params p) {
           double score = 0.0;
           if (flag) {
             const double a = f64_abs(d);
-            score = tau_own > 0.0 ? a / tau_own : __longlong_as_double(0x7ff0000000000000ll);
+            score = tau_now > 0.0 ? a / tau_now : __longlong_as_double(0x7ff0000000000000ll);
             atomicAdd(own_c ? &nc : &nr, 1);
             atomicMax(own_c ? &best_c : &best_r, (unsigned long long)__double_as_longlong(score));
           }

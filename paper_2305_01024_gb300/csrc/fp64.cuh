@@ -20,7 +20,8 @@ struct F64Params {
   const void* W;
   const double* nA;
   const double* nB;
-  double lam_u;
+  double lam_u;  // lambda * u: the norm term of the threshold
+  double mu_u;   // mu * u: the checksum-growth term, mu_u * sqrt(k) * |checksum|
   int cadence;  // k-steps per verification period (>= 1)
   const Fault* faults;
   int nfaults;

@@ -50,6 +50,19 @@ __device__ __forceinline__ unsigned long long flag_key(float score, int idx) {
 __device__ __forceinline__ int key_index(unsigned long long key) {
   return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
 }
+// Detection threshold of one row or column: lam_u * nx * ny (the norm term)
+// plus grow * |c| (the checksum-growth term, grow = mu * u * sqrt(k)).
+// Rounded step by step without contraction, so every place that forms it
+// gets the same value.
+__device__ __forceinline__ float ft_tau(float lam_u, float nx, float ny, float grow, float c) {
+  return __fmaf_rn(grow, fabsf(c), __fmul_rn(__fmul_rn(lam_u, nx), ny));
+}
+
+// The fp32 screen flags a residual above half the threshold; the fp64
+// confirmation then compares with the threshold itself.  The margin keeps
+// the screen's own rounding from hiding a residual the fp64 sum would flag.
+constexpr float kScreen = 0.5f;
+
 __device__ __forceinline__ float flag_score(float d, float tau) {
   float a = fabsf(d);
   if (tau > 0.f) return a / tau;
@@ -75,7 +88,8 @@ struct SimtParams {
   float alpha, beta;
   const float* nA;  // [M] row 2-norms of A
   const float* nB;  // [N] column 2-norms of B
-  float lam_u;      // lambda * u
+  float lam_u;      // lambda * u: the norm term of the threshold
+  float mu_u;       // mu * u: the checksum-growth term, mu_u * sqrt(k) * |checksum|
   int cadence;      // k-steps per period (>= 1)
   int ksteps;       // ceil(K / k_tb)
   int ks_per_split; // k-steps per split
@@ -84,6 +98,15 @@ struct SimtParams {
   DevReport* rep; ftgemm_fault_record* recs;
   int tiles_m, tiles_n;
   int group_m;      // tile rows per raster group
+  // learned threshold (block level): lambda of a tile = mlp_scale * 2^f(x)
+  // with f the network (device parameters, or null: analytic) and x the
+  // tile's features, which need the coherences coA [tiles_m] / coB [tiles_n]
+  const float* mlp; float mlp_scale;
+  const float* coA; const float* coB;
+  // residual sink (block level, optional): per tile the largest |residual|
+  // / (u * norm product) over its rows, columns and periods (float bits,
+  // combined with atomicMax; zeroed by the host), and its 5 features
+  float* sink_lam; float* sink_x;
 };
 
 struct SimtMaps {
@@ -128,7 +151,8 @@ struct TcProblem {
   int c_vec;                      // C rows 16-byte aligned (float4 stores)
   float alpha, beta;
   float acc_scale;                // fp8: product of the per-tensor scales; bf16: 1
-  float lam_u;                    // analytic threshold factor lambda * u
+  float lam_u;                    // analytic threshold: factor lambda * u of the norm term
+  float grow;                     // analytic threshold: mu * u * sqrt(K), factor of |checksum|
   const float* mlp;               // learned threshold: network parameters (device), or null
   float mlp_scale;                // lambda of a tile = mlp_scale * 2^network(features)
 };

@@ -16,8 +16,17 @@
 // zero (the report counters) and overwrites the rest.  Calls that overlap on
 // the GPU (on different streams, or from several host threads at once) use
 // the same bytes and race; serialise them.  The first call on each device
-// looks up the array's device address with cudaGetSymbolAddress while that
-// device is current; make that first call before any stream capture.
+// sets the device up while it is current: it looks up the array's device
+// address with cudaGetSymbolAddress and loads every kernel any later call
+// can launch.  Under lazy module loading (CUDA's default) both steps can
+// allocate device memory, so the no-allocation promise holds from the
+// second call on: make one call (any size) at start-up, before relying on it
+// and before any stream capture.
+//
+// Bounded device waits that give up are counted in the array and stay there
+// until a call with a report reads them: that call returns
+// FTGEMM_ERR_TIMEOUT and clears the count, so a give-up in a call without a
+// report is not lost.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +47,8 @@ long long kmajor_scratch_floats(int K, int L);
 cudaError_t launch_encode_kmajor(const float*, long long, int, int, int, float*, long long, float*,
                                  float*, int*, cudaStream_t);
 void set_last_error(const char* msg);
+cudaError_t preload_kmajor_kernels();
+cudaError_t simt_preload_huge16();
 
 constexpr size_t kNoallocBytes = (size_t)FTGEMM_NOALLOC_SCRATCH_BYTES;
 constexpr int kNoallocRecords = 256;  // event records kept per call
@@ -56,8 +67,20 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-// Device address of the array, looked up once per device with that device
-// current (host code only knows a host-side stand-in for the symbol).
+// Zero the event counters and set the record capacity; the count of waits
+// that gave up is left for the next call with a report to read.
+__global__ void noalloc_reset_kernel(DevReport* rep, int capacity) {
+  rep->detected = 0ull;
+  rep->corrected = 0ull;
+  rep->uncorrectable = 0ull;
+  rep->checksum_only = 0ull;
+  rep->n_records = 0;
+  rep->capacity = capacity;
+}
+
+// Per-device set-up, done once with that device current: the array's device
+// address (host code only knows a host-side stand-in for the symbol) and the
+// loading of every kernel a call can launch.
 void* scratch_address(int device, cudaError_t* err) {
   static std::mutex mu;
   static std::vector<void*> addr;
@@ -67,10 +90,26 @@ void* scratch_address(int device, cudaError_t* err) {
     void* p = nullptr;
     *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (*err != cudaSuccess) return nullptr;
+    cudaFuncAttributes a;
+    *err = cudaFuncGetAttributes(&a, noalloc_reset_kernel);
+    if (*err == cudaSuccess) *err = preload_kmajor_kernels();
+    if (*err == cudaSuccess) *err = simt_preload_huge16();
+    if (*err != cudaSuccess) return nullptr;
     addr[device] = p;
   }
   *err = cudaSuccess;
   return addr[device];
+}
+
+// The order ftgemm_report_fetch returns records in.
+bool record_before(const ftgemm_fault_record& a, const ftgemm_fault_record& b) {
+  if (a.problem != b.problem) return a.problem < b.problem;
+  if (a.tile_m != b.tile_m) return a.tile_m < b.tile_m;
+  if (a.tile_n != b.tile_n) return a.tile_n < b.tile_n;
+  if (a.kstep != b.kstep) return a.kstep < b.kstep;
+  if (a.row != b.row) return a.row < b.row;
+  if (a.col != b.col) return a.col < b.col;
+  return a.kind < b.kind;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -173,9 +212,8 @@ extern "C" int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha
   } while (0)
 
   // what must start at zero: the event counters (capacity is rewritten too)
-  DevReport zero{};
-  zero.capacity = kNoallocRecords;
-  NA_CK(cudaMemcpyAsync(rep, &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+  noalloc_reset_kernel<<<1, 1, 0, st>>>(rep, kNoallocRecords);
+  NA_CK(cudaGetLastError());
 
   int launches = 0;
   NA_CK(launch_transpose(A, lda, M, K, At, ldt, st));
@@ -203,6 +241,7 @@ extern "C" int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha
   p.nA = abft ? nA : nullptr;
   p.nB = abft ? nB : nullptr;
   p.lam_u = (float)(32.0 * std::ldexp(1.0, -24));
+  p.mu_u = (float)(8.0 * std::ldexp(1.0, -24));
   p.ksteps = (K + KT - 1) / KT;
   p.ks_per_split = p.ksteps;
   p.cadence = 256 / KT;
@@ -223,9 +262,13 @@ extern "C" int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha
     const int have = std::min(r.n_records, kNoallocRecords);
     const int w = std::min(have, std::max(0, report->capacity));
     if (w > 0 && report->records) {
-      NA_CK(cudaMemcpyAsync(report->records, recs, sizeof(ftgemm_fault_record) * w,
-                            cudaMemcpyDeviceToHost, st));
+      // all kept records, sorted as ftgemm_report_fetch sorts them, then the
+      // first `capacity` of them (host stack memory, 16 KB)
+      ftgemm_fault_record v[kNoallocRecords];
+      NA_CK(cudaMemcpyAsync(v, recs, sizeof(ftgemm_fault_record) * have, cudaMemcpyDeviceToHost, st));
       NA_CK(cudaStreamSynchronize(st));
+      std::sort(v, v + have, record_before);
+      memcpy(report->records, v, sizeof(ftgemm_fault_record) * w);
     }
     report->detected = (int64_t)r.detected;
     report->corrected = (int64_t)r.corrected;
@@ -233,7 +276,12 @@ extern "C" int ftgemm_gemm_noalloc(int64_t m, int64_t n, int64_t k, double alpha
     report->checksum_only = (int64_t)r.checksum_only;
     report->n_records = r.n_records;
     report->overflow = (r.n_records > w) ? 1 : 0;
-    if (r.timeouts > 0) return fail(FTGEMM_ERR_TIMEOUT, "%d bounded device waits gave up", r.timeouts);
+    if (r.timeouts > 0) {
+      NA_CK(cudaMemsetAsync(&rep->timeouts, 0, sizeof(int), st));
+      NA_CK(cudaStreamSynchronize(st));
+      return fail(FTGEMM_ERR_TIMEOUT, "%d bounded device waits gave up (this call or an earlier one "
+                  "without a report)", r.timeouts);
+    }
   }
 #undef NA_CK
   return FTGEMM_OK;

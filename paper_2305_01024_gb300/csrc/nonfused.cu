@@ -32,14 +32,16 @@ __global__ void nonfused_inject_kernel(const Fault* __restrict__ f, int nf, int 
 
 // One CTA per 128 x 128 tile: fp32 row and column sums of the accumulator
 // against the tile's checksums (row sums vs CrT[tile_n][row], column sums
-// vs Cc[tile_m][col]), thresholds lambda * u * norms, fp64 confirmation of
+// vs Cc[tile_m][col]), thresholds lambda * u * norms plus the checksum-growth
+// term grow * |checksum| (screened at half of them), fp64 confirmation of
 // the flagged rows and columns, location, correction (or, for a checksum
 // hit, the checksum's reset) and the report.
 __global__ void __launch_bounds__(256) nonfused_verify_kernel(float* __restrict__ acc, long long ldacc, int M, int N,
                                                               float* __restrict__ Cc, long long ldcc,
                                                               float* __restrict__ CrT, long long ldcr,
                                                               const float* __restrict__ nA,
-                                                              const float* __restrict__ nB, float lam_u, int kstep,
+                                                              const float* __restrict__ nB, float lam_u, float grow,
+                                                              int kstep,
                                                               DevReport* rep, ftgemm_fault_record* recs) {
   __shared__ float colpart[8][NF_T];
   __shared__ float rsum[NF_T], tr[NF_T], tcv[NF_T], red[8];
@@ -94,10 +96,12 @@ __global__ void __launch_bounds__(256) nonfused_verify_kernel(float* __restrict_
     float s = 0.f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s += colpart[w][i];
-    tr[i] = i < rows ? lam_u * nA[r0 + i] * froB_s : 0.f;
-    tcv[i] = i < cols ? lam_u * froA_s * nB[c0 + i] : 0.f;
-    flag_r[i] = i < rows && fabsf(rsum[i] - CrT[(long long)tn * ldcr + r0 + i]) > tr[i];
-    flag_c[i] = i < cols && fabsf(s - Cc[(long long)tm * ldcc + c0 + i]) > tcv[i];
+    const float crv = i < rows ? CrT[(long long)tn * ldcr + r0 + i] : 0.f;
+    const float ccv = i < cols ? Cc[(long long)tm * ldcc + c0 + i] : 0.f;
+    tr[i] = i < rows ? ft_tau(lam_u, nA[r0 + i], froB_s, grow, crv) : 0.f;
+    tcv[i] = i < cols ? ft_tau(lam_u, froA_s, nB[c0 + i], grow, ccv) : 0.f;
+    flag_r[i] = i < rows && fabsf(rsum[i] - crv) > kScreen * tr[i];
+    flag_c[i] = i < cols && fabsf(s - ccv) > kScreen * tcv[i];
     flag = flag_r[i] | flag_c[i];
   }
   if (!__syncthreads_or(flag)) return;
@@ -204,9 +208,10 @@ cudaError_t launch_nonfused_inject(const Fault* f, int nf, int ks_lo, int ks_hi,
 
 cudaError_t launch_nonfused_verify(float* acc, long long ldacc, int M, int N, float* Cc, long long ldcc,
                                    float* CrT, long long ldcr, const float* nA, const float* nB, float lam_u,
-                                   int kstep, DevReport* rep, ftgemm_fault_record* recs, cudaStream_t st) {
+                                   float grow, int kstep, DevReport* rep, ftgemm_fault_record* recs, cudaStream_t st) {
   dim3 g((N + NF_T - 1) / NF_T, (M + NF_T - 1) / NF_T);
-  nonfused_verify_kernel<<<g, 256, 0, st>>>(acc, ldacc, M, N, Cc, ldcc, CrT, ldcr, nA, nB, lam_u, kstep, rep, recs);
+  nonfused_verify_kernel<<<g, 256, 0, st>>>(acc, ldacc, M, N, Cc, ldcc, CrT, ldcr, nA, nB, lam_u, grow, kstep, rep,
+                                            recs);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@
 #include <cstddef>
 
 #include "internal.cuh"
+#include "mlp.cuh"
 #include "ptx.cuh"
 
 namespace ftg {
@@ -100,6 +101,8 @@ struct SimtAux {
   int fix_row, fix_col, reset_entry;
   float reset_value;
   float red[32];
+  float lam_t, mu_t;      // the tile's threshold factors (learned or analytic)
+  unsigned int sink_max;  // residual sink: largest |residual| / (u * norms), float bits
 };
 
 template <class T, int LEVEL>
@@ -314,6 +317,37 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
       if (tid == 0) { X.froAw[0] = sqrtf(a); X.froBw[0] = sqrtf(b); }
       __syncthreads();
     }
+    // the tile's threshold factors: analytic (lambda u, mu u), or at block
+    // level the learned lambda_t = mlp_scale * 2^f(x) of the tile's features
+    // (log2 K, the coherences of its row and column blocks, fp32, log2 of its
+    // size) with no growth term; the analytic pair is the fallback for a
+    // non-finite or non-positive lambda_t
+    if (tid == 0) { X.lam_t = p.lam_u; X.mu_t = p.mu_u; X.sink_max = 0u; }
+    if constexpr (LEVEL == L_BLOCK) {
+      if ((p.mlp || p.sink_lam) && warp == 0) {
+        float feat[MLP_IN];
+        feat[0] = log2f((float)p.K) * 0.0625f;
+        feat[1] = p.coA[tile_m];
+        feat[2] = p.coB[tile_n];
+        feat[3] = 0.f;  // operand type: fp32
+        feat[4] = log2f((float)min(MT, M - row0) * (float)min(NT, N - col0)) * 0.0625f;
+        if (p.mlp) {
+          MlpAct act;
+          mlp_forward_warp(p.mlp, feat, lane, act);
+          const float lam = p.mlp_scale * exp2f(act.y);
+          if (lane == 0 && isfinite(lam) && lam > 0.f) {
+            X.lam_t = lam * 5.9604644775390625e-8f;  // * 2^-24
+            X.mu_t = 0.f;
+          }
+        }
+        if (p.sink_lam && blockIdx.z == 0) {
+#pragma unroll
+          for (int q = 0; q < MLP_IN; ++q)
+            if (lane == q) p.sink_x[(long long)(tile_m * p.tiles_n + tile_n) * MLP_IN + q] = feat[q];
+        }
+      }
+    }
+    __syncthreads();
   }
 
   // ---- scheduled faults of this tile ------------------------------------
@@ -512,6 +546,9 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
     // ---- verification at the end of a period ----------------------------
     if constexpr (LEVEL != L_OFF) {
       if (((ks - ks0 + 1) % p.cadence) == 0 || ks == ks1 - 1) {
+        // growth term of the threshold after k elements of K in this split
+        const float grow = __fmul_rn(X.mu_t, sqrtf((float)(min((ks + 1) * KT, p.K) - ks0 * KT)));
+        const float lam_u = X.lam_t;
         if constexpr (LEVEL == L_THREAD) {
           // fp32 screen of the fragment's rows and columns
           unsigned rm = 0u, cm = 0u;
@@ -520,14 +557,14 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
             float s = 0.f;
 #pragma unroll
             for (int j = 0; j < TN; ++j) s += acc[i][j];
-            if (fabsf(s - cr[i]) > p.lam_u * X.nA[FROW(i)] * froBt) rm |= 1u << i;
+            if (fabsf(s - cr[i]) > kScreen * ft_tau(lam_u, X.nA[FROW(i)], froBt, grow, cr[i])) rm |= 1u << i;
           }
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
             float s = 0.f;
 #pragma unroll
             for (int i = 0; i < TM; ++i) s += acc[i][j];
-            if (fabsf(s - cc[j]) > p.lam_u * froAt * X.nB[FCOL(j)]) cm |= 1u << j;
+            if (fabsf(s - cc[j]) > kScreen * ft_tau(lam_u, froAt, X.nB[FCOL(j)], grow, cc[j])) cm |= 1u << j;
           }
           if (rm | cm) {
             // fp64 confirmation
@@ -541,7 +578,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) s += (double)acc[i][j];
                 const double d = s - (double)cr[i];
-                const float tau = p.lam_u * X.nA[FROW(i)] * froBt;
+                const float tau = ft_tau(lam_u, X.nA[FROW(i)], froBt, grow, cr[i]);
                 if (fabs(d) > (double)tau) {
                   ++nr;
                   const float sc = flag_score((float)d, tau);
@@ -555,7 +592,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #pragma unroll
                 for (int i = 0; i < TM; ++i) s += (double)acc[i][j];
                 const double d = s - (double)cc[j];
-                const float tau = p.lam_u * froAt * X.nB[FCOL(j)];
+                const float tau = ft_tau(lam_u, froAt, X.nB[FCOL(j)], grow, cc[j]);
                 if (fabs(d) > (double)tau) {
                   ++nc;
                   const float sc = flag_score((float)d, tau);
@@ -690,7 +727,8 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               float s = 0.f;
 #pragma unroll
               for (int ii = 0; ii < TM; ++ii) if (ii == i) s = pr[ii];
-              if (i < TM && fabsf(s - wr[x]) > p.lam_u * X.nA[FROW(i)] * X.froBw[wn]) rm |= 1u << x;
+              if (i < TM && fabsf(s - wr[x]) > kScreen * ft_tau(lam_u, X.nA[FROW(i)], X.froBw[wn], grow, wr[x]))
+                rm |= 1u << x;
             }
 #pragma unroll
             for (int y = 0; y < CPL; ++y) {
@@ -698,7 +736,8 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               float s = 0.f;
 #pragma unroll
               for (int jj = 0; jj < TN; ++jj) if (jj == j) s = pc[jj];
-              if (j < TN && fabsf(s - wc[y]) > p.lam_u * X.froAw[wm] * X.nB[FCOL(j)]) cm |= 1u << y;
+              if (j < TN && fabsf(s - wc[y]) > kScreen * ft_tau(lam_u, X.froAw[wm], X.nB[FCOL(j)], grow, wc[y]))
+                cm |= 1u << y;
             }
             if (__any_sync(0xffffffffu, (rm | cm) != 0u)) {
               // fp64 confirmation of every screened entry, one at a time
@@ -755,7 +794,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #pragma unroll
               for (int x = 0; x < RPL; ++x)
                 if ((rm >> x) & 1u) {
-                  const float tau = p.lam_u * X.nA[FROW(tn + x * LN)] * X.froBw[wn];
+                  const float tau = ft_tau(lam_u, X.nA[FROW(tn + x * LN)], X.froBw[wn], grow, wr[x]);
                   if (fabs(dr64[x]) > (double)tau) {
                     ++fr;
                     const unsigned long long key = flag_key(flag_score((float)dr64[x], tau), FROW(tn + x * LN));
@@ -765,7 +804,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #pragma unroll
               for (int y = 0; y < CPL; ++y)
                 if ((cm >> y) & 1u) {
-                  const float tau = p.lam_u * X.froAw[wm] * X.nB[FCOL(tm + y * LM)];
+                  const float tau = ft_tau(lam_u, X.froAw[wm], X.nB[FCOL(tm + y * LM)], grow, wc[y]);
                   if (fabs(dc64[y]) > (double)tau) {
                     ++fc;
                     const unsigned long long key = flag_key(flag_score((float)dc64[y], tau), FCOL(tm + y * LM));
@@ -780,20 +819,23 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                 const int ir = nr ? key_index(kr) : -1;  // tile-local row
                 const int jc = nc ? key_index(kc) : -1;  // tile-local column
                 double dR = 0.0, dC = 0.0, sR = 0.0, sC = 0.0;
+                float cR = 0.f, cC = 0.f;  // the located row's / column's checksum
                 bool own_r = false, own_c = false;
 #pragma unroll
                 for (int x = 0; x < RPL; ++x)
-                  if (tn + x * LN < TM && FROW(tn + x * LN) == ir) { own_r = true; dR = dr64[x]; sR = sr64[x]; }
+                  if (tn + x * LN < TM && FROW(tn + x * LN) == ir) { own_r = true; dR = dr64[x]; sR = sr64[x]; cR = wr[x]; }
 #pragma unroll
                 for (int y = 0; y < CPL; ++y)
-                  if (tm + y * LM < TN && FCOL(tm + y * LM) == jc) { own_c = true; dC = dc64[y]; sC = sc64[y]; }
+                  if (tm + y * LM < TN && FCOL(tm + y * LM) == jc) { own_c = true; dC = dc64[y]; sC = sc64[y]; cC = wc[y]; }
                 const unsigned mr = __ballot_sync(0xffffffffu, own_r);
                 const unsigned mc = __ballot_sync(0xffffffffu, own_c);
                 const int lr = mr ? __ffs(mr) - 1 : 0, lc = mc ? __ffs(mc) - 1 : 0;
                 dR = __shfl_sync(0xffffffffu, dR, lr);
                 dC = __shfl_sync(0xffffffffu, dC, lc);
-                const float tR = nr ? p.lam_u * X.nA[ir] * X.froBw[wn] : 0.f;
-                const float tC = nc ? p.lam_u * X.froAw[wm] * X.nB[jc] : 0.f;
+                cR = __shfl_sync(0xffffffffu, cR, lr);
+                cC = __shfl_sync(0xffffffffu, cC, lc);
+                const float tR = nr ? ft_tau(lam_u, X.nA[ir], X.froBw[wn], grow, cR) : 0.f;
+                const float tC = nc ? ft_tau(lam_u, X.froAw[wm], X.nB[jc], grow, cC) : 0.f;
                 int kind;
                 double delta = 0.0;
                 if (nr == 1 && nc == 1) {
@@ -868,14 +910,19 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               if (e < NT) {
 #pragma unroll
                 for (int w = 0; w < T::WGM; ++w) s += X.colpart[w][e];
-                tau = p.lam_u * X.froAw[0] * X.nB[e];
+                tau = ft_tau(lam_u, X.froAw[0], X.nB[e], grow, cq[q]);
               } else if (e < NT + MT) {
 #pragma unroll
                 for (int w = 0; w < T::WGN; ++w) s += X.rowpart[w][e - NT];
-                tau = p.lam_u * X.nA[e - NT] * X.froBw[0];
+                tau = ft_tau(lam_u, X.nA[e - NT], X.froBw[0], grow, cq[q]);
               }
               tq[q] = tau;
-              if (e < NT + MT && fabsf(s - cq[q]) > tau) { myflag = 1; fq |= 1u << q; }
+              if (e < NT + MT && fabsf(s - cq[q]) > kScreen * tau) { myflag = 1; fq |= 1u << q; }
+              if (p.sink_lam && e < NT + MT) {
+                const float den = 5.9604644775390625e-8f *
+                                  (e < NT ? X.froAw[0] * X.nB[e] : X.nA[e - NT] * X.froBw[0]);
+                if (den > 0.f) atomicMax(&X.sink_max, __float_as_uint(fabsf(s - cq[q]) / den));
+              }
             }
             if (__syncthreads_or(myflag)) {
               // fp64 confirmation: exact sums of every screened row / column
@@ -990,6 +1037,13 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
     }
   }
 
+  if constexpr (LEVEL == L_BLOCK) {
+    if (p.sink_lam) {
+      __syncthreads();
+      if (tid == 0)
+        atomicMax(reinterpret_cast<unsigned int*>(p.sink_lam) + tile_m * p.tiles_n + tile_n, X.sink_max);
+    }
+  }
   if (timeouts) atomicAdd(&p.rep->timeouts, timeouts);
   // after a give-up, let this CTA's own copies in flight land before it exits
   const int any_dead = __syncthreads_or(dead ? 1 : 0);

@@ -10,4 +10,17 @@ cudaError_t simt_launch_huge16(int level, const SimtMaps& maps, const SimtParams
   using T = SimtTile<128, 128, 16, 32, 64, 8, 8>;
   return launch_simt_level<T>(level, maps, p, split, st);
 }
+
+// Load this tuple's kernels of every fp32 level into the current device's
+// context (lazy module loading would otherwise load, and allocate, at the
+// first launch of each).
+cudaError_t simt_preload_huge16() {
+  using T = SimtTile<128, 128, 16, 32, 64, 8, 8>;
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_OFF>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_THREAD>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_WARP>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_BLOCK>);
+  return e;
+}
 }  // namespace ftg

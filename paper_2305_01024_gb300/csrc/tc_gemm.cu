@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       float nA_r = 0.f, froA_t = 0.f, froB_t = 0.f, nB_c[2] = {0.f, 0.f};
       float wsc[Cfg::NPIECE], vsc[Cfg::NPIECE];
       float lam_u = P.lam_u;
+      float grow = P.grow;  // the learned threshold replaces both analytic terms
       float feat[MLP_IN];
       if constexpr (ABFT) {
         nA_r = (data_row && gr < pM) ? P.nA[gr] : 0.f;
@@ -342,9 +343,11 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           vsc[q] = P.vscale[(size_t)x.tm * CSR + q];
         }
         // ----- threshold of this tile -----
-        // analytic: lambda * u; learned: lambda = mlp_scale * 2^f(x) with x
-        // the tile's features (log2 K, block coherences, operand type, tile
-        // size), evaluated on every epilogue warp; the analytic value is the
+        // analytic: lambda * u times the norms plus the growth term
+        // mu * u * sqrt(K) times |checksum|; learned: lambda =
+        // mlp_scale * 2^f(x) times the norms alone, with x the tile's
+        // features (log2 K, block coherences, operand type, tile size),
+        // evaluated on every epilogue warp; the analytic threshold is the
         // fallback for a non-finite or non-positive output
         const int rows = min(DM, pM - row0), cols = min(DN, pN - col0);
         feat[0] = log2f((float)P.K) * 0.0625f;
@@ -356,7 +359,10 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           MlpAct act;
           mlp_forward_warp(P.mlp, feat, lane, act);
           const float lam = P.mlp_scale * exp2f(act.y);
-          if (isfinite(lam) && lam > 0.f) lam_u = lam * 5.9604644775390625e-8f;  // * 2^-24
+          if (isfinite(lam) && lam > 0.f) {
+            lam_u = lam * 5.9604644775390625e-8f;  // * 2^-24
+            grow = 0.f;
+          }
         }
       }
       // after one wait gave up the remaining tiles are walked without waits
@@ -537,8 +543,8 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         }
         crow += T.cradj[r];
         T.crow[r] = crow;
-        T.tr[r] = (data_row && gr < pM) ? lam_u * nA_r * froB_t : 0.f;
-        int flagged = data_row && fabsf(rs - crow) > T.tr[r];
+        T.tr[r] = (data_row && gr < pM) ? ft_tau(lam_u, nA_r, froB_t, grow, crow) : 0.f;
+        int flagged = data_row && fabsf(rs - crow) > kScreen * T.tr[r];
         T.flag_r[r] = flagged;
         constexpr float kU = 5.9604644775390625e-8f;  // 2^-24
         if (run.sink_lam && data_row && gr < pM) {
@@ -556,9 +562,9 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
             for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], vsc[q], cc);
             cc += T.ccadj[c];
             const int gc = col0 + c;
-            tcv = gc < pN ? lam_u * froA_t * nB_c[h] : 0.f;
+            tcv = gc < pN ? ft_tau(lam_u, froA_t, nB_c[h], grow, cc) : 0.f;
             const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
-            fl = fabsf(s - cc) > tcv;
+            fl = fabsf(s - cc) > kScreen * tcv;
             if (run.sink_lam && gc < pN) {
               const float den = kU * froA_t * nB_c[h];
               if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(s - cc) / den));

@@ -1,0 +1,273 @@
+"""The detection threshold on the fp32 path (Section 2.2's "predetermined
+threshold"; the readings are the analytic form with its checksum-growth term,
+the fp32 screen at half the threshold with fp64 confirmation, and the learned
+threshold at block level).
+
+* Same-sign inputs, U(0,1) and N(3,1), at K = 16384 and every fp32 level: no
+  false alarm, although the norm term alone would raise them on every tile
+  (the sink's lambda_needed exceeds 32 there).
+* Faults placed against the threshold of their row and column, on zero-mean
+  and same-sign inputs: above it (1.15x to 2x) they are located and
+  corrected, below it (0.55x to 0.75x, past the fp32 screen at half the
+  threshold, so the fp64 confirmation decides) they are not -- in both cases
+  record for record as the oracle decides.  The band just above tau is left
+  out: the GPU's own rounding of the residual (about tau / 60 on zero-mean
+  data, tau / 12 or less on same-sign data) would decide there.
+* The learned threshold at block level: the sink's features equal the
+  oracle's, the network evaluated in the kernel equals the oracle's forward
+  pass, and a network trained on the method's own fp32 residuals (config 3's
+  shapes and input families) finds faults below the analytic threshold with
+  no false alarm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -24
+SCHED32 = dict(m_tb=128, n_tb=128, k_tb=32, m_w=64, n_w=64, m_t=16, n_t=8, cadence=8, split_k=1)
+SCHED16 = dict(m_tb=128, n_tb=128, k_tb=16, m_w=32, n_w=64, m_t=8, n_t=8, cadence=16, split_k=1)
+T = 128
+
+
+@pytest.fixture(scope="module")
+def ft():
+    import torch
+    import paper_2305_01024_gb300 as ft
+    assert torch.cuda.is_available()
+    ft.lib()
+    return ft
+
+
+def _inputs(kind, M, N, K, seed):
+    if kind == "normal":
+        return synth.normal((M, K), seed), synth.normal((K, N), seed + 1)
+    if kind.startswith("shift"):  # N(mu, 1)
+        mu = np.float32(kind[5:])
+        return synth.normal((M, K), seed) + mu, synth.normal((K, N), seed + 1) + mu
+    if kind == "positive":  # U(0, 1)
+        return ((synth.uniform((M, K), seed) + 1) / 2).astype(np.float32), \
+               ((synth.uniform((K, N), seed + 1) + 1) / 2).astype(np.float32)
+    raise ValueError(kind)
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def _run(ft, h, A, B, level, faults=None, sink=False):
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    tiles = -(-M // T) * -(-N // T)
+    lam = feat = None
+    if sink:
+        lam = torch.zeros(tiles, device="cuda")
+        feat = torch.zeros(tiles * 5, device="cuda")
+        h.set_residual_sink(lam, feat)
+    C = torch.zeros(M, N, device="cuda")
+    rep = h.gemm(_dev(A), _dev(B), C, level=level, inject=faults, capacity=1 << 14)
+    torch.cuda.synchronize()
+    if sink:
+        h.set_residual_sink(None)
+        return C, rep, lam.cpu().numpy().astype(np.float64), feat.cpu().numpy().reshape(-1, 5).astype(np.float64)
+    return C, rep, None, None
+
+
+def _analytic_tau(A64, B64, i, j, k, lam=32.0, mu=8.0):
+    """Row and column thresholds of element (i, j) of a 128 x 128 tile at the
+    verification after k elements of K: lam*u*norms over the full K plus
+    mu*u*sqrt(k)*|checksum after k| (checksums from the exact product)."""
+    tm_, tn_ = i // T, j // T
+    I = slice(tm_ * T, (tm_ + 1) * T)
+    J = slice(tn_ * T, (tn_ + 1) * T)
+    c_r = A64[i, :k] @ B64[:k, J].sum(1)
+    c_c = A64[I, :k].sum(0) @ B64[:k, j]
+    row = lam * U * np.linalg.norm(A64[i]) * np.linalg.norm(B64[:, J]) + mu * U * math.sqrt(k) * abs(c_r)
+    col = lam * U * np.linalg.norm(A64[I]) * np.linalg.norm(B64[:, j]) + mu * U * math.sqrt(k) * abs(c_c)
+    return row, col
+
+
+@pytest.mark.parametrize("kind", ["positive", "shift3"])
+@pytest.mark.parametrize("level,sched", [("FT_BLOCK", SCHED32), ("FT_WARP", SCHED16), ("FT_THREAD", SCHED16)])
+def test_same_sign_inputs_raise_no_false_alarm(ft, kind, level, sched):
+    M = N = 1024
+    K = 16384
+    A, B = _inputs(kind, M, N, K, 600)
+    h = ft.Handle(0)
+    h.set_schedule(sched)
+    lv = getattr(ft, level)
+    _, rep, lam, _ = _run(ft, h, A, B, lv, sink=lv == ft.FT_BLOCK)
+    assert rep.detected == 0, rep.records[:4]
+    if lam is not None:
+        assert lam.min() > 32.0  # the norm term alone would flag every tile
+    h.close()
+
+
+@pytest.mark.parametrize("kind", ["normal", "positive", "shift3"])
+def test_faults_placed_against_the_threshold_match_oracle(ft, orc, kind):
+    """Nine faults in nine tiles, all at the last k-step (verified after the
+    whole K): three at 1.15x-2x the larger of their row and column
+    thresholds, three at 0.55x-0.75x the smaller, three far above; the GPU's
+    records equal the oracle's, and C matches the oracle's within the fp32
+    bound."""
+    import torch
+    M = N = 384
+    K = 2048
+    A, B = _inputs(kind, M, N, K, 610)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    nks = K // 32
+    # one fault per tile (drawn with a single k-step, so every draw is a
+    # distinct unit), then moved to the last k-step
+    pos = synth.fault_positions(synth.config_seed(3, 60), 9, 3, 3, 1, T, T, M, N, 1)
+    pos = [(tm_, tn_, nks - 1, r, c) for (tm_, tn_, ks, r, c) in pos]
+    # the bands leave a margin of several standard deviations of the GPU's own
+    # rounding of the residual, which is larger on same-sign data
+    above = (1.25, 1.5, 2.0) if kind == "normal" else (1.5, 1.75, 2.0)
+    below = (0.55, 0.65, 0.75) if kind == "normal" else (0.55, 0.6, 0.65)
+    factors = list(above) + list(below) + [16.0, 64.0, 256.0]
+    sign = synth.unit(synth.config_seed(3, 61), 9)
+    faults = []
+    for (tm_, tn_, ks, r, c), f, sg in zip(pos, factors, sign):
+        tr, tc = _analytic_tau(A64, B64, tm_ * T + r, tn_ * T + c, K)
+        base = max(tr, tc) if f > 1 else min(tr, tc)
+        faults.append((tm_, tn_, ks, r, c, float((1 if sg < 0.5 else -1) * f * base)))
+    h = ft.Handle(0)
+    h.set_schedule(SCHED32)
+    C, rep, _, _ = _run(ft, h, A, B, ft.FT_BLOCK, faults=faults)
+    h.close()
+    res = orc.gemm_ft(A, B, orc.Schedule(**SCHED32, level=orc.BLOCK), faults=faults)
+    got = sorted((x["row"], x["col"], x["kind"], x["kstep"]) for x in rep.records)
+    want = sorted((x.row, x.col, x.kind, x.kstep) for x in res.records)
+    assert got == want
+    assert rep.corrected == 6 and len(rep.records) == 6
+    bound = 2 * K * U * (np.abs(A64) @ np.abs(B64))
+    assert np.all(np.abs(C.cpu().numpy().astype(np.float64) - res.C) <= bound)
+
+
+def _oracle_features(A, B):
+    M, K = A.shape
+    N = B.shape[1]
+    tm, tn = -(-M // T), -(-N // T)
+    co_a = [omlp.coherence(A[i * T:(i + 1) * T], axis=0) for i in range(tm)]
+    co_b = [omlp.coherence(B[:, j * T:(j + 1) * T], axis=1) for j in range(tn)]
+    out = []
+    for i in range(tm):
+        for j in range(tn):
+            out.append(omlp.features(K, min(T, M - i * T), min(T, N - j * T), co_a[i], co_b[j], "f32"))
+    return np.array(out)
+
+
+def test_block_sink_features_match_oracle(ft):
+    M, N, K = 300, 520, 1000
+    A, B = _inputs("shift1", M, N, K, 620)
+    h = ft.Handle(0)
+    h.set_schedule(SCHED32)
+    _, rep, lam, feat = _run(ft, h, A, B, ft.FT_BLOCK, sink=True)
+    h.close()
+    np.testing.assert_allclose(feat, _oracle_features(A.astype(np.float64), B.astype(np.float64)),
+                               rtol=1e-5, atol=1e-6)
+    assert np.all(np.isfinite(lam)) and np.all(lam > 0) and rep.detected == 0
+
+
+def test_block_network_in_kernel_matches_oracle_forward(ft):
+    """With the learned threshold on at block level, a fault record's tau is
+    lambda_t * u * (||A_i|| ||B_J||_F + ||A_I||_F ||B_j||), lambda_t =
+    scale * 2^f(x_t), f the oracle's network on the oracle's features."""
+    M, N, K = 256, 384, 1024
+    A, B = _inputs("normal", M, N, K, 630)
+    th = (synth.normal((omlp.N_PARAMS,), 631) * 0.2).astype(np.float32)
+    scale = 64.0
+    h = ft.Handle(0)
+    h.set_schedule(SCHED32)
+    h.set_threshold(1, scale, th)
+    faults = [(1, 1, 3, 7, 11, 50.0), (0, 2, 20, 100, 120, -40.0)]
+    _, rep, _, _ = _run(ft, h, A, B, ft.FT_BLOCK, faults=faults)
+    h.close()
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    feats = _oracle_features(A64, B64)
+    nA, nB = np.linalg.norm(A64, axis=1), np.linalg.norm(B64, axis=0)
+    tn = -(-N // T)
+    assert len(rep.records) == 2 and rep.corrected == 2
+    for r in rep.records:
+        tm_, tn_ = r["tile_m"], r["tile_n"]
+        y, _ = omlp.forward(th.astype(np.float64), feats[tm_ * tn + tn_][None, :])
+        lam_t = scale * 2.0 ** y[0]
+        I = slice(tm_ * T, (tm_ + 1) * T)
+        J = slice(tn_ * T, (tn_ + 1) * T)
+        tau = lam_t * U * (nA[r["row"]] * np.linalg.norm(B64[:, J]) + np.linalg.norm(A64[I]) * nB[r["col"]])
+        assert r["tau"] == pytest.approx(tau, rel=1e-4)
+
+
+def test_block_learned_threshold_gains_over_analytic(ft):
+    """Train the network on fp32 block-level residuals of config 3's kinds of
+    shapes (long-K, wide, small-K) over input families from N(0,1) to U(0,1),
+    calibrate on the training tiles (x2), then on zero-mean and on same-sign
+    inputs put faults at 1.25x the larger of their learned row / column
+    thresholds, below the analytic threshold on both sides: the analytic
+    threshold misses them, the learned one locates and corrects every one,
+    and neither raises a false alarm."""
+    import torch
+    kinds = ["normal", "shift0.25", "shift1", "shift3", "positive"]
+    specs = [(kd, M, N, K) for kd in kinds for (M, N, K) in
+             ((1024, 1024, 32), (1024, 1024, 128), (512, 512, 512), (640, 256, 2048), (256, 256, 8192),
+              (384, 384, 4096))]
+    h = ft.Handle(0)
+    h.set_schedule(SCHED32)
+    Xs, ts = [], []
+    for q, (kd, M, N, K) in enumerate(specs):
+        A, B = _inputs(kd, M, N, K, 700 + 10 * q)
+        _, rep, lam, feat = _run(ft, h, A, B, ft.FT_BLOCK, sink=True)
+        assert rep.detected == 0
+        Xs.append(feat)
+        ts.append(np.log2(np.maximum(lam, 2.0 ** -6)))
+    X, t = np.vstack(Xs), np.concatenate(ts)
+    th = torch.from_numpy((synth.normal((omlp.N_PARAMS,), 640) * 0.2).astype(np.float32)).cuda()
+    order = np.argsort(synth.uniform((len(t),), 641))
+    Xd, td = _dev(X[order]), _dev(t[order])
+    losses = h.mlp_train(Xd, td, th, epochs=400, batch=128, lr=3e-3)
+    assert losses[-1] < 0.25 * losses[0]
+    y = h.mlp_forward(Xd, th).cpu().numpy().astype(np.float64)
+    margin = float(np.max(t[order] - y)) + 1.0
+    theta = th.cpu().numpy()
+    for kind in ("normal", "positive"):
+        M = N = 768
+        K = 4096
+        A, B = _inputs(kind, M, N, K, 800 if kind == "normal" else 810)
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        nA, nB = np.linalg.norm(A64, axis=1), np.linalg.norm(B64, axis=0)
+        y_t, _ = omlp.forward(theta.astype(np.float64), _oracle_features(A64, B64))
+        lam_t = 2.0 ** margin * 2.0 ** y_t
+        tiles_n = -(-N // T)
+        nks = K // 32
+        pos = synth.fault_positions(synth.config_seed(3, 70), 10, M // T, N // T, 1, T, T, M, N, 1)
+        faults, ratio = [], []
+        for (tm_, tn_, ks, r, c) in pos:
+            i, j = tm_ * T + r, tn_ * T + c
+            I = slice(tm_ * T, (tm_ + 1) * T)
+            J = slice(tn_ * T, (tn_ + 1) * T)
+            lt = lam_t[tm_ * tiles_n + tn_]
+            delta = 1.25 * lt * U * max(nA[i] * np.linalg.norm(B64[:, J]), np.linalg.norm(A64[I]) * nB[j])
+            ratio.append(delta / min(_analytic_tau(A64, B64, i, j, K)))
+            faults.append((tm_, tn_, nks - 1, r, c, float(delta)))
+        print(f"{kind}: learned lambda median {np.median(lam_t):.3g}; fault / analytic threshold: "
+              f"max {max(ratio):.3g}")
+        assert max(ratio) < 1.0
+        h.set_threshold(0)
+        _, rep_ana, _, _ = _run(ft, h, A, B, ft.FT_BLOCK, faults=faults)
+        _, clean_ana, _, _ = _run(ft, h, A, B, ft.FT_BLOCK)
+        h.set_threshold(1, 2.0 ** margin, theta)
+        C, rep_mlp, _, _ = _run(ft, h, A, B, ft.FT_BLOCK, faults=faults)
+        _, clean_mlp, _, _ = _run(ft, h, A, B, ft.FT_BLOCK)
+        h.set_threshold(0)
+        assert clean_ana.detected == 0 and clean_mlp.detected == 0
+        assert rep_ana.detected == 0
+        injected = sorted((tm_ * T + r, tn_ * T + c) for (tm_, tn_, ks, r, c, d) in faults)
+        assert sorted((x["row"], x["col"]) for x in rep_mlp.records) == injected
+        assert rep_mlp.corrected == len(faults)
+    h.close()
