@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
     ap.add_argument("--case", default=None,
                     help="run one small kernel case for a profiler and exit: tc-<bf16|e4m3>-<tile|off>-<n>, "
-                         "tcgroup-bf16-<tile|off>-<problems>, f64-<d|z>-<block|off>-<n>")
+                         "tcgroup-bf16-<tile|off>-<problems>, f64-<d|z>-<block|off>-<n>, "
+                         "simt-<wide32|wide|huge16>-<off|thread|warp|block|detect>-<n>")
     return ap.parse_args()
 
 
@@ -72,8 +73,24 @@ def run_case(case):
     import paper_2305_01024_gb300 as ft
     import synth
     kind, dtn, lvn, n = case.split("-")
-    assert kind in ("tc", "tcgroup", "f64"), case
+    assert kind in ("tc", "tcgroup", "f64", "simt"), case
     n = int(n)
+    if kind == "simt":  # simt-<tuple>-<level>-<n>: the fp32 kernel on U(-1,1) operands
+        tuples = {"wide32": SCHED, "wide": SCHED16, "huge16": SCHED_OFF_BEST}
+        h = ft.Handle(0)
+        h.set_schedule(tuples[dtn])
+        A = synth.torch_make("uniform", (n, n), 11, "cuda")
+        B = synth.torch_make("uniform", (n, n), 12, "cuda")
+        Cm = torch.empty(n, n, device="cuda")
+        for _ in range(3):
+            if lvn == "detect":
+                h.gemm_offline(A, B, Cm)
+            else:
+                h.gemm(A, B, Cm, level=ft.LEVELS[lvn], report=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "detected": h.report_fetch().detected}))
+        h.close()
+        return 0
     if kind == "f64":  # f64-<d|z>-<off|block>-<n>: DGEMM / ZGEMM on N(0,1) operands, cadence 16
         h = ft.Handle(0)
         mk = lambda s: synth.torch_make("normal", (n, n), s, "cuda", torch.float64)  # noqa: E731
@@ -330,14 +347,14 @@ def _peaks():
         return {}
 
 
-def _tile_faults(synth, seed, count, M, N, K, kblk, unit=1.0):
+def _tile_faults(synth, seed, count, M, N, K, kblk, unit=1.0, lo=1e-2):
     """`count` faults on distinct 120 x 248 tiles, |delta| log-uniform in
-    [1e-2, 1e3] x the expected tile maximum of an N(0,1) product (4 sqrt K),
+    [lo, 1e3] x the expected tile maximum of an N(0,1) product (4 sqrt K),
     in accumulator units (`unit` = 1 / (scale_a scale_b) for e4m3 codes)."""
     tm, tn = -(-M // TDM), -(-N // TDN)
     nks = -(-K // kblk)
     pos = synth.fault_positions(seed, count, tm, tn, nks, TDM, TDN, M, N, nks)
-    mags = synth.log_uniform(seed + 1, count, 1e-2, 1e3)
+    mags = synth.log_uniform(seed + 1, count, lo, 1e3)
     sign = synth.unit(seed + 2, count)
     return [(a, b, ks, r, c, float((1 if sg < 0.5 else -1) * g * 4 * math.sqrt(K) * unit))
             for (a, b, ks, r, c), g, sg in zip(pos, mags, sign)]
@@ -579,6 +596,28 @@ def learned_extras(ft, h, synth, dev, timed_loop):
         ts.append(torch.log2(torch.clamp(lam, min=2.0 ** -6)))
         g.close()
         del probs
+    # single GEMMs at config 4's K (to 16384), bf16 and e4m3, so the network
+    # sees the long-K tiles and the fp8 operand type it is compared on below
+    for r, kind in enumerate(["normal", "shift1", "shift3", "positive"]):
+        for K in (4096, 16384):
+            Af, Bf = _family(synth, dev, kind, 2048, 2048, K, synth.config_seed(5, 9000 + 10 * r + K // 4096))
+            for dt in (ft.BF16, ft.E4M3):
+                if dt == ft.BF16:
+                    A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
+                else:
+                    A, sa = h.quantize(Af, ft.E4M3)
+                    B, sb = h.quantize(Bf, ft.E4M3)
+                    h.set_fp8_scales(sa, sb)
+                tiles = -(-2048 // TDM) * -(-2048 // TDN)
+                lam = torch.zeros(tiles, device=dev)
+                feat = torch.zeros(tiles * 5, device=dev)
+                h.set_residual_sink(lam, feat)
+                h.gemm(A, B, torch.empty(2048, 2048, device=dev), level=ft.FT_TILE, dtype=dt, report=False)
+                h.set_residual_sink(None)
+                h.report_fetch(capacity=1)
+                Xs.append(feat.view(-1, 5))
+                ts.append(torch.log2(torch.clamp(lam, min=2.0 ** -6)))
+    h.set_fp8_scales(1.0, 1.0)
     X = torch.cat(Xs)
     t = torch.cat(ts)
     n = X.shape[0]
@@ -652,6 +691,142 @@ def learned_extras(ft, h, synth, dev, timed_loop):
         out[name] = {"config5_faults_injected": nf, "corrected_at_position": found,
                      "detect_rate": round(found / nf, 4), "one_side_flagged": partial, "false_alarms": false,
                      "coherent_inputs_false_alarms": false_c}
+
+    # config 4 at 16384^3, bf16 and e4m3: the same comparison on one large GEMM
+    # each (64 faults on distinct tiles, |delta| log-uniform in [1e-4, 1e3] x
+    # tile max), plus a fault-free run on coherent U(0,1) inputs
+    n4 = 16384
+    c4 = {}
+    for fam in ("normal", "positive"):
+        Af, Bf = _family(synth, dev, fam, n4, n4, n4, synth.config_seed(4, 60 if fam == "normal" else 62))
+        for dname, dt in (("bf16", ft.BF16), ("e4m3", ft.E4M3)):
+            if dt == ft.BF16:
+                A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
+                sa = sb = 1.0
+            else:
+                A, sa = h.quantize(Af, ft.E4M3)
+                B, sb = h.quantize(Bf, ft.E4M3)
+            h.set_fp8_scales(sa, sb)
+            C = torch.empty(n4, n4, device=dev)
+            faults = (_tile_faults(synth, synth.config_seed(4, 70 + dt), 64, n4, n4, n4, 64 if dt == ft.BF16 else 128,
+                                   unit=1.0 / (sa * sb), lo=1e-4) if fam == "normal" else [])
+            for name, mlp in (("analytic", False), ("learned", True)):
+                if mlp:
+                    h.set_threshold(1, scale, theta.cpu().numpy())
+                else:
+                    h.set_threshold(0)
+                rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=dt, inject=faults or None, capacity=1 << 14)
+                found, false = _count(rep.records, faults, lambda f: (0, f[0] * TDM + f[3], f[1] * TDN + f[4]))
+                key = f"{dname}_{fam}"
+                c4.setdefault(key, {})[name] = {"faults_injected": len(faults), "corrected_at_position": found,
+                                                "other_records": false}
+            h.set_threshold(0)
+            del A, B, C
+            torch.cuda.empty_cache()
+        del Af, Bf
+    h.set_fp8_scales(1.0, 1.0)
+    out["config4_16384"] = c4
+    return out
+
+
+def _family(synth, dev, kind, M, N, K, seed):
+    """fp32 operands of an input family: N(0,1), N(mu,1) ("shift<mu>") or U(0,1)."""
+    if kind == "positive":
+        A = (synth.torch_make("uniform", (M, K), seed, dev) + 1) / 2
+        B = (synth.torch_make("uniform", (K, N), seed + 1, dev) + 1) / 2
+        return A, B
+    A = synth.torch_make("normal", (M, K), seed, dev)
+    B = synth.torch_make("normal", (K, N), seed + 1, dev)
+    if kind.startswith("shift"):
+        mu = float(kind[5:])
+        A += mu
+        B += mu
+    return A, B
+
+
+def learned_fp32_extras(ft, h, synth, dev, timed_loop):
+    """The learned threshold on the fp32 path at block level (the 128 x 128 x
+    32 tile): trained on fault-free tile residuals of config 3's shapes over
+    input families from N(0,1) to U(0,1), calibrated on held-out tiles, then
+    compared with the analytic threshold on config 3's shapes: faults of
+    |delta| log-uniform in [1e-4, 1e3] x tile max on N(0,1) inputs, and
+    false alarms on fault-free U(0,1) inputs."""
+    import numpy as np
+    import torch
+    shapes = [(16384, 16384, 32), (20480, 256, 20480), (256, 256, 65536), (4096, 96, 4096), (777, 1531, 2049)]
+    kinds = ["normal", "shift0.25", "shift1", "shift3", "positive"]
+    h.set_schedule(SCHED)
+    h.set_threshold(0)
+    Xs, ts = [], []
+    t0 = time.time()
+    reps = 12
+    for rep_i in range(reps):
+        for r, kind in enumerate(kinds):
+            for q, (M, N, K) in enumerate(shapes):
+                A, B = _family(synth, dev, kind, M, N, K, synth.config_seed(3, 1000 + 100 * rep_i + 10 * r + q))
+                tiles = -(-M // 128) * -(-N // 128)
+                lam = torch.zeros(tiles, device=dev)
+                feat = torch.zeros(tiles * 5, device=dev)
+                h.set_residual_sink(lam, feat)
+                h.gemm(A, B, torch.empty(M, N, device=dev), level=ft.FT_BLOCK, report=False)
+                h.set_residual_sink(None)
+                # the K = 32 shape has 16384 tiles a run, the others 4 to 320:
+                # one tile in 8 of it keeps the long-K tiles from being swamped
+                step = 8 if q == 0 else 1
+                Xs.append(feat.view(-1, 5)[::step])
+                ts.append(torch.log2(torch.clamp(lam, min=2.0 ** -6))[::step])
+                del A, B
+    h.report_fetch(capacity=1)
+    X = torch.cat(Xs)
+    t = torch.cat(ts)
+    n = X.shape[0]
+    order = torch.from_numpy(np.argsort(synth.unit(synth.config_seed(3, 9), n))).to(dev)
+    X, t = X[order].contiguous(), t[order].contiguous()
+    n_hold = n // 10
+    Xtr, ttr, Xho, tho = X[n_hold:].contiguous(), t[n_hold:].contiguous(), X[:n_hold].contiguous(), t[:n_hold].contiguous()
+    theta = torch.from_numpy((synth.normal((ft.MLP_PARAMS,), synth.config_seed(3, 11)) * 0.2).astype(np.float32)).to(dev)
+    t1 = time.time()
+    losses = h.mlp_train(Xtr, ttr, theta, epochs=8, batch=4096, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    margin = float((tho - h.mlp_forward(Xho, theta)).max().item()) + 1.0
+    scale = 2.0 ** margin
+    out = {"tile": "128x128x32 (16x8 fragments), block level", "training_tiles": n - n_hold, "held_out_tiles": n_hold,
+           "collect_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2),
+           "loss_first_last_epoch": [round(losses[0], 4), round(losses[-1], 4)], "calibration_scale": scale}
+    ev = {"analytic": {"faults": 0, "corrected_at_position": 0, "other_records": 0, "coherent_false_alarms": 0},
+          "learned": {"faults": 0, "corrected_at_position": 0, "other_records": 0, "coherent_false_alarms": 0}}
+    for q, (M, N, K) in enumerate(shapes):
+        A, B = _family(synth, dev, "normal", M, N, K, synth.config_seed(3, 5000 + q))
+        Ap, Bp = _family(synth, dev, "positive", M, N, K, synth.config_seed(3, 5100 + q))
+        C = torch.empty(M, N, device=dev)
+        tm, tn, nks = -(-M // 128), -(-N // 128), -(-K // 32)
+        cnt = min(64, tm * tn)
+        pos = synth.fault_positions(synth.config_seed(3, 5200 + q), cnt, tm, tn, nks, 128, 128, M, N, 8)
+        mags = synth.log_uniform(synth.config_seed(3, 5300 + q), cnt, 1e-4, 1e3)
+        sign = synth.unit(synth.config_seed(3, 5400 + q), cnt)
+        faults = [(a, b, ks, r, c, float((1 if sg < 0.5 else -1) * g * 4 * math.sqrt(K)))
+                  for (a, b, ks, r, c), g, sg in zip(pos, mags, sign)]
+        for name, mlp in (("analytic", False), ("learned", True)):
+            if mlp:
+                h.set_threshold(1, scale, theta.cpu().numpy())
+            else:
+                h.set_threshold(0)
+            rep = h.gemm(A, B, C, level=ft.FT_BLOCK, inject=faults, capacity=1 << 14)
+            found, other = _count(rep.records, faults, lambda f: (0, f[0] * 128 + f[3], f[1] * 128 + f[4]))
+            clean = h.gemm(Ap, Bp, C, level=ft.FT_BLOCK, capacity=1 << 10)
+            e = ev[name]
+            e["faults"] += len(faults)
+            e["corrected_at_position"] += found
+            e["other_records"] += other
+            e["coherent_false_alarms"] += clean.detected
+        h.set_threshold(0)
+        del A, B, Ap, Bp, C
+        torch.cuda.empty_cache()
+    for e in ev.values():
+        e["detect_rate"] = round(e["corrected_at_position"] / e["faults"], 4) if e["faults"] else None
+    out.update(ev)
+    h.set_schedule(SCHED)
     return out
 
 
@@ -705,14 +880,47 @@ def nonfused_extras(ft, h, synth, dev, timed_loop):
 
 
 def offline_extras(ft, h, synth, dev, timed_loop):
-    """Online vs offline ABFT (Section 5.5) at a per-tile error rate gamma0 =
-    1/256: every attempt draws a fault in each tile with probability gamma0;
+    """Online vs offline ABFT (Section 5.5).  (1) The detect-only kernel's
+    cost without faults: its kernel time against the same 128 x 128 x 32
+    tile with checksums off and with the online block-level checksums,
+    beside the paper's ~1%.  (2) At a per-tile error rate gamma0 = 1/256
+    every attempt draws a fault in each tile with probability gamma0;
     offline detects and recomputes until an attempt is clean, online corrects
     in one pass.  Reports mean attempts and the cost of offline in units of
     online, beside the paper's model (1 - gamma) / (1 - 2 gamma)."""
     import torch
     gamma0, trials, max_runs = 1.0 / 256, 24, 32
     out = {"gamma0": gamma0, "trials": trials}
+
+    def kernel_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        h.enable_timing(True)
+        h.stats(reset=True)
+        for _ in range(reps):
+            fn()
+        st = h.stats(reset=True)
+        h.enable_timing(False)
+        return st["kernel_ms"] / max(1, st["timed_launches"])
+
+    det = {}
+    for n in (4096, 8192, 16384):
+        A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 42), dev)
+        B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 43), dev)
+        Cm = torch.empty(n, n, device=dev)
+        h.set_schedule(SCHED)
+        reps = 3 if n == 16384 else 6
+        t_off = kernel_ms(lambda: h.gemm(A, B, Cm, level=ft.FT_OFF, report=False), reps)
+        t_blk = kernel_ms(lambda: h.gemm(A, B, Cm, level=ft.FT_BLOCK, report=False), reps)
+        h.report_fetch(capacity=1)
+        t_det = kernel_ms(lambda: h.gemm_offline(A, B, Cm), reps)
+        det[str(n)] = {"off_ms": round(t_off, 4), "online_block_ms": round(t_blk, 4),
+                       "detect_only_ms": round(t_det, 4),
+                       "detect_only_overhead_pct": round(100.0 * (t_det / t_off - 1.0), 2),
+                       "online_block_overhead_pct": round(100.0 * (t_blk / t_off - 1.0), 2)}
+        del A, B, Cm
+        torch.cuda.empty_cache()
+    out["detector_no_faults"] = det
     for n in (512, 1024, 1536):
         tiles_1d = -(-n // 128)
         tiles = tiles_1d * tiles_1d
@@ -727,7 +935,7 @@ def offline_extras(ft, h, synth, dev, timed_loop):
             fl = []
             for t in range(tiles):
                 if u[t] < gamma0:
-                    fl.append((t // tiles_1d, t % tiles_1d, int(u[tiles + t] * (n // 16)),
+                    fl.append((t // tiles_1d, t % tiles_1d, int(u[tiles + t] * (n // 32)),
                                int(u[2 * tiles + t] * 128), int(u[3 * tiles + t] * 128), delta))
             return fl
 
@@ -741,7 +949,7 @@ def offline_extras(ft, h, synth, dev, timed_loop):
             attempts.append(runs if st == ft.OK else max_runs)
         torch.cuda.synchronize()
         t_off = time.time() - t0
-        h.set_schedule(SCHED16)  # the offline scheme's tiling (k-steps of 16)
+        h.set_schedule(SCHED)  # the detector's tiling (128 x 128, k-steps of 32)
         t0 = time.time()
         for tr in range(trials):
             h.gemm(A, B, Cm, level=ft.FT_BLOCK, inject=plans[tr][0] or None, report=False)
@@ -1149,7 +1357,8 @@ def main():
     side = {}
     if not args.no_extras and rank == 0:
         for name, fn in (("tensor_core", tensor_core_extras), ("grouped", grouped_extras),
-                         ("learned_threshold", learned_extras), ("nonfused", nonfused_extras),
+                         ("learned_threshold", learned_extras), ("learned_threshold_fp32", learned_fp32_extras),
+                         ("nonfused", nonfused_extras),
                          ("offline", offline_extras), ("small_shapes", small_shapes_extras),
                          ("irregular", irregular_extras), ("fp64", fp64_extras)):
             try:

@@ -390,11 +390,16 @@ int ftgemm_gemm_nonfused(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k
                          ftgemm_report* report);
 
 /* Offline ABFT (Section 5.5): detect-only verification with recompute.
- * F32.  Attempt r computes C = alpha * A * B + beta * C_in with the
- * block-level checksums of the 128 x 128 x 16 tile verified once, after the
- * last k-step, and the faults of injects[r] (NULL entry or injects NULL: no
- * faults; positions as for ftgemm_gemm on that tiling); if anything is
- * detected the attempt is discarded and the next one starts from C_in.
+ * F32.  Attempt r computes C = alpha * A * B + beta * C_in with a
+ * detect-only kernel on the 128 x 128 x 32 tile (16 x 8 fragments): each
+ * tile keeps only its column checksums e^T C (no row checksums, no
+ * correction state), compared once, after the last k-step, against the
+ * analytic threshold; a mismatch is reported as a detection (kind
+ * uncorrectable, row -1, the most flagged column) and nothing is corrected.
+ * injects[r] holds the faults of attempt r (NULL entry or injects NULL: no
+ * faults; positions as for ftgemm_gemm on that tiling, k-steps of 32; a
+ * row-checksum target is not seen); if anything is detected the attempt is
+ * discarded and the next one starts from C_in.
  * *runs_out (may be NULL) receives the attempts made.  Returns
  * FTGEMM_ERR_UNRECOVERED when all max_runs attempts were hit (C then holds
  * the last attempt).  report (may be NULL): the events of all attempts.

@@ -27,6 +27,7 @@ cudaError_t simt_launch_huge(int, const SimtMaps&, const SimtParams&, int, cudaS
 cudaError_t simt_launch_huge16(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_wide(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t simt_launch_wide32(int, const SimtMaps&, const SimtParams&, int, cudaStream_t);
+cudaError_t simt_launch_wide32_detect(const SimtMaps&, const SimtParams&, int, cudaStream_t);
 cudaError_t launch_transpose(const float*, long long, int, int, float*, long long, cudaStream_t);
 cudaError_t launch_transpose_encode(const float* A, long long lda, int M, int K, float* At, long long ldt, int m_u,
                                     float* V, long long ldv, float* nrm, float* scratch, int* launches,
@@ -268,7 +269,7 @@ static void choose_schedule(const ftgemm_ctx* h, int64_t m, int64_t n, int64_t k
 static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
                      const float* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_ft_level level,
                      const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report,
-                     const float* At_given = nullptr, int64_t ldat = 0);
+                     const float* At_given = nullptr, int64_t ldat = 0, bool detect = false);
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -1269,20 +1270,25 @@ int ftgemm_gemm(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, double alpha
 // The SIMT path of ftgemm_gemm with an explicit schedule and level.
 // At_given (OFF only): A already k-major (K x M, row stride ldat, 16-byte
 // aligned rows); the transpose pass is skipped.
+// detect (level BLOCK, the 128 x 128 x 32 tuple with 16 x 8 fragments): the
+// detector of the offline scheme -- column checksums only, one verification
+// per split, detections reported and nothing corrected.
 static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
                      const float* B, int64_t ldb, double beta, float* C, int64_t ldc, ftgemm_ft_level level,
                      const ftgemm_schedule& s, const ftgemm_inject_spec* inject, ftgemm_report* report,
-                     const float* At_given, int64_t ldat) {
+                     const float* At_given, int64_t ldat, bool detect) {
   if (At_given && level != FTGEMM_FT_OFF) FAIL(FTGEMM_ERR_ARG, "internal: k-major A needs level OFF");
   const SimtConfig* cfg = find_simt(s);
   if (!cfg) FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_gemm: schedule is not a compiled kernel");
+  if (detect && (level != FTGEMM_FT_BLOCK || cfg->launch != simt_launch_wide32))
+    FAIL(FTGEMM_ERR_ARG, "internal: the detector runs the 128 x 128 x 32 tuple at block level");
 
   const int M = (int)m, N = (int)n, K = (int)k;
   const int ksteps = (K + s.k_tb - 1) / s.k_tb;
   int split = std::max(1, std::min(s.split_k, ksteps));
   const int ks_per_split = (ksteps + split - 1) / split;
   split = (ksteps + ks_per_split - 1) / ks_per_split;
-  const int cadence = s.cadence > 0 ? s.cadence : ks_per_split;
+  const int cadence = (s.cadence > 0 && !detect) ? s.cadence : ks_per_split;
   const int tiles_m = (M + s.m_tb - 1) / s.m_tb, tiles_n = (N + s.n_tb - 1) / s.n_tb;
 
   const float* Af = A;
@@ -1317,15 +1323,15 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
   const size_t nAt = At_given ? 0 : (size_t)K * ldt;
   const size_t nBp = b_ok ? 0 : (size_t)K * ldbp;
   const size_t nV = need_vw ? (size_t)nvb * ldv : 0;
-  const size_t nW = need_vw ? (size_t)nwb * ldv : 0;
+  const size_t nW = (need_vw && !detect) ? (size_t)nwb * ldv : 0;  // the detector keeps no B e
   const size_t nNa = abft ? (size_t)M : 0, nNb = abft ? (size_t)N : 0;
   const size_t nScr = abft ? (size_t)std::max<long long>((long long)((K + 31) / 32) * M,
                                                          kmajor_scratch_floats(K, N))
                            : 0;
   const size_t nPart = split > 1 ? (size_t)split * M * N : 0;
   // learned threshold and residual sink (block level): block coherences
-  const bool learned = level == FTGEMM_FT_BLOCK && h->mlp_on;
-  const bool sink = level == FTGEMM_FT_BLOCK && h->sink_lam != nullptr;
+  const bool learned = level == FTGEMM_FT_BLOCK && h->mlp_on && !detect;
+  const bool sink = level == FTGEMM_FT_BLOCK && h->sink_lam != nullptr && !detect;
   if (sink && (long long)tiles_m * tiles_n > h->sink_cap)
     FAIL(FTGEMM_ERR_ARG, "residual sink: %lld tiles, capacity %lld", (long long)tiles_m * tiles_n,
          (long long)h->sink_cap);
@@ -1351,8 +1357,9 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
     Bk = ws + oBp;
   }
   if (abft) {
-    CK(launch_encode_kmajor(Bk, ldbp, K, N, need_vw ? n_u : 2, need_vw ? ws + oW : nullptr, ldv,
-                            ws + oNb, ws + oScr, &launches, h->stream));
+    CK(launch_encode_kmajor(Bk, ldbp, K, N, (need_vw && !detect) ? n_u : 2,
+                            (need_vw && !detect) ? ws + oW : nullptr, ldv, ws + oNb, ws + oScr, &launches,
+                            h->stream));
   }
   if (learned || sink) {
     CK(launch_block_coherence(ws + oV, ws + oW, ldv, K, ws + oNa, ws + oNb, M, N, m_u, n_u, ws + oCo,
@@ -1366,9 +1373,10 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
     int rc = make_map_2d(&maps.A, At, M, K, ldt, s.m_tb, s.k_tb);
     if (!rc) rc = make_map_2d(&maps.B, Bk, N, K, ldbp, s.n_tb, s.k_tb);
     if (!rc && need_vw) rc = make_map_2d(&maps.V, ws + oV, K, nvb, ldv, s.k_tb, NV);
-    if (!rc && need_vw) rc = make_map_2d(&maps.W, ws + oW, K, nwb, ldv, s.k_tb, NW);
+    if (!rc && need_vw && !detect) rc = make_map_2d(&maps.W, ws + oW, K, nwb, ldv, s.k_tb, NW);
     if (rc) return rc;
     if (!need_vw) { maps.V = maps.A; maps.W = maps.A; }
+    if (detect) maps.W = maps.V;  // not read
   }
 
   SimtParams p;
@@ -1403,7 +1411,8 @@ static int simt_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alph
     if (rc) return rc;
     CK(cudaEventRecord(ev.first, h->stream));
   }
-  CK(cfg->launch((int)level, maps, p, split, h->stream));
+  if (detect) CK(simt_launch_wide32_detect(maps, p, split, h->stream));
+  else CK(cfg->launch((int)level, maps, p, split, h->stream));
   ++launches;
   if (h->timing) {
     CK(cudaEventRecord(ev.second, h->stream));
@@ -1645,9 +1654,9 @@ int ftgemm_gemm_offline(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, doub
     FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_offline: bad argument");
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) FAIL(FTGEMM_ERR_ARG, "ftgemm_gemm_offline: size too large");
   CK(cudaSetDevice(h->device));
-  // detector: block-level checksums of the 128 x 128 x 16 tile, one
-  // verification after the last k-step (cadence 0)
-  const ftgemm_schedule det{128, 128, 16, 64, 64, 16, 8, 0, 1};
+  // detector: the detect-only kernel on the 128 x 128 x 32 tile -- column
+  // checksums only, one verification after the last k-step, no correction
+  const ftgemm_schedule det{128, 128, 32, 64, 64, 16, 8, 0, 1};
   // C_in is kept for the recomputation when beta reads it
   float* cin = nullptr;
   const size_t cin_floats = (size_t)m * (size_t)n;
@@ -1672,7 +1681,7 @@ int ftgemm_gemm_offline(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, doub
       CK(cudaMemcpy2DAsync(C, ldc * sizeof(float), cin, n * sizeof(float), n * sizeof(float), m,
                            cudaMemcpyDeviceToDevice, h->stream));
     rc = simt_gemm(h, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, FTGEMM_FT_BLOCK, det,
-                   injects ? injects[r] : nullptr, nullptr);
+                   injects ? injects[r] : nullptr, nullptr, nullptr, 0, true);
     if (rc) return rc;
     // the detection count so far (the report accumulates over attempts)
     unsigned long long det_now = 0;

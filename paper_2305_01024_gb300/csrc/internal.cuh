@@ -8,7 +8,9 @@
 
 namespace ftg {
 
-enum Level { L_OFF = 0, L_THREAD = 1, L_WARP = 2, L_BLOCK = 3, L_TILE = 4 };
+// L_DETECT (internal, the offline scheme's detector): the tile's column
+// checksums only, verified once per split, detection without correction.
+enum Level { L_OFF = 0, L_THREAD = 1, L_WARP = 2, L_BLOCK = 3, L_TILE = 4, L_DETECT = 6 };
 enum Kind { K_CORRECTED = 0, K_UNCORRECTABLE = 1, K_CHECKSUM = 2 };
 enum Target { T_ACC = 0, T_ROWSUM = 1, T_COLSUM = 2 };
 

@@ -26,6 +26,11 @@
 //   BLOCK:  checksums of the CTA tile; each thread owns one of the MT + NT
 //           entries, updated per k-slice from the staged e^T A_tb and
 //           B_tb e (Section 4.2.3).
+//   DETECT: the detector of the offline scheme (Section 5.5): the CTA
+//           tile's column checksums e^T C only, updated by all warps,
+//           verified once at the end of the split; a confirmed mismatch is
+//           reported as a detection and nothing is corrected (the caller
+//           recomputes).  No row checksums, no correction state.
 // Verification every `cadence` k-steps and after the last one: an fp32
 // screen compares the unit's row / column sums with the checksums; anything
 // above tau is re-checked with sums formed exactly in fp64 from the
@@ -64,9 +69,9 @@ struct SimtTile {
 
 template <class T, int LEVEL>
 struct SimtLayout {
-  static constexpr bool VW = LEVEL == L_WARP || LEVEL == L_BLOCK;
+  static constexpr bool VW = LEVEL == L_WARP || LEVEL == L_BLOCK || LEVEL == L_DETECT;
   static constexpr int NV = LEVEL == L_WARP ? T::WGM : 1;
-  static constexpr int NW = LEVEL == L_WARP ? T::WGN : 1;
+  static constexpr int NW = LEVEL == L_WARP ? T::WGN : (LEVEL == L_DETECT ? 0 : 1);  // DETECT: no B e
   static constexpr int pad32(int x) { return (x + 31) / 32 * 32; }  // 128-byte multiples
   static constexpr int A_FL = T::KT * T::MT;
   static constexpr int B_FL = T::KT * T::NT;
@@ -74,7 +79,7 @@ struct SimtLayout {
   static constexpr int W_FL = VW ? pad32(NW * T::KT) : 0;
   static constexpr int STAGE_FL = A_FL + B_FL + V_FL + W_FL;
   static constexpr uint32_t TX_BYTES = (A_FL + B_FL + (VW ? (NV + NW) * T::KT : 0)) * 4;
-  static constexpr int E = LEVEL == L_BLOCK ? T::MT + T::NT : 1;
+  static constexpr int E = LEVEL == L_BLOCK ? T::MT + T::NT : (LEVEL == L_DETECT ? T::NT : 1);
 };
 
 template <class T, int LEVEL>
@@ -91,9 +96,9 @@ struct SimtAux {
   float froAw[T::WGM];
   float froBw[T::WGN];
   float rowpart[LEVEL == L_BLOCK ? T::WGN : 1][T::MT];
-  float colpart[LEVEL == L_BLOCK ? T::WGM : 1][T::NT];
+  float colpart[LEVEL == L_BLOCK || LEVEL == L_DETECT ? T::WGM : 1][T::NT];
   // running block checksums, per k-part; read and written as float4
-  alignas(16) float csum[LEVEL == L_BLOCK ? T::NWARP / 2 : 1][L::E];
+  alignas(16) float csum[LEVEL == L_BLOCK ? T::NWARP / 2 : (LEVEL == L_DETECT ? T::NWARP : 1)][L::E];
   float cval[L::E];
   float tres[L::E];
   int eflag[L::E];
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
     tma_load_2d(st + L::A_FL, &tmB, &X.full[slot], col0, k0);
     if constexpr (L::VW) {
       tma_load_2d(st + L::A_FL + L::B_FL, &tmV, &X.full[slot], k0, tile_m * NV);
-      tma_load_2d(st + L::A_FL + L::B_FL + L::V_FL, &tmW, &X.full[slot], k0, tile_n * NW);
+      if constexpr (NW > 0) tma_load_2d(st + L::A_FL + L::B_FL + L::V_FL, &tmW, &X.full[slot], k0, tile_n * NW);
     }
   };
   int issued = 0;  // k-steps whose copies this thread has issued (highest + 1)
@@ -267,6 +272,12 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   constexpr bool kSCS = LEVEL == L_BLOCK && MT == 128 && NT == 128 && (NSIDE == 2 || NSIDE == 4) &&
                         KT % NSIDE == 0 && (KT / NSIDE == 2 || KT / NSIDE == 4 || KT / NSIDE == 8 || KT / NSIDE == 16);
   constexpr int KQ = kSCS ? KT / NSIDE : 1;
+  // DETECT: every warp updates the column checksums over its k-part of the
+  // slice, lane g the four columns 4g..4g+3
+  constexpr bool kDET = LEVEL == L_DETECT;
+  constexpr int KQD = kDET ? KT / T::NWARP : 1;
+  static_assert(!kDET || (NT == 128 && KT % T::NWARP == 0 && (KQD == 2 || KQD == 4 || KQD == 8 || KQD == 16)),
+                "detect-only layout");
   float cr[LEVEL == L_THREAD ? TM : 1], cc[LEVEL == L_THREAD ? TN : 1];
   float wr[LEVEL == L_WARP ? RPL : 1], wc[LEVEL == L_WARP ? CPL : 1];
   float bc[LEVEL == L_BLOCK ? ENT : 1];
@@ -284,6 +295,9 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   float froAt = 0.f, froBt = 0.f;  // THREAD: Frobenius norms over the fragment's rows / columns
   if constexpr (kSCS) {
     for (int e = tid; e < NSIDE * (MT + NT); e += NTHR) (&X.csum[0][0])[e] = 0.f;
+  }
+  if constexpr (kDET) {
+    for (int e = tid; e < T::NWARP * NT; e += NTHR) (&X.csum[0][0])[e] = 0.f;
   }
   if constexpr (LEVEL != L_OFF) {
     for (int r = tid; r < MT; r += NTHR) X.nA[r] = (row0 + r < M) ? p.nA[row0 + r] : 0.f;
@@ -453,6 +467,26 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
       add2(o[0], o[1], o[0], o[1], s4[0], s4[1]);
       add2(o[2], o[3], o[2], o[3], s4[2], s4[3]);
       *reinterpret_cast<float4*>(cs) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (kDET) {
+      // column checksums e^T C += (e^T A_tb(:, s)) B_tb(s, :), k-part `warp`
+      const float* cvs = vs + warp * KQD;
+      float vq[KQD];
+#pragma unroll
+      for (int q = 0; q < KQD; q += 4) lds_vec<(KQD < 4 ? KQD : 4)>(&vq[q], cvs + q);
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kk = 0; kk < KQD; ++kk) {
+        float x[4];
+        lds_vec<4>(x, Bs + (warp * KQD + kk) * NT + 4 * lane);
+        fma2(s4[0], s4[1], vq[kk], vq[kk], x[0], x[1]);
+        fma2(s4[2], s4[3], vq[kk], vq[kk], x[2], x[3]);
+      }
+      float* cs = &X.csum[warp][4 * lane];
+      float o[4];
+      lds_vec<4>(o, cs);
+      add2(o[0], o[1], o[0], o[1], s4[0], s4[1]);
+      add2(o[2], o[3], o[2], o[3], s4[2], s4[3]);
+      *reinterpret_cast<float4*>(cs) = make_float4(o[0], o[1], o[2], o[3]);
     } else if constexpr (LEVEL == L_BLOCK) {
 #pragma unroll
       for (int q = 0; q < ENT; ++q) {
@@ -528,6 +562,9 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
             for (int y = 0; y < CPL; ++y)
               if (tm + y * LM < TN && FCOL(tm + y * LM) == f.col) wc[y] += f.delta;
           }
+        } else if constexpr (kDET) {
+          // no row checksums to hit; a column-checksum offset goes to part 0
+          if (f.target == T_COLSUM && tid == f.col / 4) X.csum[0][f.col] += f.delta;
         } else if constexpr (LEVEL == L_BLOCK) {
           const int e = f.target == T_ROWSUM ? NT + f.row : f.col;
           if constexpr (kSCS) {
@@ -694,12 +731,14 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               if (q == 0) rs_c0 = v; else rs_c1 = v;
             }
           } else {
+            if constexpr (LEVEL != L_DETECT) {
 #pragma unroll
-            for (int i = 0; i < TM; ++i) {
-              float s = 0.f;
+              for (int i = 0; i < TM; ++i) {
+                float s = 0.f;
 #pragma unroll
-              for (int j = 0; j < TN; ++j) s += acc[i][j];
-              pr[i] = s;
+                for (int j = 0; j < TN; ++j) s += acc[i][j];
+                pr[i] = s;
+              }
             }
 #pragma unroll
             for (int j = 0; j < TN; ++j) {
@@ -708,10 +747,12 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
               for (int i = 0; i < TM; ++i) s += acc[i][j];
               pc[j] = s;
             }
+            if constexpr (LEVEL != L_DETECT) {
 #pragma unroll
-            for (int o = 1; o < LN; o <<= 1)
+              for (int o = 1; o < LN; o <<= 1)
 #pragma unroll
-              for (int i = 0; i < TM; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], o);
+                for (int i = 0; i < TM; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], o);
+            }
 #pragma unroll
             for (int o = LN; o < 32; o <<= 1)
 #pragma unroll
@@ -876,6 +917,65 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
                   report_event(p.rep, p.recs, rec);
                 }
               }
+            }
+          } else if constexpr (LEVEL == L_DETECT) {
+            // the column checksums only; a confirmed mismatch is a detection
+            // (the most flagged column reported, nothing corrected)
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+              if ((j % LM) == tm) X.colpart[wm][FCOL(j)] = pc[j];
+            __syncthreads();
+            int flag = 0;
+            float cv = 0.f, tv = 0.f;
+            if (tid < NT) {
+              float sc = 0.f;
+#pragma unroll
+              for (int w = 0; w < T::WGM; ++w) sc += X.colpart[w][tid];
+#pragma unroll
+              for (int r = 0; r < T::NWARP; ++r) cv += X.csum[r][tid];
+              tv = ft_tau(lam_u, X.froAw[0], X.nB[tid], grow, cv);
+              flag = fabsf(sc - cv) > kScreen * tv;
+            }
+            if (__syncthreads_or(flag)) {
+              // fp64 confirmation of the screened columns
+              if (tid < NT) { X.eflag[tid] = flag; X.sum64[tid] = 0.0; }
+              if (tid == 0) { X.nc = 0; X.bestc = 0ull; }
+              __syncthreads();
+#pragma unroll
+              for (int j = 0; j < TN; ++j) {
+                const int c = FCOL(j);
+                if (X.eflag[c]) {
+                  double sd = 0.0;
+#pragma unroll
+                  for (int i = 0; i < TM; ++i) sd += (double)acc[i][j];
+                  atomicAdd(&X.sum64[c], sd);
+                }
+              }
+              __syncthreads();
+              if (tid < NT && flag) {
+                const double d = X.sum64[tid] - (double)cv;
+                X.dres[tid] = d;
+                X.tres[tid] = tv;
+                if (fabs(d) > (double)tv) {
+                  atomicAdd(&X.nc, 1);
+                  atomicMax(&X.bestc, flag_key(flag_score((float)d, tv), tid));
+                }
+              }
+              __syncthreads();
+              if (tid == 0 && X.nc) {
+                const int jc = key_index(X.bestc);
+                ftgemm_fault_record rec;
+                rec.tile_m = tile_m; rec.tile_n = tile_n; rec.kstep = ks;
+                rec.problem = 0; rec.reserved = 0;
+                rec.row = -1;
+                rec.col = col0 + jc;
+                rec.residual_r = 0.0; rec.residual_c = X.dres[jc];
+                rec.tau = (double)X.tres[jc];
+                rec.delta = 0.0;
+                rec.kind = K_UNCORRECTABLE;
+                report_event(p.rep, p.recs, rec);
+              }
+              __syncthreads();
             }
           } else {  // L_BLOCK
             if constexpr (kRS) {

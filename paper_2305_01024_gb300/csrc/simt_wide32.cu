@@ -14,4 +14,11 @@ cudaError_t simt_launch_wide32(int level, const SimtMaps& maps, const SimtParams
   using T = SimtTile<128, 128, 32, 64, 64, 16, 8, 3>;
   return launch_simt_level<T>(level, maps, p, split, st);
 }
+
+// The detector of the offline scheme (Section 5.5) on the same tile: column
+// checksums only, one verification per split, no correction.
+cudaError_t simt_launch_wide32_detect(const SimtMaps& maps, const SimtParams& p, int split, cudaStream_t st) {
+  using T = SimtTile<128, 128, 32, 64, 64, 16, 8, 3>;
+  return launch_simt<T, L_DETECT>(maps, p, split, st);
+}
 }  // namespace ftg
