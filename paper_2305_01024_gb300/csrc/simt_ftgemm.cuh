@@ -183,7 +183,11 @@ __device__ __forceinline__ float cta_sum(Aux& X, float v) {
   return t;
 }
 
-template <class T, int LEVEL>
+// INJ: the kernel applies scheduled faults (Section 5.3's injection, a test
+// and measurement harness).  Calls without faults run the INJ = false
+// instance, which carries none of that code and so keeps its registers for
+// the tile.
+template <class T, int LEVEL, bool INJ>
 __global__ void __launch_bounds__(T::NTHR, T::MINB)
     simt_ftgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmW,
@@ -365,13 +369,16 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
   }
 
   // ---- scheduled faults of this tile ------------------------------------
-  const int my_tile = tile_m * p.tiles_n + tile_n;
-  int fidx = 0, next_ks = INT_MAX;
-  if (p.nfaults > 0) {
-    fidx = first_fault(p.faults, p.nfaults, my_tile);
-    while (fidx < p.nfaults && p.faults[fidx].tile == my_tile && p.faults[fidx].kstep < ks0) ++fidx;
-    if (fidx < p.nfaults && p.faults[fidx].tile == my_tile) next_ks = p.faults[fidx].kstep;
-  }
+  // Only the k-step of the next one stays live through the K loop; the table
+  // is searched again when it comes (rarely), to keep registers for the tile.
+  auto next_fault_ks = [&](int from_ks) {
+    const int my_tile = tile_m * p.tiles_n + tile_n;
+    int f = first_fault(p.faults, p.nfaults, my_tile);
+    while (f < p.nfaults && p.faults[f].tile == my_tile && p.faults[f].kstep < from_ks) ++f;
+    return (f < p.nfaults && p.faults[f].tile == my_tile) ? p.faults[f].kstep : INT_MAX;
+  };
+  int next_ks = INT_MAX;
+  if constexpr (INJ) next_ks = p.nfaults > 0 ? next_fault_ks(ks0) : INT_MAX;
 
   for (int t = 0; t < nk; ++t) {
     const int slot = t % STAGES;
@@ -527,7 +534,10 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
     }
 
     // ---- fault injection after this k-step (Section 5.3) ----------------
-    if (ks == next_ks) {
+    if (INJ && ks == next_ks) {
+      const int my_tile = tile_m * p.tiles_n + tile_n;
+      int fidx = first_fault(p.faults, p.nfaults, my_tile);
+      while (fidx < p.nfaults && p.faults[fidx].tile == my_tile && p.faults[fidx].kstep < ks) ++fidx;
       while (fidx < p.nfaults && p.faults[fidx].tile == my_tile && p.faults[fidx].kstep == ks) {
         const Fault f = p.faults[fidx++];
         if (f.target == T_ACC) {
@@ -577,7 +587,7 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
           }
         }
       }
-      next_ks = (fidx < p.nfaults && p.faults[fidx].tile == my_tile) ? p.faults[fidx].kstep : INT_MAX;
+      next_ks = next_fault_ks(ks + 1);
     }
 
     // ---- verification at the end of a period ----------------------------
@@ -1205,15 +1215,22 @@ __global__ void __launch_bounds__(T::NTHR, T::MINB)
 #undef FCOL
 }
 
-template <class T, int LEVEL>
-cudaError_t launch_simt(const SimtMaps& maps, const SimtParams& p, int split, cudaStream_t st) {
+template <class T, int LEVEL, bool INJ>
+cudaError_t launch_simt_inj(const SimtMaps& maps, const SimtParams& p, int split, cudaStream_t st) {
   constexpr size_t smem = simt_smem_bytes<T, LEVEL>();
-  cudaError_t e = cudaFuncSetAttribute(simt_ftgemm_kernel<T, LEVEL>,
+  cudaError_t e = cudaFuncSetAttribute(simt_ftgemm_kernel<T, LEVEL, INJ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((p.N + T::NT - 1) / T::NT, (p.M + T::MT - 1) / T::MT, split);
-  simt_ftgemm_kernel<T, LEVEL><<<grid, T::NTHR, smem, st>>>(maps.A, maps.B, maps.V, maps.W, p);
+  simt_ftgemm_kernel<T, LEVEL, INJ><<<grid, T::NTHR, smem, st>>>(maps.A, maps.B, maps.V, maps.W, p);
   return cudaGetLastError();
+}
+
+// The instance with the injection harness only when the call has faults.
+template <class T, int LEVEL>
+cudaError_t launch_simt(const SimtMaps& maps, const SimtParams& p, int split, cudaStream_t st) {
+  return p.nfaults > 0 ? launch_simt_inj<T, LEVEL, true>(maps, p, split, st)
+                       : launch_simt_inj<T, LEVEL, false>(maps, p, split, st);
 }
 
 template <class T>

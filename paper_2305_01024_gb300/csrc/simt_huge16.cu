@@ -17,10 +17,10 @@ cudaError_t simt_launch_huge16(int level, const SimtMaps& maps, const SimtParams
 cudaError_t simt_preload_huge16() {
   using T = SimtTile<128, 128, 16, 32, 64, 8, 8>;
   cudaFuncAttributes a;
-  cudaError_t e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_OFF>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_THREAD>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_WARP>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_BLOCK>);
+  cudaError_t e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_OFF, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_THREAD, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_WARP, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_BLOCK, false>);
   return e;
 }
 }  // namespace ftg
