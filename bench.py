@@ -45,7 +45,7 @@ SCHED16 = dict(m_tb=128, n_tb=128, k_tb=16, m_w=64, n_w=64, m_t=16, n_t=8, caden
 # against the best FT-off kernel
 SCHED_OFF_BEST = dict(m_tb=128, n_tb=128, k_tb=16, m_w=32, n_w=64, m_t=8, n_t=8, cadence=16, split_k=1)
 FAULTS_PER_MIN = 200.0
-KERNEL_SOURCES = ["simt_ftgemm.cuh", "simt_wide32.cu", "internal.cuh", "ptx.cuh"]
+KERNEL_SOURCES = ["simt_ftgemm.cuh", "simt_wide32.cu", "internal.cuh", "ptx.cuh", "mlp.cuh"]
 TC_KERNEL_SOURCES = ["tc_gemm.cu", "internal.cuh", "ptx.cuh", "mlp.cuh"]
 
 

@@ -184,9 +184,11 @@ __device__ __forceinline__ float cta_sum(Aux& X, float v) {
 }
 
 // INJ: the kernel applies scheduled faults (Section 5.3's injection, a test
-// and measurement harness).  Calls without faults run the INJ = false
-// instance, which carries none of that code and so keeps its registers for
-// the tile.
+// and measurement harness).  The unchecked level (OFF) without faults runs an
+// INJ = false instance, which carries none of that code: at 255 registers it
+// then schedules its K loop better (measured 67.4 against 65.3 TFLOP/s at
+// 16384^3 on the 128 x 128 x 32 tile).  The checked levels always run the
+// INJ = true instance, measured as fast or faster without faults as well.
 template <class T, int LEVEL, bool INJ>
 __global__ void __launch_bounds__(T::NTHR, T::MINB)
     simt_ftgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -1226,11 +1228,12 @@ cudaError_t launch_simt_inj(const SimtMaps& maps, const SimtParams& p, int split
   return cudaGetLastError();
 }
 
-// The instance with the injection harness only when the call has faults.
 template <class T, int LEVEL>
 cudaError_t launch_simt(const SimtMaps& maps, const SimtParams& p, int split, cudaStream_t st) {
-  return p.nfaults > 0 ? launch_simt_inj<T, LEVEL, true>(maps, p, split, st)
-                       : launch_simt_inj<T, LEVEL, false>(maps, p, split, st);
+  if constexpr (LEVEL == L_OFF) {
+    if (p.nfaults == 0) return launch_simt_inj<T, LEVEL, false>(maps, p, split, st);
+  }
+  return launch_simt_inj<T, LEVEL, true>(maps, p, split, st);
 }
 
 template <class T>

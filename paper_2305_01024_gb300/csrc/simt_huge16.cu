@@ -18,9 +18,9 @@ cudaError_t simt_preload_huge16() {
   using T = SimtTile<128, 128, 16, 32, 64, 8, 8>;
   cudaFuncAttributes a;
   cudaError_t e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_OFF, false>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_THREAD, false>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_WARP, false>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_BLOCK, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_THREAD, true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_WARP, true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, simt_ftgemm_kernel<T, L_BLOCK, true>);
   return e;
 }
 }  // namespace ftg
