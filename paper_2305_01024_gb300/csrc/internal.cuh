@@ -122,6 +122,7 @@ struct SimtMaps {
 // TC_CS_SLOTS of its rows carry the pieces of e^T A and as many of its
 // columns the pieces of B e, leaving a TC_DM x TC_DN data tile of C.
 constexpr int TC_BM = 128, TC_BN = 256, TC_CS_SLOTS = 8;
+constexpr int TC_MAX_PIECES = 5;  // checksum pieces in use: 3 (bf16) or 5 (e4m3)
 constexpr int TC_DM = TC_BM - TC_CS_SLOTS, TC_DN = TC_BN - TC_CS_SLOTS;  // 120, 248
 constexpr int TC_GROUP_M = 16;  // tile rows per raster group
 

@@ -61,11 +61,15 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * 128;            // 16 KB
   static constexpr int B_BYTES = BN * 128;            // 32 KB
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int THREADS = 192;
+  // epilogue warps: with checksums two warpgroups (each tile's columns split
+  // between them), without one; plus the TMA and MMA warps
+  static constexpr int EW = ABFT ? 8 : 4;
+  static constexpr int THREADS = 64 + 32 * EW;
   static constexpr int MN_BOX = 64 * 128;  // bytes of one 64-column x 64-row box of an MN-major B
   static constexpr uint32_t TMEM_COLS = 2 * BN;       // two fp32 accumulators
   static constexpr int NPIECE = DT == 0 ? 3 : 5;      // checksum pieces in use
   static_assert(!ABFT || NPIECE <= CSR, "pieces must fit the checksum slots");
+  static_assert(NPIECE <= TC_MAX_PIECES, "column-checksum piece rows in shared memory");
   // the checksum rows start on a 1024-byte (8-row) swizzle boundary
   static_assert((DM * 128) % 1024 == 0 && (DN * 128) % 1024 == 0, "checksum slots misaligned");
 };
@@ -113,18 +117,24 @@ struct TcSmemTail {
   int fix_row[2], fix_col[2];      // per accumulator parity
   double fix_delta[2];
   unsigned int sink_max;           // residual sink: largest residual / (u * norms) of the tile
-  alignas(16) float colpart[4][256];  // per epilogue warp partial column sums (data rows); float4 stores
-  float ccp[TC_CS_SLOTS][256];     // column-checksum pieces, TMEM lanes 120..127
+  alignas(16) float colpart[4][256];  // per TMEM lane quarter partial column sums (data rows); float4 stores
+  float ccp[TC_MAX_PIECES][256];   // column-checksum pieces, TMEM lanes 120..
   float crow[128];                 // row checksums
   float ccol[256];                 // column checksums
-  float cradj[128], ccadj[256];    // injected offsets of the checksums
-  float tr[128], tc[256];          // thresholds
-  int flag_r[128], flag_c[256];
+  // thresholds; before the threshold is formed, the same entry holds the
+  // injected offset of that row's / column's checksum (read, then
+  // overwritten, by the one thread that owns the row / column)
+  float tr[128], tc[256];
+  float rsp[2][128];               // fp32 row sums of each half of the columns
+  uint8_t flag_r[128], flag_c[256];
   double sum_r[128], sum_c[256];   // fp64 confirmation sums
+  double sum_rp[128];              // fp64 row sums of the second half of the columns
   // per epilogue warp: its 32 rows x 16 columns of one accumulator chunk,
-  // rows 80 bytes apart (16-byte writes of 8 consecutive rows hit distinct
-  // banks), read back row-segment-wise so that C is written in 64-byte runs
-  alignas(16) float stg[4][32][20];
+  // 64-byte rows with the 16-byte column groups XOR-swizzled by (row / 2) % 4
+  // (16-byte writes of 8 consecutive rows, and the read-back of 4 column
+  // groups of 2 rows, hit distinct banks), read back row-segment-wise so
+  // that C is written in 64-byte runs
+  alignas(16) float stg[8][32][16];
 };
 
 static_assert(offsetof(TcSmemTail, colpart) % 16 == 0 && offsetof(TcSmemTail, stg) % 16 == 0,
@@ -132,7 +142,13 @@ static_assert(offsetof(TcSmemTail, colpart) % 16 == 0 && offsetof(TcSmemTail, st
 static_assert(1024 + TC_STAGES * TcCfg<0, true>::STAGE_BYTES + sizeof(TcSmemTail) <= 227 * 1024,
               "dynamic shared memory within the 227 KB a CTA may use");
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier 1 over the N epilogue threads (128 or 256).
+template <int N>
+__device__ __forceinline__ void epi_bar() {
+  static_assert(N == 128 || N == 256, "epilogue thread count");
+  if constexpr (N == 128) asm volatile("bar.sync 1, 128;" ::: "memory");
+  else asm volatile("bar.sync 1, 256;" ::: "memory");
+}
 
 // The tiles one CTA runs.  With a problem table: the CTA's slice of the
 // host-built tile list.  With one inline problem: every gridDim.x-th entry
@@ -185,7 +201,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&T.acc_full[a], 1);
-      mbar_init(&T.acc_empty[a], 4);  // one arrival per epilogue warp
+      mbar_init(&T.acc_empty[a], Cfg::EW);  // one arrival per epilogue warp
     }
     T.abort = 0;
     fence_mbar_init();
@@ -297,8 +313,15 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
     if (lt > 0) mbar_wait(&T.acc_full[(lt - 1) & 1], ((lt - 1) >> 1) & 1);
   } else if (warp >= 2) {
     // ---- epilogue -------------------------------------------------------
+    // With checksums two warpgroups share each tile: warp pairs with the
+    // same TMEM lane quarter, one per half of the columns (eh).
+    constexpr int EPI_T = 32 * Cfg::EW;      // epilogue threads
+    constexpr int CH2 = BN / 32 / (Cfg::EW / 4);  // 32-column loads per warp and tile
     const int lq = warp & 3;            // TMEM lane quarter this warp may access
+    const int ew = warp - 2;            // epilogue warp index
+    const int eh = ew >> 2;             // half of the columns (0 without checksums)
     const int r = lq * 32 + lane;       // tile row == TMEM lane
+    const int q = eh * 128 + r;         // this thread's index among the epilogue threads
     const bool data_row = r < DM;
     const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
     TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
@@ -334,7 +357,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         froB_t = P.froB[x.tn];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int c = r + 128 * h, gc = col0 + c;
+          const int c = q + EPI_T * h, gc = col0 + c;  // this thread's columns
           nB_c[h] = (c < DN && gc < pN) ? P.nB[gc] : 0.f;
         }
 #pragma unroll
@@ -385,17 +408,18 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       // rows of 4 columns, then an xor tree over the 8 lanes of a column
       // group.
       auto store16w = [&](int ch, const float* v) {
-        float(*S)[20] = T.stg[lq];
+        float(*S)[16] = T.stg[ew];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<float4*>(&S[lane][4 * q]) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int g = 0; g < 4; ++g)
+          *reinterpret_cast<float4*>(&S[lane][4 * (g ^ ((lane >> 1) & 3))]) =
+              make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
         __syncwarp();
         float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int sgrp = 0; sgrp < 4; ++sgrp) {
           const int rr = 8 * sgrp + (lane >> 2), cq = lane & 3;
           const int tr_ = lq * 32 + rr, gr_ = row0 + tr_;  // tile row, matrix row
-          const float4 x = *reinterpret_cast<const float4*>(&S[rr][4 * cq]);
+          const float4 x = *reinterpret_cast<const float4*>(&S[rr][4 * (cq ^ ((rr >> 1) & 3))]);
           if constexpr (ABFT) {
             if (tr_ < DM) {
               cs.x += x.x; cs.y += x.y; cs.z += x.z; cs.w += x.w;
@@ -437,16 +461,16 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       };
 
       if constexpr (ABFT) {
-        T.cradj[r] = 0.f;
-        T.ccadj[r] = 0.f;
-        T.ccadj[128 + r] = 0.f;
-        if (r == 0) {
+        // the checksums' injected offsets start at zero (in tr / tc)
+        if (eh == 0) T.tr[r] = 0.f;
+        for (int c = q; c < BN; c += EPI_T) T.tc[c] = 0.f;
+        if (q == 0) {
           T.fix_row[ab] = -1;
           T.fix_col[ab] = -1;
           T.fix_delta[ab] = 0.0;
           T.sink_max = 0u;
         }
-        epi_bar();
+        epi_bar<EPI_T>();
       }
       // ----- scheduled faults of this tile (Section 5.3) -----
       // Verification runs once per tile after its last k-step; the
@@ -459,7 +483,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
              ++f) {
           const Fault F = run.faults[f];
           if (F.target == T_ACC) {
-            if ((F.row >> 5) == lq) {  // warp-uniform: this warp owns the lane
+            if ((F.row >> 5) == lq && eh == 0) {  // warp-uniform: this warp owns the lane
               const uint32_t a = tl + (uint32_t)(F.col & ~15);
               float v[16];
               tmem_ld16(a, v);
@@ -473,9 +497,9 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
               tmem_wait_st();
             }
           } else if constexpr (ABFT) {
-            if (r == 0) {
-              if (F.target == T_ROWSUM) T.cradj[F.row] += F.delta;
-              else T.ccadj[F.col] += F.delta;
+            if (q == 0) {
+              if (F.target == T_ROWSUM) T.tr[F.row] += F.delta;
+              else T.tc[F.col] += F.delta;
             }
           }
         }
@@ -485,124 +509,144 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         // ----- alpha * acc + beta * C, store -----
         // every lane reads tensor memory (the loads are warp-collective);
         // only rows inside the matrix store
-        for (int ch = 0; ch < BN / 16; ++ch) {
-          float v[16];
-          tmem_ld16(tl + ch * 16, v);
+        // 32 columns per tensor-memory load: half the load-and-wait round trips
+        for (int c2 = 0; c2 < BN / 32; ++c2) {
+          float v2[32];
+          tmem_ld32(tl + c2 * 32, v2);
           tmem_wait_ld();
-          store16w(ch, v);
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) store16w(2 * c2 + hh, v2 + 16 * hh);
         }
       } else {
-        epi_bar();
+        epi_bar<EPI_T>();
         // ----- one pass over the accumulator: fp32 screen sums and the store -----
         // C is written before verification; a confirmed fault is then
-        // patched in place (a single element, below).
+        // patched in place (a single element, below).  Each warp covers its
+        // lane quarter's rows over its half of the columns.
         float rs = 0.f, rc = 0.f, crow = 0.f;
-        for (int ch = 0; ch < BN / 16; ++ch) {
-          float v[16];
-          tmem_ld16(tl + ch * 16, v);
+        // 32 columns per tensor-memory load, processed as two 16-column chunks
+        for (int c2 = eh * CH2; c2 < (eh + 1) * CH2; ++c2) {
+          float v2[32];
+          tmem_ld32(tl + c2 * 32, v2);
           tmem_wait_ld();
-          // row sum over the data columns: a pairwise tree over the chunk,
-          // then a compensated (two-term) add of the chunk's sum; the row
-          // checksum pieces sit in columns DN..DN+NPIECE-1 of the last chunk
-          constexpr int FULL = DN / 16, REM = DN % 16;
-          static_assert(REM + Cfg::NPIECE <= 16, "pieces inside the last chunk");
-          float part;
-          if (ch < FULL) {
-            float t[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) t[q] = v[q];
+          for (int hh = 0; hh < 2; ++hh) {
+            const int ch = 2 * c2 + hh;
+            const float* v = v2 + 16 * hh;
+            // row sum over the data columns: a pairwise tree over the chunk,
+            // then a compensated (two-term) add of the chunk's sum; the row
+            // checksum pieces sit in columns DN..DN+NPIECE-1 of the last chunk
+            constexpr int FULL = DN / 16, REM = DN % 16;
+            static_assert(REM + Cfg::NPIECE <= 16, "pieces inside the last chunk");
+            float part;
+            if (ch < FULL) {
+              float t[16];
 #pragma unroll
-            for (int st = 8; st > 0; st >>= 1)
+              for (int e = 0; e < 16; ++e) t[e] = v[e];
 #pragma unroll
-              for (int q = 0; q < st; ++q) t[q] += t[q + st];
-            part = t[0];
-          } else {
-            float t[16];
+              for (int st = 8; st > 0; st >>= 1)
 #pragma unroll
-            for (int q = 0; q < 16; ++q) t[q] = q < REM ? v[q] : 0.f;
+                for (int e = 0; e < st; ++e) t[e] += t[e + st];
+              part = t[0];
+            } else {
+              float t[16];
 #pragma unroll
-            for (int st = 8; st > 0; st >>= 1)
+              for (int e = 0; e < 16; ++e) t[e] = e < REM ? v[e] : 0.f;
 #pragma unroll
-              for (int q = 0; q < st; ++q) t[q] += t[q + st];
-            part = t[0];
+              for (int st = 8; st > 0; st >>= 1)
 #pragma unroll
-            for (int pc = 0; pc < Cfg::NPIECE; ++pc) crow = fmaf(v[REM + pc], wsc[pc], crow);
+                for (int e = 0; e < st; ++e) t[e] += t[e + st];
+              part = t[0];
+#pragma unroll
+              for (int pc = 0; pc < Cfg::NPIECE; ++pc) crow = fmaf(v[REM + pc], wsc[pc], crow);
+            }
+            {
+              const float y = part - rc;
+              const float tt = rs + y;
+              rc = (tt - rs) - y;
+              rs = tt;
+            }
+            // the column checksum pieces sit in lanes DM..DM+NPIECE-1
+            if (r >= DM && r - DM < Cfg::NPIECE) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) T.ccp[r - DM][ch * 16 + e] = v[e];
+            }
+            store16w(ch, v);  // also the warp's column partial sums of the chunk
           }
-          {
-            const float y = part - rc;
-            const float tt = rs + y;
-            rc = (tt - rs) - y;
-            rs = tt;
-          }
-          // the column checksum pieces sit in lanes DM..DM+NPIECE-1
-          if (r >= DM && r - DM < Cfg::NPIECE) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) T.ccp[r - DM][ch * 16 + q] = v[q];
-          }
-          store16w(ch, v);  // also the warp's column partial sums of the chunk
         }
-        crow += T.cradj[r];
-        T.crow[r] = crow;
-        T.tr[r] = (data_row && gr < pM) ? ft_tau(lam_u, nA_r, froB_t, grow, crow) : 0.f;
-        int flagged = data_row && fabsf(rs - crow) > kScreen * T.tr[r];
-        T.flag_r[r] = flagged;
+        T.rsp[eh][r] = rs;
+        if (eh == Cfg::EW / 4 - 1) {  // the half holding the row-checksum pieces
+          crow += T.tr[r];            // the injected offset of this row's checksum
+          T.crow[r] = crow;
+        }
+        epi_bar<EPI_T>();
         constexpr float kU = 5.9604644775390625e-8f;  // 2^-24
-        if (run.sink_lam && data_row && gr < pM) {
-          const float den = kU * nA_r * froB_t;
-          if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(rs - crow) / den));
+        int flagged = 0;
+        if (eh == 0) {
+          // this row: both halves' sums against its checksum
+          const float rsum = Cfg::EW == 8 ? T.rsp[0][r] + T.rsp[Cfg::EW / 4 - 1][r] : T.rsp[0][r];
+          const float crw = T.crow[r];
+          const float trv = (data_row && gr < pM) ? ft_tau(lam_u, nA_r, froB_t, grow, crw) : 0.f;
+          T.tr[r] = trv;
+          flagged = data_row && fabsf(rsum - crw) > kScreen * trv;
+          T.flag_r[r] = (uint8_t)flagged;
+          if (run.sink_lam && data_row && gr < pM) {
+            const float den = kU * nA_r * froB_t;
+            if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(rsum - crw) / den));
+          }
         }
-        epi_bar();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = r + 128 * h;
+        for (int c = q; c < BN; c += EPI_T) {
+          const int hc = (c - q) / EPI_T;  // which of this thread's columns (0 or 1)
           int fl = 0;
           float cc = 0.f, tcv = 0.f;
           if (c < DN) {
 #pragma unroll
-            for (int q = 0; q < Cfg::NPIECE; ++q) cc = fmaf(T.ccp[q][c], vsc[q], cc);
-            cc += T.ccadj[c];
+            for (int e = 0; e < Cfg::NPIECE; ++e) cc = fmaf(T.ccp[e][c], vsc[e], cc);
+            cc += T.tc[c];  // the injected offset of this column's checksum
             const int gc = col0 + c;
-            tcv = gc < pN ? ft_tau(lam_u, froA_t, nB_c[h], grow, cc) : 0.f;
-            const float s = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
-            fl = fabsf(s - cc) > kScreen * tcv;
+            const float nbc = hc == 0 ? nB_c[0] : nB_c[1];
+            tcv = gc < pN ? ft_tau(lam_u, froA_t, nbc, grow, cc) : 0.f;
+            const float sc2 = (T.colpart[0][c] + T.colpart[1][c]) + (T.colpart[2][c] + T.colpart[3][c]);
+            fl = fabsf(sc2 - cc) > kScreen * tcv;
             if (run.sink_lam && gc < pN) {
-              const float den = kU * froA_t * nB_c[h];
-              if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(s - cc) / den));
+              const float den = kU * froA_t * nbc;
+              if (den > 0.f) atomicMax(&T.sink_max, __float_as_uint(fabsf(sc2 - cc) / den));
             }
           }
           T.ccol[c] = cc;
           T.tc[c] = tcv;
-          T.flag_c[c] = fl;
+          T.flag_c[c] = (uint8_t)fl;
           flagged |= fl;
         }
-        // barrier + OR over the four epilogue warps: the same answer in all
-        const int any_flag = bar_red_or(1, 128, flagged);
-        if (run.sink_lam && r == 0 && ok) {
+        // barrier + OR over the epilogue warps: the same answer in all
+        const int any_flag = bar_red_or(1, EPI_T, flagged);
+        if (run.sink_lam && q == 0 && ok) {
           run.sink_lam[my_tile] = __uint_as_float(T.sink_max);
 #pragma unroll
-          for (int q = 0; q < MLP_IN; ++q) run.sink_x[(long long)my_tile * MLP_IN + q] = feat[q];
+          for (int e = 0; e < MLP_IN; ++e) run.sink_x[(long long)my_tile * MLP_IN + e] = feat[e];
         }
         if (any_flag) {
           // ----- fp64 confirmation of every screened row / column -----
-          if (r == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
-          for (int c = r; c < BN; c += 128) T.sum_c[c] = 0.0;
-          epi_bar();
+          if (q == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
+          for (int c = q; c < BN; c += EPI_T) T.sum_c[c] = 0.0;
+          epi_bar<EPI_T>();
           // fp64 sums only where the screen flagged: a flagged row in its own
-          // thread, a flagged column (the same in all lanes) by a warp
-          // shuffle reduction and one shared-memory add per warp
+          // thread (each half of the columns apart), a flagged column (the
+          // same in all lanes) by a warp shuffle reduction and one
+          // shared-memory add per warp
           const bool my_row_flagged = T.flag_r[r] != 0;
           double sr = 0.0;
-          for (int ch = 0; ch < BN / 16; ++ch) {
+          for (int ch = eh * 2 * CH2; ch < (eh + 1) * 2 * CH2; ++ch) {
             float v[16];
             tmem_ld16(tl + ch * 16, v);
             tmem_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int c = ch * 16 + q;
+            for (int e = 0; e < 16; ++e) {
+              const int c = ch * 16 + e;
               if (c < DN) {
-                if (my_row_flagged) sr += (double)v[q];
+                if (my_row_flagged) sr += (double)v[e];
                 if (T.flag_c[c]) {  // warp-uniform
-                  double xs = data_row ? (double)v[q] : 0.0;
+                  double xs = data_row ? (double)v[e] : 0.0;
 #pragma unroll
                   for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
                   if (lane == 0) atomicAdd(&T.sum_c[c], xs);
@@ -610,16 +654,21 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
               }
             }
           }
-          T.sum_r[r] = sr;
-          epi_bar();
-          if (T.flag_r[r]) {
-            const double dd = sr - (double)T.crow[r];
-            if (fabs(dd) > (double)T.tr[r]) {
-              atomicAdd(&T.nr, 1);
-              atomicMax(&T.bestr, flag_key(flag_score((float)dd, T.tr[r]), r));
+          if (eh == 0) T.sum_r[r] = sr;
+          else T.sum_rp[r] = sr;
+          epi_bar<EPI_T>();
+          if (eh == 0) {
+            const double srt = Cfg::EW == 8 ? T.sum_r[r] + T.sum_rp[r] : T.sum_r[r];
+            T.sum_r[r] = srt;
+            if (T.flag_r[r]) {
+              const double dd = srt - (double)T.crow[r];
+              if (fabs(dd) > (double)T.tr[r]) {
+                atomicAdd(&T.nr, 1);
+                atomicMax(&T.bestr, flag_key(flag_score((float)dd, T.tr[r]), r));
+              }
             }
           }
-          for (int c = r; c < DN; c += 128) {
+          for (int c = q; c < DN; c += EPI_T) {
             if (T.flag_c[c]) {
               const double dd = T.sum_c[c] - (double)T.ccol[c];
               if (fabs(dd) > (double)T.tc[c]) {
@@ -628,8 +677,8 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
               }
             }
           }
-          epi_bar();
-          if (r == 0 && (T.nr | T.nc)) {
+          epi_bar<EPI_T>();
+          if (q == 0 && (T.nr | T.nc)) {
             const int nr = T.nr, nc = T.nc;
             const int ir = nr ? key_index(T.bestr) : -1, jc = nc ? key_index(T.bestc) : -1;
             const double dR = nr ? T.sum_r[ir] - (double)T.crow[ir] : 0.0;
@@ -656,14 +705,14 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
             }
             report_event(run.rep, run.recs, rec);
           }
-          epi_bar();
+          epi_bar<EPI_T>();
           // ----- correct the located element of C (Section 4.2.1) -----
-          // The warp owning its TMEM lane rereads the accumulator: with
-          // beta == 0 the value is recomputed from acc - delta; otherwise C
-          // already holds alpha * acc + beta * C_in and alpha * delta is
-          // taken off it.
+          // The first-half warp owning its TMEM lane rereads the accumulator:
+          // with beta == 0 the value is recomputed from acc - delta;
+          // otherwise C already holds alpha * acc + beta * C_in and
+          // alpha * delta is taken off it.
           const int fr = T.fix_row[ab];
-          if (fr >= 0 && (fr >> 5) == lq) {  // warp-uniform
+          if (fr >= 0 && (fr >> 5) == lq && eh == 0) {  // warp-uniform
             const int fc = T.fix_col[ab];
             const double fd = T.fix_delta[ab];
             float v[16];
@@ -672,8 +721,8 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
             if (lane == (fr & 31) && row_ok) {
               float a = 0.f;
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (q == (fc & 15)) a = v[q];
+              for (int e = 0; e < 16; ++e)
+                if (e == (fc & 15)) a = v[e];
               float* dst = crow_ptr + fc;
               if (beta == 0.f) *dst = sc * (float)((double)a - fd);
               else *dst = (float)((double)*dst - (double)sc * fd);
