@@ -169,8 +169,9 @@ int ftgemm_get_schedule(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k,
  *   J (I) the columns (rows) of the verification unit, c the row / column
  *   checksum as it stands, u = 2^-24 (2^-53 for ftgemm_dgemm / _zgemm),
  *   mu = 8.  The first term covers the rounding error of zero-mean data, the
- *   second the growth of the partial sums of same-sign data.  lambda <= 0
- *   keeps the current value (default 32).  Turns the learned threshold off.
+ *   second the growth of the partial sums of same-sign data.  lambda (> 0)
+ *   sets the fp32 and fp64 paths' value (default 32; <= 0 keeps it); the
+ *   tensor-core path keeps lambda = 32.  Turns the learned threshold off.
  *   Every path screens residuals in fp32 against tau / 2 and confirms the
  *   screened ones in fp64 against tau.
  * mode 1, learned (no counterpart in the paper; the tensor-core path at

@@ -483,7 +483,9 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
              ++f) {
           const Fault F = run.faults[f];
           if (F.target == T_ACC) {
-            if ((F.row >> 5) == lq && eh == 0) {  // warp-uniform: this warp owns the lane
+            // warp-uniform: the warp that owns the lane and reads this column
+            // later (so its own program order orders the write and the read)
+            if ((F.row >> 5) == lq && (F.col * Cfg::EW / 4) / BN == eh) {
               const uint32_t a = tl + (uint32_t)(F.col & ~15);
               float v[16];
               tmem_ld16(a, v);
@@ -634,24 +636,37 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           // thread (each half of the columns apart), a flagged column (the
           // same in all lanes) by a warp shuffle reduction and one
           // shared-memory add per warp
+          // The fp64 work stays inside the branches that need it: this
+          // part's fp64 rate is 1/64 of fp32, and a conversion shared by
+          // the row and the column branch would otherwise be done for every
+          // element of every row.
           const bool my_row_flagged = T.flag_r[r] != 0;
           double sr = 0.0;
           for (int ch = eh * 2 * CH2; ch < (eh + 1) * 2 * CH2; ++ch) {
             float v[16];
             tmem_ld16(tl + ch * 16, v);
             tmem_wait_ld();
+            if (my_row_flagged) {  // one lane of the warp
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int c = ch * 16 + e;
-              if (c < DN) {
-                if (my_row_flagged) sr += (double)v[e];
-                if (T.flag_c[c]) {  // warp-uniform
-                  double xs = data_row ? (double)v[e] : 0.0;
+              for (int e = 0; e < 16; ++e)
+                if (ch * 16 + e < DN) sr += (double)v[e];
+            }
+            // the flagged columns of this chunk, one at a time (warp-uniform)
+            unsigned fcols = 0u;
 #pragma unroll
-                  for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
-                  if (lane == 0) atomicAdd(&T.sum_c[c], xs);
-                }
-              }
+            for (int e = 0; e < 16; ++e)
+              if (ch * 16 + e < DN && T.flag_c[ch * 16 + e]) fcols |= 1u << e;
+            while (fcols) {
+              const int e = __ffs(fcols) - 1;
+              fcols &= fcols - 1u;
+              float ve = 0.f;
+#pragma unroll
+              for (int e2 = 0; e2 < 16; ++e2)
+                if (e2 == e) ve = v[e2];
+              double xs = data_row ? (double)ve : 0.0;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
+              if (lane == 0) atomicAdd(&T.sum_c[ch * 16 + e], xs);
             }
           }
           if (eh == 0) T.sum_r[r] = sr;
@@ -707,12 +722,13 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           }
           epi_bar<EPI_T>();
           // ----- correct the located element of C (Section 4.2.1) -----
-          // The first-half warp owning its TMEM lane rereads the accumulator:
-          // with beta == 0 the value is recomputed from acc - delta;
-          // otherwise C already holds alpha * acc + beta * C_in and
-          // alpha * delta is taken off it.
+          // The warp owning its TMEM lane and its column (the one that
+          // injected there, if anything did) rereads the accumulator: with
+          // beta == 0 the value is recomputed from acc - delta; otherwise C
+          // already holds alpha * acc + beta * C_in and alpha * delta is
+          // taken off it.
           const int fr = T.fix_row[ab];
-          if (fr >= 0 && (fr >> 5) == lq && eh == 0) {  // warp-uniform
+          if (fr >= 0 && (fr >> 5) == lq && (T.fix_col[ab] * Cfg::EW / 4) / BN == eh) {  // warp-uniform
             const int fc = T.fix_col[ab];
             const double fd = T.fix_delta[ab];
             float v[16];
