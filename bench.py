@@ -105,12 +105,12 @@ def run_case(case):
         print(json.dumps({"case": case, "detected": h.report_fetch().detected}))
         h.close()
         return 0
-    if kind == "tcgroup":  # n problems of config 5's shape distribution, bf16
-        u = synth.unit(synth.config_seed(5, 0), 3 * n)
+    if kind == "tcgroup":  # n problems of the 512-problem group's shape distribution, bf16
+        u = synth.unit(synth.workload_seed("group512", 0), 3 * n)
         shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253),
                    64 + 16 * int(u[3 * q + 2] * 125)) for q in range(n)]
         h = ft.Handle(0)
-        probs = _group_inputs(synth, "cuda", shapes, "normal", synth.config_seed(5, 100))
+        probs = _group_inputs(synth, "cuda", shapes, "normal", synth.workload_seed("group512", 100))
         g = ft.Group(h, probs, dtype=ft.BF16, level=ft.LEVELS[lvn])
         for _ in range(3):
             g.run()
@@ -262,9 +262,9 @@ def cpu_oracle_sample(n, target_s, seed_base=2):
                                                      "cadence", "split_k")}, level=oracle.BLOCK)
 
     def run(rows, cols):
-        A = synth.block("uniform", synth.config_seed(2, 0), (n, K), (0, rows), (0, K))
-        B = synth.block("uniform", synth.config_seed(2, 1), (K, n), (0, K), (0, cols))
-        Cin = synth.block("uniform", synth.config_seed(2, 2), (n, n), (0, rows), (0, cols))
+        A = synth.block("uniform", synth.workload_seed("sweep_fp32", 0), (n, K), (0, rows), (0, K))
+        B = synth.block("uniform", synth.workload_seed("sweep_fp32", 1), (K, n), (0, K), (0, cols))
+        Cin = synth.block("uniform", synth.workload_seed("sweep_fp32", 2), (n, n), (0, rows), (0, cols))
         t0 = time.perf_counter()
         oracle.gemm_ft(A, B, sched, alpha=1.0, beta=0.5, Cin=Cin)
         return time.perf_counter() - t0
@@ -303,9 +303,9 @@ def run_reference(args):
     import oracle
     import synth
     rows, cols = cal["rows"], cal["cols"]
-    A = synth.block("uniform", synth.config_seed(2, 0), (n, n), (0, rows), (0, n))
-    B = synth.block("uniform", synth.config_seed(2, 1), (n, n), (0, n), (0, cols))
-    Cin = synth.block("uniform", synth.config_seed(2, 2), (n, n), (0, rows), (0, cols))
+    A = synth.block("uniform", synth.workload_seed("sweep_fp32", 0), (n, n), (0, rows), (0, n))
+    B = synth.block("uniform", synth.workload_seed("sweep_fp32", 1), (n, n), (0, n), (0, cols))
+    Cin = synth.block("uniform", synth.workload_seed("sweep_fp32", 2), (n, n), (0, rows), (0, cols))
     sched = oracle.Schedule(**{k: SCHED[k] for k in ("m_tb", "n_tb", "k_tb", "m_w", "n_w", "m_t", "n_t",
                                                      "cadence", "split_k")}, level=oracle.BLOCK)
     for _ in range(args.warmup):
@@ -334,7 +334,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 # ---------------------------------------------------------------------------
-# side measurements (configs 4, 5 and 3)
+# side measurements (tensor-core squares, the 512-problem group, irregular fp32 shapes)
 # ---------------------------------------------------------------------------
 
 TDM, TDN = 120, 248  # tensor-core data tile of C with the checksums in the MMA tile
@@ -398,18 +398,18 @@ def _count(records, faults, key_of):
 
 
 def tensor_core_extras(ft, h, synth, dev, timed_loop):
-    """Config 4 at its largest size: bf16 and fp8 E4M3 (per-tensor amax
+    """The tensor-core square workload at its largest size, 16384^3: bf16 and fp8 E4M3 (per-tensor amax
     scale), fp32 accumulation, tile-level checksums carried through the MMA,
     16 seeded faults per GEMM; error against an fp64 product on sampled rows."""
     import torch
     n = 16384
     fl = 2.0 * n ** 3
-    Af = synth.torch_make("normal", (n, n), synth.config_seed(4, 0), dev)
-    Bf = synth.torch_make("normal", (n, n), synth.config_seed(4, 1), dev)
+    Af = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 0), dev)
+    Bf = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 1), dev)
     C = torch.empty(n, n, device=dev)
     peaks = _peaks()
     out = {"workload": f"M=N=K={n}, A,B~N(0,1), alpha=1, beta=0, TILE level (120x248 data tile)"}
-    rows = sorted({int(u * n) for u in synth.unit(synth.config_seed(4, 5), 16)})
+    rows = sorted({int(u * n) for u in synth.unit(synth.workload_seed("tc_square", 5), 16)})
     for name, dt in (("bf16", ft.BF16), ("e4m3", ft.E4M3)):
         if dt == ft.BF16:
             A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
@@ -434,7 +434,7 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
         r["overhead_pct"] = 100.0 * (r["off_tflops"] / r["tile_tflops"] - 1.0)
         h.report_fetch()
         # 16 seeded faults in one GEMM: corrected at their positions?
-        faults = _tile_faults(synth, synth.config_seed(4, 20 + dt), 16, n, n, n, 64 if dt == ft.BF16 else 128,
+        faults = _tile_faults(synth, synth.workload_seed("tc_square", 20 + dt), 16, n, n, n, 64 if dt == ft.BF16 else 128,
                               unit=1.0 / (sa * sb))
         rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=dt, inject=faults)
         found, false = _count(rep.records, faults, lambda f: (0, f[0] * TDM + f[3], f[1] * TDN + f[4]))
@@ -482,19 +482,19 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
 
 
 def grouped_extras(ft, h, synth, dev, timed_loop):
-    """Config 5: 512 bf16 problems, M, N uniform on 64..4096 and K on
+    """The grouped workload: 512 bf16 problems, M, N uniform on 64..4096 and K on
     64..2048 (multiples of 16), N(0,1); one persistent launch replayed from a
     CUDA graph; 1% of the tiles get one seeded fault."""
     import torch
     nprob = 512
-    u = synth.unit(synth.config_seed(5, 0), 3 * nprob)
+    u = synth.unit(synth.workload_seed("group512", 0), 3 * nprob)
     shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253), 64 + 16 * int(u[3 * q + 2] * 125))
               for q in range(nprob)]
     fl = sum(2.0 * M * N * K for M, N, K in shapes)
     probs = []
     for q, (M, N, K) in enumerate(shapes):
-        A = synth.torch_make("normal", (M, K), synth.config_seed(5, 100 + 2 * q), dev).to(torch.bfloat16)
-        B = synth.torch_make("normal", (K, N), synth.config_seed(5, 101 + 2 * q), dev).to(torch.bfloat16)
+        A = synth.torch_make("normal", (M, K), synth.workload_seed("group512", 100 + 2 * q), dev).to(torch.bfloat16)
+        B = synth.torch_make("normal", (K, N), synth.workload_seed("group512", 101 + 2 * q), dev).to(torch.bfloat16)
         probs.append((A, B, torch.empty(M, N, device=dev)))
     out = {"workload": f"{nprob} problems, M,N~U{{64..4096 step 16}}, K~U{{64..2048 step 16}}, bf16 N(0,1)",
            "gflop": fl / 1e9}
@@ -509,7 +509,7 @@ def grouped_extras(ft, h, synth, dev, timed_loop):
                 tm, tn = g.tiles()
                 tiles = sum(a * b for a, b in zip(tm, tn))
                 nf = max(1, tiles // 100)
-                pick = synth.unit(synth.config_seed(5, 7), nf)
+                pick = synth.unit(synth.workload_seed("group512", 7), nf)
                 by_prob = {}
                 for f in range(nf):
                     q = int(pick[f] * nprob)
@@ -517,7 +517,7 @@ def grouped_extras(ft, h, synth, dev, timed_loop):
                 for q, cnt in sorted(by_prob.items()):
                     M, N, K = shapes[q]
                     cnt = min(cnt, tm[q] * tn[q])
-                    faults += [(q,) + f for f in _tile_faults(synth, synth.config_seed(5, 1000 + q), cnt, M, N, K, 64)]
+                    faults += [(q,) + f for f in _tile_faults(synth, synth.workload_seed("group512", 1000 + q), cnt, M, N, K, 64)]
                 g.set_faults(faults)
             graph = torch.cuda.CUDAGraph()
             h.set_stream(capture)  # captured on a side stream, replayed on the main one
@@ -565,15 +565,15 @@ def _group_inputs(synth, dev, shapes, kind, seed):
 
 
 def learned_extras(ft, h, synth, dev, timed_loop):
-    """The learned threshold on config 5: trained on ~10^6 fault-free tile
+    """The learned threshold on the 512-problem group: trained on ~10^6 fault-free tile
     residuals that the method itself produces (grouped bf16 runs over input
     families from N(0,1) to U(0,1)), calibrated on held-out tiles, then
-    compared with the analytic threshold on detection (faults of config 2's
+    compared with the analytic threshold on detection (faults of the fp32 sweep's
     magnitudes) and on false alarms (coherent inputs)."""
     import numpy as np
     import torch
     nprob = 512
-    u = synth.unit(synth.config_seed(5, 0), 3 * nprob)
+    u = synth.unit(synth.workload_seed("group512", 0), 3 * nprob)
     shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253), 64 + 16 * int(u[3 * q + 2] * 125))
               for q in range(nprob)]
     kinds = ["normal"] * 4 + ["shift0.25"] * 2 + ["shift1"] * 2 + ["shift3"] * 2 + ["positive"] * 4
@@ -581,7 +581,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
     Xs, ts = [], []
     t0 = time.time()
     for r, kind in enumerate(kinds):
-        probs = _group_inputs(synth, dev, shapes, kind, synth.config_seed(5, 3000 + 2000 * r))
+        probs = _group_inputs(synth, dev, shapes, kind, synth.workload_seed("group512", 3000 + 2000 * r))
         g = ft.Group(h, probs, dtype=ft.BF16, level=ft.FT_TILE)
         tm, tn = g.tiles()
         tiles = sum(a * b for a, b in zip(tm, tn))
@@ -596,11 +596,11 @@ def learned_extras(ft, h, synth, dev, timed_loop):
         ts.append(torch.log2(torch.clamp(lam, min=2.0 ** -6)))
         g.close()
         del probs
-    # single GEMMs at config 4's K (to 16384), bf16 and e4m3, so the network
+    # single GEMMs at the tensor-core squares' K (to 16384), bf16 and e4m3, so the network
     # sees the long-K tiles and the fp8 operand type it is compared on below
     for r, kind in enumerate(["normal", "shift1", "shift3", "positive"]):
         for K in (4096, 16384):
-            Af, Bf = _family(synth, dev, kind, 2048, 2048, K, synth.config_seed(5, 9000 + 10 * r + K // 4096))
+            Af, Bf = _family(synth, dev, kind, 2048, 2048, K, synth.workload_seed("group512", 9000 + 10 * r + K // 4096))
             for dt in (ft.BF16, ft.E4M3):
                 if dt == ft.BF16:
                     A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
@@ -621,11 +621,11 @@ def learned_extras(ft, h, synth, dev, timed_loop):
     X = torch.cat(Xs)
     t = torch.cat(ts)
     n = X.shape[0]
-    order = torch.from_numpy(np.argsort(synth.unit(synth.config_seed(5, 9), n))).to(dev)
+    order = torch.from_numpy(np.argsort(synth.unit(synth.workload_seed("group512", 9), n))).to(dev)
     X, t = X[order].contiguous(), t[order].contiguous()
     n_hold = n // 10
     Xtr, ttr, Xho, tho = X[n_hold:].contiguous(), t[n_hold:].contiguous(), X[:n_hold].contiguous(), t[:n_hold].contiguous()
-    theta = torch.from_numpy((synth.normal((ft.MLP_PARAMS,), synth.config_seed(5, 11)) * 0.2).astype(np.float32)).to(dev)
+    theta = torch.from_numpy((synth.normal((ft.MLP_PARAMS,), synth.workload_seed("group512", 11)) * 0.2).astype(np.float32)).to(dev)
     t1 = time.time()
     losses = h.mlp_train(Xtr, ttr, theta, epochs=8, batch=4096, lr=3e-3)
     torch.cuda.synchronize()
@@ -669,7 +669,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
         tm, tn = g.tiles()
         tiles = sum(a * b for a, b in zip(tm, tn))
         nf = max(1, tiles // 100)
-        pick = synth.unit(synth.config_seed(5, 7), nf)
+        pick = synth.unit(synth.workload_seed("group512", 7), nf)
         by_prob = {}
         for f in range(nf):
             q = int(pick[f] * nprob)
@@ -679,26 +679,26 @@ def learned_extras(ft, h, synth, dev, timed_loop):
             M, N, K = shapes[q]
             cnt = min(cnt, tm[q] * tn[q])
             # magnitudes log-uniform in [1e-4, 1e3] x tile max: also below the analytic threshold
-            fl = _tile_faults(synth, synth.config_seed(5, 1000 + q), cnt, M, N, K, 64)
-            mags = synth.log_uniform(synth.config_seed(5, 5000 + q), cnt, 1e-4, 1e3)
+            fl = _tile_faults(synth, synth.workload_seed("group512", 1000 + q), cnt, M, N, K, 64)
+            mags = synth.log_uniform(synth.workload_seed("group512", 5000 + q), cnt, 1e-4, 1e3)
             faults += [(q, a, b, ks, r, c, float(np.sign(d) * m * 4 * math.sqrt(K))) for (a, b, ks, r, c, d), m in
                        zip(fl, mags)]
         return faults
 
     for name, mlp in (("analytic", False), ("learned", True)):
-        found, partial, false, nf = evaluate("normal", synth.config_seed(5, 7000), faults_fn, mlp)
-        _, _, false_c, _ = evaluate("positive", synth.config_seed(5, 8000), None, mlp)
-        out[name] = {"config5_faults_injected": nf, "corrected_at_position": found,
+        found, partial, false, nf = evaluate("normal", synth.workload_seed("group512", 7000), faults_fn, mlp)
+        _, _, false_c, _ = evaluate("positive", synth.workload_seed("group512", 8000), None, mlp)
+        out[name] = {"faults_injected": nf, "corrected_at_position": found,
                      "detect_rate": round(found / nf, 4), "one_side_flagged": partial, "false_alarms": false,
                      "coherent_inputs_false_alarms": false_c}
 
-    # config 4 at 16384^3, bf16 and e4m3: the same comparison on one large GEMM
+    # the 16384^3 tensor-core square, bf16 and e4m3: the same comparison on one large GEMM
     # each (64 faults on distinct tiles, |delta| log-uniform in [1e-4, 1e3] x
     # tile max), plus a fault-free run on coherent U(0,1) inputs
     n4 = 16384
     c4 = {}
     for fam in ("normal", "positive"):
-        Af, Bf = _family(synth, dev, fam, n4, n4, n4, synth.config_seed(4, 60 if fam == "normal" else 62))
+        Af, Bf = _family(synth, dev, fam, n4, n4, n4, synth.workload_seed("tc_square", 60 if fam == "normal" else 62))
         for dname, dt in (("bf16", ft.BF16), ("e4m3", ft.E4M3)):
             if dt == ft.BF16:
                 A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
@@ -708,7 +708,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
                 B, sb = h.quantize(Bf, ft.E4M3)
             h.set_fp8_scales(sa, sb)
             C = torch.empty(n4, n4, device=dev)
-            faults = (_tile_faults(synth, synth.config_seed(4, 70 + dt), 64, n4, n4, n4, 64 if dt == ft.BF16 else 128,
+            faults = (_tile_faults(synth, synth.workload_seed("tc_square", 70 + dt), 64, n4, n4, n4, 64 if dt == ft.BF16 else 128,
                                    unit=1.0 / (sa * sb), lo=1e-4) if fam == "normal" else [])
             for name, mlp in (("analytic", False), ("learned", True)):
                 if mlp:
@@ -725,7 +725,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
             torch.cuda.empty_cache()
         del Af, Bf
     h.set_fp8_scales(1.0, 1.0)
-    out["config4_16384"] = c4
+    out["square_16384"] = c4
     return out
 
 
@@ -746,9 +746,9 @@ def _family(synth, dev, kind, M, N, K, seed):
 
 def learned_fp32_extras(ft, h, synth, dev, timed_loop):
     """The learned threshold on the fp32 path at block level (the 128 x 128 x
-    32 tile): trained on fault-free tile residuals of config 3's shapes over
+    32 tile): trained on fault-free tile residuals of the irregular fp32 shapes over
     input families from N(0,1) to U(0,1), calibrated on held-out tiles, then
-    compared with the analytic threshold on config 3's shapes: faults of
+    compared with the analytic threshold on the irregular fp32 shapes: faults of
     |delta| log-uniform in [1e-4, 1e3] x tile max on N(0,1) inputs, and
     false alarms on fault-free U(0,1) inputs."""
     import numpy as np
@@ -763,7 +763,7 @@ def learned_fp32_extras(ft, h, synth, dev, timed_loop):
     for rep_i in range(reps):
         for r, kind in enumerate(kinds):
             for q, (M, N, K) in enumerate(shapes):
-                A, B = _family(synth, dev, kind, M, N, K, synth.config_seed(3, 1000 + 100 * rep_i + 10 * r + q))
+                A, B = _family(synth, dev, kind, M, N, K, synth.workload_seed("irregular_fp32", 1000 + 100 * rep_i + 10 * r + q))
                 tiles = -(-M // 128) * -(-N // 128)
                 lam = torch.zeros(tiles, device=dev)
                 feat = torch.zeros(tiles * 5, device=dev)
@@ -780,11 +780,11 @@ def learned_fp32_extras(ft, h, synth, dev, timed_loop):
     X = torch.cat(Xs)
     t = torch.cat(ts)
     n = X.shape[0]
-    order = torch.from_numpy(np.argsort(synth.unit(synth.config_seed(3, 9), n))).to(dev)
+    order = torch.from_numpy(np.argsort(synth.unit(synth.workload_seed("irregular_fp32", 9), n))).to(dev)
     X, t = X[order].contiguous(), t[order].contiguous()
     n_hold = n // 10
     Xtr, ttr, Xho, tho = X[n_hold:].contiguous(), t[n_hold:].contiguous(), X[:n_hold].contiguous(), t[:n_hold].contiguous()
-    theta = torch.from_numpy((synth.normal((ft.MLP_PARAMS,), synth.config_seed(3, 11)) * 0.2).astype(np.float32)).to(dev)
+    theta = torch.from_numpy((synth.normal((ft.MLP_PARAMS,), synth.workload_seed("irregular_fp32", 11)) * 0.2).astype(np.float32)).to(dev)
     t1 = time.time()
     losses = h.mlp_train(Xtr, ttr, theta, epochs=8, batch=4096, lr=3e-3)
     torch.cuda.synchronize()
@@ -797,14 +797,14 @@ def learned_fp32_extras(ft, h, synth, dev, timed_loop):
     ev = {"analytic": {"faults": 0, "corrected_at_position": 0, "other_records": 0, "coherent_false_alarms": 0},
           "learned": {"faults": 0, "corrected_at_position": 0, "other_records": 0, "coherent_false_alarms": 0}}
     for q, (M, N, K) in enumerate(shapes):
-        A, B = _family(synth, dev, "normal", M, N, K, synth.config_seed(3, 5000 + q))
-        Ap, Bp = _family(synth, dev, "positive", M, N, K, synth.config_seed(3, 5100 + q))
+        A, B = _family(synth, dev, "normal", M, N, K, synth.workload_seed("irregular_fp32", 5000 + q))
+        Ap, Bp = _family(synth, dev, "positive", M, N, K, synth.workload_seed("irregular_fp32", 5100 + q))
         C = torch.empty(M, N, device=dev)
         tm, tn, nks = -(-M // 128), -(-N // 128), -(-K // 32)
         cnt = min(64, tm * tn)
-        pos = synth.fault_positions(synth.config_seed(3, 5200 + q), cnt, tm, tn, nks, 128, 128, M, N, 8)
-        mags = synth.log_uniform(synth.config_seed(3, 5300 + q), cnt, 1e-4, 1e3)
-        sign = synth.unit(synth.config_seed(3, 5400 + q), cnt)
+        pos = synth.fault_positions(synth.workload_seed("irregular_fp32", 5200 + q), cnt, tm, tn, nks, 128, 128, M, N, 8)
+        mags = synth.log_uniform(synth.workload_seed("irregular_fp32", 5300 + q), cnt, 1e-4, 1e3)
+        sign = synth.unit(synth.workload_seed("irregular_fp32", 5400 + q), cnt)
         faults = [(a, b, ks, r, c, float((1 if sg < 0.5 else -1) * g * 4 * math.sqrt(K)))
                   for (a, b, ks, r, c), g, sg in zip(pos, mags, sign)]
         for name, mlp in (("analytic", False), ("learned", True)):
@@ -834,7 +834,7 @@ def nonfused_extras(ft, h, synth, dev, timed_loop):
     """The paper's headline comparison (Section 5.3): the fused block-level
     ABFT GEMM against the non-fused scheme (rank-256 updates, separate
     checksum GEMMs and verification kernels), both with the same faults, one
-    per step of K_s = 256 of K, on config 2's inputs."""
+    per step of K_s = 256 of K, on the fp32 sweep's U(-1,1) inputs."""
     import ctypes as C
     import torch
     L = ft.lib()
@@ -845,14 +845,14 @@ def nonfused_extras(ft, h, synth, dev, timed_loop):
     out = {"ks": 256, "faults": "one per K_s step at seeded tiles, |delta| log-uniform [1e-2, 1e3] x tile max"}
     h.set_schedule(SCHED16)  # the non-fused scheme's tiling (k-steps of 16)
     for n in (4096, 8192, 16384):
-        A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 20), dev)
-        B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 21), dev)
+        A = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 20), dev)
+        B = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 21), dev)
         Cm = torch.empty(n, n, device=dev)
         tiles = -(-n // 128)
         ksteps = n // 16
         nf = n // 256
-        pos = synth.fault_positions(synth.config_seed(2, 30), nf, tiles, tiles, ksteps, 128, 128, n, n, 16)
-        mags = synth.log_uniform(synth.config_seed(2, 31), nf, 1e-2, 1e3)
+        pos = synth.fault_positions(synth.workload_seed("sweep_fp32", 30), nf, tiles, tiles, ksteps, 128, 128, n, n, 16)
+        mags = synth.log_uniform(synth.workload_seed("sweep_fp32", 31), nf, 1e-2, 1e3)
         faults = [(tm, tn, 16 * (q % (ksteps // 16)) + (ks % 16), r, c, float(g * 4 * math.sqrt(n / 9)))
                   for q, ((tm, tn, ks, r, c), g) in enumerate(zip(pos, mags))]
         spec = ft.make_inject(faults)
@@ -905,8 +905,8 @@ def offline_extras(ft, h, synth, dev, timed_loop):
 
     det = {}
     for n in (4096, 8192, 16384):
-        A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 42), dev)
-        B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 43), dev)
+        A = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 42), dev)
+        B = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 43), dev)
         Cm = torch.empty(n, n, device=dev)
         h.set_schedule(SCHED)
         reps = 3 if n == 16384 else 6
@@ -925,13 +925,13 @@ def offline_extras(ft, h, synth, dev, timed_loop):
         tiles_1d = -(-n // 128)
         tiles = tiles_1d * tiles_1d
         gamma = 1 - (1 - gamma0) ** tiles
-        A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 40), dev)
-        B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 41), dev)
+        A = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 40), dev)
+        B = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 41), dev)
         Cm = torch.empty(n, n, device=dev)
         delta = 64 * 4 * math.sqrt(n / 9)
 
         def draw(trial, attempt):
-            u = synth.unit(synth.config_seed(2, 100000 + 1000 * n + 64 * trial + attempt), 4 * tiles)
+            u = synth.unit(synth.workload_seed("sweep_fp32", 100000 + 1000 * n + 64 * trial + attempt), 4 * tiles)
             fl = []
             for t in range(tiles):
                 if u[t] < gamma0:
@@ -976,8 +976,8 @@ def small_shapes_extras(ft, h, synth, dev, timed_loop):
     for K in (256, 1024):
         for M in sizes:
             for N in sizes:
-                A = synth.torch_make("uniform", (M, K), synth.config_seed(2, 60), dev)
-                B = synth.torch_make("uniform", (K, N), synth.config_seed(2, 61), dev)
+                A = synth.torch_make("uniform", (M, K), synth.workload_seed("sweep_fp32", 60), dev)
+                B = synth.torch_make("uniform", (K, N), synth.workload_seed("sweep_fp32", 61), dev)
                 Cm = torch.empty(M, N, device=dev)
                 h.autotune(A, B, Cm, level=ft.FT_OFF, reps=3)
                 ms = timed_loop(lambda i: h.gemm(A, B, Cm, level=ft.FT_OFF, report=False), 20, warm=3)
@@ -1004,18 +1004,18 @@ def fp64_extras(ft, h, synth, dev, timed_loop):
     out = {"fp64_nominal_tflops": fp64_nominal}
     for kind, n, tile, flop_per in (("dgemm", 4096, ft.DGEMM_TILE, 2.0), ("zgemm", 2048, ft.ZGEMM_TILE, 8.0)):
         if kind == "dgemm":
-            A = synth.torch_make("normal", (n, n), synth.config_seed(6, 0), dev, torch.float64)
-            B = synth.torch_make("normal", (n, n), synth.config_seed(6, 1), dev, torch.float64)
+            A = synth.torch_make("normal", (n, n), synth.workload_seed("dgemm", 0), dev, torch.float64)
+            B = synth.torch_make("normal", (n, n), synth.workload_seed("dgemm", 1), dev, torch.float64)
             call = h.dgemm
         else:
-            A = torch.complex(synth.torch_make("normal", (n, n), synth.config_seed(7, 0), dev, torch.float64),
-                              synth.torch_make("normal", (n, n), synth.config_seed(7, 1), dev, torch.float64))
-            B = torch.complex(synth.torch_make("normal", (n, n), synth.config_seed(7, 2), dev, torch.float64),
-                              synth.torch_make("normal", (n, n), synth.config_seed(7, 3), dev, torch.float64))
+            A = torch.complex(synth.torch_make("normal", (n, n), synth.workload_seed("zgemm", 0), dev, torch.float64),
+                              synth.torch_make("normal", (n, n), synth.workload_seed("zgemm", 1), dev, torch.float64))
+            B = torch.complex(synth.torch_make("normal", (n, n), synth.workload_seed("zgemm", 2), dev, torch.float64),
+                              synth.torch_make("normal", (n, n), synth.workload_seed("zgemm", 3), dev, torch.float64))
             call = h.zgemm
         Cm = torch.empty_like(A)
         tiles, ks = n // tile, n // ft.F64_KSTEP
-        pos = synth.fault_positions(synth.config_seed(6 if kind == "dgemm" else 7, 9), 4, tiles, tiles, ks,
+        pos = synth.fault_positions(synth.workload_seed(kind, 9), 4, tiles, tiles, ks,
                                     tile, tile, n, n, 16)
         faults = [(a, b, k, r, c, 1e-8 * math.sqrt(n)) for (a, b, k, r, c) in pos]
         ms_off = timed_loop(lambda i: call(A, B, Cm, level=ft.FT_OFF, report=False), 3, warm=1)
@@ -1038,15 +1038,15 @@ def fp64_extras(ft, h, synth, dev, timed_loop):
 
 
 def irregular_extras(ft, h, synth, dev, timed_loop):
-    """Config 3: irregular fp32 shapes, N(0,1), schedule and checksum level
+    """Irregular fp32 shapes, N(0,1), schedule and checksum level
     picked per shape by the autotuner, one seeded fault per GEMM."""
     import torch
     h.set_schedule(None)
     out = {}
     for q, (M, N, K) in enumerate([(16384, 16384, 32), (20480, 256, 20480), (256, 256, 65536), (4096, 96, 4096),
                                    (777, 1531, 2049)]):
-        A = synth.torch_make("normal", (M, K), synth.config_seed(3, 2 * q), dev)
-        B = synth.torch_make("normal", (K, N), synth.config_seed(3, 2 * q + 1), dev)
+        A = synth.torch_make("normal", (M, K), synth.workload_seed("irregular_fp32", 2 * q), dev)
+        B = synth.torch_make("normal", (K, N), synth.workload_seed("irregular_fp32", 2 * q + 1), dev)
         C = torch.empty(M, N, device=dev)
         s, lv = h.autotune(A, B, C, level=ft.FT_AUTO, reps=2)
         fl = 2.0 * M * N * K
@@ -1055,7 +1055,7 @@ def irregular_extras(ft, h, synth, dev, timed_loop):
         ct = torch.empty_like(C)
         ms_t = timed_loop(lambda i: torch.matmul(A, B, out=ct), 5, warm=1)
         tiles_m, tiles_n = -(-M // s.m_tb), -(-N // s.n_tb)
-        (a, b, ks, r, c), = synth.fault_positions(synth.config_seed(3, 50 + q), 1, tiles_m, tiles_n,
+        (a, b, ks, r, c), = synth.fault_positions(synth.workload_seed("irregular_fp32", 50 + q), 1, tiles_m, tiles_n,
                                                   -(-K // s.k_tb), s.m_tb, s.n_tb, M, N, max(1, s.cadence))
         rep = h.gemm(A, B, C, level=ft.FT_AUTO, inject=[(a, b, ks, r, c, 64.0 * math.sqrt(K))])
         ok = [(x["row"], x["col"], x["kind"]) for x in rep.records] == [(a * s.m_tb + r, b * s.n_tb + c, 0)]
@@ -1118,9 +1118,9 @@ def main():
     sms = props.multi_processor_count
 
     # inputs: each rank its own problem (a different batch element)
-    A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 0) + 1000 * rank, dev)
-    B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 1) + 1000 * rank, dev)
-    C0 = synth.torch_make("uniform", (n, n), synth.config_seed(2, 2) + 1000 * rank, dev)
+    A = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 0) + 1000 * rank, dev)
+    B = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 1) + 1000 * rank, dev)
+    C0 = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 2) + 1000 * rank, dev)
     C = C0.clone()
     torch.cuda.synchronize()
 
@@ -1153,7 +1153,7 @@ def main():
     t_est = timed_loop(lambda i: step(level), 1) / 1e3
     h.report_fetch()
 
-    faults = [make_faults(synth.config_seed(2, 10) + 7919 * (s + 1) + 1000 * rank, t_est, n, ksteps)
+    faults = [make_faults(synth.workload_seed("sweep_fp32", 10) + 7919 * (s + 1) + 1000 * rank, t_est, n, ksteps)
               for s in range(args.steps)]
     injected = sum(len(f) for f in faults)
 
@@ -1353,7 +1353,7 @@ def main():
            "host_link": link, "clocks": e2e_clk}
     del bufs
 
-    # ---- configs 4, 5, 3: tensor cores, grouped, irregular (side lines) ----
+    # ---- tensor cores, grouped, irregular fp32 shapes (side lines) ----
     side = {}
     if not args.no_extras and rank == 0:
         for name, fn in (("tensor_core", tensor_core_extras), ("grouped", grouped_extras),

@@ -26,9 +26,21 @@ _M2 = np.uint64(0x94D049BB133111EB)
 BASE_SEED = 2305_01024
 
 
-def config_seed(config: int, index: int) -> int:
-    """Seed of input ``index`` of workload ``config`` (seed = 230501024 + 100*config + index)."""
-    return BASE_SEED + 100 * config + index
+# Each workload draws its inputs from its own block of 100 streams.
+WORKLOADS = {
+    "int256": 1,          # 256^3 integer-valued fp32, block level, 4 faults of 2^10
+    "sweep_fp32": 2,      # square fp32 sweep 1024..16384, U(-1,1), beta = 0.5
+    "irregular_fp32": 3,  # five irregular fp32 shapes, N(0,1)
+    "tc_square": 4,       # bf16 / e4m3 squares 4096..16384, N(0,1)
+    "group512": 5,        # 512 bf16 problems, M, N on 64..4096, K on 64..2048
+    "dgemm": 6,           # fp64 DGEMM, N(0,1)
+    "zgemm": 7,           # complex fp64 ZGEMM, N(0,1)
+}
+
+
+def workload_seed(workload: str, index: int) -> int:
+    """Seed of input ``index`` of a named workload (seed = 230501024 + 100*block + index)."""
+    return BASE_SEED + 100 * WORKLOADS[workload] + index
 
 
 def _mix(z: np.ndarray) -> np.ndarray:

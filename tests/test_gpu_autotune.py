@@ -30,8 +30,8 @@ def test_autotuned_irregular_shape_one_fault(ft, orc, shape):
     M, N, K = shape
     q = SHAPES.index(shape)
     h = ft.Handle(0)
-    A = synth.torch_make("normal", (M, K), synth.config_seed(3, 2 * q), "cuda")
-    B = synth.torch_make("normal", (K, N), synth.config_seed(3, 2 * q + 1), "cuda")
+    A = synth.torch_make("normal", (M, K), synth.workload_seed("irregular_fp32", 2 * q), "cuda")
+    B = synth.torch_make("normal", (K, N), synth.workload_seed("irregular_fp32", 2 * q + 1), "cuda")
     C = torch.empty(M, N, device="cuda")
     s, lv = h.autotune(A, B, C, level=ft.FT_AUTO, reps=2)
     assert lv in (ft.FT_THREAD, ft.FT_WARP, ft.FT_BLOCK)
@@ -42,7 +42,7 @@ def test_autotuned_irregular_shape_one_fault(ft, orc, shape):
     # one seeded fault on the tuned tiling
     tiles_m, tiles_n = -(-M // s.m_tb), -(-N // s.n_tb)
     ksteps = -(-K // s.k_tb)
-    (tm, tn, ks, r, c), = synth.fault_positions(synth.config_seed(3, 50 + q), 1, tiles_m, tiles_n, ksteps,
+    (tm, tn, ks, r, c), = synth.fault_positions(synth.workload_seed("irregular_fp32", 50 + q), 1, tiles_m, tiles_n, ksteps,
                                                 s.m_tb, s.n_tb, M, N, max(1, s.cadence))
     delta = 64.0 * np.sqrt(K)
     C.zero_()
@@ -50,7 +50,7 @@ def test_autotuned_irregular_shape_one_fault(ft, orc, shape):
     torch.cuda.synchronize()
     i, j = tm * s.m_tb + r, tn * s.n_tb + c
     assert [(x["row"], x["col"], x["kind"]) for x in rep.records] == [(i, j, 0)]
-    sample = [int(u * M) for u in synth.unit(synth.config_seed(3, 60 + q), 32)]
+    sample = [int(u * M) for u in synth.unit(synth.workload_seed("irregular_fp32", 60 + q), 32)]
     rows = sorted(set([i] + sample) | set(range(min(M, 8))))
     Ar = A[rows].cpu().numpy()
     Bh = B.cpu().numpy()

@@ -133,17 +133,17 @@ def test_dgemm_full_size_sampled_rows(ft, orc):
     every fault located and corrected, sampled rows against the oracle."""
     import torch
     n = 4096
-    A = synth.torch_make("normal", (n, n), synth.config_seed(6, 0), "cuda", torch.float64)
-    B = synth.torch_make("normal", (n, n), synth.config_seed(6, 1), "cuda", torch.float64)
+    A = synth.torch_make("normal", (n, n), synth.workload_seed("dgemm", 0), "cuda", torch.float64)
+    B = synth.torch_make("normal", (n, n), synth.workload_seed("dgemm", 1), "cuda", torch.float64)
     tiles, ks = n // 128, n // 8
-    pos = synth.fault_positions(synth.config_seed(6, 2), 8, tiles, tiles, ks, 128, 128, n, n, 16)
+    pos = synth.fault_positions(synth.workload_seed("dgemm", 2), 8, tiles, tiles, ks, 128, 128, n, n, 16)
     faults = [(a, b, k, r, c, _f32(1e-8 * math.sqrt(n))) for (a, b, k, r, c) in pos]
     h = ft.Handle(0)
     C_ = torch.empty(n, n, dtype=torch.float64, device="cuda")
     rep = h.dgemm(A, B, C_, cadence=16, inject=faults)
     where = [(a * 128 + r, b * 128 + c) for (a, b, k, r, c, d) in faults]
     assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
-    rows = sorted(set(int(u * n) for u in synth.unit(synth.config_seed(6, 3), 8)) | {i for i, _ in where})
+    rows = sorted(set(int(u * n) for u in synth.unit(synth.workload_seed("dgemm", 3), 8)) | {i for i, _ in where})
     Ar, Bh = A[rows].cpu().numpy(), B.cpu().numpy()
     ref = orc.gemm_ref(Ar, Bh)
     got = C_[rows].cpu().numpy()

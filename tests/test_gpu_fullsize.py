@@ -2,12 +2,12 @@
 times, on outputs the oracle computes one by one: sampled rows of C (every
 row holding a fault among them), and every fault located and corrected.
 
-* config 2: 16384^3 fp32, block-level checksums on the 128 x 128 tile with
+* the fp32 headline: 16384^3 fp32, block-level checksums on the 128 x 128 tile with
   16 x 8 fragments and k-steps of 32, verification every 256 of K, alpha 1,
   beta 0.5;
-* config 4: 16384^3 bf16 and e4m3, tile-level checksums through the tensor
+* the tensor-core square: 16384^3 bf16 and e4m3, tile-level checksums through the tensor
   cores (e4m3: the quantizer against the oracle's on sampled rows);
-* config 5: the 512-problem bf16 group, one persistent launch, 1% of tiles
+* the 512-problem bf16 group, one persistent launch, 1% of tiles
   faulted; sampled problems compared in full.
 """
 import math
@@ -54,16 +54,16 @@ def _rows(seed, M, extra):
     return sorted(set(int(u * M) for u in synth.unit(seed, 12)) | set(extra))
 
 
-def test_config2_full_size_sampled_rows(ft, orc):
+def test_fp32_block_16384_sampled_rows(ft, orc):
     import torch
     n = 16384
     sched = dict(m_tb=128, n_tb=128, k_tb=32, m_w=64, n_w=64, m_t=16, n_t=8, cadence=8, split_k=1)
-    A = synth.torch_make("uniform", (n, n), synth.config_seed(2, 0), "cuda")
-    B = synth.torch_make("uniform", (n, n), synth.config_seed(2, 1), "cuda")
-    C0 = synth.torch_make("uniform", (n, n), synth.config_seed(2, 2), "cuda")
+    A = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 0), "cuda")
+    B = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 1), "cuda")
+    C0 = synth.torch_make("uniform", (n, n), synth.workload_seed("sweep_fp32", 2), "cuda")
     tiles, ksteps = n // 128, n // 32
-    pos = synth.fault_positions(synth.config_seed(2, 70), 6, tiles, tiles, ksteps, 128, 128, n, n, 8)
-    mags = synth.log_uniform(synth.config_seed(2, 71), 6, 1e-1, 1e3)
+    pos = synth.fault_positions(synth.workload_seed("sweep_fp32", 70), 6, tiles, tiles, ksteps, 128, 128, n, n, 8)
+    mags = synth.log_uniform(synth.workload_seed("sweep_fp32", 71), 6, 1e-1, 1e3)
     faults = [(tm, tn, ks, r, c, float(g * 4 * math.sqrt(n / 9))) for (tm, tn, ks, r, c), g in zip(pos, mags)]
     h = ft.Handle(0)
     h.set_schedule(sched)
@@ -72,7 +72,7 @@ def test_config2_full_size_sampled_rows(ft, orc):
     torch.cuda.synchronize()
     where = [(tm * 128 + r, tn * 128 + c) for (tm, tn, ks, r, c, d) in faults]
     assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
-    rows = _rows(synth.config_seed(2, 72), n, [i for i, _ in where])
+    rows = _rows(synth.workload_seed("sweep_fp32", 72), n, [i for i, _ in where])
     Ar, Bh, Cr = A[rows].cpu().numpy(), B.cpu().numpy(), C0[rows].cpu().numpy()
     ref = orc.gemm_ref(Ar, Bh, 1.0, 0.5, Cr)
     got = C[rows].cpu().numpy().astype(np.float64)
@@ -85,15 +85,15 @@ def test_config2_full_size_sampled_rows(ft, orc):
     h.close()
 
 
-def test_config4_full_size_bf16_sampled_rows(ft, orc):
+def test_tc_bf16_16384_sampled_rows(ft, orc):
     import torch
     n = 16384
-    Af = synth.torch_make("normal", (n, n), synth.config_seed(4, 0), "cuda")
-    Bf = synth.torch_make("normal", (n, n), synth.config_seed(4, 1), "cuda")
+    Af = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 0), "cuda")
+    Bf = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 1), "cuda")
     A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
     del Af, Bf
     tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 64
-    pos = synth.fault_positions(synth.config_seed(4, 80), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 80), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
     faults = [(a, b, ks, r, c, float(64 * math.sqrt(n))) for (a, b, ks, r, c) in pos]
     h = ft.Handle(0)
     C = torch.empty(n, n, device="cuda")
@@ -101,7 +101,7 @@ def test_config4_full_size_bf16_sampled_rows(ft, orc):
     torch.cuda.synchronize()
     where = [(a * 120 + r, b * 248 + c) for (a, b, ks, r, c, d) in faults]
     assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
-    rows = _rows(synth.config_seed(4, 81), n, [i for i, _ in where])
+    rows = _rows(synth.workload_seed("tc_square", 81), n, [i for i, _ in where])
     Ar = A[rows].float().cpu().numpy()
     Bh = B.float().cpu().numpy()
     ref = orc.gemm_ref(Ar, Bh)
@@ -115,23 +115,23 @@ def test_config4_full_size_bf16_sampled_rows(ft, orc):
     h.close()
 
 
-def test_config5_full_group_sampled_problems(ft, orc):
+def test_group_512_sampled_problems(ft, orc):
     import torch
     nprob = 512
-    u = synth.unit(synth.config_seed(5, 0), 3 * nprob)
+    u = synth.unit(synth.workload_seed("group512", 0), 3 * nprob)
     shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253), 64 + 16 * int(u[3 * q + 2] * 125))
               for q in range(nprob)]
     probs = []
     for q, (M, N, K) in enumerate(shapes):
-        A = synth.torch_make("normal", (M, K), synth.config_seed(5, 100 + 2 * q), "cuda").to(torch.bfloat16)
-        B = synth.torch_make("normal", (K, N), synth.config_seed(5, 101 + 2 * q), "cuda").to(torch.bfloat16)
+        A = synth.torch_make("normal", (M, K), synth.workload_seed("group512", 100 + 2 * q), "cuda").to(torch.bfloat16)
+        B = synth.torch_make("normal", (K, N), synth.workload_seed("group512", 101 + 2 * q), "cuda").to(torch.bfloat16)
         probs.append((A, B, torch.empty(M, N, device="cuda")))
     h = ft.Handle(0)
     g = ft.Group(h, probs, dtype=ft.BF16, level=ft.FT_TILE)
     tm, tn = g.tiles()
     tiles = sum(a * b for a, b in zip(tm, tn))
     nf = tiles // 100
-    pick = synth.unit(synth.config_seed(5, 7), nf)
+    pick = synth.unit(synth.workload_seed("group512", 7), nf)
     by_prob = {}
     for f in range(nf):
         q = int(pick[f] * nprob)
@@ -140,7 +140,7 @@ def test_config5_full_group_sampled_problems(ft, orc):
     for q, cnt in sorted(by_prob.items()):
         M, N, K = shapes[q]
         cnt = min(cnt, tm[q] * tn[q])
-        for (a, b, ks, r, c) in synth.fault_positions(synth.config_seed(5, 1000 + q), cnt, tm[q], tn[q],
+        for (a, b, ks, r, c) in synth.fault_positions(synth.workload_seed("group512", 1000 + q), cnt, tm[q], tn[q],
                                                       -(-K // 64), 120, 248, M, N, -(-K // 64)):
             faults.append((q, a, b, ks, r, c, float(64 * math.sqrt(K))))
     g.set_faults(faults)
@@ -150,7 +150,7 @@ def test_config5_full_group_sampled_problems(ft, orc):
     want = sorted((f[0], f[1] * 120 + f[4], f[2] * 248 + f[5], 0) for f in faults)
     assert sorted((x["problem"], x["row"], x["col"], x["kind"]) for x in rep.records) == want
     # sampled problems in full, and every faulted problem among them
-    sample = sorted(set(int(x * nprob) for x in synth.unit(synth.config_seed(5, 8), 6)) | {faults[0][0]})
+    sample = sorted(set(int(x * nprob) for x in synth.unit(synth.workload_seed("group512", 8), 6)) | {faults[0][0]})
     for q in sample:
         A, B, Cq = probs[q]
         Ah, Bh = A.float().cpu().numpy(), B.float().cpu().numpy()
@@ -168,8 +168,8 @@ def test_config5_full_group_sampled_problems(ft, orc):
     h.close()
 
 
-def test_config4_full_size_e4m3_sampled_rows(ft, orc):
-    """Config 4 in fp8: 16384^3 N(0,1) quantized to E4M3 with per-tensor
+def test_tc_e4m3_16384_sampled_rows(ft, orc):
+    """The tensor-core square in fp8: 16384^3 N(0,1) quantized to E4M3 with per-tensor
     scales, checksums through the MMA, 16 faults.  The quantizer matches the
     oracle's on sampled rows (the sample carries the tensor's largest
     element, so the per-tensor scale is the same); every fault is located
@@ -178,11 +178,11 @@ def test_config4_full_size_e4m3_sampled_rows(ft, orc):
     import torch
     n = 16384
     tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 128
-    pos = synth.fault_positions(synth.config_seed(4, 23), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 23), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
     where = [(a * 120 + r, b * 248 + c) for (a, b, ks, r, c) in pos]
-    rows = _rows(synth.config_seed(4, 22), n, [i for i, _ in where])
-    Af = synth.torch_make("normal", (n, n), synth.config_seed(4, 20), "cuda")
-    Bf = synth.torch_make("normal", (n, n), synth.config_seed(4, 21), "cuda")
+    rows = _rows(synth.workload_seed("tc_square", 22), n, [i for i, _ in where])
+    Af = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 20), "cuda")
+    Bf = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 21), "cuda")
     h = ft.Handle(0)
     A8, sa = h.quantize(Af, ft.E4M3)
     B8, sb = h.quantize(Bf, ft.E4M3)

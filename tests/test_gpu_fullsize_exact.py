@@ -102,11 +102,11 @@ def test_headline_fp32_block_16384_integers_bit_exact(ft, orc):
     import torch
     n = N_FULL
     sched = dict(m_tb=128, n_tb=128, k_tb=32, m_w=64, n_w=64, m_t=16, n_t=8, cadence=8, split_k=1)
-    A = synth.torch_make("int", (n, n), synth.config_seed(2, 40), "cuda")
-    B = synth.torch_make("int", (n, n), synth.config_seed(2, 41), "cuda")
+    A = synth.torch_make("int", (n, n), synth.workload_seed("sweep_fp32", 40), "cuda")
+    B = synth.torch_make("int", (n, n), synth.workload_seed("sweep_fp32", 41), "cuda")
     tiles, ksteps = n // 128, n // 32
-    pos = synth.fault_positions(synth.config_seed(2, 42), 16, tiles, tiles, ksteps, 128, 128, n, n, 8)
-    faults = [p + (d,) for p, d in zip(pos, _offsets(synth.config_seed(2, 43), 16))]
+    pos = synth.fault_positions(synth.workload_seed("sweep_fp32", 42), 16, tiles, tiles, ksteps, 128, 128, n, n, 8)
+    faults = [p + (d,) for p, d in zip(pos, _offsets(synth.workload_seed("sweep_fp32", 43), 16))]
     h = ft.Handle(0)
     h.set_schedule(sched)
     C = torch.full((n, n), float("nan"), device="cuda")
@@ -114,7 +114,7 @@ def test_headline_fp32_block_16384_integers_bit_exact(ft, orc):
     torch.cuda.synchronize()
     _check_records(rep, faults, 128, 128, lambda ks: (ks // 8) * 8 + 7)
     A8, B8 = _int8_host(A), _int8_host(B)
-    rows = _sample_rows(synth.config_seed(2, 44), n, [f[0] * 128 + f[3] for f in faults])
+    rows = _sample_rows(synth.workload_seed("sweep_fp32", 44), n, [f[0] * 128 + f[3] for f in faults])
     assert len(rows) >= 16
     _check_rows(orc, C, A8.astype(np.float32), B8.astype(np.float32), rows)
     _check_line_sums(C, A8, B8)
@@ -126,18 +126,18 @@ def test_tile_bf16_16384_integers_bit_exact(ft, orc):
     of 120 x 248, checksums carried through the MMA), integer operands."""
     import torch
     n = N_FULL
-    A = synth.torch_make("int", (n, n), synth.config_seed(4, 40), "cuda").to(torch.bfloat16)
-    B = synth.torch_make("int", (n, n), synth.config_seed(4, 41), "cuda").to(torch.bfloat16)
+    A = synth.torch_make("int", (n, n), synth.workload_seed("tc_square", 40), "cuda").to(torch.bfloat16)
+    B = synth.torch_make("int", (n, n), synth.workload_seed("tc_square", 41), "cuda").to(torch.bfloat16)
     tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 64
-    pos = synth.fault_positions(synth.config_seed(4, 42), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
-    faults = [p + (d,) for p, d in zip(pos, _offsets(synth.config_seed(4, 43), 16))]
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 42), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    faults = [p + (d,) for p, d in zip(pos, _offsets(synth.workload_seed("tc_square", 43), 16))]
     h = ft.Handle(0)
     C = torch.full((n, n), float("nan"), device="cuda")
     rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=ft.BF16, inject=faults)
     torch.cuda.synchronize()
     _check_records(rep, faults, 120, 248, lambda ks: nks - 1)
     A8, B8 = _int8_host(A), _int8_host(B)
-    rows = _sample_rows(synth.config_seed(4, 44), n, [f[0] * 120 + f[3] for f in faults])
+    rows = _sample_rows(synth.workload_seed("tc_square", 44), n, [f[0] * 120 + f[3] for f in faults])
     assert len(rows) >= 16
     _check_rows(orc, C, A8.astype(np.float32), B8.astype(np.float32), rows)
     _check_line_sums(C, A8, B8)
@@ -145,27 +145,27 @@ def test_tile_bf16_16384_integers_bit_exact(ft, orc):
 
 
 def test_group_512_bf16_integers_bit_exact(ft, orc):
-    """Config 5's 512 problems (M, N on 64..4096, K on 64..2048, steps of 16)
+    """The grouped workload's 512 problems (M, N on 64..4096, K on 64..2048, steps of 16)
     in one persistent grouped launch, integer operands in bf16, 1% of the
     tiles faulted: every problem's row and column sums exact, the record set
     exact, sampled problems (every faulted one of the first few among them)
     exact element by element."""
     import torch
     nprob = 512
-    u = synth.unit(synth.config_seed(5, 0), 3 * nprob)
+    u = synth.unit(synth.workload_seed("group512", 0), 3 * nprob)
     shapes = [(64 + 16 * int(u[3 * q] * 253), 64 + 16 * int(u[3 * q + 1] * 253), 64 + 16 * int(u[3 * q + 2] * 125))
               for q in range(nprob)]
     probs = []
     for q, (M, N, K) in enumerate(shapes):
-        A = synth.torch_make("int", (M, K), synth.config_seed(5, 300 + 2 * q), "cuda").to(torch.bfloat16)
-        B = synth.torch_make("int", (K, N), synth.config_seed(5, 301 + 2 * q), "cuda").to(torch.bfloat16)
+        A = synth.torch_make("int", (M, K), synth.workload_seed("group512", 300 + 2 * q), "cuda").to(torch.bfloat16)
+        B = synth.torch_make("int", (K, N), synth.workload_seed("group512", 301 + 2 * q), "cuda").to(torch.bfloat16)
         probs.append((A, B, torch.full((M, N), float("nan"), device="cuda")))
     h = ft.Handle(0)
     g = ft.Group(h, probs, dtype=ft.BF16, level=ft.FT_TILE)
     tm, tn = g.tiles()
     tiles = sum(a * b for a, b in zip(tm, tn))
     nf = tiles // 100
-    pick = synth.unit(synth.config_seed(5, 47), nf)
+    pick = synth.unit(synth.workload_seed("group512", 47), nf)
     by_prob = {}
     for f in range(nf):
         q = int(pick[f] * nprob)
@@ -175,8 +175,8 @@ def test_group_512_bf16_integers_bit_exact(ft, orc):
         M, N, K = shapes[q]
         cnt = min(cnt, tm[q] * tn[q])
         nkb = -(-K // 64)
-        sites = synth.fault_positions(synth.config_seed(5, 2000 + q), cnt, tm[q], tn[q], nkb, 120, 248, M, N, nkb)
-        for (a, b, ks, r, c), d in zip(sites, _offsets(synth.config_seed(5, 3000 + q), cnt)):
+        sites = synth.fault_positions(synth.workload_seed("group512", 2000 + q), cnt, tm[q], tn[q], nkb, 120, 248, M, N, nkb)
+        for (a, b, ks, r, c), d in zip(sites, _offsets(synth.workload_seed("group512", 3000 + q), cnt)):
             faults.append((q, a, b, ks, r, c, d))
     g.set_faults(faults)
     g.run()
@@ -189,7 +189,7 @@ def test_group_512_bf16_integers_bit_exact(ft, orc):
     for q, (A, B, Cq) in enumerate(probs):
         _check_line_sums(Cq, _int8_host(A), _int8_host(B))
     faulted = sorted({f[0] for f in faults})
-    sample = sorted(set(int(x * nprob) for x in synth.unit(synth.config_seed(5, 48), 4)) | set(faulted[:4]))
+    sample = sorted(set(int(x * nprob) for x in synth.unit(synth.workload_seed("group512", 48), 4)) | set(faulted[:4]))
     for q in sample:
         A, B, Cq = probs[q]
         Ah, Bh = _int8_host(A).astype(np.float32), _int8_host(B).astype(np.float32)

@@ -71,7 +71,7 @@ def test_persistent_faults_in_late_tiles_match_oracle(ft, handle, orc):
     A, B, _ = _int_problem(M, N, K, 4200)
     tiles_m, tiles_n = -(-M // TDM), -(-N // TDN)
     nks = -(-K // 64)
-    pos = synth.fault_positions(synth.config_seed(5, 30), 12, tiles_m, tiles_n, nks, TDM, TDN, M, N, nks)
+    pos = synth.fault_positions(synth.workload_seed("group512", 30), 12, tiles_m, tiles_n, nks, TDM, TDN, M, N, nks)
     faults = [(tm, tn, ks, r, c, float(2 ** 10)) for (tm, tn, ks, r, c) in pos]
     dC = torch.zeros(M, N, device="cuda")
     rep = handle.gemm(_dev_bf16(A), _dev_bf16(B), dC, level=ft.FT_TILE, dtype=ft.BF16, inject=faults)
@@ -137,7 +137,7 @@ def test_group_faults_per_problem_match_oracle(ft, handle, orc):
         tiles_m, tiles_n, nks = -(-M // TDM), -(-N // TDN), -(-K // 64)
         # at most one fault per tile: the tile is the unit, verified once
         nf = min(2, tiles_m * tiles_n)
-        for (a, b, ks, r, c) in synth.fault_positions(synth.config_seed(5, 40 + q), nf, tiles_m, tiles_n, nks,
+        for (a, b, ks, r, c) in synth.fault_positions(synth.workload_seed("group512", 40 + q), nf, tiles_m, tiles_n, nks,
                                                       TDM, TDN, M, N, nks):
             faults.append((q, a, b, ks, r, c, 2.0 ** 9))
             per_problem.setdefault(q, []).append((a, b, ks, r, c, 2.0 ** 9))
@@ -161,8 +161,8 @@ def test_group_fp8_within_bound(ft, handle, orc):
     shapes = [(300, 500, 256), (64, 1000, 512), (777, 129, 384)]
     dev, host = [], []
     for q, (M, N, K) in enumerate(shapes):
-        A = synth.normal((M, K), synth.config_seed(5, 50 + q))
-        B = synth.normal((K, N), synth.config_seed(5, 60 + q))
+        A = synth.normal((M, K), synth.workload_seed("group512", 50 + q))
+        B = synth.normal((K, N), synth.workload_seed("group512", 60 + q))
         dA, sa = handle.quantize(torch.from_numpy(A).cuda(), ft.E4M3)
         dB, sb = handle.quantize(torch.from_numpy(np.ascontiguousarray(B)).cuda(), ft.E4M3)
         _, Aq, _ = orc.quant_e4m3(A)

@@ -231,7 +231,7 @@ def test_learned_threshold_gains_over_analytic(ft, handle, orc):
     tiles_m, tiles_n = -(-M // TDM), -(-N // TDN)
     y_tiles, _ = omlp.forward(th.cpu().numpy().astype(np.float64), _oracle_features(A, B, K))
     lam_t = 2.0 ** margin * 2.0 ** y_tiles
-    pos = synth.fault_positions(synth.config_seed(4, 91), 12, tiles_m, tiles_n, K // 64, TDM, TDN, M, N, K // 64)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 91), 12, tiles_m, tiles_n, K // 64, TDM, TDN, M, N, K // 64)
     faults, ratio = [], []
     for (tm_, tn_, ks, r, c) in pos:
         i, j = tm_ * TDM + r, tn_ * TDN + c
@@ -267,7 +267,7 @@ def test_learned_threshold_gains_over_analytic(ft, handle, orc):
     x_tiles = _oracle_features(A, B, K)
     y_tiles, _ = omlp.forward(th.cpu().numpy().astype(np.float64), x_tiles)
     lam_t = 2.0 ** margin * 2.0 ** y_tiles
-    pos = synth.fault_positions(synth.config_seed(4, 90), 12, tiles_m, tiles_n, 32, TDM, TDN, M, N, 32)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 90), 12, tiles_m, tiles_n, 32, TDM, TDN, M, N, 32)
     faults, gain = [], []
     for (tm_, tn_, ks, r, c) in pos:
         I = slice(tm_ * TDM, (tm_ + 1) * TDM)

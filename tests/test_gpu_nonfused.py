@@ -53,11 +53,11 @@ def _key(r):
     return (r.tile_m, r.tile_n, r.kstep, r.row, r.col, r.kind)
 
 
-def test_config1_integers_bit_exact(ft, orc):
+def test_int256_integers_bit_exact(ft, orc):
     M = N = K = 256
-    A = synth.integers((M, K), synth.config_seed(1, 0))
-    B = synth.integers((K, N), synth.config_seed(1, 1))
-    pos = synth.fault_positions(synth.config_seed(1, 2), 4, 2, 2, 16, 128, 128, M, N, 16)
+    A = synth.integers((M, K), synth.workload_seed("int256", 0))
+    B = synth.integers((K, N), synth.workload_seed("int256", 1))
+    pos = synth.fault_positions(synth.workload_seed("int256", 2), 4, 2, 2, 16, 128, 128, M, N, 16)
     faults = [(tm, tn, ks, r, c, 2.0 ** 10) for (tm, tn, ks, r, c) in pos]
     h = ft.Handle(0)
     got, recs, rep = _nonfused(ft, h, A, B, np.zeros((M, N), np.float32), 1.0, 0.0, 256, faults)

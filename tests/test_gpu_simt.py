@@ -97,15 +97,15 @@ def _compare_exact(rep, res):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("level", ["block", "warp", "thread"])
-def test_config1_bit_exact(ft, handle, orc, level):
+def test_int256_bit_exact(ft, handle, orc, level):
     """M=N=K=256, integers in [-4,4], 4 faults of +2^10 at seeded (tile, k-step, element)."""
     M = N = K = 256
-    A = synth.integers((M, K), synth.config_seed(1, 0))
-    B = synth.integers((K, N), synth.config_seed(1, 1))
+    A = synth.integers((M, K), synth.workload_seed("int256", 0))
+    B = synth.integers((K, N), synth.workload_seed("int256", 1))
     Cin = np.zeros((M, N), np.float32)
     lv = LEVELS[level]
     s = _sched("huge", cadence=4)
-    pos = synth.fault_positions(synth.config_seed(1, 2), 4, 2, 2, 32, 128, 128, M, N, 4,
+    pos = synth.fault_positions(synth.workload_seed("int256", 2), 4, 2, 2, 32, 128, 128, M, N, 4,
                                 unit_of=_unit_fn(s, lv))
     faults = [p + (1024.0,) for p in pos]
     C, rep = _run(ft, handle, A, B, Cin, 1.0, 0.0, lv, s, faults)
@@ -281,9 +281,9 @@ def test_float_parity_and_faults(ft, handle, orc, level):
     C within the worst-case bound, no false alarm, faults of 1e-2..1e3 x the
     tile max located exactly as the oracle does and corrected to within tau."""
     M, N, K = 384, 256, 1024
-    A = synth.uniform((M, K), synth.config_seed(2, 0))
-    B = synth.uniform((K, N), synth.config_seed(2, 1))
-    Cin = synth.uniform((M, N), synth.config_seed(2, 2))
+    A = synth.uniform((M, K), synth.workload_seed("sweep_fp32", 0))
+    B = synth.uniform((K, N), synth.workload_seed("sweep_fp32", 1))
+    Cin = synth.uniform((M, N), synth.workload_seed("sweep_fp32", 2))
     lv = LEVELS[level]
     s = _sched("huge", cadence=32)
     clean_o = orc.gemm_ft(A, B, _oracle_sched(orc, s, lv), alpha=1.0, beta=0.5, Cin=Cin)
@@ -293,9 +293,9 @@ def test_float_parity_and_faults(ft, handle, orc, level):
     assert rep0.detected == 0 and clean_o.detected == 0
     # faults: magnitudes log-uniform in [1e-2, 1e3] x the tile's max |A B|
     AB = A.astype(np.float64) @ B.astype(np.float64)
-    pos = synth.fault_positions(synth.config_seed(2, 3), 6, 3, 2, K // 8, 128, 128, M, N, 32,
+    pos = synth.fault_positions(synth.workload_seed("sweep_fp32", 3), 6, 3, 2, K // 8, 128, 128, M, N, 32,
                                 unit_of=_unit_fn(s, lv))
-    mags = synth.log_uniform(synth.config_seed(2, 4), 6, 1e-2, 1e3)
+    mags = synth.log_uniform(synth.workload_seed("sweep_fp32", 4), 6, 1e-2, 1e3)
     faults = []
     for (tm, tn, ks, r, c), g in zip(pos, mags):
         tmax = np.abs(AB[tm * 128:(tm + 1) * 128, tn * 128:(tn + 1) * 128]).max()

@@ -82,8 +82,8 @@ def test_tc_bf16_integers_exact(ft, handle, orc, level, shape):
 @pytest.mark.parametrize("level", ["off", "tile"])
 def test_tc_bf16_normal_within_bound(ft, handle, orc, level):
     M, N, K = 384, 512, 1024
-    A, B = _bf16_inputs(orc, "normal", M, N, K, synth.config_seed(4, 0))
-    Cin = synth.normal((M, N), synth.config_seed(4, 2))
+    A, B = _bf16_inputs(orc, "normal", M, N, K, synth.workload_seed("tc_square", 0))
+    Cin = synth.normal((M, N), synth.workload_seed("tc_square", 2))
     C, rep = _run_bf16(ft, handle, A, B, Cin, 1.0, 0.5, ft.LEVELS[level])
     ref = orc.gemm_ref(A, B, 1.0, 0.5, Cin)
     assert np.all(np.abs(C - ref) <= _bound(A, B, Cin, 1.0, 0.5, K))
@@ -109,8 +109,8 @@ def test_quantize_matches_oracle(ft, handle, orc):
 def test_tc_fp8_normal_within_bound(ft, handle, orc, level):
     import torch
     M, N, K = 256, 512, 1024
-    A = synth.normal((M, K), synth.config_seed(4, 10))
-    B = synth.normal((K, N), synth.config_seed(4, 11))
+    A = synth.normal((M, K), synth.workload_seed("tc_square", 10))
+    B = synth.normal((K, N), synth.workload_seed("tc_square", 11))
     dA8, sa = handle.quantize(torch.from_numpy(A).cuda(), ft.E4M3)
     # B is quantized as the K x N matrix it is
     dB8, sb = handle.quantize(torch.from_numpy(np.ascontiguousarray(B)).cuda(), ft.E4M3)
@@ -135,8 +135,8 @@ def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
     verification after the last k-step)."""
     import torch
     M, N, K = 384, 768, 1024
-    A = synth.normal((M, K), synth.config_seed(4, 20))
-    B = synth.normal((K, N), synth.config_seed(4, 21))
+    A = synth.normal((M, K), synth.workload_seed("tc_square", 20))
+    B = synth.normal((K, N), synth.workload_seed("tc_square", 21))
     if dt == "bf16":
         Aq = orc.round_bf16(A).astype(np.float32)
         Bq = orc.round_bf16(B).astype(np.float32)
@@ -153,8 +153,8 @@ def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
     sched = _tc_sched(orc, K, dt)
     ksteps = -(-K // sched.k_tb)
     AB = Aq.astype(np.float64) @ Bq.astype(np.float64)
-    pos = synth.fault_positions(synth.config_seed(4, 22), 5, 3, 3, ksteps, TDM, TDN, M, N, ksteps)
-    mags = synth.log_uniform(synth.config_seed(4, 23), 5, 1e-2, 1e3)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 22), 5, 3, 3, ksteps, TDM, TDN, M, N, ksteps)
+    mags = synth.log_uniform(synth.workload_seed("tc_square", 23), 5, 1e-2, 1e3)
     faults = []
     for (tm, tn, ks, r, c), g in zip(pos, mags):
         tmax = np.abs(AB[tm * TDM:(tm + 1) * TDM, tn * TDN:(tn + 1) * TDN]).max()

@@ -15,8 +15,8 @@ threshold at block level).
   data, tau / 12 or less on same-sign data) would decide there.
 * The learned threshold at block level: the sink's features equal the
   oracle's, the network evaluated in the kernel equals the oracle's forward
-  pass, and a network trained on the method's own fp32 residuals (config 3's
-  shapes and input families) finds faults below the analytic threshold with
+  pass, and a network trained on the method's own fp32 residuals (the irregular
+  fp32 workload's shapes and input families) finds faults below the analytic threshold with
   no false alarm.
 """
 import math
@@ -124,14 +124,14 @@ def test_faults_placed_against_the_threshold_match_oracle(ft, orc, kind):
     nks = K // 32
     # one fault per tile (drawn with a single k-step, so every draw is a
     # distinct unit), then moved to the last k-step
-    pos = synth.fault_positions(synth.config_seed(3, 60), 9, 3, 3, 1, T, T, M, N, 1)
+    pos = synth.fault_positions(synth.workload_seed("irregular_fp32", 60), 9, 3, 3, 1, T, T, M, N, 1)
     pos = [(tm_, tn_, nks - 1, r, c) for (tm_, tn_, ks, r, c) in pos]
     # the bands leave a margin of several standard deviations of the GPU's own
     # rounding of the residual, which is larger on same-sign data
     above = (1.25, 1.5, 2.0) if kind == "normal" else (1.5, 1.75, 2.0)
     below = (0.55, 0.65, 0.75) if kind == "normal" else (0.55, 0.6, 0.65)
     factors = list(above) + list(below) + [16.0, 64.0, 256.0]
-    sign = synth.unit(synth.config_seed(3, 61), 9)
+    sign = synth.unit(synth.workload_seed("irregular_fp32", 61), 9)
     faults = []
     for (tm_, tn_, ks, r, c), f, sg in zip(pos, factors, sign):
         tr, tc = _analytic_tau(A64, B64, tm_ * T + r, tn_ * T + c, K)
@@ -205,7 +205,7 @@ def test_block_network_in_kernel_matches_oracle_forward(ft):
 
 
 def test_block_learned_threshold_gains_over_analytic(ft):
-    """Train the network on fp32 block-level residuals of config 3's kinds of
+    """Train the network on fp32 block-level residuals of the irregular fp32 workload's kinds of
     shapes (long-K, wide, small-K) over input families from N(0,1) to U(0,1),
     calibrate on the training tiles (x2), then on zero-mean and on same-sign
     inputs put faults at 1.25x the larger of their learned row / column
@@ -245,7 +245,7 @@ def test_block_learned_threshold_gains_over_analytic(ft):
         lam_t = 2.0 ** margin * 2.0 ** y_t
         tiles_n = -(-N // T)
         nks = K // 32
-        pos = synth.fault_positions(synth.config_seed(3, 70), 10, M // T, N // T, 1, T, T, M, N, 1)
+        pos = synth.fault_positions(synth.workload_seed("irregular_fp32", 70), 10, M // T, N // T, 1, T, T, M, N, 1)
         faults, ratio = [], []
         for (tm_, tn_, ks, r, c) in pos:
             i, j = tm_ * T + r, tn_ * T + c

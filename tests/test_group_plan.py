@@ -48,7 +48,7 @@ def _loads(tiles, start):
 def test_balance_bound_on_a_mixed_group(ft):
     # 512 problems with the mixed shapes of the grouped benchmark: greedy list
     # scheduling leaves no CTA more than one tile's cost above the least loaded
-    u = synth.unit(synth.config_seed(5, 90), 3 * 512)
+    u = synth.unit(synth.workload_seed("group512", 90), 3 * 512)
     m = 64 + 16 * np.floor(u[0::3] * 253).astype(int)
     n = 64 + 16 * np.floor(u[1::3] * 253).astype(int)
     k = 64 + 16 * np.floor(u[2::3] * 125).astype(int)

@@ -163,16 +163,16 @@ def _thread_unit(r, c, m_w=32, n_w=64, m_t=8, n_t=8):
 
 
 @pytest.mark.parametrize("level", ["BLOCK", "WARP", "THREAD"])
-def test_config1_style_faults_corrected_bitwise(orc, level):
+def test_int256_style_faults_corrected_bitwise(orc, level):
     """256^3 integers, 4 faults of +2^10 at distinct units/periods: all corrected, C exact."""
     M = N = K = 256
-    A = synth.integers((M, K), synth.config_seed(1, 0))
-    B = synth.integers((K, N), synth.config_seed(1, 1))
+    A = synth.integers((M, K), synth.workload_seed("int256", 0))
+    B = synth.integers((K, N), synth.workload_seed("int256", 1))
     lv = getattr(orc, level)
     s = orc.Schedule(**HUGE, cadence=4, level=lv)
     unit_of = {"BLOCK": lambda r, c: 0, "WARP": lambda r, c: (r // 32, c // 64),
                "THREAD": _thread_unit}[level]
-    pos = synth.fault_positions(synth.config_seed(1, 2), 4, 2, 2, 32, 128, 128, M, N, 4,
+    pos = synth.fault_positions(synth.workload_seed("int256", 2), 4, 2, 2, 32, 128, 128, M, N, 4,
                                 unit_of=unit_of)
     faults = [p + (1024.0,) for p in pos]
     clean = orc.gemm_ft(A, B, s)
