@@ -632,25 +632,17 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           if (q == 0) { T.nr = 0; T.nc = 0; T.bestr = 0ull; T.bestc = 0ull; }
           for (int c = q; c < BN; c += EPI_T) T.sum_c[c] = 0.0;
           epi_bar<EPI_T>();
-          // fp64 sums only where the screen flagged: a flagged row in its own
-          // thread (each half of the columns apart), a flagged column (the
-          // same in all lanes) by a warp shuffle reduction and one
-          // shared-memory add per warp
+          // fp64 sums only where the screen flagged, each half of the
+          // columns apart: a flagged column (the same in all lanes) by a
+          // warp shuffle reduction and one shared-memory add per warp; a
+          // flagged row spread over 16 lanes (below).
           // The fp64 work stays inside the branches that need it: this
-          // part's fp64 rate is 1/64 of fp32, and a conversion shared by
-          // the row and the column branch would otherwise be done for every
-          // element of every row.
-          const bool my_row_flagged = T.flag_r[r] != 0;
-          double sr = 0.0;
+          // part's fp64 rate is 1/64 of fp32, and a warp instruction costs
+          // the same whether one lane or all are active.
           for (int ch = eh * 2 * CH2; ch < (eh + 1) * 2 * CH2; ++ch) {
             float v[16];
             tmem_ld16(tl + ch * 16, v);
             tmem_wait_ld();
-            if (my_row_flagged) {  // one lane of the warp
-#pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (ch * 16 + e < DN) sr += (double)v[e];
-            }
             // the flagged columns of this chunk, one at a time (warp-uniform)
             unsigned fcols = 0u;
 #pragma unroll
@@ -668,6 +660,35 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
               for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
               if (lane == 0) atomicAdd(&T.sum_c[ch * 16 + e], xs);
             }
+          }
+          // the flagged rows of this warp, one at a time (warp-uniform): the
+          // row's lane passes each 16-column chunk through the warp's
+          // staging row 0, lane e < 16 adds column e in fp64, and a shuffle
+          // tree over the 16 lanes ends the sum (one lane summing alone
+          // would issue 16 times the fp64 instructions)
+          double sr = 0.0;
+          for (unsigned frows = __ballot_sync(0xffffffffu, T.flag_r[r] != 0); frows; frows &= frows - 1u) {
+            const int l0 = __ffs(frows) - 1;
+            float* srow = T.stg[ew][0];
+            double part = 0.0;
+            for (int ch = eh * 2 * CH2; ch < (eh + 1) * 2 * CH2; ++ch) {
+              float v[16];
+              tmem_ld16(tl + ch * 16, v);
+              tmem_wait_ld();
+              if (lane == l0) {
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                  *reinterpret_cast<float4*>(&srow[4 * g]) =
+                      make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+              }
+              __syncwarp();
+              if (lane < 16 && ch * 16 + lane < DN) part += (double)srow[lane];
+              __syncwarp();  // the row is rewritten by the next chunk
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const double tot = __shfl_sync(0xffffffffu, part, 0);
+            if (lane == l0) sr = tot;
           }
           if (eh == 0) T.sum_r[r] = sr;
           else T.sum_rp[r] = sr;
