@@ -341,6 +341,40 @@ int ftgemm_group_set_faults(ftgemm_group_t group, const int32_t* problem, const 
  * accumulate in the handle; read them with ftgemm_report_fetch. */
 int ftgemm_grouped_gemm(ftgemm_handle_t handle, ftgemm_group_t group);
 
+/* ftgemm_grouped_gemm with the operands taken from a DEVICE array:
+ * `problems` is a device pointer to `count` ftgemm_problem (count = the
+ * group's, the caller's order, 8-byte aligned), read on the handle's stream
+ * when the call runs, so a captured graph replays with whatever the array
+ * holds at replay time (no host synchronisation, no allocation; the call
+ * enqueues a small rebinding kernel, then what ftgemm_grouped_gemm does).
+ * Each entry's m, n, k, lda and ldb must be those the group was created
+ * with (they fix its tile schedule, its workspace and its tensor maps); A,
+ * B, C, ldc, alpha, beta and the e4m3 scales are taken from the entry.  The
+ * other rules, checked on the device, are those of ftgemm_group_bind_rule.
+ * An entry that breaks one is skipped: its problem is neither read nor
+ * written by this call or by later calls of the group until a rebinding
+ * meets the rules, and the next ftgemm_report_fetch returns FTGEMM_ERR_ARG
+ * (after filling the report).  A binding persists: a later
+ * ftgemm_grouped_gemm computes on the operands last bound.  (No
+ * counterpart in the paper, which runs one GEMM at a time.)
+ * Host-side errors: FTGEMM_ERR_ARG (NULL, count differs, array misaligned,
+ * another handle's group), FTGEMM_ERR_CUDA. */
+int ftgemm_grouped_gemm_dev(ftgemm_handle_t handle, ftgemm_group_t group, int32_t count,
+                            const ftgemm_problem* problems);
+
+/* The rule ftgemm_grouped_gemm_dev applies on the device to an entry
+ * `bound` of a group whose problem was `created` (both host structs; no
+ * device work), for a group of `dtype` and `level`.  Returns 0 when `bound`
+ * may rebind the problem, else the first rule broken: 1 m, n or k differ;
+ * 2 lda or ldb differ; 3 A, B or C NULL; 4 A not 16-byte aligned; 5 B not
+ * aligned to its element (bf16), or not 16-byte aligned where the MMA reads
+ * it in place (bf16 at level OFF when the created B was 16-byte aligned with
+ * a 16-byte multiple row stride); 6 ldc < n or C not 4-byte aligned; 7 an
+ * e4m3 scale not positive or their product not finite.  Negative: an
+ * error code (NULL argument, FTGEMM_ERR_UNSUPPORTED dtype or level). */
+int ftgemm_group_bind_rule(const ftgemm_problem* created, const ftgemm_problem* bound, ftgemm_dtype dtype,
+                           ftgemm_ft_level level);
+
 /* Release a group (synchronises the handle's stream first).  (No
  * counterpart in the paper.) */
 int ftgemm_group_destroy(ftgemm_group_t group);
@@ -458,7 +492,11 @@ int ftgemm_zgemm(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, const 
 
 /* Synchronise the handle's stream, copy out the events accumulated since the
  * last fetch (or the last call that returned a report) and clear them: the
- * located and corrected errors of Section 4.2.1, one record each. */
+ * located and corrected errors of Section 4.2.1, one record each.  The
+ * report is filled in any case; the return value is then FTGEMM_ERR_TIMEOUT
+ * if a bounded device wait gave up, else FTGEMM_ERR_ARG if entries of a
+ * device problem array were skipped (ftgemm_grouped_gemm_dev), else
+ * FTGEMM_OK. */
 int ftgemm_report_fetch(ftgemm_handle_t handle, ftgemm_report* report);
 
 /* Checksum encoding on its own (Eq. 1-2), fp32:

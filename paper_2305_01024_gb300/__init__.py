@@ -123,6 +123,8 @@ def lib():
                                     C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.ftgemm_group_set_faults.argtypes = [vp, C.POINTER(i32), C.POINTER(InjectSpec)]
     L.ftgemm_grouped_gemm.argtypes = [vp, vp]
+    L.ftgemm_grouped_gemm_dev.argtypes = [vp, vp, i32, vp]
+    L.ftgemm_group_bind_rule.argtypes = [C.POINTER(Problem), C.POINTER(Problem), C.c_int, C.c_int]
     L.ftgemm_group_destroy.argtypes = [vp]
     L.ftgemm_set_residual_sink.argtypes = [vp, vp, vp, i64]
     L.ftgemm_mlp_forward.argtypes = [vp, i64, vp, vp, vp]
@@ -147,7 +149,8 @@ def lib():
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
                "ftgemm_group_create", "ftgemm_group_plan", "ftgemm_group_tiles", "ftgemm_group_set_faults",
-               "ftgemm_grouped_gemm", "ftgemm_group_destroy", "ftgemm_set_residual_sink",
+               "ftgemm_grouped_gemm", "ftgemm_grouped_gemm_dev", "ftgemm_group_bind_rule",
+               "ftgemm_group_destroy", "ftgemm_set_residual_sink",
                "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune",
                "ftgemm_selftest_wait", "ftgemm_gemm_offline", "ftgemm_gemm_nonfused", "ftgemm_dgemm",
                "ftgemm_zgemm"):
@@ -449,6 +452,37 @@ def group_plan(shapes, dtype=BF16, level=FT_TILE, ncta: int = 152):
     return [tuple(flat[i:i + 4]) for i in range(0, len(flat), 4)], list(start)
 
 
+def problem_structs(problems):
+    """ftgemm_problem structs (host) of (A, B, C[, alpha, beta[, scale_a,
+    scale_b]]) tuples of CUDA tensors."""
+    arr = (Problem * len(problems))()
+    for q, pr in enumerate(problems):
+        A, B, Cm = pr[:3]
+        alpha = float(pr[3]) if len(pr) > 3 else 1.0
+        beta = float(pr[4]) if len(pr) > 4 else 0.0
+        sa = float(pr[5]) if len(pr) > 5 else 1.0
+        sb = float(pr[6]) if len(pr) > 6 else 1.0
+        m, k = A.shape
+        n = B.shape[1]
+        arr[q] = Problem(m, n, k, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                         Cm.data_ptr(), Cm.stride(0), alpha, beta, sa, sb)
+    return arr
+
+
+def problem_table(problems, device="cuda"):
+    """The ftgemm_problem array of `problems` (as for Group) copied into a
+    device tensor (int64 words), for Group.run_device."""
+    import torch
+    arr = problem_structs(problems)
+    host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.int64)
+    return host.to(device)
+
+
+def bind_rule(created, bound, dtype=BF16, level=FT_TILE):
+    """ftgemm_group_bind_rule on two Problem structs (host only)."""
+    return lib().ftgemm_group_bind_rule(C.byref(created), C.byref(bound), dtype, level)
+
+
 class Group:
     """A prepared group of tensor-core GEMMs (ftgemm_group_create).
 
@@ -459,17 +493,7 @@ class Group:
     def __init__(self, handle: "Handle", problems, dtype=BF16, level=FT_TILE):
         self.handle = handle
         self.count = len(problems)
-        arr = (Problem * self.count)()
-        for q, pr in enumerate(problems):
-            A, B, Cm = pr[:3]
-            alpha = float(pr[3]) if len(pr) > 3 else 1.0
-            beta = float(pr[4]) if len(pr) > 4 else 0.0
-            sa = float(pr[5]) if len(pr) > 5 else 1.0
-            sb = float(pr[6]) if len(pr) > 6 else 1.0
-            m, k = A.shape
-            n = B.shape[1]
-            arr[q] = Problem(m, n, k, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
-                             Cm.data_ptr(), Cm.stride(0), alpha, beta, sa, sb)
+        arr = problem_structs(problems)
         self._keep = list(problems)
         self._g = C.c_void_p()
         _check(lib().ftgemm_group_create(handle._h, self.count, arr, dtype, level, C.byref(self._g)))
@@ -492,6 +516,14 @@ class Group:
     def run(self):
         """Enqueue the whole group on the handle's stream (no host sync)."""
         _check(lib().ftgemm_grouped_gemm(self.handle._h, self._g))
+
+    def run_device(self, table):
+        """Enqueue the group with its operands read from `table`, a CUDA
+        tensor holding `count` ftgemm_problem structs (problem_table), when
+        the call runs on the stream (ftgemm_grouped_gemm_dev).  The tensors it
+        points at must outlive every launch that reads them."""
+        assert table.is_cuda and table.numel() * table.element_size() >= self.count * C.sizeof(Problem)
+        _check(lib().ftgemm_grouped_gemm_dev(self.handle._h, self._g, self.count, C.c_void_p(table.data_ptr())))
 
     def close(self):
         if getattr(self, "_g", None) and self._g.value:

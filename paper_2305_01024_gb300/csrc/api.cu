@@ -42,6 +42,8 @@ cudaError_t launch_splitk_reduce(const float*, int, int, int, float, float, floa
                                  cudaStream_t);
 void tc_prep_blocks(const TcProblem& P, int dt, int out[P_KINDS]);
 int tc_nb_parts(int dt, long long K);
+cudaError_t launch_tc_bind(TcProblem* probs, TcProbMaps* maps, const int* pos, const ftgemm_problem* in, int count,
+                           int dt, DevReport* rep, cudaStream_t st);
 cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[P_KINDS],
                            const int* const* bmap, int* launches, cudaStream_t st);
 cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
@@ -397,7 +399,7 @@ static int drain_events(ftgemm_ctx* h) {
 
 static int clear_report(ftgemm_ctx* h) {
   CK(cudaMemsetAsync(h->rep, 0, offsetof(DevReport, capacity), h->stream));
-  CK(cudaMemsetAsync(&h->rep->timeouts, 0, sizeof(int), h->stream));
+  CK(cudaMemsetAsync(&h->rep->timeouts, 0, 2 * sizeof(int), h->stream));  // timeouts, bind_errors
   return FTGEMM_OK;
 }
 extern "C" int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out);
@@ -419,9 +421,7 @@ static void tc_set_problem(TcProblem& P, int dt, bool abft, int M, int N, int K,
   P.nkb = (K + kblk - 1) / kblk;
   P.A = A; P.lda = lda; P.B = B; P.ldb = ldb;
   P.ldk = (K + 127) / 128 * 128;  // elements; a 16-byte multiple for both types
-  // without checksums a bf16 B is read in place by the MMA (MN-major) when
-  // TMA can address it: 256-column tiles keep its boxes on 128-byte lines
-  P.b_mn = !abft && dt == 0 && ((uintptr_t)B & 15) == 0 && (ldb * 2) % 16 == 0;
+  P.b_mn = tc_b_in_place(dt, abft, B, ldb);
   P.C = C; P.ldc = ldc;
   P.c_vec = (ldc % 4 == 0) && (((uintptr_t)C & 15) == 0);
   P.alpha = (float)alpha; P.beta = (float)beta;
@@ -588,6 +588,7 @@ struct ftgemm_group {
   int4* d_tiles = nullptr;      // the schedule: per-CTA tile lists, concatenated
   int* d_cta_start = nullptr;   // [ncta + 1]
   int* d_bmap = nullptr;        // encode launches: the problem of every block, kinds concatenated
+  int* d_pos = nullptr;         // caller index -> schedule position (device-array rebinding)
   const int* bmap[P_KINDS] = {};
   int ncta = 0;
   float* ws = nullptr;
@@ -654,11 +655,14 @@ static void group_free(ftgemm_group* g) {
   if (g->d_tiles) cudaFree(g->d_tiles);
   if (g->d_cta_start) cudaFree(g->d_cta_start);
   if (g->d_bmap) cudaFree(g->d_bmap);
+  if (g->d_pos) cudaFree(g->d_pos);
   if (g->ws) cudaFree(g->ws);
   if (g->d_faults) cudaFree(g->d_faults);
   if (g->d_fbits) cudaFree(g->d_fbits);
   delete g;
 }
+
+static int group_enqueue(ftgemm_ctx* h, ftgemm_group* g);
 
 extern "C" {
 
@@ -759,6 +763,8 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
       bmap.insert(bmap.end(), (size_t)nb[kd], q);
     }
   }
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_pos, sizeof(int) * count);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_pos, g->pos.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !bmap.empty()) e = cudaMalloc(&g->d_bmap, sizeof(int) * bmap.size());
   if (e == cudaSuccess && !bmap.empty())
     e = cudaMemcpy(g->d_bmap, bmap.data(), sizeof(int) * bmap.size(), cudaMemcpyHostToDevice);
@@ -878,6 +884,41 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   if (!h || !g) FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm: NULL argument");
   if (g->h != h) FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm: the group was created on another handle");
   CK(cudaSetDevice(h->device));
+  return group_enqueue(h, g);
+}
+
+int ftgemm_grouped_gemm_dev(ftgemm_handle_t h, ftgemm_group_t g, int32_t count, const ftgemm_problem* problems) {
+  if (!h || !g || !problems) FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm_dev: NULL argument");
+  if (g->h != h) FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm_dev: the group was created on another handle");
+  if (count != g->count)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm_dev: %d problems, the group has %d", (int)count, g->count);
+  if ((uintptr_t)problems % alignof(ftgemm_problem))
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_grouped_gemm_dev: the problem array is not %zu-byte aligned",
+         alignof(ftgemm_problem));
+  if (h->sink_lam && g->abft && g->total_tiles > h->sink_cap)
+    FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the group has %d", (long long)h->sink_cap, g->total_tiles);
+  CK(cudaSetDevice(h->device));
+  CK(launch_tc_bind(g->d_probs, g->d_maps, g->d_pos, problems, g->count, g->dt, h->rep, h->stream));
+  h->launches += 1;
+  return group_enqueue(h, g);
+}
+
+int ftgemm_group_bind_rule(const ftgemm_problem* created, const ftgemm_problem* bound, ftgemm_dtype dtype,
+                           ftgemm_ft_level level) {
+  if (!created || !bound) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_bind_rule: NULL argument");
+  if ((dtype != FTGEMM_BF16 && dtype != FTGEMM_E4M3) || (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE))
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_group_bind_rule: dtype %d, level %d", (int)dtype, (int)level);
+  const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
+  const int b_mn = tc_b_in_place(dt, level == FTGEMM_FT_TILE, created->B, created->ldb);
+  return tc_bind_rule(created->m, created->n, created->k, created->lda, created->ldb, b_mn, dt, *bound);
+}
+
+}  // extern "C"
+
+// The encode pass and the persistent launch of a group, on the handle's stream.
+static int group_enqueue(ftgemm_ctx* h, ftgemm_group* g) {
+  if (h->sink_lam && g->abft && g->total_tiles > h->sink_cap)
+    FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the group has %d", (long long)h->sink_cap, g->total_tiles);
   TcBatch b;
   memset(&b, 0, sizeof(b));
   b.table = g->d_probs;
@@ -890,8 +931,6 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   TcMapsBatch mb;
   memset(&mb, 0, sizeof(mb));
   mb.table = g->d_maps;
-  if (h->sink_lam && g->abft && g->total_tiles > h->sink_cap)
-    FAIL(FTGEMM_ERR_ARG, "residual sink holds %lld tiles, the group has %d", (long long)h->sink_cap, g->total_tiles);
   TcRun run{g->nfaults > 0 ? g->d_faults : nullptr, g->nfaults, g->d_fbits, h->rep, h->recs,
             g->abft ? h->sink_lam : nullptr, g->abft ? h->sink_x : nullptr};
   const int grid = g->ncta;  // the schedule was built for this many CTAs
@@ -913,6 +952,8 @@ int ftgemm_grouped_gemm(ftgemm_handle_t h, ftgemm_group_t g) {
   h->launches += launches;
   return FTGEMM_OK;
 }
+
+extern "C" {
 
 int ftgemm_group_destroy(ftgemm_group_t g) {
   if (!g) return FTGEMM_OK;
@@ -1217,6 +1258,9 @@ int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out) {
   int rc = clear_report(h);
   if (rc) return rc;
   if (r.timeouts > 0) FAIL(FTGEMM_ERR_TIMEOUT, "%d bounded device waits gave up", r.timeouts);
+  if (r.bind_errors > 0)
+    FAIL(FTGEMM_ERR_ARG, "%d device-array entries broke a rebinding rule; their problems were skipped",
+         r.bind_errors);
   return FTGEMM_OK;
 }
 

@@ -27,8 +27,8 @@ struct DevReport {
   unsigned long long detected, corrected, uncorrectable, checksum_only;
   int n_records;
   int capacity;
-  int timeouts;  // bounded device waits that gave up
-  int pad;
+  int timeouts;     // bounded device waits that gave up
+  int bind_errors;  // device-array entries that broke a rebinding rule (problem skipped)
 };
 
 static_assert(sizeof(ftgemm_fault_record) == 64, "record layout");
@@ -158,7 +158,42 @@ struct TcProblem {
   float grow;                     // analytic threshold: mu * u * sqrt(K), factor of |checksum|
   const float* mlp;               // learned threshold: network parameters (device), or null
   float mlp_scale;                // lambda of a tile = mlp_scale * 2^network(features)
+  int off;                        // 1: skipped (its last device-array rebinding broke a rule):
+                                  // nothing of it is read or written
 };
+
+// Without checksums a bf16 B is read in place by the MMA (MN-major) when
+// TMA can address it: 256-column tiles keep its boxes on 128-byte lines.
+__host__ __device__ inline int tc_b_in_place(int dt, bool abft, const void* B, long long ldb) {
+  return !abft && dt == 0 && ((uintptr_t)B & 15) == 0 && (ldb * 2) % 16 == 0;
+}
+
+// Rules a device-array entry `u` must meet to rebind a group's problem
+// (ftgemm_grouped_gemm_dev).  The sizes and the leading dimensions of A and B
+// are the ones the group was created with (M..ldb): they fix the tile
+// schedule, the encode workspace and the tensor maps' strides.  A, B and C
+// are non-null; A is 16-byte aligned (TMA); B is aligned to its element, and
+// to 16 bytes when the MMA reads it in place (b_mn); C is 4-byte aligned
+// with ldc >= N; e4m3 scales are positive and their product finite.
+// Returns TC_BIND_OK or the first rule broken.
+enum {
+  TC_BIND_OK = 0, TC_BIND_SIZES = 1, TC_BIND_LD = 2, TC_BIND_NULL = 3, TC_BIND_ALIGN_A = 4,
+  TC_BIND_ALIGN_B = 5, TC_BIND_C = 6, TC_BIND_SCALE = 7
+};
+__host__ __device__ inline int tc_bind_rule(long long M, long long N, long long K, long long lda, long long ldb,
+                                            int b_mn, int dt, const ftgemm_problem& u) {
+  if (u.m != M || u.n != N || u.k != K) return TC_BIND_SIZES;
+  if (u.lda != lda || u.ldb != ldb) return TC_BIND_LD;
+  if (!u.A || !u.B || !u.C) return TC_BIND_NULL;
+  if ((uintptr_t)u.A & 15) return TC_BIND_ALIGN_A;
+  if ((dt == 0 && ((uintptr_t)u.B & 1)) || (b_mn && ((uintptr_t)u.B & 15))) return TC_BIND_ALIGN_B;
+  if (u.ldc < N || ((uintptr_t)u.C & 3)) return TC_BIND_C;
+  if (dt == 1) {
+    const float s = u.scale_a * u.scale_b;
+    if (!(u.scale_a > 0.f && u.scale_b > 0.f && s > 0.f && s <= 3.4028234663852886e38f)) return TC_BIND_SCALE;
+  }
+  return TC_BIND_OK;
+}
 
 struct TcBatch {
   const TcProblem* table;  // device table of nprob problems, or null: use `one`

@@ -82,6 +82,18 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
                : "memory");
 }
 
+// Replace the global address of a tensor map held in global memory (the
+// map's other fields stay), then make the write visible to later TMA use
+// through the tensormap proxy (the user acquires with tensormap_acquire).
+__device__ __forceinline__ void tensormap_replace_address(CUtensorMap* map, const void* p) {
+  asm volatile("tensormap.replace.tile.global_address.global.b1024.b64 [%0], %1;"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "l"(reinterpret_cast<uint64_t>(p))
+               : "memory");
+}
+__device__ __forceinline__ void tensormap_release() {
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
+
 // Barrier `id` over `n` threads that also ORs a predicate across them: every
 // participating thread gets the same result.
 __device__ __forceinline__ int bar_red_or(int id, int n, int pred) {

@@ -239,12 +239,19 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         last_pi = x.pi;
       }
       const int row0 = x.tm * DM, col0 = x.tn * DN;
-      const bool mn = !ABFT && DT == 0 && tc_problem(b, x.pi).b_mn;
+      const TcProblem& Px = tc_problem(b, x.pi);
+      const bool mn = !ABFT && DT == 0 && Px.b_mn;
+      const bool off = Px.off;  // skipped: the stages are released unloaded
       for (int kb = 0; kb < x.nkb; ++kb, ++it) {
         const int s = it % S;
         if (it >= S && !mbar_wait(&T.empty[s], ((it / S) & 1u) ^ 1u)) {
           dead = true;
           break;
+        }
+        if (off) {
+          mbar_arrive(&T.full[s]);
+          if (kb == 0 && j + 1 < n_my) nx = tc_my_tile(b, my0, j + 1);
+          continue;
         }
         // the same byte count either way: an MN-major B is 4 boxes of 8 KB
         mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
@@ -333,6 +340,19 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       const int ab = lt & 1;
       const int row0 = x.tm * DM, col0 = x.tn * DN, gr = row0 + r;
       const uint32_t tl = tmem + (uint32_t)(ab * BN) + ((uint32_t)(lq * 32) << 16);
+      if (P.off) {
+        // a problem skipped by a device-array rebinding: its accumulator
+        // (from unloaded stages) is handed back without a store or a check
+        if (!dead && !mbar_wait(&T.acc_full[ab], (lt >> 1) & 1)) {
+          dead = true;
+          atomicExch(&T.abort, 1);
+        }
+        tc_fence_after();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&T.acc_empty[ab]);
+        continue;
+      }
       // Everything this tile needs from global memory, and its threshold,
       // is fetched and computed before waiting for the accumulator, so the
       // load latency hides behind the tile's main loop.

@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace ftg {
 
@@ -47,6 +48,7 @@ __device__ __forceinline__ float ld_elem(const void* base, long long idx) {
 #define TC_BLOCK_OF(KIND)                                                  \
   const int pi = bmap ? bmap[blockIdx.x] : tc_find_block(b, KIND, blockIdx.x); \
   const TcProblem& P = tc_problem(b, pi);                                  \
+  if (P.off) return; /* skipped by a device-array rebinding: not read */   \
   const int lb = (int)blockIdx.x - P.blk_start[KIND]
 
 // Eight consecutive elements of row `row` (columns c0..c0+7, zero past
@@ -564,6 +566,47 @@ cudaError_t launch_tc_prep(int dt, bool abft, const TcBatch& b, const int total[
   if (dt == 0) tc_pieces_kernel<0><<<total[P_PIECES], 256, 0, st>>>(b, mp(P_PIECES));
   else tc_pieces_kernel<1><<<total[P_PIECES], 256, 0, st>>>(b, mp(P_PIECES));
   *launches += 4;
+  return cudaGetLastError();
+}
+
+// Rebinding of a group to a device array of problems (ftgemm_grouped_gemm_dev),
+// one thread per problem of the caller's array; pos[q] is the schedule
+// position of the caller's problem q.  An entry that meets tc_bind_rule
+// replaces the operand pointers and epilogue scalars of its problem and the
+// global address of the tensor maps that point at caller memory (A; B when
+// the MMA reads it in place); the encode workspace and the other maps are
+// the group's own.  An entry that breaks a rule marks its problem skipped
+// (until a later rebinding meets the rules) and is counted in the report.
+__global__ void tc_bind_kernel(TcProblem* __restrict__ probs, TcProbMaps* __restrict__ maps,
+                               const int* __restrict__ pos, const ftgemm_problem* __restrict__ in, int count,
+                               int dt, DevReport* rep) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const ftgemm_problem u = in[q];
+  const int p = pos[q];
+  TcProblem& P = probs[p];
+  if (tc_bind_rule(P.M, P.N, P.K, P.lda, P.ldb, P.b_mn, dt, u) != TC_BIND_OK) {
+    P.off = 1;
+    atomicAdd(&rep->bind_errors, 1);
+    return;
+  }
+  P.A = u.A;
+  P.B = u.B;
+  P.C = u.C;
+  P.ldc = u.ldc;
+  P.c_vec = (u.ldc % 4 == 0) && (((uintptr_t)u.C & 15) == 0);
+  P.alpha = (float)u.alpha;
+  P.beta = (float)u.beta;
+  P.acc_scale = dt == 1 ? u.scale_a * u.scale_b : 1.f;
+  P.off = 0;
+  tensormap_replace_address(&maps[p].A, u.A);
+  if (P.b_mn) tensormap_replace_address(&maps[p].B, u.B);
+  tensormap_release();
+}
+
+cudaError_t launch_tc_bind(TcProblem* probs, TcProbMaps* maps, const int* pos, const ftgemm_problem* in, int count,
+                           int dt, DevReport* rep, cudaStream_t st) {
+  tc_bind_kernel<<<(count + 127) / 128, 128, 0, st>>>(probs, maps, pos, in, count, dt, rep);
   return cudaGetLastError();
 }
 
