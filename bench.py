@@ -174,6 +174,15 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi's start-up holds the driver long enough to stall this
+        # process's CUDA calls (about 0.2 s): return once it has written its
+        # first sample, so that no timed region pays for it
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -1338,7 +1347,9 @@ def main():
     e2e_clocks.start()
     s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s_.record(stream)
+    t_issue = time.perf_counter()
     e2e_run(e2e_steps, gemm_ev)
+    t_issue = time.perf_counter() - t_issue  # host time to enqueue every step (all of it is asynchronous)
     e_.record(stream)
     torch.cuda.synchronize()
     e2e_clk = e2e_clocks.stop()
@@ -1350,6 +1361,9 @@ def main():
            "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
            "ms_per_step": ms_e2e, "pipelining": "inputs double-buffered on a copy stream",
            "gemm_ms_mean": sum(gemm_ms) / len(gemm_ms), "gemm_ms_max": max(gemm_ms),
+           "first_gemm_start_ms": s_.elapsed_time(gemm_ev[0][0]),
+           "gemm_gap_ms_max": max([gemm_ev[i][1].elapsed_time(gemm_ev[i + 1][0]) for i in range(e2e_steps - 1)] or [0.0]),
+           "host_issue_ms": 1e3 * t_issue, "host_buffers_pinned": bool(hA.is_pinned() and hOut[0].is_pinned()),
            "host_link": link, "clocks": e2e_clk}
     del bufs
 
