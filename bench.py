@@ -154,6 +154,12 @@ def workload_config(n, level):
 # clocks
 # ---------------------------------------------------------------------------
 
+def clock_gpu_index(local):
+    """nvidia-smi's index of this process's device `local`."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    return int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -431,14 +437,29 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
             Aval = A.view(torch.float8_e4m3fn).double() * sa
             Bval = B.view(torch.float8_e4m3fn).double() * sb
         r = {}
+        # the default schedule (bf16 on CTA pairs, e4m3 on single CTAs), and
+        # the other one right after it, each with the SM clock sampled
+        default_pair = dt == ft.BF16
+        modes = {}
         for lvn, lv in (("off", ft.FT_OFF), ("tile", ft.FT_TILE)):
-            h.enable_timing(True)
-            h.stats(reset=True)
-            ms = timed_loop(lambda i: h.gemm(A, B, C, level=lv, dtype=dt, report=False), 5, warm=2)
-            st = h.stats(reset=True)
-            h.enable_timing(False)
-            r[f"{lvn}_tflops"] = fl / (ms / 1e3) / 1e12
-            r[f"{lvn}_kernel_tflops"] = fl / (st["kernel_ms"] / max(1, st["timed_launches"]) / 1e3) / 1e12
+            for pair in (default_pair, not default_pair):
+                h.set_tc_pair(pair)
+                clk = ClockSampler(clock_gpu_index(0))
+                clk.start()
+                h.enable_timing(True)
+                h.stats(reset=True)
+                ms = timed_loop(lambda i: h.gemm(A, B, C, level=lv, dtype=dt, report=False), 5, warm=2)
+                st = h.stats(reset=True)
+                h.enable_timing(False)
+                c = clk.stop()
+                kt = fl / (st["kernel_ms"] / max(1, st["timed_launches"]) / 1e3) / 1e12
+                modes[f"{lvn}_kernel_tflops_{'pairs' if pair else 'single'}"] = round(kt, 1)
+                modes[f"{lvn}_sm_mhz_{'pairs' if pair else 'single'}"] = c.get("sm_mhz")
+                if pair == default_pair:
+                    r[f"{lvn}_tflops"] = fl / (ms / 1e3) / 1e12
+                    r[f"{lvn}_kernel_tflops"] = kt
+        h.set_tc_pair(None)
+        r["cta_schedule"] = dict(modes, default="pairs" if default_pair else "single")
         r["overhead_pct_kernel"] = 100.0 * (r["off_kernel_tflops"] / r["tile_kernel_tflops"] - 1.0)
         r["overhead_pct"] = 100.0 * (r["off_tflops"] / r["tile_tflops"] - 1.0)
         h.report_fetch()
@@ -1169,8 +1190,7 @@ def main():
     # ---- timed region: the ABFT GEMM with faults --------------------------
     h.enable_timing(True)
     h.stats(reset=True)
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
-    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    clocks = ClockSampler(clock_gpu_index(local))
     clocks.start()
     ms = timed_loop(lambda i: step(level, faults[i]), args.steps)
     clk = clocks.stop()

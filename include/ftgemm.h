@@ -521,6 +521,18 @@ typedef struct {
   double kernel_ms;
 } ftgemm_stats;
 
+/* Tensor-core calls on CTA pairs (mode 1), on single CTAs (0), or chosen by
+ * operand type (-1, the default: bf16 on pairs, e4m3 on single CTAs, the
+ * faster of the two as measured), for later ftgemm_gemm calls and groups
+ * created afterwards.  Other modes: FTGEMM_ERR_ARG.  A pair is a
+ * cluster of two CTAs on two SMs that compute one 256 x 256 MMA tile with
+ * cta_group::2 MMAs: each CTA holds its own 128 rows of A and half of B's
+ * columns, and verifies its own tile of C exactly as a single CTA does
+ * (same tile grid, same checksum layout, same records), so results are
+ * identical either way; each SM then moves 32 KB of operands per k-block
+ * instead of 48 KB.  (Kernel schedule, no counterpart in the paper.) */
+int ftgemm_set_tc_pair(ftgemm_handle_t handle, int mode);
+
 /* Enable (1) or disable (0) the events around the main GEMM kernel.
  * (Measurement plumbing, no counterpart in the paper.) */
 int ftgemm_enable_timing(ftgemm_handle_t handle, int enable);

@@ -116,6 +116,7 @@ def lib():
     L.ftgemm_set_fp8_scales.argtypes = [vp, C.c_float, C.c_float]
     L.ftgemm_quantize.argtypes = [vp, i64, vp, vp, C.c_int, C.POINTER(C.c_float)]
     L.ftgemm_enable_timing.argtypes = [vp, C.c_int]
+    L.ftgemm_set_tc_pair.argtypes = [vp, C.c_int]
     L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.ftgemm_group_create.argtypes = [vp, i32, C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(vp)]
     L.ftgemm_group_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
@@ -146,7 +147,7 @@ def lib():
     L.ftgemm_last_error.restype = C.c_char_p
     for fn in ("ftgemm_create", "ftgemm_destroy", "ftgemm_set_stream", "ftgemm_set_schedule",
                "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
-               "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing",
+               "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing", "ftgemm_set_tc_pair",
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
                "ftgemm_group_create", "ftgemm_group_plan", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_grouped_gemm_dev", "ftgemm_group_bind_rule",
@@ -228,6 +229,11 @@ class Handle:
 
     def set_stream(self, stream):
         _check(lib().ftgemm_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_tc_pair(self, enable):
+        """Tensor-core GEMMs (and groups created later) on 2-CTA pairs (True),
+        single CTAs (False), or by operand type (None, the default)."""
+        _check(lib().ftgemm_set_tc_pair(self._h, -1 if enable is None else (1 if enable else 0)))
 
     def set_schedule(self, sched: Schedule | dict | None):
         if isinstance(sched, dict):

@@ -212,6 +212,10 @@ struct alignas(128) TcProbMaps {
   CUtensorMap B;  // B^T: dims {K, N}, box {k-block, data columns}; b_mn: B, dims {N, K}, box {64, k-block}
   CUtensorMap W;  // pieces of B e:   dims {K, 8 * tiles_n}, box {k-block, 8}
   CUtensorMap V;  // pieces of e^T A: dims {K, 8 * tiles_m}, box {k-block, 8}
+  // CTA pairs (K-major B^T): B holds the first 128 columns of a pair's MMA
+  // tile (box {k-block, 128}), B1 the second half's data columns (box
+  // {k-block, 120} with checksums, whose pieces follow from W; else 128)
+  CUtensorMap B1;
 };
 
 struct TcMapsBatch {

@@ -49,7 +49,15 @@
 
 namespace ftg {
 
-template <int DT, bool ABFT>
+// PAIR: a 2-CTA cluster computes a 256 x 256 MMA tile with one cta_group::2
+// MMA (issued by the even CTA): each CTA holds 128 rows of A (its own 120 x
+// 248 data tile with checksums) and half of B's 256 columns, and its tensor
+// memory holds its 128 rows of the accumulator, so the epilogue is the same
+// as a single CTA's.  Per SM a k-block then moves 32 KB of operands into
+// shared memory instead of 48 KB, and the ring holds 6 stages instead of 4.
+constexpr int TC_PAIR_STAGES = 6, TC_MAX_STAGES = 6;
+
+template <int DT, bool ABFT, bool PAIR = false>
 struct TcCfg {
   static constexpr int BM = TC_BM, BN = TC_BN;        // MMA tile
   static constexpr int CSR = ABFT ? TC_CS_SLOTS : 0;  // checksum rows of A / columns of B
@@ -57,9 +65,10 @@ struct TcCfg {
   static constexpr int ELEM = DT == 0 ? 2 : 1;        // bytes per operand element
   static constexpr int BK = 128 / ELEM;               // one 128-byte row per k-block
   static constexpr int UK = 32 / ELEM;                // K per MMA instruction
-  static constexpr int STAGES = 4;
-  static constexpr int A_BYTES = BM * 128;            // 16 KB
-  static constexpr int B_BYTES = BN * 128;            // 32 KB
+  static constexpr int STAGES = PAIR ? TC_PAIR_STAGES : 4;
+  static constexpr int A_BYTES = BM * 128;                   // 16 KB
+  static constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * 128;  // 32 KB, or 16 KB a CTA of a pair
+  static constexpr int MMA_M = PAIR ? 2 * BM : BM;            // rows of one MMA
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   // epilogue warps: with checksums two warpgroups (each tile's columns split
   // between them), without one; plus the TMA and MMA warps
@@ -105,10 +114,8 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
   else tc_mma_f8(d, a, b, idesc, acc);
 }
 
-constexpr int TC_STAGES = 4;
-
 struct TcSmemTail {
-  uint64_t full[TC_STAGES], empty[TC_STAGES];
+  uint64_t full[TC_MAX_STAGES], empty[TC_MAX_STAGES];
   uint64_t acc_full[2], acc_empty[2];
   uint32_t tmem_base;
   int abort;
@@ -139,7 +146,9 @@ struct TcSmemTail {
 
 static_assert(offsetof(TcSmemTail, colpart) % 16 == 0 && offsetof(TcSmemTail, stg) % 16 == 0,
               "vector stores into the epilogue's shared arrays");
-static_assert(1024 + TC_STAGES * TcCfg<0, true>::STAGE_BYTES + sizeof(TcSmemTail) <= 227 * 1024,
+static_assert(1024 + TcCfg<0, true>::STAGES * TcCfg<0, true>::STAGE_BYTES + sizeof(TcSmemTail) <= 227 * 1024 &&
+                  1024 + TcCfg<0, true, true>::STAGES * TcCfg<0, true, true>::STAGE_BYTES + sizeof(TcSmemTail) <=
+                      227 * 1024,
               "dynamic shared memory within the 227 KB a CTA may use");
 
 // Named barrier 1 over the N epilogue threads (128 or 256).
@@ -150,17 +159,30 @@ __device__ __forceinline__ void epi_bar() {
   else asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
-// The tiles one CTA runs.  With a problem table: the CTA's slice of the
-// host-built tile list.  With one inline problem: every gridDim.x-th entry
-// of a raster of TC_GROUP_M tile rows by all tile columns, column-major
-// inside a group.
+// The tiles one worker (a CTA, or a CTA pair) runs.  With a problem table:
+// the worker's slice of the host-built tile list.  With one inline problem:
+// every n-th entry (n workers) of a raster of TC_GROUP_M tile rows by all
+// tile columns, column-major inside a group.  A pair's tile is two tile rows
+// high: its tm counts pairs of tile rows, and CTA r of the pair takes tile
+// row 2 tm + r.
 struct TcTile {
   int pi, tm, tn, nkb;
 };
-__device__ __forceinline__ int tc_my_count(const TcBatch& b) {
-  if (b.table) return b.cta_start[blockIdx.x + 1] - b.cta_start[blockIdx.x];
-  return (int)blockIdx.x < b.total_tiles ? (b.total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+template <bool PAIR>
+__device__ __forceinline__ int tc_worker() {
+  return PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
 }
+template <bool PAIR>
+__device__ __forceinline__ int tc_my_count(const TcBatch& b) {
+  const int w = tc_worker<PAIR>(), nw = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  if (b.table) return b.cta_start[w + 1] - b.cta_start[w];
+  return w < b.total_tiles ? (b.total_tiles - 1 - w) / nw + 1 : 0;
+}
+template <bool PAIR>
+__device__ __forceinline__ int tc_my_first(const TcBatch& b) {
+  return b.table ? b.cta_start[tc_worker<PAIR>()] : 0;
+}
+template <bool PAIR>
 __device__ __forceinline__ TcTile tc_my_tile(const TcBatch& b, int my0, int j) {
   TcTile x;
   if (b.table) {
@@ -169,9 +191,11 @@ __device__ __forceinline__ TcTile tc_my_tile(const TcBatch& b, int my0, int j) {
     return x;
   }
   const TcProblem& P = b.one;
-  const int id = (int)blockIdx.x + j * (int)gridDim.x, per_group = TC_GROUP_M * P.tiles_n;
-  const int first_m = (id / per_group) * TC_GROUP_M;
-  const int gsize = min(P.tiles_m - first_m, TC_GROUP_M);
+  const int nw = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int rows = PAIR ? (P.tiles_m + 1) / 2 : P.tiles_m, gm = PAIR ? TC_GROUP_M / 2 : TC_GROUP_M;
+  const int id = tc_worker<PAIR>() + j * nw, per_group = gm * P.tiles_n;
+  const int first_m = (id / per_group) * gm;
+  const int gsize = min(rows - first_m, gm);
   x.pi = 0;
   x.tm = first_m + (id % per_group) % gsize;
   x.tn = (id % per_group) / gsize;
@@ -179,18 +203,20 @@ __device__ __forceinline__ TcTile tc_my_tile(const TcBatch& b, int my0, int j) {
   return x;
 }
 
-template <int DT, bool ABFT>
-__global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
+template <int DT, bool ABFT, bool PAIR>
+__global__ void __launch_bounds__(TcCfg<DT, ABFT, PAIR>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcBatch b, const __grid_constant__ TcMapsBatch mb, const TcRun run) {
-  using Cfg = TcCfg<DT, ABFT>;
-  constexpr int BM = Cfg::BM, BN = Cfg::BN, DM = Cfg::DM, DN = Cfg::DN, BK = Cfg::BK, UK = Cfg::UK;
+  using Cfg = TcCfg<DT, ABFT, PAIR>;
+  constexpr int BN = Cfg::BN, DM = Cfg::DM, DN = Cfg::DN, BK = Cfg::BK, UK = Cfg::UK;
   constexpr int S = Cfg::STAGES, CSR = Cfg::CSR;
-  static_assert(S == TC_STAGES, "ring depth");
+  static_assert(S <= TC_MAX_STAGES, "ring depth");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~uintptr_t(1023));
   TcSmemTail& T = *reinterpret_cast<TcSmemTail*>(base + S * Cfg::STAGE_BYTES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rank = PAIR ? (int)cluster_ctarank() : 0;  // CTA of the pair (0 issues the MMAs)
+  const bool leader = rank == 0;
   auto sA = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
   auto sB = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
 
@@ -201,27 +227,38 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&T.acc_full[a], 1);
-      mbar_init(&T.acc_empty[a], Cfg::EW);  // one arrival per epilogue warp
+      mbar_init(&T.acc_empty[a], PAIR ? 2 * Cfg::EW : Cfg::EW);  // one arrival per epilogue warp (of both CTAs)
     }
     T.abort = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(&T.tmem_base, Cfg::TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(&T.tmem_base, Cfg::TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(&T.tmem_base, Cfg::TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  // the leader's barriers are initialised before the other CTA signals them
+  if constexpr (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = T.tmem_base;
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: data rows of A and B^T, then the checksum slots -----
+    // A CTA of a pair loads its own 128 rows of A and its half of B (columns
+    // 128 r .. 128 r + 127 of the MMA tile; the second half ends with the
+    // pieces of B e), and completes the bytes on the leader's barrier, which
+    // expects both CTAs' bytes.
     uint32_t it = 0;  // k-blocks issued, over all tiles of this CTA
     int last_pi = -1;
     bool dead = false;
-    const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
-    TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
+    const int n_my = tc_my_count<PAIR>(b), my0 = tc_my_first<PAIR>(b);
+    TcTile nx = n_my > 0 ? tc_my_tile<PAIR>(b, my0, 0) : TcTile{0, 0, 0, 0};
     for (int j = 0; j < n_my && !dead; ++j) {
       const TcTile x = nx;
       const TcProbMaps* mp = mb.table ? &mb.table[x.pi] : &mb.one;
@@ -229,16 +266,18 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         if (mb.table) {
           tensormap_acquire(&mp->A);
           tensormap_acquire(&mp->B);
+          if constexpr (PAIR) tensormap_acquire(&mp->B1);
           if constexpr (ABFT) {
             tensormap_acquire(&mp->W);
             tensormap_acquire(&mp->V);
           }
         }
         prefetch_tmap(&mp->A);
-        prefetch_tmap(&mp->B);
+        prefetch_tmap(rank ? &mp->B1 : &mp->B);
         last_pi = x.pi;
       }
-      const int row0 = x.tm * DM, col0 = x.tn * DN;
+      const int tm = PAIR ? 2 * x.tm + rank : x.tm;  // this CTA's tile row
+      const int row0 = tm * DM, col0 = x.tn * DN;
       const TcProblem& Px = tc_problem(b, x.pi);
       const bool mn = !ABFT && DT == 0 && Px.b_mn;
       const bool off = Px.off;  // skipped: the stages are released unloaded
@@ -249,39 +288,59 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           break;
         }
         if (off) {
-          mbar_arrive(&T.full[s]);
-          if (kb == 0 && j + 1 < n_my) nx = tc_my_tile(b, my0, j + 1);
+          if (leader) mbar_arrive(&T.full[s]);
+          if (kb == 0 && j + 1 < n_my) nx = tc_my_tile<PAIR>(b, my0, j + 1);
           continue;
         }
-        // the same byte count either way: an MN-major B is 4 boxes of 8 KB
-        mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
-        tma_load_2d(sA(s), &mp->A, &T.full[s], kb * BK, row0);
-        if (mn) {
+        if constexpr (PAIR) {
+          const uint32_t cbar = mapa_rank(&T.full[s], 0);
+          if (leader) mbar_arrive_expect_tx(&T.full[s], 2 * Cfg::STAGE_BYTES);
+          tma_load_2d_pair(sA(s), &mp->A, cbar, kb * BK, row0);
+          if (mn) {
 #pragma unroll
-          for (int g = 0; g < BN / 64; ++g)
-            tma_load_2d(sB(s) + g * Cfg::MN_BOX, &mp->B, &T.full[s], col0 + 64 * g, kb * BK);
+            for (int g = 0; g < BN / 128; ++g)
+              tma_load_2d_pair(sB(s) + g * Cfg::MN_BOX, &mp->B, cbar, col0 + 128 * rank + 64 * g, kb * BK);
+          } else {
+            tma_load_2d_pair(sB(s), rank ? &mp->B1 : &mp->B, cbar, kb * BK, col0 + 128 * rank);
+          }
+          if constexpr (ABFT) {
+            tma_load_2d_pair(sA(s) + DM * 128, &mp->V, cbar, kb * BK, tm * CSR);
+            if (rank) tma_load_2d_pair(sB(s) + (DN - 128) * 128, &mp->W, cbar, kb * BK, x.tn * CSR);
+          }
         } else {
-          tma_load_2d(sB(s), &mp->B, &T.full[s], kb * BK, col0);
-        }
-        if constexpr (ABFT) {
-          tma_load_2d(sA(s) + DM * 128, &mp->V, &T.full[s], kb * BK, x.tm * CSR);
-          tma_load_2d(sB(s) + DN * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
+          // the same byte count either way: an MN-major B is 4 boxes of 8 KB
+          mbar_arrive_expect_tx(&T.full[s], Cfg::STAGE_BYTES);
+          tma_load_2d(sA(s), &mp->A, &T.full[s], kb * BK, row0);
+          if (mn) {
+#pragma unroll
+            for (int g = 0; g < BN / 64; ++g)
+              tma_load_2d(sB(s) + g * Cfg::MN_BOX, &mp->B, &T.full[s], col0 + 64 * g, kb * BK);
+          } else {
+            tma_load_2d(sB(s), &mp->B, &T.full[s], kb * BK, col0);
+          }
+          if constexpr (ABFT) {
+            tma_load_2d(sA(s) + DM * 128, &mp->V, &T.full[s], kb * BK, tm * CSR);
+            tma_load_2d(sB(s) + DN * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
+          }
         }
         // look one tile ahead while this tile's loads are in flight
-        if (kb == 0 && j + 1 < n_my) nx = tc_my_tile(b, my0, j + 1);
+        if (kb == 0 && j + 1 < n_my) nx = tc_my_tile<PAIR>(b, my0, j + 1);
       }
     }
     if (dead) atomicExch(&T.abort, 1);
-    // let the last loads land before the CTA may exit (bounded)
-    for (uint32_t q = it > (uint32_t)S ? it - S : 0; q < it; ++q) mbar_wait(&T.full[q % S], (q / S) & 1u);
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: one 128 x 256 MMA per 32-byte k-slice ----------------
-    constexpr uint32_t idesc = tc_idesc(DT, BM, BN);
+    // let the last loads land before the CTA may exit (bounded); in a pair
+    // they complete on the leader's barriers, and the cluster barrier at
+    // the end keeps both CTAs until the leader's MMAs have read them
+    if (leader)
+      for (uint32_t q = it > (uint32_t)S ? it - S : 0; q < it; ++q) mbar_wait(&T.full[q % S], (q / S) & 1u);
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---- MMA issuer: one 128 x 256 (a pair: 256 x 256) MMA per 32-byte k-slice
+    constexpr uint32_t idesc = tc_idesc(DT, Cfg::MMA_M, BN);
     uint32_t it = 0;
     int lt = 0;  // tiles of this CTA so far
     bool dead = false;
-    const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
-    TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
+    const int n_my = tc_my_count<PAIR>(b), my0 = tc_my_first<PAIR>(b);
+    TcTile nx = n_my > 0 ? tc_my_tile<PAIR>(b, my0, 0) : TcTile{0, 0, 0, 0};
     for (; lt < n_my && !dead; ++lt) {
       const int nkb = nx.nkb;
       const bool mn = !ABFT && DT == 0 && tc_problem(b, nx.pi).b_mn;
@@ -308,12 +367,20 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
           // MN-major: UK k-rows of 128 bytes
           const uint64_t step_a = (uint64_t)(kk * 32) >> 4;
           const uint64_t step_b = mn ? (uint64_t)(kk * UK * 128) >> 4 : step_a;
-          tc_mma<DT>(d, da + step_a, db + step_b, id_t, (kb | kk) != 0);
+          if constexpr (PAIR) {
+            if constexpr (DT == 0) tc_mma_f16_pair(d, da + step_a, db + step_b, id_t, (kb | kk) != 0);
+            else tc_mma_f8_pair(d, da + step_a, db + step_b, id_t, (kb | kk) != 0);
+          } else {
+            tc_mma<DT>(d, da + step_a, db + step_b, id_t, (kb | kk) != 0);
+          }
         }
-        tc_commit(&T.empty[s]);  // the stage is free once these MMAs completed
-        if (kb == 0 && lt + 1 < n_my) nx = tc_my_tile(b, my0, lt + 1);
+        // the stage (in both CTAs of a pair) is free once these MMAs completed
+        if constexpr (PAIR) tc_commit_pair(&T.empty[s], (uint16_t)3);
+        else tc_commit(&T.empty[s]);
+        if (kb == 0 && lt + 1 < n_my) nx = tc_my_tile<PAIR>(b, my0, lt + 1);
       }
-      tc_commit(&T.acc_full[ab]);
+      if constexpr (PAIR) tc_commit_pair(&T.acc_full[ab], (uint16_t)3);
+      else tc_commit(&T.acc_full[ab]);
     }
     if (dead) atomicExch(&T.abort, 1);
     // let the last MMAs finish before TMEM may be released (bounded)
@@ -330,17 +397,25 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
     const int r = lq * 32 + lane;       // tile row == TMEM lane
     const int q = eh * 128 + r;         // this thread's index among the epilogue threads
     const bool data_row = r < DM;
-    const int n_my = tc_my_count(b), my0 = b.table ? b.cta_start[blockIdx.x] : 0;
-    TcTile nx = n_my > 0 ? tc_my_tile(b, my0, 0) : TcTile{0, 0, 0, 0};
+    const int n_my = tc_my_count<PAIR>(b), my0 = tc_my_first<PAIR>(b);
+    TcTile nx = n_my > 0 ? tc_my_tile<PAIR>(b, my0, 0) : TcTile{0, 0, 0, 0};
     bool dead = false;
+    // hand an accumulator back to the MMA warp (the leader's, in a pair)
+    auto acc_release = [&](int ab) {
+      if constexpr (PAIR) mbar_arrive_cluster(mapa_rank(&T.acc_empty[ab], 0));
+      else mbar_arrive(&T.acc_empty[ab]);
+    };
     for (int lt = 0; lt < n_my; ++lt) {
       const TcTile x = nx;
-      if (lt + 1 < n_my) nx = tc_my_tile(b, my0, lt + 1);  // consumed next tile
+      if (lt + 1 < n_my) nx = tc_my_tile<PAIR>(b, my0, lt + 1);  // consumed next tile
       const TcProblem& P = tc_problem(b, x.pi);
       const int ab = lt & 1;
-      const int row0 = x.tm * DM, col0 = x.tn * DN, gr = row0 + r;
+      const int tm = PAIR ? 2 * x.tm + rank : x.tm;  // this CTA's tile row
+      const int row0 = tm * DM, col0 = x.tn * DN, gr = row0 + r;
       const uint32_t tl = tmem + (uint32_t)(ab * BN) + ((uint32_t)(lq * 32) << 16);
-      if (P.off) {
+      // a problem skipped by a rebinding, or the second tile row of a pair
+      // past the problem's last one
+      if (P.off || tm >= P.tiles_m) {
         // a problem skipped by a device-array rebinding: its accumulator
         // (from unloaded stages) is handed back without a store or a check
         if (!dead && !mbar_wait(&T.acc_full[ab], (lt >> 1) & 1)) {
@@ -350,7 +425,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         tc_fence_after();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&T.acc_empty[ab]);
+        if (lane == 0) acc_release(ab);
         continue;
       }
       // Everything this tile needs from global memory, and its threshold,
@@ -363,7 +438,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       const int c_vec = P.c_vec;
       const long long ldc = P.ldc;
       float* const Cp = P.C;
-      const int my_tile = P.tile_start + x.tm * P.tiles_n + x.tn;
+      const int my_tile = P.tile_start + tm * P.tiles_n + x.tn;
       const bool has_fault =
           run.nfaults > 0 && ((run.fault_bits[my_tile >> 5] >> (my_tile & 31)) & 1u);
       float nA_r = 0.f, froA_t = 0.f, froB_t = 0.f, nB_c[2] = {0.f, 0.f};
@@ -373,7 +448,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       float feat[MLP_IN];
       if constexpr (ABFT) {
         nA_r = (data_row && gr < pM) ? P.nA[gr] : 0.f;
-        froA_t = P.froA[x.tm];
+        froA_t = P.froA[tm];
         froB_t = P.froB[x.tn];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -383,7 +458,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
 #pragma unroll
         for (int q = 0; q < Cfg::NPIECE; ++q) {
           wsc[q] = P.wscale[(size_t)x.tn * CSR + q];
-          vsc[q] = P.vscale[(size_t)x.tm * CSR + q];
+          vsc[q] = P.vscale[(size_t)tm * CSR + q];
         }
         // ----- threshold of this tile -----
         // analytic: lambda * u times the norms plus the growth term
@@ -394,7 +469,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
         // fallback for a non-finite or non-positive output
         const int rows = min(DM, pM - row0), cols = min(DN, pN - col0);
         feat[0] = log2f((float)P.K) * 0.0625f;
-        feat[1] = P.coA ? P.coA[x.tm] : 0.f;
+        feat[1] = P.coA ? P.coA[tm] : 0.f;
         feat[2] = P.coB ? P.coB[x.tn] : 0.f;
         feat[3] = DT == 0 ? 0.5f : 1.f;
         feat[4] = log2f((float)rows * (float)cols) * 0.0625f;
@@ -741,7 +816,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
             const double dC = nc ? T.sum_c[jc] - (double)T.ccol[jc] : 0.0;
             const float tR = nr ? T.tr[ir] : 0.f, tC = nc ? T.tc[jc] : 0.f;
             ftgemm_fault_record rec;
-            rec.tile_m = x.tm; rec.tile_n = x.tn; rec.kstep = x.nkb - 1;
+            rec.tile_m = tm; rec.tile_n = x.tn; rec.kstep = x.nkb - 1;
             rec.problem = P.id; rec.reserved = 0;
             rec.row = ir >= 0 ? row0 + ir : -1;
             rec.col = jc >= 0 ? col0 + jc : -1;
@@ -790,35 +865,63 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT>::THREADS, 1)
       // this warp is done with the accumulator: hand it back to the MMA warp
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&T.acc_empty[ab]);
+      if (lane == 0) acc_release(ab);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (tid == 0 && T.abort) atomicAdd(&run.rep->timeouts, 1);
+  // a pair stays together until both CTAs are done with each other's
+  // barriers and tensor memory
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, Cfg::TMEM_COLS);
+    if constexpr (PAIR) tmem_dealloc_pair(tmem, Cfg::TMEM_COLS);
+    else tmem_dealloc(tmem, Cfg::TMEM_COLS);
   }
 }
 
-template <int DT, bool ABFT>
+template <int DT, bool ABFT, bool PAIR>
 cudaError_t launch_tc_impl(const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid, cudaStream_t st) {
-  using Cfg = TcCfg<DT, ABFT>;
+  using Cfg = TcCfg<DT, ABFT, PAIR>;
   const size_t smem = 1024 + (size_t)Cfg::STAGES * Cfg::STAGE_BYTES + sizeof(TcSmemTail);
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<DT, ABFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<DT, ABFT, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  tc_gemm_kernel<DT, ABFT><<<grid, Cfg::THREADS, smem, st>>>(b, mb, run);
-  return cudaGetLastError();
+  if constexpr (!PAIR) {
+    tc_gemm_kernel<DT, ABFT, false><<<grid, Cfg::THREADS, smem, st>>>(b, mb, run);
+    return cudaGetLastError();
+  } else {
+    // clusters of two CTAs (an SM pair each)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(Cfg::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<DT, ABFT, true>, b, mb, run);
+  }
 }
 
-// Persistent launch over b.total_tiles tiles with `grid` CTAs (<= one per SM).
-cudaError_t launch_tc_gemm(int dt, bool abft, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run, int grid,
-                           cudaStream_t st) {
-  if (dt == 0) return abft ? launch_tc_impl<0, true>(b, mb, run, grid, st) : launch_tc_impl<0, false>(b, mb, run, grid, st);
-  return abft ? launch_tc_impl<1, true>(b, mb, run, grid, st) : launch_tc_impl<1, false>(b, mb, run, grid, st);
+// Persistent launch over b.total_tiles tiles with `grid` CTAs (<= one per SM;
+// pair: an even number, two CTAs per tile of two tile rows).
+cudaError_t launch_tc_gemm(int dt, bool abft, bool pair, const TcBatch& b, const TcMapsBatch& mb, const TcRun& run,
+                           int grid, cudaStream_t st) {
+  if (pair) {
+    if (dt == 0)
+      return abft ? launch_tc_impl<0, true, true>(b, mb, run, grid, st) : launch_tc_impl<0, false, true>(b, mb, run, grid, st);
+    return abft ? launch_tc_impl<1, true, true>(b, mb, run, grid, st) : launch_tc_impl<1, false, true>(b, mb, run, grid, st);
+  }
+  if (dt == 0)
+    return abft ? launch_tc_impl<0, true, false>(b, mb, run, grid, st) : launch_tc_impl<0, false, false>(b, mb, run, grid, st);
+  return abft ? launch_tc_impl<1, true, false>(b, mb, run, grid, st) : launch_tc_impl<1, false, false>(b, mb, run, grid, st);
 }
 
 }  // namespace ftg

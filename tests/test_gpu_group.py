@@ -22,9 +22,12 @@ def ft():
     return ft
 
 
-@pytest.fixture()
-def handle(ft):
+@pytest.fixture(params=[False, True], ids=["cta", "pair"])
+def handle(ft, request):
+    # every test runs on single CTAs and on CTA pairs (cta_group::2 MMAs),
+    # which must give the same tiles, checksums and records
     h = ft.Handle(0)
+    h.set_tc_pair(request.param)
     yield h
     h.close()
 

@@ -20,9 +20,12 @@ def ft():
     return ft
 
 
-@pytest.fixture()
-def handle(ft):
+@pytest.fixture(params=[False, True], ids=["cta", "pair"])
+def handle(ft, request):
+    # every test runs on single CTAs and on CTA pairs (cta_group::2 MMAs),
+    # which must give the same tiles, checksums and records
     h = ft.Handle(0)
+    h.set_tc_pair(request.param)
     yield h
     h.close()
 
@@ -129,7 +132,7 @@ def test_tc_fp8_normal_within_bound(ft, handle, orc, level):
 
 @pytest.mark.parametrize("dt", ["bf16", "fp8"])
 def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
-    """Seeded faults in several tiles (config-4 style, reduced): every fault is
+    """Seeded faults in several tiles (the tensor-core square workload's, reduced): every fault is
     flagged at its element, corrected, and C matches the fault-free result
     within the bound; the records match the oracle's (tile-level unit, one
     verification after the last k-step)."""
