@@ -379,6 +379,16 @@ int ftgemm_group_bind_rule(const ftgemm_problem* created, const ftgemm_problem* 
  * counterpart in the paper.) */
 int ftgemm_group_destroy(ftgemm_group_t group);
 
+/* ftgemm_group_create with the schedule chosen by measurement: the group is
+ * built on single CTAs and on CTA pairs, each run `reps` times after one
+ * warm-up (every C is overwritten), and the faster is returned in *out (the
+ * other is released); *pair_out (may be NULL): 1 pairs, 0 single CTAs.
+ * Synchronises the handle's stream.  Errors: FTGEMM_ERR_ARG (NULL, count,
+ * reps < 1) and those of ftgemm_group_create / ftgemm_grouped_gemm. */
+int ftgemm_group_autotune(ftgemm_handle_t handle, int32_t count, const ftgemm_problem* problems,
+                          ftgemm_dtype dtype, ftgemm_ft_level ft_level, int32_t reps, ftgemm_group_t* out,
+                          int32_t* pair_out);
+
 /* Autotuner (F32 SIMT path).  The paper picks kernel parameters per shape
  * by a code-generation search (Section 3.2); here the compiled tile tuples,
  * split-K and the verification cadence are timed on the given operands and
@@ -396,6 +406,19 @@ int ftgemm_autotune(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, con
                     int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc,
                     ftgemm_ft_level ft_level, int32_t reps, ftgemm_schedule* out,
                     ftgemm_ft_level* level_out);
+
+/* Autotuner for the tensor-core path (the parameter selection of Section
+ * 3.2, done by measurement): times ftgemm_gemm on the given operands (C is
+ * overwritten; alpha 1, beta 0, no faults) on single CTAs and on CTA pairs,
+ * `reps` times each after one warm-up, and caches the faster for (m, n, k,
+ * dtype, ft_level); later ftgemm_gemm calls with that shape use it while
+ * ftgemm_set_tc_pair is at its default (-1).  dtype BF16 or E4M3 (set the
+ * fp8 scales first), ft_level OFF or TILE.  *pair_out (may be NULL): 1 if
+ * pairs were faster, else 0.  Synchronises the handle's stream.  Errors:
+ * FTGEMM_ERR_ARG, FTGEMM_ERR_UNSUPPORTED, and those of ftgemm_gemm. */
+int ftgemm_autotune_tc(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, float* C, int64_t ldc, ftgemm_dtype dtype,
+                       ftgemm_ft_level ft_level, int32_t reps, int32_t* pair_out);
 
 /* Self-test of the bounded device waits (no counterpart in the paper).
  * Every mbarrier wait of the GEMM kernels gives up after about 2^31 SM

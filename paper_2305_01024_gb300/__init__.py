@@ -117,6 +117,10 @@ def lib():
     L.ftgemm_quantize.argtypes = [vp, i64, vp, vp, C.c_int, C.POINTER(C.c_float)]
     L.ftgemm_enable_timing.argtypes = [vp, C.c_int]
     L.ftgemm_set_tc_pair.argtypes = [vp, C.c_int]
+    L.ftgemm_autotune_tc.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_int, C.c_int, i32,
+                                     C.POINTER(i32)]
+    L.ftgemm_group_autotune.argtypes = [vp, i32, C.POINTER(Problem), C.c_int, C.c_int, i32, C.POINTER(vp),
+                                        C.POINTER(i32)]
     L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.ftgemm_group_create.argtypes = [vp, i32, C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(vp)]
     L.ftgemm_group_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
@@ -148,6 +152,7 @@ def lib():
     for fn in ("ftgemm_create", "ftgemm_destroy", "ftgemm_set_stream", "ftgemm_set_schedule",
                "ftgemm_get_schedule", "ftgemm_set_threshold", "ftgemm_gemm",
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing", "ftgemm_set_tc_pair",
+               "ftgemm_autotune_tc", "ftgemm_group_autotune",
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
                "ftgemm_group_create", "ftgemm_group_plan", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_grouped_gemm_dev", "ftgemm_group_bind_rule",
@@ -229,6 +234,18 @@ class Handle:
 
     def set_stream(self, stream):
         _check(lib().ftgemm_set_stream(self._h, _stream_ptr(stream)))
+
+    def autotune_tc(self, A, B, C_out, level=FT_TILE, dtype=BF16, reps: int = 3):
+        """Time single CTAs against CTA pairs for this shape (C_out is
+        overwritten) and cache the faster; returns True for pairs."""
+        if isinstance(level, str):
+            level = LEVELS[level]
+        M, K = A.shape
+        N = B.shape[1]
+        pick = C.c_int32(0)
+        _check(lib().ftgemm_autotune_tc(self._h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C_out),
+                                        C_out.stride(0), dtype, level, reps, C.byref(pick)))
+        return bool(pick.value)
 
     def set_tc_pair(self, enable):
         """Tensor-core GEMMs (and groups created later) on 2-CTA pairs (True),
@@ -496,13 +513,23 @@ class Group:
     scale_a, scale_b]); A m x k and B k x n of `dtype` (bf16 tensors, or
     uint8 E4M3 codes), C fp32 m x n.  The tensors must outlive the group."""
 
-    def __init__(self, handle: "Handle", problems, dtype=BF16, level=FT_TILE):
+    def __init__(self, handle: "Handle", problems, dtype=BF16, level=FT_TILE, tune: int = 0):
+        """tune > 0: the schedule (single CTAs or CTA pairs) is chosen by
+        running the group both ways `tune` times (every C is overwritten);
+        self.pair tells which."""
         self.handle = handle
         self.count = len(problems)
         arr = problem_structs(problems)
         self._keep = list(problems)
         self._g = C.c_void_p()
-        _check(lib().ftgemm_group_create(handle._h, self.count, arr, dtype, level, C.byref(self._g)))
+        self.pair = None
+        if tune > 0:
+            pick = C.c_int32(0)
+            _check(lib().ftgemm_group_autotune(handle._h, self.count, arr, dtype, level, tune, C.byref(self._g),
+                                               C.byref(pick)))
+            self.pair = bool(pick.value)
+        else:
+            _check(lib().ftgemm_group_create(handle._h, self.count, arr, dtype, level, C.byref(self._g)))
 
     def tiles(self):
         tm = (C.c_int32 * self.count)()

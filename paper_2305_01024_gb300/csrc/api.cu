@@ -150,6 +150,8 @@ struct ftgemm_ctx {
   size_t mlp_ws_floats = 0;
   // autotuned SIMT schedules: (m, n, k, requested level) -> (schedule, level to run)
   std::map<std::tuple<int64_t, int64_t, int64_t, int>, std::pair<ftgemm_schedule, int>> tuned;
+  // autotuned tensor-core schedules: (m, n, k, dtype, level) -> 1 CTA pairs, 0 single CTAs
+  std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, int> tc_tuned;
   // second workspace (non-fused baseline: its buffers live across the GEMM calls it makes)
   float* ws2 = nullptr;
   size_t ws2_floats = 0;
@@ -413,8 +415,12 @@ extern "C" int ftgemm_report_fetch(ftgemm_handle_t h, ftgemm_report* out);
 // 8192^3 and 16384^3, with or without checksums), e4m3 on single CTAs (its
 // operands are half the bytes per flop; pairs measured level without
 // checksums and 4% slower with them).
-static bool tc_use_pair(const ftgemm_ctx* h, int dt) {
-  return h->tc_pair < 0 ? dt == 0 : h->tc_pair != 0;
+// A shape tuned by ftgemm_autotune_tc takes the schedule measured fastest.
+static bool tc_use_pair(const ftgemm_ctx* h, int dt, int64_t m = 0, int64_t n = 0, int64_t k = 0, int level = 0) {
+  if (h->tc_pair >= 0) return h->tc_pair != 0;
+  const auto it = h->tc_tuned.find(std::make_tuple(m, n, k, dt, level));
+  if (it != h->tc_tuned.end()) return it->second != 0;
+  return dt == 0;
 }
 
 // Shape, tiling and epilogue fields of a tensor-core problem.
@@ -528,7 +534,7 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   P.mlp_scale = h->mlp_scale;
   b.table = nullptr;
   b.nprob = 1;
-  const bool pair = tc_use_pair(h, dt);
+  const bool pair = tc_use_pair(h, dt, m, n, k, (int)level);
   const int ntiles = P.tiles_m * P.tiles_n;
   // the raster's tiles: a pair's tile is two tile rows high
   b.total_tiles = pair ? ((P.tiles_m + 1) / 2) * P.tiles_n : ntiles;
@@ -1619,6 +1625,93 @@ int ftgemm_autotune(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const fl
   h->tuned[std::make_tuple(m, n, k, (int)level)] = {best, (int)best_lv};
   if (out) *out = best;
   if (level_out) *level_out = best_lv;
+  return FTGEMM_OK;
+}
+
+// ---- tensor-core autotuner: single CTAs or CTA pairs, by measurement ----
+
+// Best of `reps` timings of `call` (after one warm-up) on the handle's stream.
+template <class F>
+static int time_best(ftgemm_ctx* h, F call, int reps, float* best_ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a);
+    FAIL(FTGEMM_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  int rc = call();
+  float best = 3.4e38f;
+  for (int r = 0; rc == FTGEMM_OK && r < reps; ++r) {
+    e = cudaEventRecord(a, h->stream);
+    if (e == cudaSuccess) rc = call();
+    if (e == cudaSuccess && rc == FTGEMM_OK) e = cudaEventRecord(b, h->stream);
+    if (e == cudaSuccess && rc == FTGEMM_OK) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess && rc == FTGEMM_OK) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess && rc == FTGEMM_OK) rc = FTGEMM_ERR_CUDA;
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  *best_ms = best;
+  return FTGEMM_OK;
+}
+
+int ftgemm_autotune_tc(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, float* C, int64_t ldc, ftgemm_dtype dtype,
+                       ftgemm_ft_level level, int32_t reps, int32_t* pair_out) {
+  if (!h || !A || !B || !C || m <= 0 || n <= 0 || k <= 0 || reps < 1 || m > INT32_MAX || n > INT32_MAX ||
+      k > INT32_MAX || lda < k || ldb < n || ldc < n)
+    FAIL(FTGEMM_ERR_ARG, "ftgemm_autotune_tc: bad argument");
+  if (dtype != FTGEMM_BF16 && dtype != FTGEMM_E4M3)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_autotune_tc: bf16 or e4m3 operands only");
+  if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_autotune_tc: level OFF or TILE, not %d", (int)level);
+  CK(cudaSetDevice(h->device));
+  const int saved = h->tc_pair;
+  float ms[2] = {0.f, 0.f};
+  for (int p = 0; p < 2; ++p) {
+    h->tc_pair = p;
+    int rc = time_best(
+        h, [&]() { return tc_gemm(h, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, dtype, level, nullptr, nullptr); },
+        reps, &ms[p]);
+    if (rc) {
+      h->tc_pair = saved;
+      return rc;
+    }
+  }
+  h->tc_pair = saved;
+  const int pick = ms[1] < ms[0] ? 1 : 0;
+  const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
+  h->tc_tuned[std::make_tuple(m, n, k, dt, (int)level)] = pick;
+  if (pair_out) *pair_out = pick;
+  return FTGEMM_OK;
+}
+
+int ftgemm_group_autotune(ftgemm_handle_t h, int32_t count, const ftgemm_problem* problems, ftgemm_dtype dtype,
+                          ftgemm_ft_level level, int32_t reps, ftgemm_group_t* out, int32_t* pair_out) {
+  if (!h || !problems || !out || count <= 0 || reps < 1) FAIL(FTGEMM_ERR_ARG, "ftgemm_group_autotune: bad argument");
+  *out = nullptr;
+  const int saved = h->tc_pair;
+  ftgemm_group_t g[2] = {nullptr, nullptr};
+  float ms[2] = {0.f, 0.f};
+  int rc = FTGEMM_OK;
+  for (int p = 0; p < 2 && rc == FTGEMM_OK; ++p) {
+    h->tc_pair = p;
+    rc = ftgemm_group_create(h, count, problems, dtype, level, &g[p]);
+    if (rc == FTGEMM_OK) rc = time_best(h, [&]() { return ftgemm_grouped_gemm(h, g[p]); }, reps, &ms[p]);
+  }
+  h->tc_pair = saved;
+  if (rc) {
+    for (int p = 0; p < 2; ++p) ftgemm_group_destroy(g[p]);
+    return rc;
+  }
+  const int pick = ms[1] < ms[0] ? 1 : 0;
+  ftgemm_group_destroy(g[1 - pick]);
+  *out = g[pick];
+  if (pair_out) *pair_out = pick;
   return FTGEMM_OK;
 }
 

@@ -1,7 +1,9 @@
-"""The autotuner on the irregular FP32 shapes of the paper's evaluation
+"""The autotuners.  The fp32 one on the irregular FP32 shapes of the paper's evaluation
 (tall-skinny, small-K, long-K, unaligned), each with one seeded fault, at
 full size.  C is checked against the oracle on sampled rows (every row the
-fault touches among them); the fault is located and corrected."""
+fault touches among them); the fault is located and corrected.  The
+tensor-core ones (single CTAs or CTA pairs) on a GEMM and on a group, whose
+results stay exact on integer inputs whichever schedule they pick."""
 import numpy as np
 import pytest
 
@@ -60,4 +62,58 @@ def test_autotuned_irregular_shape_one_fault(ft, orc, shape):
     slack = np.zeros_like(got)
     slack[rows.index(i), j] = rep.records[0]["tau"]  # the corrected value carries the threshold
     assert np.all(np.abs(got - ref) <= bound + slack)
+    h.close()
+
+
+# ---- tensor-core schedules: single CTAs or CTA pairs, by measurement -------
+
+def _int_bf16(shape, seed):
+    import torch
+    x = synth.integers(shape, seed).astype(np.float32)
+    return x, torch.from_numpy(x).cuda().to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("level", ["off", "tile"])
+def test_tc_autotune_picks_a_schedule_and_keeps_results_exact(ft, level):
+    """ftgemm_autotune_tc times both schedules on the operands and caches the
+    faster for the shape; calls of that shape then run on it, and stay
+    exact on integer inputs whichever it is."""
+    import torch
+    M, N, K = 1000, 1536, 520
+    A, dA = _int_bf16((M, K), 7100)
+    B, dB = _int_bf16((K, N), 7101)
+    h = ft.Handle(0)
+    C = torch.empty(M, N, device="cuda")
+    pick = h.autotune_tc(dA, dB, C, level=ft.LEVELS[level], dtype=ft.BF16, reps=2)
+    assert isinstance(pick, bool)
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    assert np.array_equal(C.cpu().numpy().astype(np.int64), ref)  # the last timed call
+    C.zero_()
+    rep = h.gemm(dA, dB, C, level=ft.LEVELS[level], dtype=ft.BF16)
+    assert np.array_equal(C.cpu().numpy().astype(np.int64), ref) and rep.detected == 0
+    with pytest.raises(ft.FtgemmError):
+        h.autotune_tc(dA, dB, C, level=ft.FT_BLOCK, dtype=ft.BF16)
+    h.close()
+
+
+def test_group_autotune_returns_the_faster_schedule(ft):
+    import torch
+    shapes = [(300, 500, 256), (1000, 260, 640), (64, 64, 64), (777, 1248, 1008)]
+    h = ft.Handle(0)
+    host, probs = [], []
+    for q, (M, N, K) in enumerate(shapes):
+        A, dA = _int_bf16((M, K), 7200 + 2 * q)
+        B, dB = _int_bf16((K, N), 7201 + 2 * q)
+        host.append((A, B))
+        probs.append((dA, dB, torch.empty(M, N, device="cuda")))
+    g = ft.Group(h, probs, dtype=ft.BF16, level=ft.FT_TILE, tune=2)
+    assert g.pair in (True, False)
+    for pr in probs:
+        pr[2].zero_()
+    g.run()
+    torch.cuda.synchronize()
+    assert h.report_fetch().detected == 0
+    for (A, B), pr in zip(host, probs):
+        assert np.array_equal(pr[2].cpu().numpy().astype(np.int64), A.astype(np.int64) @ B.astype(np.int64))
+    g.close()
     h.close()
