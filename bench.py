@@ -352,7 +352,10 @@ def run_reference(args):
 # side measurements (tensor-core squares, the 512-problem group, irregular fp32 shapes)
 # ---------------------------------------------------------------------------
 
-TDM, TDN = 120, 248  # tensor-core data tile of C with the checksums in the MMA tile
+# tensor-core data tile of C with the checksums in the MMA tile (ftgemm_tc_tile):
+# 125 x 252 for bf16, 123 x 248 for e4m3 (keyed by the dtype code)
+TDM = {1: 125, 2: 123}
+TDN = {1: 252, 2: 248}
 
 
 def _peaks():
@@ -362,20 +365,22 @@ def _peaks():
         return {}
 
 
-def _tile_faults(synth, seed, count, M, N, K, kblk, unit=1.0, lo=1e-2):
-    """`count` faults on distinct 120 x 248 tiles, |delta| log-uniform in
-    [lo, 1e3] x the expected tile maximum of an N(0,1) product (4 sqrt K),
-    in accumulator units (`unit` = 1 / (scale_a scale_b) for e4m3 codes)."""
-    tm, tn = -(-M // TDM), -(-N // TDN)
+def _tile_faults(synth, seed, count, M, N, K, dt, unit=1.0, lo=1e-2):
+    """`count` faults on distinct data tiles of dtype code `dt`, |delta|
+    log-uniform in [lo, 1e3] x the expected tile maximum of an N(0,1) product
+    (4 sqrt K), in accumulator units (`unit` = 1 / (scale_a scale_b) for e4m3
+    codes)."""
+    tdm, tdn, kblk = TDM[dt], TDN[dt], 64 if dt == 1 else 128
+    tm, tn = -(-M // tdm), -(-N // tdn)
     nks = -(-K // kblk)
-    pos = synth.fault_positions(seed, count, tm, tn, nks, TDM, TDN, M, N, nks)
+    pos = synth.fault_positions(seed, count, tm, tn, nks, tdm, tdn, M, N, nks)
     mags = synth.log_uniform(seed + 1, count, lo, 1e3)
     sign = synth.unit(seed + 2, count)
     return [(a, b, ks, r, c, float((1 if sg < 0.5 else -1) * g * 4 * math.sqrt(K) * unit))
             for (a, b, ks, r, c), g, sg in zip(pos, mags, sign)]
 
 
-def _above_threshold(A, B, i, j, r0, c0, lam=32.0, mu=8.0):
+def _above_threshold(A, B, i, j, r0, c0, tdm, tdn, lam=32.0, mu=8.0):
     """|delta| that the analytic threshold flags on both the row and the
     column of element (i, j) of the tile at (r0, c0), verified once after the
     whole K: the larger of lam*u*norms + mu*u*sqrt(K)*|checksum| over the two
@@ -386,8 +391,8 @@ def _above_threshold(A, B, i, j, r0, c0, lam=32.0, mu=8.0):
         return (x.view(torch.float8_e4m3fn) if x.dtype == torch.uint8 else x).double()
     M, N = A.shape[0], B.shape[1]
     K = A.shape[1]
-    AI = val(A[r0:min(M, r0 + TDM)])
-    BJ = val(B[:, c0:min(N, c0 + TDN)])
+    AI = val(A[r0:min(M, r0 + tdm)])
+    BJ = val(B[:, c0:min(N, c0 + tdn)])
     ai, bj = val(A[i]), val(B[:, j])
     c_r = (ai @ BJ.sum(1)).abs()
     c_c = (AI.sum(0) @ bj).abs()
@@ -423,7 +428,8 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
     Bf = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 1), dev)
     C = torch.empty(n, n, device=dev)
     peaks = _peaks()
-    out = {"workload": f"M=N=K={n}, A,B~N(0,1), alpha=1, beta=0, TILE level (120x248 data tile)"}
+    out = {"workload": f"M=N=K={n}, A,B~N(0,1), alpha=1, beta=0, TILE level "
+                       f"({TDM[ft.BF16]}x{TDN[ft.BF16]} bf16, {TDM[ft.E4M3]}x{TDN[ft.E4M3]} e4m3 data tiles)"}
     rows = sorted({int(u * n) for u in synth.unit(synth.workload_seed("tc_square", 5), 16)})
     for name, dt in (("bf16", ft.BF16), ("e4m3", ft.E4M3)):
         if dt == ft.BF16:
@@ -466,11 +472,12 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
         r["overhead_pct"] = 100.0 * (r["off_tflops"] / r["tile_tflops"] - 1.0)
         h.report_fetch()
         # 16 seeded faults in one GEMM: corrected at their positions?
-        faults = _tile_faults(synth, synth.workload_seed("tc_square", 20 + dt), 16, n, n, n, 64 if dt == ft.BF16 else 128,
-                              unit=1.0 / (sa * sb))
+        faults = _tile_faults(synth, synth.workload_seed("tc_square", 20 + dt), 16, n, n, n, dt, unit=1.0 / (sa * sb))
         rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=dt, inject=faults)
-        found, false = _count(rep.records, faults, lambda f: (0, f[0] * TDM + f[3], f[1] * TDN + f[4]))
-        above = sum(abs(f[5]) > _above_threshold(A, B, f[0] * TDM + f[3], f[1] * TDN + f[4], f[0] * TDM, f[1] * TDN)
+        tdm, tdn = TDM[dt], TDN[dt]
+        found, false = _count(rep.records, faults, lambda f: (0, f[0] * tdm + f[3], f[1] * tdn + f[4]))
+        above = sum(abs(f[5]) > _above_threshold(A, B, f[0] * tdm + f[3], f[1] * tdn + f[4], f[0] * tdm, f[1] * tdn,
+                                                 tdm, tdn)
                     for f in faults)
         r["faults"] = {"injected": len(faults), "above_analytic_threshold": above,
                        "corrected_at_position": found, "false_alarms": false,
@@ -551,7 +558,8 @@ def grouped_extras(ft, h, synth, dev, timed_loop):
                 for q, cnt in sorted(by_prob.items()):
                     M, N, K = shapes[q]
                     cnt = min(cnt, tm[q] * tn[q])
-                    faults += [(q,) + f for f in _tile_faults(synth, synth.workload_seed("group512", 1000 + q), cnt, M, N, K, 64)]
+                    faults += [(q,) + f for f in _tile_faults(synth, synth.workload_seed("group512", 1000 + q), cnt, M, N, K,
+                                                              ft.BF16)]
                 g.set_faults(faults)
             graph = torch.cuda.CUDAGraph()
             h.set_stream(capture)  # captured on a side stream, replayed on the main one
@@ -564,10 +572,11 @@ def grouped_extras(ft, h, synth, dev, timed_loop):
             out[f"graph_{lvn}_tflops"] = fl / (ms / 1e3) / 1e12
             if faults:
                 rep = h.report_fetch(capacity=1 << 16)
+                tdm, tdn = TDM[ft.BF16], TDN[ft.BF16]
                 found, false = _count(rep.records, faults * reps,
-                                      lambda f: (f[0], f[1] * TDM + f[4], f[2] * TDN + f[5]))
-                above = sum(abs(f[6]) > _above_threshold(probs[f[0]][0], probs[f[0]][1], f[1] * TDM + f[4],
-                                                          f[2] * TDN + f[5], f[1] * TDM, f[2] * TDN)
+                                      lambda f: (f[0], f[1] * tdm + f[4], f[2] * tdn + f[5]))
+                above = sum(abs(f[6]) > _above_threshold(probs[f[0]][0], probs[f[0]][1], f[1] * tdm + f[4],
+                                                          f[2] * tdn + f[5], f[1] * tdm, f[2] * tdn, tdm, tdn)
                             for f in faults)
                 out["faults"] = {"tiles": tiles, "injected_per_launch": len(faults), "launches": reps,
                                  "above_analytic_threshold_per_launch": above,
@@ -642,7 +651,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
                     A, sa = h.quantize(Af, ft.E4M3)
                     B, sb = h.quantize(Bf, ft.E4M3)
                     h.set_fp8_scales(sa, sb)
-                tiles = -(-2048 // TDM) * -(-2048 // TDN)
+                tiles = -(-2048 // TDM[dt]) * -(-2048 // TDN[dt])
                 lam = torch.zeros(tiles, device=dev)
                 feat = torch.zeros(tiles * 5, device=dev)
                 h.set_residual_sink(lam, feat)
@@ -683,7 +692,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
         h.report_fetch(capacity=1)
         g.run()
         rep = h.report_fetch(capacity=1 << 16)
-        at = {(f[0], f[1] * TDM + f[4], f[2] * TDN + f[5]) for f in faults}
+        at = {(f[0], f[1] * TDM[ft.BF16] + f[4], f[2] * TDN[ft.BF16] + f[5]) for f in faults}
         rows = {(p, i) for (p, i, j) in at}
         cols = {(p, j) for (p, i, j) in at}
         found = partial = false = 0
@@ -713,7 +722,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
             M, N, K = shapes[q]
             cnt = min(cnt, tm[q] * tn[q])
             # magnitudes log-uniform in [1e-4, 1e3] x tile max: also below the analytic threshold
-            fl = _tile_faults(synth, synth.workload_seed("group512", 1000 + q), cnt, M, N, K, 64)
+            fl = _tile_faults(synth, synth.workload_seed("group512", 1000 + q), cnt, M, N, K, ft.BF16)
             mags = synth.log_uniform(synth.workload_seed("group512", 5000 + q), cnt, 1e-4, 1e3)
             faults += [(q, a, b, ks, r, c, float(np.sign(d) * m * 4 * math.sqrt(K))) for (a, b, ks, r, c, d), m in
                        zip(fl, mags)]
@@ -742,7 +751,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
                 B, sb = h.quantize(Bf, ft.E4M3)
             h.set_fp8_scales(sa, sb)
             C = torch.empty(n4, n4, device=dev)
-            faults = (_tile_faults(synth, synth.workload_seed("tc_square", 70 + dt), 64, n4, n4, n4, 64 if dt == ft.BF16 else 128,
+            faults = (_tile_faults(synth, synth.workload_seed("tc_square", 70 + dt), 64, n4, n4, n4, dt,
                                    unit=1.0 / (sa * sb), lo=1e-4) if fam == "normal" else [])
             for name, mlp in (("analytic", False), ("learned", True)):
                 if mlp:
@@ -750,7 +759,7 @@ def learned_extras(ft, h, synth, dev, timed_loop):
                 else:
                     h.set_threshold(0)
                 rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=dt, inject=faults or None, capacity=1 << 14)
-                found, false = _count(rep.records, faults, lambda f: (0, f[0] * TDM + f[3], f[1] * TDN + f[4]))
+                found, false = _count(rep.records, faults, lambda f: (0, f[0] * TDM[dt] + f[3], f[1] * TDN[dt] + f[4]))
                 key = f"{dname}_{fam}"
                 c4.setdefault(key, {})[name] = {"faults_injected": len(faults), "corrected_at_position": found,
                                                 "other_records": false}

@@ -251,9 +251,10 @@ int ftgemm_quantize(ftgemm_handle_t handle, int64_t n, const float* x, void* y,
  * and the events of this call are returned.
  * Supported: F32 with OFF/THREAD/WARP/BLOCK; BF16 and E4M3 with OFF/TILE.
  * Tensor-core path (BF16/E4M3): the MMA tile is 128 x 256; at level TILE
- * 8 of its rows and 8 of its columns carry the checksums, so a CTA computes
- * a 120 x 248 tile of C (128 x 256 at level OFF) and inject tile indices
- * and in-tile offsets refer to that grid; the k-step is one
+ * its last 3 (BF16) or 5 (E4M3) rows and its last 4 (BF16) or 8 (E4M3)
+ * columns carry the checksums, so a CTA computes a 125 x 252 (BF16) or 123 x 248 (E4M3) tile
+ * of C (128 x 256 at level OFF; ftgemm_tc_tile returns it) and inject tile
+ * indices and in-tile offsets refer to that grid; the k-step is one
  * 128-byte k-block (64 bf16 or 128 e4m3 elements); A must have a 16-byte
  * aligned base and row stride (FTGEMM_ERR_ALIGN otherwise); the checksums
  * of the tile are verified once, after its last k-step, from tensor memory;
@@ -301,6 +302,16 @@ typedef struct ftgemm_group* ftgemm_group_t;
 int ftgemm_group_create(ftgemm_handle_t handle, int32_t count, const ftgemm_problem* problems,
                         ftgemm_dtype dtype, ftgemm_ft_level ft_level, ftgemm_group_t* out);
 
+/* Data tile of C that one tensor-core CTA computes and verifies (the
+ * verification unit of the tensor-core path, Section 4.2's threadblock level
+ * on the MMA tile): *rows x *cols = 128 x 256 at level OFF; at level TILE
+ * 125 x 252 for BF16 and 123 x 248 for E4M3, the rest of the 128 x 256 MMA
+ * tile carrying the checksum pieces.  Fault tile indices and in-tile offsets
+ * of ftgemm_gemm and the grouped calls refer to this grid.  Host only, no
+ * handle.  Errors: FTGEMM_ERR_ARG (NULL), FTGEMM_ERR_UNSUPPORTED (dtype F32,
+ * levels other than OFF and TILE). */
+int ftgemm_tc_tile(ftgemm_dtype dtype, ftgemm_ft_level ft_level, int32_t* rows, int32_t* cols);
+
 /* The static schedule ftgemm_group_create builds, computed on the host
  * alone: no handle, no device work (no counterpart in the paper).  m, n, k:
  * host arrays of `count` problem sizes; dtype and ft_level as for
@@ -320,8 +331,9 @@ int ftgemm_group_plan(int32_t count, const int64_t* m, const int64_t* n, const i
                       ftgemm_dtype dtype, ftgemm_ft_level ft_level, int32_t ncta, int32_t* tiles,
                       int32_t* cta_start, int32_t* total_tiles);
 
-/* Tile grid of each problem (caller arrays of `count`): 120 x 248 tiles of C
- * at level TILE, 128 x 256 at OFF.  (No counterpart in the paper.) */
+/* Tile grid of each problem (caller arrays of `count`): tiles of C of the
+ * size ftgemm_tc_tile gives for the group's dtype and level.  (No
+ * counterpart in the paper.) */
 int ftgemm_group_tiles(ftgemm_group_t group, int32_t* tiles_m, int32_t* tiles_n);
 
 /* Faults applied by every later ftgemm_grouped_gemm of the group (the

@@ -124,6 +124,7 @@ def lib():
     L.ftgemm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.ftgemm_group_create.argtypes = [vp, i32, C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(vp)]
     L.ftgemm_group_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.ftgemm_tc_tile.argtypes = [C.c_int, C.c_int, C.POINTER(i32), C.POINTER(i32)]
     L.ftgemm_group_plan.argtypes = [i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.c_int, C.c_int, i32,
                                     C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.ftgemm_group_set_faults.argtypes = [vp, C.POINTER(i32), C.POINTER(InjectSpec)]
@@ -154,7 +155,7 @@ def lib():
                "ftgemm_report_fetch", "ftgemm_encode", "ftgemm_enable_timing", "ftgemm_set_tc_pair",
                "ftgemm_autotune_tc", "ftgemm_group_autotune",
                "ftgemm_get_stats", "ftgemm_set_fp8_scales", "ftgemm_quantize",
-               "ftgemm_group_create", "ftgemm_group_plan", "ftgemm_group_tiles", "ftgemm_group_set_faults",
+               "ftgemm_group_create", "ftgemm_group_plan", "ftgemm_tc_tile", "ftgemm_group_tiles", "ftgemm_group_set_faults",
                "ftgemm_grouped_gemm", "ftgemm_grouped_gemm_dev", "ftgemm_group_bind_rule",
                "ftgemm_group_destroy", "ftgemm_set_residual_sink",
                "ftgemm_mlp_forward", "ftgemm_mlp_grad", "ftgemm_mlp_train", "ftgemm_autotune",
@@ -454,6 +455,16 @@ class Handle:
         _, N = B.shape
         _check(lib().ftgemm_encode(self._h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
                                    m_u, n_u, _ptr(V), _ptr(W), _ptr(nA), _ptr(nB)))
+
+
+def tc_tile(dtype=BF16, level=FT_TILE):
+    """(rows, cols) of the data tile of C one tensor-core CTA computes and
+    verifies (ftgemm_tc_tile): 128 x 256 at level OFF; at TILE 125 x 248 for
+    bf16 and 123 x 248 for e4m3.  Fault tile indices and in-tile offsets
+    refer to this grid."""
+    r, c = C.c_int32(0), C.c_int32(0)
+    _check(lib().ftgemm_tc_tile(dtype, level, C.byref(r), C.byref(c)))
+    return r.value, c.value
 
 
 def group_plan(shapes, dtype=BF16, level=FT_TILE, ncta: int = 152):

@@ -430,7 +430,7 @@ static void tc_set_problem(TcProblem& P, int dt, bool abft, int M, int N, int K,
   memset(&P, 0, sizeof(P));
   // checksum-growth term of the analytic threshold at the one verification, k = K
   P.grow = (float)(mu * std::ldexp(1.0, -24) * std::sqrt((double)K));
-  const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
+  const int dm = tc_dm(dt, abft), dn = tc_dn(dt, abft);
   const int kblk = dt == 0 ? 64 : 128;
   P.M = M; P.N = N; P.K = K;
   P.tiles_m = (M + dm - 1) / dm;
@@ -449,7 +449,7 @@ static void tc_set_problem(TcProblem& P, int dt, bool abft, int M, int N, int K,
 // Encode buffers of one problem laid out from `ws` (floats); with ws null
 // only the size is computed.  Returns the floats used.
 static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
-  const size_t eb = dt == 0 ? 2 : 1, ns = TC_CS_SLOTS;
+  const size_t eb = dt == 0 ? 2 : 1, ns = TC_TAIL;
   const size_t tm = P.tiles_m, tn = P.tiles_n, K = P.K;
   auto fl = [&](size_t bytes) { return (bytes + 3) / 4; };
   size_t o = 0;
@@ -482,18 +482,20 @@ static size_t tc_layout(TcProblem& P, int dt, bool abft, float* ws) {
 
 static int tc_make_maps(TcProbMaps& mp, const TcProblem& P, int dt, bool abft, bool pair) {
   const int elem = dt == 0 ? 2 : 1, BK = 128 / elem;
-  const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
-  const uint32_t ns = TC_CS_SLOTS;
+  // main boxes: every row of the MMA tile, or with checksums all but the
+  // 8-row tail (the tile's last data rows and its pieces, from V / W)
+  const int am = abft ? TC_AROWS : TC_BM, bn = abft ? TC_BROWS : TC_BN;
+  const uint32_t ns = TC_TAIL;
   memset(&mp, 0, sizeof(mp));
-  int rc = make_map_sw128(&mp.A, P.A, elem, P.K, P.M, P.lda, BK, dm);
+  int rc = make_map_sw128(&mp.A, P.A, elem, P.K, P.M, P.lda, BK, am);
   if (!rc) {
     if (P.b_mn) {
       rc = make_map_sw128(&mp.B, P.B, elem, P.N, P.K, P.ldb, 64, BK);  // 64-column boxes
     } else if (pair) {  // the two halves of a pair's 256-column MMA tile
       rc = make_map_sw128(&mp.B, P.Bt, elem, P.K, P.N, P.ldk, BK, 128);
-      if (!rc) rc = make_map_sw128(&mp.B1, P.Bt, elem, P.K, P.N, P.ldk, BK, dn - 128);
+      if (!rc) rc = make_map_sw128(&mp.B1, P.Bt, elem, P.K, P.N, P.ldk, BK, bn - 128);
     } else {
-      rc = make_map_sw128(&mp.B, P.Bt, elem, P.K, P.N, P.ldk, BK, dn);
+      rc = make_map_sw128(&mp.B, P.Bt, elem, P.K, P.N, P.ldk, BK, bn);
     }
   }
   if (!rc && abft) rc = make_map_sw128(&mp.W, P.Wt, elem, P.K, (uint64_t)P.tiles_n * ns, P.ldk, BK, ns);
@@ -540,7 +542,7 @@ static int tc_gemm(ftgemm_ctx* h, int64_t m, int64_t n, int64_t k, double alpha,
   b.total_tiles = pair ? ((P.tiles_m + 1) / 2) * P.tiles_n : ntiles;
   int nf = 0;
   {
-    const int dm = abft ? TC_DM : TC_BM, dn = abft ? TC_DN : TC_BN;
+    const int dm = tc_dm(dt, abft), dn = tc_dn(dt, abft);
     ftgemm_schedule tcs{dm, dn, dt == 0 ? 64 : 128, dm, dn, dm, dn, 0, 1};
     int rc = upload_faults(h, inject, tcs, P.M, P.N, P.nkb, P.tiles_m, P.tiles_n, level, &nf);
     if (rc) return rc;
@@ -815,6 +817,18 @@ int ftgemm_group_create(ftgemm_handle_t h, int32_t count, const ftgemm_problem* 
   return FTGEMM_OK;
 }
 
+int ftgemm_tc_tile(ftgemm_dtype dtype, ftgemm_ft_level level, int32_t* rows, int32_t* cols) {
+  if (!rows || !cols) FAIL(FTGEMM_ERR_ARG, "ftgemm_tc_tile: NULL argument");
+  if (dtype != FTGEMM_BF16 && dtype != FTGEMM_E4M3)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_tc_tile: bf16 or e4m3 operands only");
+  if (level != FTGEMM_FT_OFF && level != FTGEMM_FT_TILE)
+    FAIL(FTGEMM_ERR_UNSUPPORTED, "ftgemm_tc_tile: level OFF or TILE, not %d", (int)level);
+  const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
+  *rows = tc_dm(dt, level == FTGEMM_FT_TILE);
+  *cols = tc_dn(dt, level == FTGEMM_FT_TILE);
+  return FTGEMM_OK;
+}
+
 int ftgemm_group_plan(int32_t count, const int64_t* m, const int64_t* n, const int64_t* k, ftgemm_dtype dtype,
                       ftgemm_ft_level level, int32_t ncta, int32_t* tiles, int32_t* cta_start,
                       int32_t* total_tiles) {
@@ -876,7 +890,7 @@ int ftgemm_group_set_faults(ftgemm_group_t g, const int32_t* problem, const ftge
                  !inject->delta))
     FAIL(FTGEMM_ERR_ARG, "ftgemm_group_set_faults: NULL array");
   std::vector<Fault> fv(nf);
-  const int dm = g->abft ? TC_DM : TC_BM, dn = g->abft ? TC_DN : TC_BN;
+  const int dm = tc_dm(g->dt, g->abft), dn = tc_dn(g->dt, g->abft);
   for (int i = 0; i < nf; ++i) {
     const int pi = problem[i];
     if (pi < 0 || pi >= g->count) FAIL(FTGEMM_ERR_ARG, "inject[%d]: problem %d outside [0,%d)", i, pi, g->count);

@@ -118,12 +118,24 @@ struct SimtMaps {
   CUtensorMap W;  // B e per column block: dims {K, blocks}, box {k_tb, NW}
 };
 
-// Tensor-core path geometry: the MMA tile is 128 x 256; with checksums on,
-// TC_CS_SLOTS of its rows carry the pieces of e^T A and as many of its
-// columns the pieces of B e, leaving a TC_DM x TC_DN data tile of C.
-constexpr int TC_BM = 128, TC_BN = 256, TC_CS_SLOTS = 8;
+// Tensor-core path geometry: the MMA tile is 128 x 256.  With checksums on,
+// the last NP rows of A's tile carry the pieces of e^T A_I and NP columns of
+// B's tile those of B_J e (NP = 3 for bf16, 5 for e4m3), leaving a data tile
+// of C of 128 - NP rows and 256 - NP columns rounded down to a multiple of 4
+// (every tile's first column then starts a 16-byte group of C's rows, which
+// the epilogue stores as float4): 125 x 252 for bf16, 123 x 248 for e4m3.
+// Each operand tile arrives as a main box (TC_AROWS rows of A, TC_BROWS rows
+// of B^T) and an 8-row tail box, one 1024-byte swizzle group, so every box
+// lands on a swizzle boundary: a tail holds the tile's remaining data rows of
+// A (of B^T), copied there by the encode pass, then the NP pieces (zeros in
+// the slots left over).
+constexpr int TC_BM = 128, TC_BN = 256, TC_TAIL = 8;
 constexpr int TC_MAX_PIECES = 5;  // checksum pieces in use: 3 (bf16) or 5 (e4m3)
-constexpr int TC_DM = TC_BM - TC_CS_SLOTS, TC_DN = TC_BN - TC_CS_SLOTS;  // 120, 248
+constexpr int TC_AROWS = TC_BM - TC_TAIL, TC_BROWS = TC_BN - TC_TAIL;  // 120, 248: main boxes
+__host__ __device__ constexpr int tc_npiece(int dt) { return dt == 0 ? 3 : 5; }
+// data tile of C: rows, columns (checksums on: 125 x 252 bf16, 123 x 248 e4m3)
+__host__ __device__ constexpr int tc_dm(int dt, bool abft) { return abft ? TC_BM - tc_npiece(dt) : TC_BM; }
+__host__ __device__ constexpr int tc_dn(int dt, bool abft) { return abft ? (TC_BN - tc_npiece(dt)) & ~3 : TC_BN; }
 constexpr int TC_GROUP_M = 16;  // tile rows per raster group
 
 // Batched encode launches of the tensor-core path; a problem's first block
@@ -143,8 +155,9 @@ struct TcProblem {
   int b_mn;                       // checksums off, bf16, B 16-byte aligned: the MMA reads B
                                   // in place as an MN-major operand (no B^T, no encode pass)
   float* Vf; float* Wf;           // fp32 e^T A [tiles_m][ldk], B e [tiles_n][ldk] (first K used)
-  void* Vt; void* Wt;             // pieces [tiles * TC_CS_SLOTS][ldk], operand type
-  float* vscale; float* wscale;   // [tiles * TC_CS_SLOTS] multiplier of each piece
+  void* Vt; void* Wt;             // tails [tiles * TC_TAIL][ldk], operand type: a tile's last
+                                  // data rows of A (of B^T), then its pieces
+  float* vscale; float* wscale;   // [tiles * TC_TAIL] multiplier of piece p at p
   float* s0v; float* s0w;         // [tiles] fp8 piece base scales
   float* nA; float* nB;           // [M] row 2-norms of A, [N] column 2-norms of B
   float* nA_part; float* nB_part; // squared-norm partials per k-chunk: [ceil(K/256)][M], [ceil(K/kc)][N]
@@ -208,13 +221,13 @@ struct TcBatch {
 };
 
 struct alignas(128) TcProbMaps {
-  CUtensorMap A;  // A:   dims {K, M}, box {k-block, data rows}, 128-byte swizzle
-  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, data columns}; b_mn: B, dims {N, K}, box {64, k-block}
-  CUtensorMap W;  // pieces of B e:   dims {K, 8 * tiles_n}, box {k-block, 8}
-  CUtensorMap V;  // pieces of e^T A: dims {K, 8 * tiles_m}, box {k-block, 8}
+  CUtensorMap A;  // A:   dims {K, M}, box {k-block, 128, or TC_AROWS with checksums}, 128-byte swizzle
+  CUtensorMap B;  // B^T: dims {K, N}, box {k-block, 256, or TC_BROWS}; b_mn: B, dims {N, K}, box {64, k-block}
+  CUtensorMap W;  // tails of B^T:    dims {K, 8 * tiles_n}, box {k-block, 8}
+  CUtensorMap V;  // tails of A:      dims {K, 8 * tiles_m}, box {k-block, 8}
   // CTA pairs (K-major B^T): B holds the first 128 columns of a pair's MMA
   // tile (box {k-block, 128}), B1 the second half's data columns (box
-  // {k-block, 120} with checksums, whose pieces follow from W; else 128)
+  // {k-block, TC_BROWS - 128} with checksums, whose tail follows from W; else 128)
   CUtensorMap B1;
 };
 

@@ -8,18 +8,23 @@
 // corrupted element whose residual is subtracted (Section 4.2.1).
 //
 // On the tensor cores the encoded operands of Eq. 1-3 are formed inside one
-// MMA tile: with checksums on, the 128 x 256 MMA tile holds 120 data rows of
-// A plus 8 rows carrying the pieces of v = e^T A_I, and 248 data columns of
-// B plus 8 columns carrying the pieces of w = B_J e.  Each piece is
-// representable in the operand type and sum_c scale_c * piece_c rebuilds the
-// fp32 checksum vector.  The one MMA of each k-slice then accumulates C_IJ,
-// its row checksums A_I w (TMEM columns 248..255) and its column checksums
-// v B_J (TMEM lanes 120..127) -- Eq. 3, k-step by k-step as in Eq. 4 -- with
-// no extra MMA instruction and no extra shared-memory operand traffic; the
-// cost is the 1 - (120 * 248) / (128 * 256) = 9.2% of the tile that carries
-// checksums instead of data.  Verification runs once per tile, after its
-// last k-step, from TMEM: fp32 sums screen every row and column, fp64 sums
-// confirm the flagged ones.
+// MMA tile: with checksums on, the 128 x 256 MMA tile holds 128 - NP data
+// rows of A plus NP rows carrying the pieces of v = e^T A_I, and DN data
+// columns of B plus NP columns carrying the pieces of w = B_J e (NP = 3 for
+// bf16, 5 for e4m3; DN = 256 - NP rounded down to a multiple of 4, so that
+// C's rows take 16-byte stores: 252 and 248).  Each piece is representable
+// in the operand type and sum_c scale_c * piece_c rebuilds the fp32 checksum
+// vector.  The one MMA of each k-slice then accumulates C_IJ, its row
+// checksums A_I w (TMEM columns DN ..) and its column checksums v B_J (TMEM
+// lanes 128 - NP ..) -- Eq. 3, k-step by k-step as in Eq. 4 -- with no extra
+// MMA instruction and no extra shared-memory operand traffic; the cost is
+// the 1 - (125 * 252) / (128 * 256) = 3.9% (bf16; 6.9% for e4m3's 123 x
+// 248) of the tile that carries checksums instead of data.  Each operand tile is
+// loaded as a main box of 120 rows of A (248 of B^T) and an 8-row tail box
+// that the encode pass fills with the tile's remaining data rows and its
+// pieces, so every box starts on a 1024-byte swizzle group.  Verification
+// runs once per tile, after its last k-step, from TMEM: fp32 sums screen
+// every row and column, fp64 sums confirm the flagged ones.
 //
 // The kernel is persistent: one CTA per SM walks a static list of output
 // tiles over a table of problems (one problem for ftgemm_gemm, many for the
@@ -34,9 +39,9 @@
 // reads B where it lies, as an MN-major operand: four TMA boxes of 64
 // columns x 64 k-rows per stage, each k-row a whole 128-byte line of B (the
 // tiles are 256 columns wide), so no encode pass runs at all.  With
-// checksums the data tile is 248 columns wide, its boxes would start off
-// the 128-byte lines of B, and the kernel reads B^T (written by the encode
-// pass) K-major instead, as for e4m3 and unaligned B.
+// checksums the data tile is 252 (e4m3: 248) columns wide, its boxes would
+// start off the 128-byte lines of B, and the kernel reads B^T (written by
+// the encode pass) K-major instead, as for e4m3 and unaligned B.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -50,8 +55,8 @@
 namespace ftg {
 
 // PAIR: a 2-CTA cluster computes a 256 x 256 MMA tile with one cta_group::2
-// MMA (issued by the even CTA): each CTA holds 128 rows of A (its own 120 x
-// 248 data tile with checksums) and half of B's 256 columns, and its tensor
+// MMA (issued by the even CTA): each CTA holds 128 rows of A (its own data
+// tile with checksums) and half of B's 256 columns, and its tensor
 // memory holds its 128 rows of the accumulator, so the epilogue is the same
 // as a single CTA's.  Per SM a k-block then moves 32 KB of operands into
 // shared memory instead of 48 KB, and the ring holds 6 stages instead of 4.
@@ -60,8 +65,8 @@ constexpr int TC_PAIR_STAGES = 6, TC_MAX_STAGES = 6;
 template <int DT, bool ABFT, bool PAIR = false>
 struct TcCfg {
   static constexpr int BM = TC_BM, BN = TC_BN;        // MMA tile
-  static constexpr int CSR = ABFT ? TC_CS_SLOTS : 0;  // checksum rows of A / columns of B
-  static constexpr int DM = BM - CSR, DN = BN - CSR;  // data rows / columns of C per tile
+  static constexpr int NPIECE = DT == 0 ? 3 : 5;      // checksum pieces in use
+  static constexpr int DM = tc_dm(DT, ABFT), DN = tc_dn(DT, ABFT);  // data rows / columns of C per tile
   static constexpr int ELEM = DT == 0 ? 2 : 1;        // bytes per operand element
   static constexpr int BK = 128 / ELEM;               // one 128-byte row per k-block
   static constexpr int UK = 32 / ELEM;                // K per MMA instruction
@@ -76,11 +81,11 @@ struct TcCfg {
   static constexpr int THREADS = 64 + 32 * EW;
   static constexpr int MN_BOX = 64 * 128;  // bytes of one 64-column x 64-row box of an MN-major B
   static constexpr uint32_t TMEM_COLS = 2 * BN;       // two fp32 accumulators
-  static constexpr int NPIECE = DT == 0 ? 3 : 5;      // checksum pieces in use
-  static_assert(!ABFT || NPIECE <= CSR, "pieces must fit the checksum slots");
-  static_assert(NPIECE <= TC_MAX_PIECES, "column-checksum piece rows in shared memory");
-  // the checksum rows start on a 1024-byte (8-row) swizzle boundary
-  static_assert((DM * 128) % 1024 == 0 && (DN * 128) % 1024 == 0, "checksum slots misaligned");
+  static_assert(NPIECE == tc_npiece(DT) && NPIECE <= TC_MAX_PIECES, "column-checksum piece rows in shared memory");
+  static_assert(!ABFT || (DM == TC_BM - NPIECE && DN + NPIECE <= TC_BN), "pieces inside the MMA tile");
+  static_assert(DN % 4 == 0, "tile columns start 16-byte groups of C's rows (float4 stores)");
+  // the tail boxes start on a 1024-byte (8-row) swizzle boundary
+  static_assert((TC_AROWS * 128) % 1024 == 0 && (TC_BROWS * 128) % 1024 == 0, "tail boxes misaligned");
 };
 
 // instruction descriptor: fp32 accumulator, K-major A and B, M x N
@@ -125,7 +130,7 @@ struct TcSmemTail {
   double fix_delta[2];
   unsigned int sink_max;           // residual sink: largest residual / (u * norms) of the tile
   alignas(16) float colpart[4][256];  // per TMEM lane quarter partial column sums (data rows); float4 stores
-  float ccp[TC_MAX_PIECES][256];   // column-checksum pieces, TMEM lanes 120..
+  float ccp[TC_MAX_PIECES][256];   // column-checksum pieces, TMEM lanes 128 - NP ..
   float crow[128];                 // row checksums
   float ccol[256];                 // column checksums
   // thresholds; before the threshold is formed, the same entry holds the
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT, PAIR>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcBatch b, const __grid_constant__ TcMapsBatch mb, const TcRun run) {
   using Cfg = TcCfg<DT, ABFT, PAIR>;
   constexpr int BN = Cfg::BN, DM = Cfg::DM, DN = Cfg::DN, BK = Cfg::BK, UK = Cfg::UK;
-  constexpr int S = Cfg::STAGES, CSR = Cfg::CSR;
+  constexpr int S = Cfg::STAGES, CSR = TC_TAIL;
   static_assert(S <= TC_MAX_STAGES, "ring depth");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -249,10 +254,10 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT, PAIR>::THREADS, 1)
   const uint32_t tmem = T.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: data rows of A and B^T, then the checksum slots -----
+    // ---- TMA producer: main boxes of A and B^T, then their tails ----------
     // A CTA of a pair loads its own 128 rows of A and its half of B (columns
     // 128 r .. 128 r + 127 of the MMA tile; the second half ends with the
-    // pieces of B e), and completes the bytes on the leader's barrier, which
+    // tail of B^T), and completes the bytes on the leader's barrier, which
     // expects both CTAs' bytes.
     uint32_t it = 0;  // k-blocks issued, over all tiles of this CTA
     int last_pi = -1;
@@ -304,8 +309,8 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT, PAIR>::THREADS, 1)
             tma_load_2d_pair(sB(s), rank ? &mp->B1 : &mp->B, cbar, kb * BK, col0 + 128 * rank);
           }
           if constexpr (ABFT) {
-            tma_load_2d_pair(sA(s) + DM * 128, &mp->V, cbar, kb * BK, tm * CSR);
-            if (rank) tma_load_2d_pair(sB(s) + (DN - 128) * 128, &mp->W, cbar, kb * BK, x.tn * CSR);
+            tma_load_2d_pair(sA(s) + TC_AROWS * 128, &mp->V, cbar, kb * BK, tm * CSR);
+            if (rank) tma_load_2d_pair(sB(s) + (TC_BROWS - 128) * 128, &mp->W, cbar, kb * BK, x.tn * CSR);
           }
         } else {
           // the same byte count either way: an MN-major B is 4 boxes of 8 KB
@@ -319,8 +324,8 @@ __global__ void __launch_bounds__(TcCfg<DT, ABFT, PAIR>::THREADS, 1)
             tma_load_2d(sB(s), &mp->B, &T.full[s], kb * BK, col0);
           }
           if constexpr (ABFT) {
-            tma_load_2d(sA(s) + DM * 128, &mp->V, &T.full[s], kb * BK, tm * CSR);
-            tma_load_2d(sB(s) + DN * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
+            tma_load_2d(sA(s) + TC_AROWS * 128, &mp->V, &T.full[s], kb * BK, tm * CSR);
+            tma_load_2d(sB(s) + TC_BROWS * 128, &mp->W, &T.full[s], kb * BK, x.tn * CSR);
           }
         }
         // look one tile ahead while this tile's loads are in flight

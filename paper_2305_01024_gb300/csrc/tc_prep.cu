@@ -1,10 +1,10 @@
 // tc_prep.cu -- encoding pass of the tensor-core path and the operand
 // quantizer.
 //
-// Encoding (Eq. 1-2 of Wu, Zhai et al., ICS'23) for a TC_DM x TC_DN
-// (120 x 248) data tile of C:
-//   v_I[k] = sum_{i in I} A[i][k]   (e^T A per 120-row block of A)
-//   w_J[k] = sum_{j in J} B[k][j]   (B e per 248-column block of B)
+// Encoding (Eq. 1-2 of Wu, Zhai et al., ICS'23) for a DM x DN data tile of
+// C (DM x DN = 125 x 252 for bf16, 123 x 248 for e4m3):
+//   v_I[k] = sum_{i in I} A[i][k]   (e^T A per DM-row block of A)
+//   w_J[k] = sum_{j in J} B[k][j]   (B e per DN-column block of B)
 // accumulated in fp32 from the operand values as stored, then split into
 // pieces representable in the operand type so the MMA can carry them:
 //   bf16: x = hi + mid + lo, each piece a bf16 (24 significant bits in all);
@@ -117,19 +117,25 @@ __device__ __forceinline__ void cvt8(const uint4 q, float* v) {
   }
 }
 
-// A: block sums over TC_DM-row blocks (-> Vf) and squared row-norm partials
-// over 256-wide k-chunks (-> nA_part), one pass.  Block = (row block, chunk);
-// warp w takes rows w, w+8, ..., lane l the 8 columns 8l..8l+7 of the chunk.
+// A: block sums over DM-row blocks (-> Vf), squared row-norm partials over
+// 256-wide k-chunks (-> nA_part), and the copy of each block's rows
+// TC_AROWS .. DM - 1 into the first rows of its tail in Vt (the MMA reads a
+// tile's first TC_AROWS rows from A and the rest from the tail), one pass.
+// Block = (row block, chunk); warp w takes rows w, w+8, ..., lane l the 8
+// columns 8l..8l+7 of the chunk.
 template <int DT>
 __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_ENC_A);
+  constexpr int DM = tc_dm(DT, true);
   __shared__ float part[8][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkx = (P.K + 255) / 256;
   const int kx = lb % nkx, blk = lb / nkx;
-  const int k0 = kx * 256, r0 = blk * TC_DM;
+  const int k0 = kx * 256, r0 = blk * DM;
   const int elem = DT == 0 ? 2 : 1;
   const bool vec_ok = ((uintptr_t)P.A % (8 * elem) == 0) && ((P.lda * elem) % (8 * elem) == 0);
+  using E = typename std::conditional<DT == 0, uint16_t, uint8_t>::type;
+  E* const tail = reinterpret_cast<E*>(P.Vt) + (long long)blk * TC_TAIL * P.ldk;
   float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   auto take = [&](const float* v, int r) {
     float sq = 0.f;
@@ -143,33 +149,48 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
     if (lane == 0) P.nA_part[(long long)kx * P.M + r] = sq;
   };
   if (__all_sync(0xffffffffu, vec_ok && k0 + lane * 8 + 8 <= P.K)) {
-    // whole chunk aligned and inside K: the warp's 15 rows in groups of 5,
-    // five raw loads in flight (rows past M read row M - 1, then skipped)
-    constexpr int RPW = TC_DM / 8, GRP = 5;
+    // whole chunk aligned and inside K: the warp's 15 or 16 rows in two
+    // groups of 8, eight raw loads in flight (a row past the block or past M
+    // reads the block's last row, then is skipped); the kernel is bound by
+    // these rounds of load latency
+    constexpr int RPW = (DM + 7) / 8, GRP = 8;
     static_assert(RPW % GRP == 0, "row groups");
     for (int g0 = 0; g0 < RPW; g0 += GRP) {
       uint4 q[GRP];
 #pragma unroll
       for (int gi = 0; gi < GRP; ++gi)
-        q[gi] = ldraw8<DT>(P.A, P.lda, min(r0 + warp + 8 * (g0 + gi), P.M - 1), k0 + lane * 8);
+        q[gi] = ldraw8<DT>(P.A, P.lda, min(r0 + min(warp + 8 * (g0 + gi), DM - 1), P.M - 1), k0 + lane * 8);
 #pragma unroll
       for (int gi = 0; gi < GRP; ++gi) {
-        const int r = r0 + warp + 8 * (g0 + gi);
-        if (r < P.M) {
+        const int lr = warp + 8 * (g0 + gi), r = r0 + lr;
+        if (lr < DM && r < P.M) {
           float v[8];
           cvt8<DT>(q[gi], v);
           take(v, r);
+          if (lr >= TC_AROWS) {  // one 16-byte (bf16) / 8-byte (e4m3) store of the codes
+            E* dst = tail + (long long)(lr - TC_AROWS) * P.ldk + k0 + lane * 8;
+            if constexpr (DT == 0) *reinterpret_cast<uint4*>(dst) = q[gi];
+            else *reinterpret_cast<uint2*>(dst) = make_uint2(q[gi].x, q[gi].y);
+          }
         }
       }
     }
   } else {
-    for (int rr = warp; rr < TC_DM; rr += 8) {
-      const int r = r0 + rr;
+    for (int lr = warp; lr < DM; lr += 8) {
+      const int r = r0 + lr;
       if (r >= P.M) break;  // warp-uniform
       float v[8];
       uint16_t raw[8];
       ld8<DT>(P.A, P.lda, r, k0 + lane * 8, P.K, vec_ok, v, raw);
       take(v, r);
+      if (lr >= TC_AROWS) {
+        E* dst = tail + (long long)(lr - TC_AROWS) * P.ldk;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = k0 + lane * 8 + e;
+          if (k < P.K) dst[k] = (E)raw[e];
+        }
+      }
     }
   }
 #pragma unroll
@@ -186,26 +207,45 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
 
 // B (K x N, N contiguous): B^T (N x ldk, K contiguous) in KC x NBW tiles
 // through shared memory, TC_ENC_B_SUB consecutive tiles along K per block;
-// with checksums also the block sums over NBW-column blocks (-> Wf) and
-// squared column-norm partials per block (-> nB_part, one per
-// TC_ENC_B_SUB * KC rows of K).  KC is one 128-byte k-block of the operand
-// type.
+// KC is one 128-byte k-block of the operand type.  With checksums a block
+// covers one DN-column data block of B (NBW = DN) and also writes its block
+// sums (-> Wf), the squared column-norm partials (-> nB_part, one per
+// TC_ENC_B_SUB * KC rows of K) and the copy of B^T's rows TC_BROWS .. DN - 1
+// of the block into the first rows of its tail in Wt.  DN being a multiple
+// of 4, every block starts on an 8-byte boundary of B's rows: lane l reads
+// columns 8l .. 8l + 7 of a k-row as two 8-byte loads (bf16) or one (e4m3).
 constexpr int TC_ENC_B_SUB = 4;
+
+// Raw codes of eight consecutive elements at an 8-byte aligned address (two
+// 8-byte loads for bf16, one for e4m3, in .x/.y(/.z/.w)).
+template <int DT>
+__device__ __forceinline__ uint4 ldraw8_a8(const void* base, long long ld, long long row, int c0) {
+  if constexpr (DT == 0) {
+    const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(base) + row * ld + c0);
+    const uint2 a = __ldg(p), c = __ldg(p + 1);
+    return make_uint4(a.x, a.y, c.x, c.y);
+  } else {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint8_t*>(base) + row * ld + c0));
+    return make_uint4(q.x, q.y, 0u, 0u);
+  }
+}
 
 template <int DT, bool ABFT>
 __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_ENC_B);
   using E = typename std::conditional<DT == 0, uint16_t, uint8_t>::type;
   constexpr int KC = 128 / (int)sizeof(E);
-  constexpr int NBW = ABFT ? TC_DN : TC_BN;
-  constexpr int PITCH = NBW + (DT == 0 ? 10 : 20);  // elements; staggers the banks
+  constexpr int NBW = ABFT ? tc_dn(DT, true) : TC_BN;
+  static_assert(NBW % 4 == 0 && NBW > 31 * 8 - 8 && NBW <= 256, "block columns: 8-byte aligned, 31 or 32 lanes");
+  constexpr int PITCH = 256 + (DT == 0 ? 10 : 20);  // elements; staggers the banks (a lane may store 8 past NBW)
   __shared__ __align__(16) E tile[KC][PITCH];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkc = (P.K + KC - 1) / KC, nkg = (nkc + TC_ENC_B_SUB - 1) / TC_ENC_B_SUB;
   const int kg = lb % nkg, nb = lb / nkg;
   const int n0 = nb * NBW;
-  const bool vec_ok = ((uintptr_t)P.B % (8 * sizeof(E)) == 0) && ((P.ldb * (long long)sizeof(E)) % (8 * sizeof(E)) == 0);
-  const bool in_cols = lane * 8 < NBW;  // 31 of 32 lanes for 248 columns
+  const int lim = min(8, NBW - lane * 8);  // this lane's columns inside the block (8, 4 or <= 0)
+  const bool in_cols = lim > 0;
+  const bool vec_ok = ((uintptr_t)P.B % 8 == 0) && ((P.ldb * (long long)sizeof(E)) % 8 == 0);
   const bool fast = __all_sync(0xffffffffu, vec_ok && (!in_cols || n0 + lane * 8 + 8 <= P.N));
   float sq[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   auto take = [&](const float* v, int k) {
@@ -213,8 +253,9 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
       float rs = 0.f;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        rs += v[e];
-        sq[e] = fmaf(v[e], v[e], sq[e]);
+        const float x = e < lim ? v[e] : 0.f;  // columns of the next block do not count
+        rs += x;
+        sq[e] = fmaf(x, x, sq[e]);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
@@ -237,14 +278,15 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
         uint4 q[GRP];
 #pragma unroll
         for (int gi = 0; gi < GRP; ++gi)
-          q[gi] = in_cols ? ldraw8<DT>(P.B, P.ldb, min(k0 + warp + 8 * (g0 + gi), P.K - 1), n0 + lane * 8)
+          q[gi] = in_cols ? ldraw8_a8<DT>(P.B, P.ldb, min(k0 + warp + 8 * (g0 + gi), P.K - 1), n0 + lane * 8)
                           : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int gi = 0; gi < GRP; ++gi) {
           const int kk = warp + 8 * (g0 + gi), k = k0 + kk;
           const uint4 w = k < P.K ? q[gi] : make_uint4(0u, 0u, 0u, 0u);
           if (in_cols) {
-            // row pitch and column offset are multiples of 4 bytes
+            // row pitch and column offset are multiples of 4 bytes; a lane
+            // past the block's last column writes inside the padded row
             uint32_t* t = reinterpret_cast<uint32_t*>(&tile[kk][lane * 8]);
             t[0] = w.x;
             t[1] = w.y;
@@ -259,11 +301,13 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
         }
       }
     } else {
+      // columns past the block or past N read as zeros
+      const int ncols = min(P.N, n0 + NBW);
       for (int kk = warp; kk < KC; kk += 8) {
         const int k = k0 + kk;
         float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         uint16_t raw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (k < P.K && in_cols) ld8<DT>(P.B, P.ldb, k, n0 + lane * 8, P.N, vec_ok, v, raw);
+        if (k < P.K && in_cols) ld8<DT>(P.B, P.ldb, k, n0 + lane * 8, ncols, false, v, raw);
         if (in_cols) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) tile[kk][lane * 8 + e] = (E)raw[e];
@@ -273,7 +317,8 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
     }
     __syncthreads();
     // B^T rows n0..n0+NBW-1, k0..k0+KC-1: 8 threads write one 128-byte row
-    // segment (the k-range past K is zero, inside the padded row)
+    // segment (the k-range past K is zero, inside the padded row); with
+    // checksums the block's rows TC_BROWS.. also go to its tail
     for (int i = threadIdx.x; i < NBW * 8; i += 256) {
       const int nn = i >> 3, vq = i & 7;
       const int n = n0 + nn;
@@ -294,16 +339,17 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
         w = make_uint4(q[0], q[1], q[2], q[3]);
       }
       *reinterpret_cast<uint4*>(Bt + (long long)n * P.ldk + k0 + vq * EPV) = w;
+      if (ABFT && nn >= TC_BROWS)
+        *reinterpret_cast<uint4*>(reinterpret_cast<E*>(P.Wt) + ((long long)nb * TC_TAIL + nn - TC_BROWS) * P.ldk + k0 +
+                                  vq * EPV) = w;
     }
     __syncthreads();  // the tile is refilled by the next chunk
   }
   if constexpr (ABFT) {
     // each warp saw 1/8 of the block's k rows: sum the warps' column partials
-    __shared__ float sqw[8][NBW];
-    if (in_cols) {
+    __shared__ float sqw[8][256];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) sqw[warp][lane * 8 + e] = sq[e];
-    }
+    for (int e = 0; e < 8; ++e) sqw[warp][lane * 8 + e] = sq[e];
     __syncthreads();
     for (int c = threadIdx.x; c < NBW; c += blockDim.x) {
       const int n = n0 + c;
@@ -327,10 +373,11 @@ __global__ void __launch_bounds__(256) tc_norms_kernel(const __grid_constant__ T
   __shared__ float red[8], red2[8];
   __shared__ float sred[8][256];
   constexpr int KC = DT == 0 ? 64 : 128;
-  static_assert(TC_DM <= 256 && TC_DN <= 256, "one thread per row of a block");
+  constexpr int DM = tc_dm(DT, true), DN = tc_dn(DT, true);
+  static_assert(DM <= 256 && DN <= 256, "one thread per row of a block");
   const bool side_a = lb < P.tiles_m;
   const int blk = side_a ? lb : lb - P.tiles_m;
-  const int R = side_a ? P.M : P.N, bs = side_a ? TC_DM : TC_DN;
+  const int R = side_a ? P.M : P.N, bs = side_a ? DM : DN;
   const int nparts = side_a ? (P.K + 255) / 256 : (P.K + KC * TC_ENC_B_SUB - 1) / (KC * TC_ENC_B_SUB);
   const float* part = side_a ? P.nA_part : P.nB_part;
   float* nrm = side_a ? P.nA : P.nB;
@@ -410,13 +457,18 @@ __global__ void tc_blockscale_kernel(const __grid_constant__ TcBatch b, const in
   }
 }
 
-// Pieces of S[blk][k] into Pc[(blk*TC_CS_SLOTS + c)][k] (unused slots zero)
-// and their multipliers scale[blk*TC_CS_SLOTS + c]; row blocks of A first,
-// then column blocks of B.
+// Pieces of S[blk][k] into the block's tail rows in Pc (rows blk*TC_TAIL ..
+// + 7) and their multipliers scale[blk*TC_TAIL + p] (piece p; 0 past the
+// pieces in use); row blocks of A first, then column blocks of B.  A tail's
+// rows 0 .. TC_TAIL - NP - 1 are rows TC_AROWS.. of the block of A (written
+// by tc_encode_a), a B tail's rows 0 .. DN - TC_BROWS - 1 the same rows of
+// B^T (tc_encode_b); those past M (N) are zeroed here; the NP pieces follow,
+// then zeros.
 template <int DT>
 __global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_PIECES);
-  constexpr int NS = TC_CS_SLOTS, KPT = 8;  // k per thread: one 16-byte (bf16) / 8-byte (fp8) store per slot
+  constexpr int NS = TC_TAIL, KPT = 8;  // k per thread: one 16-byte (bf16) / 8-byte (fp8) store per slot
+  constexpr int NP = tc_npiece(DT), DM = tc_dm(DT, true), DN = tc_dn(DT, true);
   const int nkx = (P.K + 256 * KPT - 1) / (256 * KPT);
   const int k0 = (lb % nkx) * 256 * KPT + threadIdx.x * KPT, bi = lb / nkx;
   const bool side_a = bi < P.tiles_m;
@@ -438,8 +490,14 @@ __global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b, const int* _
     scale[blk * NS + c] = m;
   }
   if (k0 >= P.K) return;
-  // rows are ldk long (a multiple of 128), so k0 .. k0+7 stay inside the row;
-  // values past K are zero (the GEMM's TMA never reads them)
+  // slot of piece c, and whether slot c is left alone (a data row of A's
+  // tail inside the matrix); rows are ldk long (a multiple of 128), so
+  // k0 .. k0+7 stay inside the row; values past K are zero (the GEMM's TMA
+  // never reads them)
+  const int first = side_a ? DM - TC_AROWS : DN - TC_BROWS;  // slot of the first piece
+  static_assert(DM - TC_AROWS + NP == NS && DN - TC_BROWS + NP <= NS, "pieces inside the tail");
+  const int live_rows = side_a ? max(0, min(first, P.M - (blk * DM + TC_AROWS)))
+                               : max(0, min(first, P.N - (blk * DN + TC_BROWS)));
   float x[KPT];
   {
     const float4* src = reinterpret_cast<const float4*>(S + (long long)blk * P.ldk + k0);
@@ -463,10 +521,14 @@ __global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b, const int* _
     uint16_t* out = reinterpret_cast<uint16_t*>(Pc);
 #pragma unroll
     for (int c = 0; c < NS; ++c) {
+      if (c < live_rows) continue;
+      const int pc = c - first;  // piece in this slot
       uint4 w = make_uint4(0u, 0u, 0u, 0u);
-      if (c < 3)
-        w = make_uint4((uint32_t)q[c][0] | ((uint32_t)q[c][1] << 16), (uint32_t)q[c][2] | ((uint32_t)q[c][3] << 16),
-                       (uint32_t)q[c][4] | ((uint32_t)q[c][5] << 16), (uint32_t)q[c][6] | ((uint32_t)q[c][7] << 16));
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (p == pc)
+          w = make_uint4((uint32_t)q[p][0] | ((uint32_t)q[p][1] << 16), (uint32_t)q[p][2] | ((uint32_t)q[p][3] << 16),
+                         (uint32_t)q[p][4] | ((uint32_t)q[p][5] << 16), (uint32_t)q[p][6] | ((uint32_t)q[p][7] << 16));
       *reinterpret_cast<uint4*>(out + (long long)(blk * NS + c) * P.ldk + k0) = w;
     }
   } else {
@@ -489,8 +551,15 @@ __global__ void tc_pieces_kernel(const __grid_constant__ TcBatch b, const int* _
       }
     }
 #pragma unroll
-    for (int c = 0; c < NS; ++c)
-      *reinterpret_cast<uint2*>(out + (long long)(blk * NS + c) * P.ldk + k0) = make_uint2(lo4[c], hi4[c]);
+    for (int c = 0; c < NS; ++c) {
+      if (c < live_rows) continue;
+      const int pc = c - first;
+      uint2 w = make_uint2(0u, 0u);
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (p == pc) w = make_uint2(lo4[p], hi4[p]);
+      *reinterpret_cast<uint2*>(out + (long long)(blk * NS + c) * P.ldk + k0) = w;
+    }
   }
 }
 

@@ -105,3 +105,20 @@ def test_every_handle_entry_point_rejects_null_before_device_work(libpath):
     noalloc.restype = ctypes.c_int
     assert noalloc(64, 64, 64, 1.0, None, 64, None, 64, 0.0, None, 64, ft.FT_BLOCK, None, None) == ft.ERR_ARG
     assert b"ftgemm_gemm_noalloc" in L.ftgemm_last_error()
+
+
+def test_tensor_core_data_tile(libpath):
+    # The 128 x 256 MMA tile gives up its last 3 (bf16) or 5 (e4m3) rows to
+    # the pieces of e^T A and as many columns to those of B e at level TILE:
+    # bf16 needs 3 pieces for the 24 significant bits of an fp32 checksum,
+    # e4m3 5 pieces of scale steps of 16; the data columns are rounded down
+    # to a multiple of 4 (16-byte stores of C); OFF computes the whole tile.
+    import paper_2305_01024_gb300 as ft
+    assert ft.tc_tile(ft.BF16, ft.FT_TILE) == (125, 252)
+    assert ft.tc_tile(ft.E4M3, ft.FT_TILE) == (123, 248)
+    assert ft.tc_tile(ft.BF16, ft.FT_OFF) == ft.tc_tile(ft.E4M3, ft.FT_OFF) == (128, 256)
+    L = ft.lib()
+    r = ctypes.c_int32()
+    assert L.ftgemm_tc_tile(ft.F32, ft.FT_TILE, ctypes.byref(r), ctypes.byref(r)) == ft.ERR_UNSUPPORTED
+    assert L.ftgemm_tc_tile(ft.BF16, ft.FT_BLOCK, ctypes.byref(r), ctypes.byref(r)) == ft.ERR_UNSUPPORTED
+    assert L.ftgemm_tc_tile(ft.BF16, ft.FT_TILE, None, ctypes.byref(r)) == ft.ERR_ARG

@@ -27,6 +27,8 @@ U32 = 2.0 ** -24
 # K = 16384, so the check below catches it where the worst-case 2Ku bound
 # (about 10^4 times looser) does not.
 STAT_C = 8.0
+# data tile of the tensor-core path with checksums (ftgemm_tc_tile)
+TDM_BF16, TDN_BF16, TDM_E4M3, TDN_E4M3 = 125, 252, 123, 248
 
 
 def _stat_check(got, ref, Ar, Bh, K, cin_abs=None, scale=1.0):
@@ -92,14 +94,14 @@ def test_tc_bf16_16384_sampled_rows(ft, orc):
     Bf = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 1), "cuda")
     A, B = Af.to(torch.bfloat16), Bf.to(torch.bfloat16)
     del Af, Bf
-    tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 64
-    pos = synth.fault_positions(synth.workload_seed("tc_square", 80), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    tm_n, tn_n, nks = -(-n // TDM_BF16), -(-n // TDN_BF16), n // 64
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 80), 16, tm_n, tn_n, nks, TDM_BF16, TDN_BF16, n, n, nks)
     faults = [(a, b, ks, r, c, float(64 * math.sqrt(n))) for (a, b, ks, r, c) in pos]
     h = ft.Handle(0)
     C = torch.empty(n, n, device="cuda")
     rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=ft.BF16, inject=faults)
     torch.cuda.synchronize()
-    where = [(a * 120 + r, b * 248 + c) for (a, b, ks, r, c, d) in faults]
+    where = [(a * TDM_BF16 + r, b * TDN_BF16 + c) for (a, b, ks, r, c, d) in faults]
     assert sorted((x["row"], x["col"], x["kind"]) for x in rep.records) == sorted((i, j, 0) for i, j in where)
     rows = _rows(synth.workload_seed("tc_square", 81), n, [i for i, _ in where])
     Ar = A[rows].float().cpu().numpy()
@@ -141,13 +143,13 @@ def test_group_512_sampled_problems(ft, orc):
         M, N, K = shapes[q]
         cnt = min(cnt, tm[q] * tn[q])
         for (a, b, ks, r, c) in synth.fault_positions(synth.workload_seed("group512", 1000 + q), cnt, tm[q], tn[q],
-                                                      -(-K // 64), 120, 248, M, N, -(-K // 64)):
+                                                      -(-K // 64), TDM_BF16, TDN_BF16, M, N, -(-K // 64)):
             faults.append((q, a, b, ks, r, c, float(64 * math.sqrt(K))))
     g.set_faults(faults)
     g.run()
     torch.cuda.synchronize()
     rep = h.report_fetch(capacity=1 << 15)
-    want = sorted((f[0], f[1] * 120 + f[4], f[2] * 248 + f[5], 0) for f in faults)
+    want = sorted((f[0], f[1] * TDM_BF16 + f[4], f[2] * TDN_BF16 + f[5], 0) for f in faults)
     assert sorted((x["problem"], x["row"], x["col"], x["kind"]) for x in rep.records) == want
     # sampled problems in full, and every faulted problem among them
     sample = sorted(set(int(x * nprob) for x in synth.unit(synth.workload_seed("group512", 8), 6)) | {faults[0][0]})
@@ -177,9 +179,9 @@ def test_tc_e4m3_16384_sampled_rows(ft, orc):
     oracle-quantized operands."""
     import torch
     n = 16384
-    tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 128
-    pos = synth.fault_positions(synth.workload_seed("tc_square", 23), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
-    where = [(a * 120 + r, b * 248 + c) for (a, b, ks, r, c) in pos]
+    tm_n, tn_n, nks = -(-n // TDM_E4M3), -(-n // TDN_E4M3), n // 128
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 23), 16, tm_n, tn_n, nks, TDM_E4M3, TDN_E4M3, n, n, nks)
+    where = [(a * TDM_E4M3 + r, b * TDN_E4M3 + c) for (a, b, ks, r, c) in pos]
     rows = _rows(synth.workload_seed("tc_square", 22), n, [i for i, _ in where])
     Af = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 20), "cuda")
     Bf = synth.torch_make("normal", (n, n), synth.workload_seed("tc_square", 21), "cuda")

@@ -26,6 +26,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 N_FULL = 16384
+TDM_BF16, TDN = 125, 252  # bf16 tensor-core data tile with checksums (ftgemm_tc_tile)
 
 
 @pytest.fixture(scope="module")
@@ -122,22 +123,22 @@ def test_headline_fp32_block_16384_integers_bit_exact(ft, orc):
 
 
 def test_tile_bf16_16384_integers_bit_exact(ft, orc):
-    """bf16 TILE at 16384^3 (the persistent tcgen05 kernel over 137 x 67 tiles
-    of 120 x 248, checksums carried through the MMA), integer operands."""
+    """bf16 TILE at 16384^3 (the persistent tcgen05 kernel over 132 x 66 tiles
+    of 125 x 252, checksums carried through the MMA), integer operands."""
     import torch
     n = N_FULL
     A = synth.torch_make("int", (n, n), synth.workload_seed("tc_square", 40), "cuda").to(torch.bfloat16)
     B = synth.torch_make("int", (n, n), synth.workload_seed("tc_square", 41), "cuda").to(torch.bfloat16)
-    tm_n, tn_n, nks = -(-n // 120), -(-n // 248), n // 64
-    pos = synth.fault_positions(synth.workload_seed("tc_square", 42), 16, tm_n, tn_n, nks, 120, 248, n, n, nks)
+    tm_n, tn_n, nks = -(-n // TDM_BF16), -(-n // TDN), n // 64
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 42), 16, tm_n, tn_n, nks, TDM_BF16, TDN, n, n, nks)
     faults = [p + (d,) for p, d in zip(pos, _offsets(synth.workload_seed("tc_square", 43), 16))]
     h = ft.Handle(0)
     C = torch.full((n, n), float("nan"), device="cuda")
     rep = h.gemm(A, B, C, level=ft.FT_TILE, dtype=ft.BF16, inject=faults)
     torch.cuda.synchronize()
-    _check_records(rep, faults, 120, 248, lambda ks: nks - 1)
+    _check_records(rep, faults, TDM_BF16, TDN, lambda ks: nks - 1)
     A8, B8 = _int8_host(A), _int8_host(B)
-    rows = _sample_rows(synth.workload_seed("tc_square", 44), n, [f[0] * 120 + f[3] for f in faults])
+    rows = _sample_rows(synth.workload_seed("tc_square", 44), n, [f[0] * TDM_BF16 + f[3] for f in faults])
     assert len(rows) >= 16
     _check_rows(orc, C, A8.astype(np.float32), B8.astype(np.float32), rows)
     _check_line_sums(C, A8, B8)
@@ -175,14 +176,14 @@ def test_group_512_bf16_integers_bit_exact(ft, orc):
         M, N, K = shapes[q]
         cnt = min(cnt, tm[q] * tn[q])
         nkb = -(-K // 64)
-        sites = synth.fault_positions(synth.workload_seed("group512", 2000 + q), cnt, tm[q], tn[q], nkb, 120, 248, M, N, nkb)
+        sites = synth.fault_positions(synth.workload_seed("group512", 2000 + q), cnt, tm[q], tn[q], nkb, TDM_BF16, TDN, M, N, nkb)
         for (a, b, ks, r, c), d in zip(sites, _offsets(synth.workload_seed("group512", 3000 + q), cnt)):
             faults.append((q, a, b, ks, r, c, d))
     g.set_faults(faults)
     g.run()
     torch.cuda.synchronize()
     rep = h.report_fetch(capacity=1 << 15)
-    want = sorted((f[0], f[1] * 120 + f[4], f[2] * 248 + f[5], 0, f[6], f[6], f[6]) for f in faults)
+    want = sorted((f[0], f[1] * TDM_BF16 + f[4], f[2] * TDN + f[5], 0, f[6], f[6], f[6]) for f in faults)
     got = sorted((x["problem"], x["row"], x["col"], x["kind"], x["delta"], x["residual_r"], x["residual_c"])
                  for x in rep.records)
     assert got == want

@@ -10,7 +10,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
-TDM, TDN = 120, 248  # data tile of C when checksums ride in the MMA tile
+TDM, TDN = 125, 252  # bf16 data tile of C when checksums ride in the MMA tile (ftgemm_tc_tile)
 
 
 @pytest.fixture(scope="module")

@@ -18,7 +18,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TDM, TDN = 120, 248
+TDM, TDN = {"bf16": 125, "e4m3": 123}, {"bf16": 252, "e4m3": 248}  # data tile with checksums (ftgemm_tc_tile)
 # K a multiple of 16 (A's rows 16-byte aligned for TMA in bf16 and e4m3); N
 # mixes bf16 rows that are and are not 16-byte multiples (B read in place or
 # through B^T at level OFF)
@@ -81,7 +81,7 @@ def test_rebound_operands_are_the_ones_computed(ft, orc, dtype_name, level_name)
     faults = []
     if level == ft.FT_TILE:
         # offsets far above the threshold, set on the group (they follow the binding)
-        faults = [(0, 0, 0, -1, 5, 7, 1024.0), (2, 1, 0, -1, 30, 100, -2048.0), (5, 6, 1, -1, 50, 0, 512.0)]
+        faults = [(0, 0, 0, -1, 5, 7, 1024.0), (2, 1, 0, -1, 30, 100, -2048.0), (5, 5, 1, -1, 50, 0, 512.0)]
         g.set_faults(faults)
     table = ft.problem_table(dy)
     g.run_device(table)
@@ -92,7 +92,7 @@ def test_rebound_operands_are_the_ones_computed(ft, orc, dtype_name, level_name)
         assert np.array_equal(pr[2].cpu().numpy(), Cin)
     if faults:
         got = sorted((r["problem"], r["row"], r["col"], r["kind"]) for r in rep.records)
-        want = sorted((f[0], f[1] * TDM + f[4], f[2] * TDN + f[5], 0) for f in faults)
+        want = sorted((f[0], f[1] * TDM[dtype_name] + f[4], f[2] * TDN[dtype_name] + f[5], 0) for f in faults)
         assert got == want and rep.corrected == len(faults)
     else:
         assert rep.detected == 0

@@ -19,7 +19,7 @@ from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
-TDM, TDN = 120, 248
+TDM, TDN = 125, 252  # bf16 data tile with checksums (ftgemm_tc_tile)
 
 
 @pytest.fixture(scope="module")

@@ -30,15 +30,18 @@ def handle(ft, request):
     h.close()
 
 
-# With checksums on, 8 rows and 8 columns of the 128 x 256 MMA tile carry the
-# checksum pieces: a CTA computes a 120 x 248 tile of C.
-TDM, TDN = 120, 248
+# With checksums on, the last 3 (bf16) or 5 (e4m3) rows and as many columns
+# of the 128 x 256 MMA tile carry the checksum pieces (the data columns a
+# multiple of 4): a CTA computes a 125 x 252 (bf16) or 123 x 248 (e4m3) tile
+# of C.
+TDM, TDN = {"bf16": 125, "fp8": 123}, {"bf16": 252, "fp8": 248}
 
 
 def _tc_sched(orc, K, dt):
     bk = 64 if dt == "bf16" else 128
     nks = -(-K // bk)
-    return orc.Schedule(m_tb=TDM, n_tb=TDN, k_tb=bk, m_w=TDM, n_w=TDN, m_t=TDM, n_t=TDN,
+    dm, dn = TDM[dt], TDN[dt]
+    return orc.Schedule(m_tb=dm, n_tb=dn, k_tb=bk, m_w=dm, n_w=dn, m_t=dm, n_t=dn,
                         cadence=nks, split_k=1, level=orc.TILE, lam=32.0, u=U32)
 
 
@@ -67,7 +70,8 @@ def _bound(A, B, Cin, alpha, beta, K):
 # N a multiple of 8: B is read in place (MN-major), including ragged last tiles (264, 504);
 # N = 300, 260: B goes through the transposed copy
 @pytest.mark.parametrize("shape", [(256, 512, 320), (200, 300, 136), (128, 256, 64), (130, 260, 72),
-                                   (200, 264, 136), (136, 504, 200)])
+                                   (200, 264, 136), (136, 504, 200), (125, 252, 64), (126, 253, 72),
+                                   (376, 760, 128), (250, 504, 64)])
 def test_tc_bf16_integers_exact(ft, handle, orc, level, shape):
     M, N, K = shape
     A, B = _bf16_inputs(orc, "int", M, N, K, 500 + M)
@@ -130,6 +134,42 @@ def test_tc_fp8_normal_within_bound(ft, handle, orc, level):
     assert rep.detected == 0
 
 
+@pytest.mark.parametrize("shape", [(246, 496, 256), (250, 500, 320), (123, 248, 128), (7, 9, 128), (130, 760, 128)])
+def test_tc_e4m3_integers_exact(ft, handle, orc, shape):
+    """E4M3 codes of integers in [-4, 4] (exact in the format) with unit
+    scales: C, the checksums and every partial sum are exact in fp32, so C
+    equals the int64 product bit for bit at both levels, and at TILE the
+    records of seeded faults of +-2^10 (one per tile, 123 x 248 tiles) equal
+    the oracle's, with C restored exactly."""
+    import torch
+    M, N, K = shape
+    A = synth.integers((M, K), 710 + M)
+    B = synth.integers((K, N), 720 + N)
+    dA = torch.from_numpy(A).cuda().to(torch.float8_e4m3fn)
+    dB = torch.from_numpy(np.ascontiguousarray(B)).cuda().to(torch.float8_e4m3fn)
+    handle.set_fp8_scales(1.0, 1.0)
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    for level in ("off", "tile"):
+        dC = torch.zeros(M, N, device="cuda")
+        rep = handle.gemm(dA, dB, dC, alpha=1.0, beta=0.0, level=ft.LEVELS[level], dtype=ft.E4M3)
+        torch.cuda.synchronize()
+        assert np.array_equal(dC.cpu().numpy().astype(np.int64), ref) and rep.detected == 0
+    sched = _tc_sched(orc, K, "fp8")
+    tm_n, tn_n, nks = -(-M // TDM["fp8"]), -(-N // TDN["fp8"]), -(-K // 128)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 50), tm_n * tn_n, tm_n, tn_n, nks,
+                                TDM["fp8"], TDN["fp8"], M, N, nks)
+    faults = [(tm, tn, ks, r, c, 1024.0 if (tm + tn) % 2 == 0 else -1024.0) for (tm, tn, ks, r, c) in pos]
+    dC = torch.zeros(M, N, device="cuda")
+    rep = handle.gemm(dA, dB, dC, alpha=1.0, beta=0.0, level=ft.FT_TILE, dtype=ft.E4M3, inject=faults)
+    torch.cuda.synchronize()
+    res = orc.gemm_ft(A, B, sched, faults=faults)
+    assert np.array_equal(dC.cpu().numpy().astype(np.int64), ref) and np.array_equal(res.C, ref)
+    key = lambda r: (r["tile_m"], r["tile_n"], r["row"], r["col"], r["kind"], r["delta"]) if isinstance(r, dict) \
+        else (r.tile_m, r.tile_n, r.row, r.col, r.kind, r.delta)
+    assert sorted(map(key, rep.records)) == sorted(map(key, res.records))
+    assert rep.corrected == len(faults) == res.corrected
+
+
 @pytest.mark.parametrize("dt", ["bf16", "fp8"])
 def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
     """Seeded faults in several tiles (the tensor-core square workload's, reduced): every fault is
@@ -156,11 +196,11 @@ def test_tc_faults_located_and_corrected(ft, handle, orc, dt):
     sched = _tc_sched(orc, K, dt)
     ksteps = -(-K // sched.k_tb)
     AB = Aq.astype(np.float64) @ Bq.astype(np.float64)
-    pos = synth.fault_positions(synth.workload_seed("tc_square", 22), 5, 3, 3, ksteps, TDM, TDN, M, N, ksteps)
+    pos = synth.fault_positions(synth.workload_seed("tc_square", 22), 5, 3, 3, ksteps, TDM[dt], TDN[dt], M, N, ksteps)
     mags = synth.log_uniform(synth.workload_seed("tc_square", 23), 5, 1e-2, 1e3)
     faults = []
     for (tm, tn, ks, r, c), g in zip(pos, mags):
-        tmax = np.abs(AB[tm * TDM:(tm + 1) * TDM, tn * TDN:(tn + 1) * TDN]).max()
+        tmax = np.abs(AB[tm * TDM[dt]:(tm + 1) * TDM[dt], tn * TDN[dt]:(tn + 1) * TDN[dt]]).max()
         faults.append((tm, tn, ks, r, c, float(np.float32(g * tmax))))
     dC = torch.zeros(M, N, device="cuda")
     rep = handle.gemm(dA, dB, dC, level=ft.FT_TILE, dtype=dtype, inject=faults)

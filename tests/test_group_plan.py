@@ -20,7 +20,10 @@ EPILOGUE_KB = 6  # a tile costs at least this many k-blocks in the schedule
 
 
 def _grid(ft, m, n, k, dtype, level):
-    dm, dn = (120, 248) if level == ft.FT_TILE else (128, 256)
+    # the data tile of C (ftgemm_tc_tile): 3 (bf16) or 5 (e4m3) rows and
+    # columns of the 128 x 256 MMA tile carry checksums at level TILE, the
+    # data columns rounded down to a multiple of 4
+    dm, dn = ((125, 252) if dtype == ft.BF16 else (123, 248)) if level == ft.FT_TILE else (128, 256)
     kblk = 64 if dtype == ft.BF16 else 128
     return -(-m // dm), -(-n // dn), -(-k // kblk)
 
@@ -29,7 +32,8 @@ def _grid(ft, m, n, k, dtype, level):
                                                    ("E4M3", "FT_TILE")])
 def test_every_tile_once_with_its_k_blocks(ft, dtype_name, level_name):
     dtype, level = getattr(ft, dtype_name), getattr(ft, level_name)
-    shapes = [(300, 500, 256), (2048, 96, 1024), (64, 64, 64), (777, 1531, 2049), (120, 248, 128)]
+    shapes = [(300, 500, 256), (2048, 96, 1024), (64, 64, 64), (777, 1531, 2049), (125, 252, 128),
+              (123, 248, 128), (126, 253, 64)]
     tiles, start = ft.group_plan(shapes, dtype, level, ncta=7)
     want = set()
     for p, (m, n, k) in enumerate(shapes):
@@ -78,7 +82,7 @@ def test_longest_k_first_and_stable(ft):
 def test_raster_inside_a_problem(ft):
     # one CTA runs the whole problem in the kernel's raster: bands of 16 tile
     # rows, each band column by column, rows in order inside a column
-    m, n = 40 * 120, 3 * 248
+    m, n = 40 * 125, 3 * 252
     tiles, _ = ft.group_plan([(m, n, 256)], ft.BF16, ft.FT_TILE, ncta=1)
     seq = [(t[1], t[2]) for t in tiles]
     want = []
