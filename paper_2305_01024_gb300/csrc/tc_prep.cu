@@ -102,6 +102,27 @@ __device__ __forceinline__ uint4 ldraw8(const void* base, long long ld, long lon
   }
 }
 
+// Raw codes of eight consecutive elements at an 8-byte aligned address (two
+// 8-byte loads for bf16, one for e4m3, in .x/.y(/.z/.w)), with the columns
+// at or past `ncols` read as zero codes, by predicated loads (no branch, so
+// a thread's loads stay in flight together); for bf16 each 8-byte half is
+// loaded if it lies inside, so the caller guarantees that ncols - c0 is
+// >= 8, <= 0 or (bf16) 4.
+template <int DT>
+__device__ __forceinline__ uint4 ldraw8_a8_upto(const void* base, long long ld, long long row, int c0, int ncols) {
+  const uint2 z = make_uint2(0u, 0u);
+  if constexpr (DT == 0) {
+    const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(base) + row * ld + c0);
+    const uint2 a = c0 + 4 <= ncols ? __ldg(p) : z;
+    const uint2 c = c0 + 8 <= ncols ? __ldg(p + 1) : z;
+    return make_uint4(a.x, a.y, c.x, c.y);
+  } else {
+    const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint8_t*>(base) + row * ld + c0);
+    const uint2 q = c0 + 8 <= ncols ? __ldg(p) : z;
+    return make_uint4(q.x, q.y, 0u, 0u);
+  }
+}
+
 template <int DT>
 __device__ __forceinline__ void cvt8(const uint4 q, float* v) {
   const uint32_t w[4] = {q.x, q.y, q.z, q.w};
@@ -148,18 +169,23 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if (lane == 0) P.nA_part[(long long)kx * P.M + r] = sq;
   };
-  if (__all_sync(0xffffffffu, vec_ok && k0 + lane * 8 + 8 <= P.K)) {
-    // whole chunk aligned and inside K: the warp's 15 or 16 rows in two
-    // groups of 8, eight raw loads in flight (a row past the block or past M
-    // reads the block's last row, then is skipped); the kernel is bound by
-    // these rounds of load latency
+  const int kl = k0 + lane * 8;
+  if (vec_ok && !__any_sync(0xffffffffu, kl < P.K && kl + 8 > P.K)) {
+    // aligned A, and no lane's 8 columns straddle K (K a multiple of 8):
+    // the warp's 15 or 16 rows in two groups of 8, eight raw loads in flight
+    // (a row past the block or past M reads the block's last row, then is
+    // skipped; a lane past K loads nothing and reads zeros, so the last
+    // chunk of a K that is not a multiple of 256 takes this path too); the
+    // kernel is bound by these rounds of load latency
     constexpr int RPW = (DM + 7) / 8, GRP = 8;
     static_assert(RPW % GRP == 0, "row groups");
+    const bool in_k = kl < P.K;
     for (int g0 = 0; g0 < RPW; g0 += GRP) {
       uint4 q[GRP];
 #pragma unroll
       for (int gi = 0; gi < GRP; ++gi)
-        q[gi] = ldraw8<DT>(P.A, P.lda, min(r0 + min(warp + 8 * (g0 + gi), DM - 1), P.M - 1), k0 + lane * 8);
+        q[gi] = in_k ? ldraw8<DT>(P.A, P.lda, min(r0 + min(warp + 8 * (g0 + gi), DM - 1), P.M - 1), kl)
+                     : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
       for (int gi = 0; gi < GRP; ++gi) {
         const int lr = warp + 8 * (g0 + gi), r = r0 + lr;
@@ -167,8 +193,9 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
           float v[8];
           cvt8<DT>(q[gi], v);
           take(v, r);
-          if (lr >= TC_AROWS) {  // one 16-byte (bf16) / 8-byte (e4m3) store of the codes
-            E* dst = tail + (long long)(lr - TC_AROWS) * P.ldk + k0 + lane * 8;
+          // one 16-byte (bf16) / 8-byte (e4m3) store of the codes
+          if (lr >= TC_AROWS && in_k) {
+            E* dst = tail + (long long)(lr - TC_AROWS) * P.ldk + kl;
             if constexpr (DT == 0) *reinterpret_cast<uint4*>(dst) = q[gi];
             else *reinterpret_cast<uint2*>(dst) = make_uint2(q[gi].x, q[gi].y);
           }
@@ -216,20 +243,6 @@ __global__ void __launch_bounds__(256) tc_encode_a_kernel(const __grid_constant_
 // columns 8l .. 8l + 7 of a k-row as two 8-byte loads (bf16) or one (e4m3).
 constexpr int TC_ENC_B_SUB = 4;
 
-// Raw codes of eight consecutive elements at an 8-byte aligned address (two
-// 8-byte loads for bf16, one for e4m3, in .x/.y(/.z/.w)).
-template <int DT>
-__device__ __forceinline__ uint4 ldraw8_a8(const void* base, long long ld, long long row, int c0) {
-  if constexpr (DT == 0) {
-    const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(base) + row * ld + c0);
-    const uint2 a = __ldg(p), c = __ldg(p + 1);
-    return make_uint4(a.x, a.y, c.x, c.y);
-  } else {
-    const uint2 q = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint8_t*>(base) + row * ld + c0));
-    return make_uint4(q.x, q.y, 0u, 0u);
-  }
-}
-
 template <int DT, bool ABFT>
 __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant__ TcBatch b, const int* __restrict__ bmap) {
   TC_BLOCK_OF(P_ENC_B);
@@ -246,7 +259,11 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
   const int lim = min(8, NBW - lane * 8);  // this lane's columns inside the block (8, 4 or <= 0)
   const bool in_cols = lim > 0;
   const bool vec_ok = ((uintptr_t)P.B % 8 == 0) && ((P.ldb * (long long)sizeof(E)) % 8 == 0);
-  const bool fast = __all_sync(0xffffffffu, vec_ok && (!in_cols || n0 + lane * 8 + 8 <= P.N));
+  // vector loads, with a lane's columns past N read as zeros, unless some
+  // lane's 8 columns straddle N otherwise than at an 8-byte half
+  const int c0 = n0 + lane * 8;
+  const bool fast = vec_ok && !__any_sync(0xffffffffu, in_cols && c0 < P.N && c0 + 8 > P.N &&
+                                                            (DT != 0 || c0 + 4 != P.N));
   float sq[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   auto take = [&](const float* v, int k) {
     if constexpr (ABFT) {
@@ -269,16 +286,17 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
     if (kc >= nkc) break;  // block-uniform
     const int k0 = kc * KC;
     if (fast) {
-      // columns aligned and inside N: the warp's KC/8 k-rows in groups of
-      // 4, four raw loads in flight (rows past K read row K - 1, then count
-      // as zeros)
-      constexpr int RPW = KC / 8, GRP = 4;
+      // columns aligned: the warp's KC/8 k-rows in groups of 8, eight raw
+      // loads in flight (rows past K read row K - 1, then count as zeros;
+      // columns past N read as zeros, so the last, ragged block of a
+      // problem takes this path too)
+      constexpr int RPW = KC / 8, GRP = 8;
       static_assert(RPW % GRP == 0, "row groups");
       for (int g0 = 0; g0 < RPW; g0 += GRP) {
         uint4 q[GRP];
 #pragma unroll
         for (int gi = 0; gi < GRP; ++gi)
-          q[gi] = in_cols ? ldraw8_a8<DT>(P.B, P.ldb, min(k0 + warp + 8 * (g0 + gi), P.K - 1), n0 + lane * 8)
+          q[gi] = in_cols ? ldraw8_a8_upto<DT>(P.B, P.ldb, min(k0 + warp + 8 * (g0 + gi), P.K - 1), c0, P.N)
                           : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int gi = 0; gi < GRP; ++gi) {
@@ -301,7 +319,8 @@ __global__ void __launch_bounds__(256) tc_encode_b_kernel(const __grid_constant_
         }
       }
     } else {
-      // columns past the block or past N read as zeros
+      // B's base or row pitch not 8-byte aligned: element loads; columns
+      // past the block or past N read as zeros
       const int ncols = min(P.N, n0 + NBW);
       for (int kk = warp; kk < KC; kk += 8) {
         const int k = k0 + kk;

@@ -86,6 +86,29 @@ def test_tc_bf16_integers_exact(ft, handle, orc, level, shape):
         assert np.array_equal(res.C, ref) and res.detected == 0
 
 
+@pytest.mark.parametrize("shape,lda", [((130, 264, 75), 80), ((300, 500, 331), 336), ((64, 100, 13), 16)])
+def test_tc_bf16_ragged_k_strided_a_exact(ft, handle, orc, shape, lda):
+    """K not a multiple of 8, A a row-strided view into a wider buffer: the
+    encode pass's last 8-element group of each row straddles K (elements
+    past K, which lie inside A's padded rows, must not count), and N
+    multiples of 4 but not of 8 put a B group across N as well."""
+    import torch
+    M, N, K = shape
+    A, B = _bf16_inputs(orc, "int", M, N, K, 900 + K)
+    Cin = synth.integers((M, N), 901 + K)
+    buf = torch.full((M, lda), 3.0, dtype=torch.bfloat16, device="cuda")  # nonzero padding
+    buf[:, :K] = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    dA = buf[:, :K]
+    dB = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    ref = A.astype(np.int64) @ B.astype(np.int64) + Cin.astype(np.int64)
+    for lv in (ft.FT_OFF, ft.FT_TILE):
+        dC = torch.from_numpy(Cin.copy()).cuda()
+        rep = handle.gemm(dA, dB, dC, alpha=1.0, beta=1.0, level=lv, dtype=ft.BF16)
+        torch.cuda.synchronize()
+        assert np.array_equal(dC.cpu().numpy().astype(np.float64), ref)
+        assert rep.detected == 0
+
+
 @pytest.mark.parametrize("level", ["off", "tile"])
 def test_tc_bf16_normal_within_bound(ft, handle, orc, level):
     M, N, K = 384, 512, 1024
