@@ -448,7 +448,7 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
         modes = {}
         for lvn, lv in (("off", ft.FT_OFF), ("tile", ft.FT_TILE)):
             h.set_tc_pair(None)
-            modes[f"{lvn}_tuned"] = "pairs" if h.autotune_tc(A, B, C, level=lv, dtype=dt, reps=2) else "single"
+            modes[f"{lvn}_tuned"] = "pairs" if h.autotune_tc(A, B, C, level=lv, dtype=dt, reps=3) else "single"
             for pair in (None, False, True):
                 h.set_tc_pair(pair)
                 clk = ClockSampler(clock_gpu_index(0))
@@ -542,7 +542,7 @@ def grouped_extras(ft, h, synth, dev, timed_loop):
     try:
         for lvn, lv in (("off", ft.FT_OFF), ("tile", ft.FT_TILE)):
             # the group's schedule (single CTAs or CTA pairs) chosen by measurement
-            g = ft.Group(h, probs, dtype=ft.BF16, level=lv, tune=3)
+            g = ft.Group(h, probs, dtype=ft.BF16, level=lv, tune=5)
             out[f"schedule_{lvn}"] = "pairs" if g.pair else "single"
             faults = []
             if lv == ft.FT_TILE:

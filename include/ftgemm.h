@@ -392,9 +392,11 @@ int ftgemm_group_bind_rule(const ftgemm_problem* created, const ftgemm_problem* 
 int ftgemm_group_destroy(ftgemm_group_t group);
 
 /* ftgemm_group_create with the schedule chosen by measurement: the group is
- * built on single CTAs and on CTA pairs, each run `reps` times after one
- * warm-up (every C is overwritten), and the faster is returned in *out (the
- * other is released); *pair_out (may be NULL): 1 pairs, 0 single CTAs.
+ * built on single CTAs and on CTA pairs, both run once untimed and then
+ * timed in `reps` rounds of one call each, the order alternating between
+ * rounds (every C is overwritten); the one with the better best time is
+ * returned in *out (the other is released); *pair_out (may be NULL): 1
+ * pairs, 0 single CTAs.
  * Synchronises the handle's stream.  Errors: FTGEMM_ERR_ARG (NULL, count,
  * reps < 1) and those of ftgemm_group_create / ftgemm_grouped_gemm. */
 int ftgemm_group_autotune(ftgemm_handle_t handle, int32_t count, const ftgemm_problem* problems,
@@ -422,7 +424,9 @@ int ftgemm_autotune(ftgemm_handle_t handle, int64_t m, int64_t n, int64_t k, con
 /* Autotuner for the tensor-core path (the parameter selection of Section
  * 3.2, done by measurement): times ftgemm_gemm on the given operands (C is
  * overwritten; alpha 1, beta 0, no faults) on single CTAs and on CTA pairs,
- * `reps` times each after one warm-up, and caches the faster for (m, n, k,
+ * once each untimed and then in `reps` rounds of one call each (the order
+ * alternating between rounds, so that a drift of the clocks weighs on both
+ * alike), and caches the one with the better best time for (m, n, k,
  * dtype, ft_level); later ftgemm_gemm calls with that shape use it while
  * ftgemm_set_tc_pair is at its default (-1).  dtype BF16 or E4M3 (set the
  * fp8 scales first), ft_level OFF or TILE.  *pair_out (may be NULL): 1 if

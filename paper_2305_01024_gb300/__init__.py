@@ -526,8 +526,8 @@ class Group:
 
     def __init__(self, handle: "Handle", problems, dtype=BF16, level=FT_TILE, tune: int = 0):
         """tune > 0: the schedule (single CTAs or CTA pairs) is chosen by
-        running the group both ways `tune` times (every C is overwritten);
-        self.pair tells which."""
+        running the group both ways in `tune` interleaved rounds (every C is
+        overwritten); self.pair tells which."""
         self.handle = handle
         self.count = len(problems)
         arr = problem_structs(problems)

@@ -1673,6 +1673,41 @@ static int time_best(ftgemm_ctx* h, F call, int reps, float* best_ms) {
   return FTGEMM_OK;
 }
 
+// Best time of two candidates over `reps` rounds, timed interleaved (one
+// call of each per round, the order alternating) so that a drift of the
+// clocks or of the memory system during the tuning weighs on both alike;
+// each candidate is called once, untimed, first.
+template <class F0, class F1>
+static int time_best_pair(ftgemm_ctx* h, F0 call0, F1 call1, int reps, float* ms0, float* ms1) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a);
+    FAIL(FTGEMM_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  int rc = call0();
+  if (rc == FTGEMM_OK) rc = call1();
+  float best[2] = {3.4e38f, 3.4e38f};
+  for (int r = 0; rc == FTGEMM_OK && r < 2 * reps; ++r) {
+    const int c = (r & 1) ^ ((r >> 1) & 1);  // 0 1 1 0 0 1 1 0 ...
+    e = cudaEventRecord(a, h->stream);
+    if (e == cudaSuccess) rc = c ? call1() : call0();
+    if (e == cudaSuccess && rc == FTGEMM_OK) e = cudaEventRecord(b, h->stream);
+    if (e == cudaSuccess && rc == FTGEMM_OK) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess && rc == FTGEMM_OK) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess && rc == FTGEMM_OK) rc = FTGEMM_ERR_CUDA;
+    best[c] = std::min(best[c], ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  *ms0 = best[0];
+  *ms1 = best[1];
+  return FTGEMM_OK;
+}
+
 int ftgemm_autotune_tc(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
                        const void* B, int64_t ldb, float* C, int64_t ldc, ftgemm_dtype dtype,
                        ftgemm_ft_level level, int32_t reps, int32_t* pair_out) {
@@ -1686,17 +1721,13 @@ int ftgemm_autotune_tc(ftgemm_handle_t h, int64_t m, int64_t n, int64_t k, const
   CK(cudaSetDevice(h->device));
   const int saved = h->tc_pair;
   float ms[2] = {0.f, 0.f};
-  for (int p = 0; p < 2; ++p) {
+  auto run = [&](int p) {
     h->tc_pair = p;
-    int rc = time_best(
-        h, [&]() { return tc_gemm(h, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, dtype, level, nullptr, nullptr); },
-        reps, &ms[p]);
-    if (rc) {
-      h->tc_pair = saved;
-      return rc;
-    }
-  }
+    return tc_gemm(h, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, dtype, level, nullptr, nullptr);
+  };
+  const int rc = time_best_pair(h, [&]() { return run(0); }, [&]() { return run(1); }, reps, &ms[0], &ms[1]);
   h->tc_pair = saved;
+  if (rc) return rc;
   const int pick = ms[1] < ms[0] ? 1 : 0;
   const int dt = dtype == FTGEMM_BF16 ? 0 : 1;
   h->tc_tuned[std::make_tuple(m, n, k, dt, (int)level)] = pick;
@@ -1715,9 +1746,11 @@ int ftgemm_group_autotune(ftgemm_handle_t h, int32_t count, const ftgemm_problem
   for (int p = 0; p < 2 && rc == FTGEMM_OK; ++p) {
     h->tc_pair = p;
     rc = ftgemm_group_create(h, count, problems, dtype, level, &g[p]);
-    if (rc == FTGEMM_OK) rc = time_best(h, [&]() { return ftgemm_grouped_gemm(h, g[p]); }, reps, &ms[p]);
   }
   h->tc_pair = saved;
+  if (rc == FTGEMM_OK)
+    rc = time_best_pair(h, [&]() { return ftgemm_grouped_gemm(h, g[0]); },
+                        [&]() { return ftgemm_grouped_gemm(h, g[1]); }, reps, &ms[0], &ms[1]);
   if (rc) {
     for (int p = 0; p < 2; ++p) ftgemm_group_destroy(g[p]);
     return rc;
