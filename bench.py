@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip levels/sweep side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
     ap.add_argument("--case", default=None,
-                    help="run one small kernel case for a profiler and exit: tc-<bf16|e4m3>-<tile|off>-<n>, "
+                    help="run one small kernel case for a profiler and exit: tc-<bf16|e4m3>-<tile|off>-<n> "
+                         "(tc1- single CTAs, tc2- CTA pairs, tc- the default), "
                          "tcgroup-bf16-<tile|off>-<problems>, f64-<d|z>-<block|off>-<n>, "
                          "simt-<wide32|wide|huge16>-<off|thread|warp|block|detect>-<n>")
     return ap.parse_args()
@@ -73,7 +74,7 @@ def run_case(case):
     import paper_2305_01024_gb300 as ft
     import synth
     kind, dtn, lvn, n = case.split("-")
-    assert kind in ("tc", "tcgroup", "f64", "simt"), case
+    assert kind in ("tc", "tc1", "tc2", "tcgroup", "f64", "simt"), case
     n = int(n)
     if kind == "simt":  # simt-<tuple>-<level>-<n>: the fp32 kernel on U(-1,1) operands
         tuples = {"wide32": SCHED, "wide": SCHED16, "huge16": SCHED_OFF_BEST}
@@ -129,6 +130,8 @@ def run_case(case):
         A, sa = h.quantize(Af, ft.E4M3)
         B, sb = h.quantize(Bf, ft.E4M3)
         h.set_fp8_scales(sa, sb)
+    if kind != "tc":  # tc1: single CTAs, tc2: CTA pairs (tc: the default for the operand type)
+        h.set_tc_pair(kind == "tc2")
     C = torch.empty(n, n, device="cuda")
     for _ in range(3):
         h.gemm(A, B, C, level=ft.LEVELS[lvn], dtype=dt, report=False)
@@ -492,7 +495,8 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
             pk = peaks.get("bf16_tflops")
             r["roofline"] = {"bound": "tensor", "achieved": r["tile_kernel_tflops"], "peak": pk, "unit": "TFLOP/s",
                              "frac": r["tile_kernel_tflops"] / pk if pk else None,
-                             "traffic": committed_traffic("tc_gemm_bf16_tile_16384", TC_KERNEL_SOURCES),
+                             "traffic": committed_traffic(f"tc_gemm_bf16_tile_16384_{modes['tile_tuned']}",
+                                                          TC_KERNEL_SOURCES),
                              "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"}
             del ct
         else:
@@ -510,7 +514,8 @@ def tensor_core_extras(ft, h, synth, dev, timed_loop):
             r["roofline"] = {"bound": "tensor", "achieved": r["tile_kernel_tflops"],
                              "peak": 2 * pk if pk else None, "unit": "TFLOP/s",
                              "frac": r["tile_kernel_tflops"] / (2 * pk) if pk else None,
-                             "traffic": committed_traffic("tc_gemm_e4m3_tile_16384", TC_KERNEL_SOURCES),
+                             "traffic": committed_traffic(f"tc_gemm_e4m3_tile_16384_{modes['tile_tuned']}",
+                                                          TC_KERNEL_SOURCES),
                              "peak_basis": "measured bf16 burst x 2 (nominal fp8 / bf16 dense ratio)"}
         h.report_fetch()
         out[name] = {k: (float(f"{v:.5g}") if isinstance(v, float) else v) for k, v in r.items()}
